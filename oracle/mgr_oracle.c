@@ -1,0 +1,1169 @@
+/*
+ * mgr_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded FP64 restatement of multigrid-reduction
+ * (MGR) preconditioned FGMRES, written from the paper (arXiv 2101.11649) so
+ * that the CUDA path can be checked against it.  Only tests/, the smoke
+ * check and the benchmark's CPU-baseline leg may load this library; the
+ * product path never does.  It shares no code, header or constant with the
+ * CUDA library.
+ *
+ * Every loop below runs in the order written in its comment; where the
+ * paper fixes no order (summations), the order stated here is the reading
+ * the CUDA setup kernels also follow, so that setup results agree bit for
+ * bit.  Compile with -ffp-contract=off (no fused multiply-add).
+ *
+ * Parity pins: see tests/test_oracle_*.py.  AMG coarsening and
+ * interpolation (PMIS, extended+i) are not defined by the paper; they are
+ * pinned only by structural invariants (parity partially unpinned).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { OR_OK = 0, OR_INVALID = 1, OR_NOMEM = 2, OR_SINGULAR = 4, OR_NOT_CONVERGED = 5 };
+enum { OR_JACOBI = 0, OR_L1_JACOBI = 1, OR_BLOCK_JACOBI = 2 };
+
+/* ------------------------------------------------------------------ CSR */
+typedef struct {
+    int n, m;       /* rows, cols */
+    int nnz;
+    int *rp, *ci;   /* rp[n+1], ci[nnz] strictly ascending per row */
+    double *v;
+} csr;
+
+static void csr_free(csr *a) {
+    if (!a) return;
+    free(a->rp); free(a->ci); free(a->v);
+    memset(a, 0, sizeof(*a));
+}
+
+static int csr_alloc(csr *a, int n, int m, int nnz) {
+    a->n = n; a->m = m; a->nnz = nnz;
+    a->rp = (int *)calloc((size_t)n + 1, sizeof(int));
+    a->ci = (int *)malloc(((size_t)nnz + 1) * sizeof(int));
+    a->v = (double *)malloc(((size_t)nnz + 1) * sizeof(double));
+    return (a->rp && a->ci && a->v) ? OR_OK : OR_NOMEM;
+}
+
+/* y = A x  (row i: sum over entries in ascending column order) */
+static void csr_matvec(const csr *a, const double *x, double *y) {
+    for (int i = 0; i < a->n; i++) {
+        double s = 0.0;
+        for (int p = a->rp[i]; p < a->rp[i + 1]; p++) s += a->v[p] * x[a->ci[p]];
+        y[i] = s;
+    }
+}
+
+/* explicit transpose; entries of each output row ascend in source row order */
+static int csr_transpose(const csr *a, csr *t) {
+    int rc = csr_alloc(t, a->m, a->n, a->nnz);
+    if (rc) return rc;
+    for (int p = 0; p < a->nnz; p++) t->rp[a->ci[p] + 1]++;
+    for (int j = 0; j < a->m; j++) t->rp[j + 1] += t->rp[j];
+    int *pos = (int *)malloc(((size_t)a->m + 1) * sizeof(int));
+    if (!pos) return OR_NOMEM;
+    memcpy(pos, t->rp, (size_t)a->m * sizeof(int));
+    for (int i = 0; i < a->n; i++)
+        for (int p = a->rp[i]; p < a->rp[i + 1]; p++) {
+            int q = pos[a->ci[p]]++;
+            t->ci[q] = i;
+            t->v[q] = a->v[p];
+        }
+    free(pos);
+    return OR_OK;
+}
+
+static int cmp_int(const void *x, const void *y) {
+    int a = *(const int *)x, b = *(const int *)y;
+    return (a > b) - (a < b);
+}
+
+/*
+ * Sparse product C = A * B (+ E added last when E != NULL).
+ * Row i of C: for each entry (i,k) of A in ascending k, for each entry (k,j)
+ * of B in ascending j: acc[j] += a_ik * b_kj (acc starts at +0.0 on first
+ * touch); then acc[j] += e_ij for each entry of E's row.  The pattern is the
+ * union of everything touched (computed zeros kept, no dropping), columns
+ * ascending.  This is the Galerkin/Petrov-Galerkin product of Sec. 3
+ * (A_{l+1} = R A P) written as a row-wise accumulation.
+ */
+static int csr_matmat_add(const csr *a, const csr *b, const csr *e, csr *c) {
+    int n = a->n, m = b->m;
+    int *mark = (int *)malloc(((size_t)m + 1) * sizeof(int));
+    double *acc = (double *)malloc(((size_t)m + 1) * sizeof(double));
+    int *list = (int *)malloc(((size_t)m + 1) * sizeof(int));
+    if (!mark || !acc || !list) return OR_NOMEM;
+    for (int j = 0; j < m; j++) mark[j] = -1;
+    /* pass 1: pattern sizes */
+    int *rp = (int *)calloc((size_t)n + 1, sizeof(int));
+    long long tot = 0;
+    for (int i = 0; i < n; i++) {
+        int cnt = 0;
+        for (int p = a->rp[i]; p < a->rp[i + 1]; p++) {
+            int k = a->ci[p];
+            for (int q = b->rp[k]; q < b->rp[k + 1]; q++) {
+                int j = b->ci[q];
+                if (mark[j] != i) { mark[j] = i; cnt++; }
+            }
+        }
+        if (e)
+            for (int q = e->rp[i]; q < e->rp[i + 1]; q++) {
+                int j = e->ci[q];
+                if (mark[j] != i) { mark[j] = i; cnt++; }
+            }
+        tot += cnt;
+        rp[i + 1] = cnt;
+    }
+    if (tot > 2000000000LL) return OR_NOMEM;
+    for (int i = 0; i < n; i++) rp[i + 1] += rp[i];
+    c->n = n; c->m = m; c->nnz = (int)tot; c->rp = rp;
+    c->ci = (int *)malloc(((size_t)tot + 1) * sizeof(int));
+    c->v = (double *)malloc(((size_t)tot + 1) * sizeof(double));
+    if (!c->ci || !c->v) return OR_NOMEM;
+    for (int j = 0; j < m; j++) mark[j] = -1;
+    /* pass 2: values in the stated order */
+    for (int i = 0; i < n; i++) {
+        int cnt = 0;
+        for (int p = a->rp[i]; p < a->rp[i + 1]; p++) {
+            int k = a->ci[p];
+            double aik = a->v[p];
+            for (int q = b->rp[k]; q < b->rp[k + 1]; q++) {
+                int j = b->ci[q];
+                if (mark[j] != i) { mark[j] = i; acc[j] = 0.0; list[cnt++] = j; }
+                acc[j] = acc[j] + aik * b->v[q];
+            }
+        }
+        if (e)
+            for (int q = e->rp[i]; q < e->rp[i + 1]; q++) {
+                int j = e->ci[q];
+                if (mark[j] != i) { mark[j] = i; acc[j] = 0.0; list[cnt++] = j; }
+                acc[j] = acc[j] + e->v[q];
+            }
+        qsort(list, (size_t)cnt, sizeof(int), cmp_int);
+        int base = rp[i];
+        for (int t = 0; t < cnt; t++) { c->ci[base + t] = list[t]; c->v[base + t] = acc[list[t]]; }
+    }
+    free(mark); free(acc); free(list);
+    return OR_OK;
+}
+
+/* --------------------------------------------------------- BSR -> CSR */
+/*
+ * Scalar view of the block system of Eq. 1: scalar row I*b+r holds, for each
+ * block (I,J) in ascending J, the entries (r, 0..b-1) of that block at
+ * columns J*b+0..J*b+b-1.  Stored zeros are kept.
+ */
+static int bsr_to_csr(int nb, int b, const int *rp, const int *ci, const double *val, csr *a) {
+    int n = nb * b;
+    long long nnz = (long long)rp[nb] * b * b;
+    if (nnz > 2000000000LL) return OR_NOMEM;
+    int rc = csr_alloc(a, n, n, (int)nnz);
+    if (rc) return rc;
+    int pos = 0;
+    for (int I = 0; I < nb; I++)
+        for (int r = 0; r < b; r++) {
+            a->rp[I * b + r] = pos;
+            for (int p = rp[I]; p < rp[I + 1]; p++)
+                for (int c = 0; c < b; c++) {
+                    a->ci[pos] = ci[p] * b + c;
+                    a->v[pos] = val[((size_t)p * b + r) * b + c];
+                    pos++;
+                }
+        }
+    a->rp[n] = pos;
+    return OR_OK;
+}
+
+/* y = A x for the block matrix itself (definition of the product). */
+void or_spmv_bsr(int nb, int b, const int *rp, const int *ci, const double *val,
+                 const double *x, double *y) {
+    for (int I = 0; I < nb; I++)
+        for (int r = 0; r < b; r++) {
+            double s = 0.0;
+            for (int p = rp[I]; p < rp[I + 1]; p++)
+                for (int c = 0; c < b; c++) s += val[((size_t)p * b + r) * b + c] * x[ci[p] * b + c];
+            y[I * b + r] = s;
+        }
+}
+
+/* ------------------------------------------------------ dense helpers */
+/*
+ * In-place Gauss-Jordan inversion with partial pivoting of a k x k block
+ * (k <= 4), row-major.  Pivot: first row of largest |m[r][c]|.  Singular when
+ * |pivot| <= 1e-14 * ||B||_inf.  Output inv (row-major).
+ */
+static int block_inverse(int k, const double *B, double *inv) {
+    double m[16], x[16];
+    double nrm = 0.0;
+    for (int r = 0; r < k; r++) {
+        double s = 0.0;
+        for (int c = 0; c < k; c++) s += fabs(B[r * k + c]);
+        if (s > nrm) nrm = s;
+    }
+    for (int t = 0; t < k * k; t++) { m[t] = B[t]; x[t] = 0.0; }
+    for (int r = 0; r < k; r++) x[r * k + r] = 1.0;
+    for (int c = 0; c < k; c++) {
+        int p = c;
+        for (int r = c + 1; r < k; r++)
+            if (fabs(m[r * k + c]) > fabs(m[p * k + c])) p = r;
+        if (!(fabs(m[p * k + c]) > 1e-14 * nrm)) return OR_SINGULAR;
+        if (p != c)
+            for (int t = 0; t < k; t++) {
+                double s = m[c * k + t]; m[c * k + t] = m[p * k + t]; m[p * k + t] = s;
+                s = x[c * k + t]; x[c * k + t] = x[p * k + t]; x[p * k + t] = s;
+            }
+        double piv = m[c * k + c];
+        for (int t = 0; t < k; t++) { m[c * k + t] = m[c * k + t] / piv; x[c * k + t] = x[c * k + t] / piv; }
+        for (int r = 0; r < k; r++) {
+            if (r == c) continue;
+            double f = m[r * k + c];
+            for (int t = 0; t < k; t++) {
+                m[r * k + t] = m[r * k + t] - f * m[c * k + t];
+                x[r * k + t] = x[r * k + t] - f * x[c * k + t];
+            }
+        }
+    }
+    for (int t = 0; t < k * k; t++) inv[t] = x[t];
+    return OR_OK;
+}
+
+/* LU with partial pivoting (Doolittle, row swaps), column-major-free plain
+ * row-major n x n.  Gaussian elimination of the coarsest AMG grid (Sec. 5.1). */
+static int lu_factor(int n, double *a, int *piv) {
+    for (int k = 0; k < n; k++) {
+        int p = k;
+        for (int r = k + 1; r < n; r++)
+            if (fabs(a[(size_t)r * n + k]) > fabs(a[(size_t)p * n + k])) p = r;
+        piv[k] = p;
+        if (a[(size_t)p * n + k] == 0.0) return OR_SINGULAR;
+        if (p != k)
+            for (int c = 0; c < n; c++) {
+                double s = a[(size_t)k * n + c]; a[(size_t)k * n + c] = a[(size_t)p * n + c]; a[(size_t)p * n + c] = s;
+            }
+        for (int r = k + 1; r < n; r++) {
+            double l = a[(size_t)r * n + k] / a[(size_t)k * n + k];
+            a[(size_t)r * n + k] = l;
+            for (int c = k + 1; c < n; c++) a[(size_t)r * n + c] -= l * a[(size_t)k * n + c];
+        }
+    }
+    return OR_OK;
+}
+
+/* solve with the factors: trans = 0 -> A x = b, trans = 1 -> A^T x = b */
+static void lu_solve(int n, const double *lu, const int *piv, const double *b, double *x, int trans) {
+    for (int i = 0; i < n; i++) x[i] = b[i];
+    if (!trans) {
+        for (int k = 0; k < n; k++) if (piv[k] != k) { double s = x[k]; x[k] = x[piv[k]]; x[piv[k]] = s; }
+        for (int i = 0; i < n; i++) {
+            double s = x[i];
+            for (int c = 0; c < i; c++) s -= lu[(size_t)i * n + c] * x[c];
+            x[i] = s;
+        }
+        for (int i = n - 1; i >= 0; i--) {
+            double s = x[i];
+            for (int c = i + 1; c < n; c++) s -= lu[(size_t)i * n + c] * x[c];
+            x[i] = s / lu[(size_t)i * n + i];
+        }
+    } else {
+        /* A = P^T L U  ->  A^T = U^T L^T P ; solve U^T y = b, L^T w = y, x = P^T w */
+        for (int i = 0; i < n; i++) {
+            double s = x[i];
+            for (int c = 0; c < i; c++) s -= lu[(size_t)c * n + i] * x[c];
+            x[i] = s / lu[(size_t)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; i--) {
+            double s = x[i];
+            for (int c = i + 1; c < n; c++) s -= lu[(size_t)c * n + i] * x[c];
+            x[i] = s;
+        }
+        for (int k = n - 1; k >= 0; k--) if (piv[k] != k) { double s = x[k]; x[k] = x[piv[k]]; x[piv[k]] = s; }
+    }
+}
+
+/* Dense solve A x = b by the LU above (A row-major, not modified). */
+int or_dense_solve(int n, const double *A, const double *b, double *x) {
+    double *a = (double *)malloc((size_t)n * n * sizeof(double));
+    int *piv = (int *)malloc((size_t)(n + 1) * sizeof(int));
+    if (!a || !piv) return OR_NOMEM;
+    memcpy(a, A, (size_t)n * n * sizeof(double));
+    int rc = lu_factor(n, a, piv);
+    if (!rc) lu_solve(n, a, piv, b, x, 0);
+    free(a); free(piv);
+    return rc;
+}
+
+/* ------------------------------------------------------------ hashing */
+/*
+ * PMIS tie-breaking weight in [0,1): the SplitMix64 output function
+ * (Steele, Lea & Flood, 2014) applied to the state i + 2^32 * level, top 53
+ * bits scaled by 2^-53.
+ */
+static double pmis_u01(uint32_t i, uint32_t level) {
+    uint64_t z = (uint64_t)i + ((uint64_t)level << 32);
+    z += 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+double or_pmis_u01(unsigned i, unsigned level) { return pmis_u01(i, level); }
+
+/* ------------------------------------------------------- AMG hierarchy */
+typedef struct {
+    csr A, P, R, AT;   /* R = P^T; AT = A^T (transposed cycle) */
+    double *dl1inv;    /* l1-Jacobi smoother inverse diagonal */
+    int *cf;           /* +1 C, -1 F */
+    int *func;         /* unknown-approach function id per row */
+    int nc;
+    double *x, *r, *t; /* work vectors */
+} amg_level;
+
+typedef struct {
+    int nlev;
+    amg_level lev[32];
+    double *lu; int *piv; int nco; /* dense coarsest */
+} amg_h;
+
+/*
+ * Classical strength of connection (a reading: the paper cites BoomerAMG's
+ * defaults, Sec. 5.1).  s_i = -1 if a_ii < 0 else +1.  j != i is a strong
+ * dependency of i iff (same function) and -s_i a_ij >= theta * m_i where
+ * m_i = max over off-diagonal same-function j of -s_i a_ij, and m_i > 0.
+ */
+static int amg_strength(const csr *A, const int *func, double theta, csr *S) {
+    int n = A->n;
+    int rc = csr_alloc(S, n, n, A->nnz);
+    if (rc) return rc;
+    S->nnz = 0;
+    for (int i = 0; i < n; i++) {
+        double aii = 0.0;
+        for (int p = A->rp[i]; p < A->rp[i + 1]; p++) if (A->ci[p] == i) aii = A->v[p];
+        int neg = aii < 0.0;
+        double m = 0.0;
+        for (int p = A->rp[i]; p < A->rp[i + 1]; p++) {
+            int j = A->ci[p];
+            if (j == i || func[j] != func[i]) continue;
+            double val = neg ? A->v[p] : -A->v[p];
+            if (val > m) m = val;
+        }
+        S->rp[i] = S->nnz;
+        if (m > 0.0) {
+            double thr = theta * m;
+            for (int p = A->rp[i]; p < A->rp[i + 1]; p++) {
+                int j = A->ci[p];
+                if (j == i || func[j] != func[i]) continue;
+                double val = neg ? A->v[p] : -A->v[p];
+                if (val >= thr) { S->ci[S->nnz] = j; S->v[S->nnz] = 1.0; S->nnz++; }
+            }
+        }
+    }
+    S->rp[n] = S->nnz;
+    return OR_OK;
+}
+
+/*
+ * PMIS coarsening (De Sterck, Yang & Heys, 2006).  w_i = |S^T_i| + u(i,level).
+ * Points that influence nobody (|S^T_i| = 0) are F.  Then repeat: every
+ * undecided i whose weight beats all undecided neighbours in S_i u S^T_i
+ * (ties: larger index wins) becomes C, judged on the state at the start of
+ * the round; then every undecided point with a C point in S_i becomes F.
+ */
+static int amg_pmis(const csr *S, int level, int *cf) {
+    int n = S->n;
+    csr ST;
+    int rc = csr_transpose(S, &ST);
+    if (rc) return rc;
+    double *w = (double *)malloc(((size_t)n + 1) * sizeof(double));
+    int *sel = (int *)malloc(((size_t)n + 1) * sizeof(int));
+    if (!w || !sel) return OR_NOMEM;
+    int und = 0;
+    for (int i = 0; i < n; i++) {
+        int cnt = ST.rp[i + 1] - ST.rp[i];
+        w[i] = (double)cnt + pmis_u01((uint32_t)i, (uint32_t)level);
+        cf[i] = cnt == 0 ? -1 : 0;
+        if (!cf[i]) und++;
+    }
+    while (und > 0) {
+        for (int i = 0; i < n; i++) {
+            sel[i] = 0;
+            if (cf[i] != 0) continue;
+            int best = 1;
+            for (int p = S->rp[i]; p < S->rp[i + 1] && best; p++) {
+                int j = S->ci[p];
+                if (cf[j] == 0 && (w[j] > w[i] || (w[j] == w[i] && j > i))) best = 0;
+            }
+            for (int p = ST.rp[i]; p < ST.rp[i + 1] && best; p++) {
+                int j = ST.ci[p];
+                if (cf[j] == 0 && (w[j] > w[i] || (w[j] == w[i] && j > i))) best = 0;
+            }
+            sel[i] = best;
+        }
+        for (int i = 0; i < n; i++) if (sel[i]) { cf[i] = 1; und--; }
+        for (int i = 0; i < n; i++) {
+            if (cf[i] != 0) continue;
+            for (int p = S->rp[i]; p < S->rp[i + 1]; p++)
+                if (cf[S->ci[p]] == 1) { cf[i] = -1; und--; break; }
+        }
+    }
+    free(w); free(sel); csr_free(&ST);
+    return OR_OK;
+}
+
+/* abar_kl of extended+i: a_kl when its sign is opposite to a_kk's, else 0 */
+static double abar(double akk, double akl) {
+    if (akk >= 0.0) return akl < 0.0 ? akl : 0.0;
+    return akl > 0.0 ? akl : 0.0;
+}
+
+/*
+ * Extended+i interpolation (De Sterck, Falgout, Nolting & Yang, 2008),
+ * truncated to pmax entries per row with row-sum rescaling.  Only entries
+ * whose row and column share a function id take part (unknown approach).
+ * For F point i:
+ *   Chat_i = C_i^s  u  (u over k in F_i^s of C_k^s)
+ *   phase 1, row i ascending:  num[j] += a_ij  (j in Chat_i);
+ *                              diag  += a_ij  (j weak and not in Chat_i)
+ *   phase 2, k in F_i^s ascending:
+ *       den = sum over row k ascending of abar_kl, l in Chat_i u {i}
+ *       den == 0 -> diag += a_ik
+ *       else f = a_ik / den; row k ascending: l in Chat_i -> num[l] += f*abar_kl,
+ *                                             l == i     -> diag   += f*abar_ki
+ *   w_ij = -(num[j] / diag)  (diag == 0 -> empty row)
+ * Truncation: keep the pmax largest |w| (ties: lower column), scale kept
+ * weights by (sum of all w) / (sum of kept w) when the latter is non-zero
+ * (both sums in ascending column order).
+ */
+static int amg_extpi(const csr *A, const csr *S, const int *cf, const int *func, int pmax, csr *P,
+                     int *nc_out) {
+    int n = A->n;
+    int *cnum = (int *)malloc(((size_t)n + 1) * sizeof(int));
+    int *mark = (int *)malloc(((size_t)n + 1) * sizeof(int));   /* == i: in Chat_i */
+    int *smark = (int *)malloc(((size_t)n + 1) * sizeof(int));  /* == i: in S_i */
+    double *num = (double *)malloc(((size_t)n + 1) * sizeof(double));
+    int *list = (int *)malloc(((size_t)n + 1) * sizeof(int));
+    double *wl = (double *)malloc(((size_t)n + 1) * sizeof(double));
+    int *ord = (int *)malloc(((size_t)n + 1) * sizeof(int));
+    if (!cnum || !mark || !smark || !num || !list || !wl || !ord) return OR_NOMEM;
+    int nc = 0;
+    for (int i = 0; i < n; i++) { cnum[i] = cf[i] == 1 ? nc++ : -1; mark[i] = -1; smark[i] = -1; }
+    *nc_out = nc;
+    int cap = n * (pmax > 0 ? pmax : 1) + 1;
+    int rc = csr_alloc(P, n, nc, cap);
+    if (rc) return rc;
+    int pos = 0;
+    for (int i = 0; i < n; i++) {
+        P->rp[i] = pos;
+        if (cf[i] == 1) { P->ci[pos] = cnum[i]; P->v[pos] = 1.0; pos++; continue; }
+        /* Chat_i */
+        int cnt = 0;
+        for (int p = S->rp[i]; p < S->rp[i + 1]; p++) smark[S->ci[p]] = i;
+        for (int p = S->rp[i]; p < S->rp[i + 1]; p++) {
+            int j = S->ci[p];
+            if (cf[j] == 1) { if (mark[j] != i) { mark[j] = i; list[cnt++] = j; } }
+            else {
+                for (int q = S->rp[j]; q < S->rp[j + 1]; q++) {
+                    int l = S->ci[q];
+                    if (cf[l] == 1 && mark[l] != i) { mark[l] = i; list[cnt++] = l; }
+                }
+            }
+        }
+        if (cnt == 0) continue;
+        qsort(list, (size_t)cnt, sizeof(int), cmp_int);
+        for (int t = 0; t < cnt; t++) num[list[t]] = 0.0;
+        double diag = 0.0;
+        for (int p = A->rp[i]; p < A->rp[i + 1]; p++) if (A->ci[p] == i) diag = A->v[p];
+        /* phase 1 */
+        for (int p = A->rp[i]; p < A->rp[i + 1]; p++) {
+            int j = A->ci[p];
+            if (j == i || func[j] != func[i]) continue;
+            if (mark[j] == i) num[j] = num[j] + A->v[p];
+            else if (smark[j] != i) diag = diag + A->v[p];
+        }
+        /* phase 2 */
+        for (int p = A->rp[i]; p < A->rp[i + 1]; p++) {
+            int k = A->ci[p];
+            if (k == i || smark[k] != i || cf[k] == 1) continue;
+            double aik = A->v[p];
+            double akk = 0.0;
+            for (int q = A->rp[k]; q < A->rp[k + 1]; q++) if (A->ci[q] == k) akk = A->v[q];
+            double den = 0.0;
+            for (int q = A->rp[k]; q < A->rp[k + 1]; q++) {
+                int l = A->ci[q];
+                if (l == k || func[l] != func[k]) continue;
+                if (mark[l] == i || l == i) den = den + abar(akk, A->v[q]);
+            }
+            if (den == 0.0) { diag = diag + aik; continue; }
+            double f = aik / den;
+            for (int q = A->rp[k]; q < A->rp[k + 1]; q++) {
+                int l = A->ci[q];
+                if (l == k || func[l] != func[k]) continue;
+                if (mark[l] == i) num[l] = num[l] + f * abar(akk, A->v[q]);
+                else if (l == i) diag = diag + f * abar(akk, A->v[q]);
+            }
+        }
+        if (diag == 0.0) continue;
+        for (int t = 0; t < cnt; t++) wl[t] = -(num[list[t]] / diag);
+        int keep = cnt;
+        if (pmax > 0 && cnt > pmax) {
+            /* selection of the pmax largest |w|, ties to lower column */
+            for (int t = 0; t < cnt; t++) ord[t] = t;
+            for (int s = 0; s < pmax; s++) {
+                int b = s;
+                for (int t = s + 1; t < cnt; t++) {
+                    double x = fabs(wl[ord[t]]), y = fabs(wl[ord[b]]);
+                    if (x > y || (x == y && ord[t] < ord[b])) b = t;
+                }
+                int tmp = ord[s]; ord[s] = ord[b]; ord[b] = tmp;
+            }
+            qsort(ord, (size_t)pmax, sizeof(int), cmp_int);
+            double sall = 0.0, skept = 0.0;
+            for (int t = 0; t < cnt; t++) sall = sall + wl[t];
+            for (int s = 0; s < pmax; s++) skept = skept + wl[ord[s]];
+            double scale = skept != 0.0 ? sall / skept : 1.0;
+            for (int s = 0; s < pmax; s++) {
+                P->ci[pos] = cnum[list[ord[s]]];
+                P->v[pos] = skept != 0.0 ? wl[ord[s]] * scale : wl[ord[s]];
+                pos++;
+            }
+            keep = 0;
+        }
+        for (int t = 0; t < keep; t++) { P->ci[pos] = cnum[list[t]]; P->v[pos] = wl[t]; pos++; }
+    }
+    P->rp[n] = pos;
+    P->nnz = pos;
+    free(cnum); free(mark); free(smark); free(num); free(list); free(wl); free(ord);
+    return OR_OK;
+}
+
+/* l1 row scaling d_i = a_ii + sign(a_ii) sum_{j != i} |a_ij| (sign(0) = +1),
+ * off-diagonal sum in ascending column order; returns 1/d_i. */
+static int l1_inverse(const csr *A, const int *func_or_null, double *dinv) {
+    for (int i = 0; i < A->n; i++) {
+        double aii = 0.0, s = 0.0;
+        for (int p = A->rp[i]; p < A->rp[i + 1]; p++) {
+            int j = A->ci[p];
+            if (j == i) { aii = A->v[p]; continue; }
+            if (func_or_null && func_or_null[j] != func_or_null[i]) continue;
+            s = s + fabs(A->v[p]);
+        }
+        double d = aii < 0.0 ? aii - s : aii + s;
+        if (d == 0.0) return OR_SINGULAR;
+        dinv[i] = 1.0 / d;
+    }
+    return OR_OK;
+}
+
+static void amg_free(amg_h *h) {
+    for (int k = 0; k < h->nlev; k++) {
+        amg_level *L = &h->lev[k];
+        csr_free(&L->A); csr_free(&L->P); csr_free(&L->R); csr_free(&L->AT);
+        free(L->dl1inv); free(L->cf); free(L->func); free(L->x); free(L->r); free(L->t);
+    }
+    free(h->lu); free(h->piv);
+    memset(h, 0, sizeof(*h));
+}
+
+/*
+ * AMG setup on A0 (takes ownership): strength, PMIS, ext+i, Galerkin
+ * A_{k+1} = P^T A_k P, until n <= max_coarse, max_levels, or no coarsening.
+ * Coarsest: dense LU with partial pivoting (Gaussian elimination, Sec. 5.1).
+ */
+static int amg_setup(csr *A0, int nfunc, double theta, int max_levels, int max_coarse, int pmax,
+                     amg_h *h) {
+    memset(h, 0, sizeof(*h));
+    if (max_levels > 32) max_levels = 32;
+    h->lev[0].A = *A0;
+    memset(A0, 0, sizeof(*A0));
+    int n = h->lev[0].A.n;
+    h->lev[0].func = (int *)malloc(((size_t)n + 1) * sizeof(int));
+    for (int i = 0; i < n; i++) h->lev[0].func[i] = nfunc > 1 ? i % nfunc : 0;
+    int k = 0, rc;
+    for (;;) {
+        amg_level *L = &h->lev[k];
+        n = L->A.n;
+        L->x = (double *)calloc((size_t)n + 1, sizeof(double));
+        L->r = (double *)calloc((size_t)n + 1, sizeof(double));
+        L->t = (double *)calloc((size_t)n + 1, sizeof(double));
+        if ((rc = csr_transpose(&L->A, &L->AT))) return rc;
+        h->nlev = k + 1;
+        if (n <= max_coarse || k + 1 >= max_levels) break;
+        csr S;
+        if ((rc = amg_strength(&L->A, L->func, theta, &S))) return rc;
+        L->cf = (int *)malloc(((size_t)n + 1) * sizeof(int));
+        if ((rc = amg_pmis(&S, k, L->cf))) return rc;
+        int nc;
+        if ((rc = amg_extpi(&L->A, &S, L->cf, L->func, pmax, &L->P, &nc))) return rc;
+        csr_free(&S);
+        if (nc == 0 || nc == n) { csr_free(&L->P); break; }
+        L->nc = nc;
+        if ((rc = csr_transpose(&L->P, &L->R))) return rc;
+        csr AP;
+        if ((rc = csr_matmat_add(&L->A, &L->P, NULL, &AP))) return rc;
+        amg_level *C = &h->lev[k + 1];
+        memset(C, 0, sizeof(*C));
+        if ((rc = csr_matmat_add(&L->R, &AP, NULL, &C->A))) return rc;
+        csr_free(&AP);
+        C->func = (int *)malloc(((size_t)nc + 1) * sizeof(int));
+        for (int i = 0; i < n; i++) if (L->cf[i] == 1) C->func[L->P.ci[L->P.rp[i]]] = L->func[i];
+        L->dl1inv = (double *)malloc(((size_t)n + 1) * sizeof(double));
+        if ((rc = l1_inverse(&L->A, NULL, L->dl1inv))) return rc;
+        k++;
+    }
+    /* coarsest dense LU */
+    amg_level *L = &h->lev[h->nlev - 1];
+    int nco = L->A.n;
+    if (nco > 8192) return OR_INVALID;
+    h->nco = nco;
+    h->lu = (double *)calloc((size_t)nco * nco + 1, sizeof(double));
+    h->piv = (int *)malloc(((size_t)nco + 1) * sizeof(int));
+    for (int i = 0; i < nco; i++)
+        for (int p = L->A.rp[i]; p < L->A.rp[i + 1]; p++) h->lu[(size_t)i * nco + L->A.ci[p]] = L->A.v[p];
+    return lu_factor(nco, h->lu, h->piv);
+}
+
+/*
+ * AMG V(1,1): l1-Jacobi pre-smoothing from x = 0 (omega = 1), residual,
+ * restriction by P^T, recursion, prolongation by P, l1-Jacobi post-smoothing.
+ * trans = 1 runs the same cycle on A_k^T with the transposed coarse solve,
+ * which is the exact transpose of the trans = 0 operator (diagonal smoother,
+ * restriction = interpolation^T).
+ */
+static void amg_vcycle(amg_h *h, int k, const double *rhs, double *x, int trans) {
+    amg_level *L = &h->lev[k];
+    int n = L->A.n;
+    const csr *A = trans ? &L->AT : &L->A;
+    if (k == h->nlev - 1) { lu_solve(h->nco, h->lu, h->piv, rhs, x, trans); return; }
+    for (int i = 0; i < n; i++) x[i] = L->dl1inv[i] * rhs[i];
+    csr_matvec(A, x, L->t);
+    for (int i = 0; i < n; i++) L->r[i] = rhs[i] - L->t[i];
+    amg_level *C = &h->lev[k + 1];
+    double *rc = (double *)malloc(((size_t)C->A.n + 1) * sizeof(double));
+    double *ec = (double *)malloc(((size_t)C->A.n + 1) * sizeof(double));
+    csr_matvec(&L->R, L->r, rc);
+    amg_vcycle(h, k + 1, rc, ec, trans);
+    csr_matvec(&L->P, ec, L->t);
+    for (int i = 0; i < n; i++) x[i] = x[i] + L->t[i];
+    csr_matvec(A, x, L->t);
+    for (int i = 0; i < n; i++) x[i] = x[i] + L->dl1inv[i] * (rhs[i] - L->t[i]);
+    free(rc); free(ec);
+}
+
+/* ---------------------------------------------------------- MGR levels */
+typedef struct {
+    int n, nF, nC;
+    int *fidx, *cidx;          /* local indices of F and C points, ascending */
+    int *gdof;                 /* original dof of each local index */
+    csr A, AFF, AFC, ACF, W;   /* A_l and its blocks; W = -D^{-1} A_FC */
+    csr AFFT, ACFT, WT;        /* transposes for the adjoint cycle */
+    int relax, sweeps;
+    double omega;
+    int *gstart, *gsize;       /* D block of every F point: first F position and size */
+    double *dinv;              /* per F point: row of its block inverse (gsize entries) */
+    double *zF, *rF, *tF, *vC, *eC;
+} mgr_level;
+
+typedef struct or_ctx {
+    int n, b, nlev;
+    csr A, AT;
+    mgr_level lev[8];
+    amg_h amg;
+    double *work[6];
+} or_ctx;
+
+/* A_FF, A_FC, A_CF, A_CC blocks of A for a C/F split (the partition of Eq. 2) */
+static int split_blocks(const csr *A, const int *fpos, const int *cpos, int nF, int nC,
+                        const int *fidx, const int *cidx, csr *AFF, csr *AFC, csr *ACF, csr *ACC) {
+    csr *outs[4] = {AFF, AFC, ACF, ACC};
+    int rows_n[4] = {nF, nF, nC, nC}, cols_n[4] = {nF, nC, nF, nC};
+    for (int t = 0; t < 4; t++) {
+        const int *ridx = t < 2 ? fidx : cidx;
+        const int *cmap = (t == 0 || t == 2) ? fpos : cpos;
+        int cnt = 0;
+        for (int r = 0; r < rows_n[t]; r++) {
+            int i = ridx[r];
+            for (int p = A->rp[i]; p < A->rp[i + 1]; p++) if (cmap[A->ci[p]] >= 0) cnt++;
+        }
+        int rc = csr_alloc(outs[t], rows_n[t], cols_n[t], cnt);
+        if (rc) return rc;
+        cnt = 0;
+        for (int r = 0; r < rows_n[t]; r++) {
+            int i = ridx[r];
+            outs[t]->rp[r] = cnt;
+            for (int p = A->rp[i]; p < A->rp[i + 1]; p++) {
+                int c = cmap[A->ci[p]];
+                if (c >= 0) { outs[t]->ci[cnt] = c; outs[t]->v[cnt] = A->v[p]; cnt++; }
+            }
+        }
+        outs[t]->rp[rows_n[t]] = cnt;
+    }
+    return OR_OK;
+}
+
+static double csr_get(const csr *a, int i, int j) {
+    for (int p = a->rp[i]; p < a->rp[i + 1]; p++) if (a->ci[p] == j) return a->v[p];
+    return 0.0;
+}
+
+/*
+ * D_FF^{-1} of Eq. 4 and of the F-relaxation M_FF.  Jacobi: 1/a_ii;
+ * l1-Jacobi: 1/(a_ii + sign(a_ii) sum_{j in F, j != i} |a_ij|);
+ * block-Jacobi: the inverse of the F-by-F block of each original BSR block
+ * row (Gauss-Jordan with partial pivoting).  The same D is used for W.
+ */
+static int mgr_dinv(mgr_level *L, int b) {
+    int nF = L->nF;
+    L->gstart = (int *)malloc(((size_t)nF + 1) * sizeof(int));
+    L->gsize = (int *)malloc(((size_t)nF + 1) * sizeof(int));
+    L->dinv = (double *)malloc(((size_t)nF * 4 + 1) * sizeof(double));
+    if (!L->gstart || !L->gsize || !L->dinv) return OR_NOMEM;
+    if (L->relax != OR_BLOCK_JACOBI) {
+        for (int f = 0; f < nF; f++) {
+            L->gstart[f] = f; L->gsize[f] = 1;
+            double aii = csr_get(&L->AFF, f, f);
+            double d = aii;
+            if (L->relax == OR_L1_JACOBI) {
+                double s = 0.0;
+                for (int p = L->AFF.rp[f]; p < L->AFF.rp[f + 1]; p++)
+                    if (L->AFF.ci[p] != f) s = s + fabs(L->AFF.v[p]);
+                d = aii < 0.0 ? aii - s : aii + s;
+            }
+            if (d == 0.0) return OR_SINGULAR;
+            L->dinv[(size_t)f * 4] = 1.0 / d;
+        }
+        return OR_OK;
+    }
+    int f = 0;
+    while (f < nF) {
+        int blk = L->gdof[L->fidx[f]] / b;
+        int g = f;
+        while (g < nF && L->gdof[L->fidx[g]] / b == blk) g++;
+        int k = g - f;
+        double B[16], inv[16];
+        for (int r = 0; r < k; r++)
+            for (int c = 0; c < k; c++) B[r * k + c] = csr_get(&L->AFF, f + r, f + c);
+        if (block_inverse(k, B, inv)) return OR_SINGULAR;
+        for (int r = 0; r < k; r++) {
+            L->gstart[f + r] = f; L->gsize[f + r] = k;
+            for (int c = 0; c < k; c++) L->dinv[(size_t)(f + r) * 4 + c] = inv[r * k + c];
+        }
+        f = g;
+    }
+    return OR_OK;
+}
+
+/*
+ * W = -D^{-1} A_FC (the interpolation block of Eq. 4).  Row f: pattern = union
+ * of the A_FC rows of f's D block; value at column j: acc = sum over the
+ * block's rows q ascending of dinv[f][q] * a_{q j}, then W = -acc.
+ */
+static int mgr_build_w(mgr_level *L) {
+    int nF = L->nF, nC = L->nC;
+    const csr *B = &L->AFC;
+    int *mark = (int *)malloc(((size_t)nC + 1) * sizeof(int));
+    int *list = (int *)malloc(((size_t)nC + 1) * sizeof(int));
+    double *acc = (double *)malloc(((size_t)nC + 1) * sizeof(double));
+    if (!mark || !list || !acc) return OR_NOMEM;
+    for (int j = 0; j < nC; j++) mark[j] = -1;
+    long long tot = 0;
+    for (int f = 0; f < nF; f++) {
+        int cnt = 0;
+        for (int q = 0; q < L->gsize[f]; q++) {
+            int r = L->gstart[f] + q;
+            for (int p = B->rp[r]; p < B->rp[r + 1]; p++)
+                if (mark[B->ci[p]] != f) { mark[B->ci[p]] = f; cnt++; }
+        }
+        tot += cnt;
+    }
+    int rc = csr_alloc(&L->W, nF, nC, (int)tot);
+    if (rc) return rc;
+    for (int j = 0; j < nC; j++) mark[j] = -1;
+    int pos = 0;
+    for (int f = 0; f < nF; f++) {
+        int cnt = 0;
+        for (int q = 0; q < L->gsize[f]; q++) {
+            int r = L->gstart[f] + q;
+            double d = L->dinv[(size_t)f * 4 + q];
+            for (int p = B->rp[r]; p < B->rp[r + 1]; p++) {
+                int j = B->ci[p];
+                if (mark[j] != f) { mark[j] = f; acc[j] = 0.0; list[cnt++] = j; }
+                acc[j] = acc[j] + d * B->v[p];
+            }
+        }
+        qsort(list, (size_t)cnt, sizeof(int), cmp_int);
+        L->W.rp[f] = pos;
+        for (int t = 0; t < cnt; t++) { L->W.ci[pos] = list[t]; L->W.v[pos] = -acc[list[t]]; pos++; }
+    }
+    L->W.rp[nF] = pos;
+    free(mark); free(list); free(acc);
+    return OR_OK;
+}
+
+static void mgr_level_free(mgr_level *L) {
+    free(L->fidx); free(L->cidx); free(L->gdof);
+    csr_free(&L->A); csr_free(&L->AFF); csr_free(&L->AFC); csr_free(&L->ACF); csr_free(&L->W);
+    csr_free(&L->AFFT); csr_free(&L->ACFT); csr_free(&L->WT);
+    free(L->gstart); free(L->gsize); free(L->dinv);
+    free(L->zF); free(L->rF); free(L->tF); free(L->vC); free(L->eC);
+}
+
+void or_free(or_ctx *c) {
+    if (!c) return;
+    csr_free(&c->A); csr_free(&c->AT);
+    for (int l = 0; l < c->nlev; l++) mgr_level_free(&c->lev[l]);
+    amg_free(&c->amg);
+    for (int t = 0; t < 6; t++) free(c->work[t]);
+    free(c);
+}
+
+/*
+ * MGR setup (Sec. 3): for each level l < num_levels, F = {dof_level == l},
+ * C = {dof_level > l}; D_FF^{-1}; W = -D^{-1} A_FC; the coarse operator
+ * A_{l+1} = R~ A P~ = A_CC + A_CF W (Eq. 4 operators; the product order of
+ * csr_matmat_add with A_CC added last).  The final coarse block gets AMG.
+ */
+or_ctx *or_setup(int nb, int b, const int *rp, const int *ci, const double *val,
+                 const signed char *dof_level, int num_levels, const int *relax_type,
+                 const int *relax_sweeps, const double *relax_weight, double theta,
+                 int max_levels, int max_coarse, int pmax, int num_functions, int *status) {
+    *status = OR_INVALID;
+    if (b < 1 || b > 4 || nb < 1 || num_levels < 0 || num_levels > 8) return NULL;
+    or_ctx *c = (or_ctx *)calloc(1, sizeof(or_ctx));
+    if (!c) { *status = OR_NOMEM; return NULL; }
+    c->n = nb * b; c->b = b; c->nlev = num_levels;
+    int rc = bsr_to_csr(nb, b, rp, ci, val, &c->A);
+    if (!rc) rc = csr_transpose(&c->A, &c->AT);
+    if (rc) { or_free(c); *status = rc; return NULL; }
+    for (int t = 0; t < 6; t++) c->work[t] = (double *)calloc((size_t)c->n + 1, sizeof(double));
+    /* level 0 matrix = A with the identity map */
+    csr cur;
+    rc = csr_alloc(&cur, c->n, c->n, c->A.nnz);
+    if (rc) { or_free(c); *status = rc; return NULL; }
+    memcpy(cur.rp, c->A.rp, ((size_t)c->n + 1) * sizeof(int));
+    memcpy(cur.ci, c->A.ci, (size_t)c->A.nnz * sizeof(int));
+    memcpy(cur.v, c->A.v, (size_t)c->A.nnz * sizeof(double));
+    int *gdof = (int *)malloc(((size_t)c->n + 1) * sizeof(int));
+    for (int i = 0; i < c->n; i++) gdof[i] = i;
+    for (int l = 0; l < num_levels; l++) {
+        mgr_level *L = &c->lev[l];
+        L->A = cur; L->gdof = gdof; L->n = cur.n;
+        L->relax = relax_type[l]; L->sweeps = relax_sweeps[l] < 1 ? 1 : relax_sweeps[l];
+        L->omega = relax_weight[l];
+        int n = L->n;
+        int *fpos = (int *)malloc(((size_t)n + 1) * sizeof(int));
+        int *cpos = (int *)malloc(((size_t)n + 1) * sizeof(int));
+        L->fidx = (int *)malloc(((size_t)n + 1) * sizeof(int));
+        L->cidx = (int *)malloc(((size_t)n + 1) * sizeof(int));
+        int nF = 0, nC = 0;
+        for (int i = 0; i < n; i++) {
+            int lv = dof_level[gdof[i]];
+            fpos[i] = cpos[i] = -1;
+            if (lv == l) { fpos[i] = nF; L->fidx[nF++] = i; }
+            else if (lv > l) { cpos[i] = nC; L->cidx[nC++] = i; }
+            else { *status = OR_INVALID; or_free(c); return NULL; }
+        }
+        L->nF = nF; L->nC = nC;
+        if (nF == 0 || nC == 0) { free(fpos); free(cpos); c->nlev = l + 1; *status = OR_INVALID; or_free(c); return NULL; }
+        csr ACC;
+        rc = split_blocks(&L->A, fpos, cpos, nF, nC, L->fidx, L->cidx, &L->AFF, &L->AFC, &L->ACF, &ACC);
+        free(fpos); free(cpos);
+        if (!rc) rc = mgr_dinv(L, b);
+        if (!rc) rc = mgr_build_w(L);
+        csr next;
+        memset(&next, 0, sizeof(next));
+        if (!rc) rc = csr_matmat_add(&L->ACF, &L->W, &ACC, &next);
+        csr_free(&ACC);
+        if (!rc) rc = csr_transpose(&L->AFF, &L->AFFT);
+        if (!rc) rc = csr_transpose(&L->ACF, &L->ACFT);
+        if (!rc) rc = csr_transpose(&L->W, &L->WT);
+        if (rc) { c->nlev = l + 1; csr_free(&next); or_free(c); *status = rc; return NULL; }
+        L->zF = (double *)calloc((size_t)nF + 1, sizeof(double));
+        L->rF = (double *)calloc((size_t)nF + 1, sizeof(double));
+        L->tF = (double *)calloc((size_t)nF + 1, sizeof(double));
+        L->vC = (double *)calloc((size_t)nC + 1, sizeof(double));
+        L->eC = (double *)calloc((size_t)nC + 1, sizeof(double));
+        int *g2 = (int *)malloc(((size_t)nC + 1) * sizeof(int));
+        for (int t = 0; t < nC; t++) g2[t] = gdof[L->cidx[t]];
+        gdof = g2;
+        cur = next;
+    }
+    free(gdof);
+    rc = amg_setup(&cur, num_functions, theta, max_levels, max_coarse, pmax, &c->amg);
+    if (rc) { or_free(c); *status = rc; return NULL; }
+    *status = OR_OK;
+    return c;
+}
+
+/* z_F <- sweeps of z_F += omega D^{-1} (y - A z_F) from z_F = 0 (Alg. 1,
+ * F-relaxation with M_FF = D); trans uses A_FF^T and D^{-T}. */
+static void mgr_frelax(mgr_level *L, const double *y, int trans) {
+    const csr *AFF = trans ? &L->AFFT : &L->AFF;
+    int nF = L->nF;
+    for (int f = 0; f < nF; f++) L->zF[f] = 0.0;
+    for (int s = 0; s < L->sweeps; s++) {
+        csr_matvec(AFF, L->zF, L->tF);
+        for (int f = 0; f < nF; f++) L->rF[f] = y[f] - L->tF[f];
+        for (int f = 0; f < nF; f++) {
+            int g = L->gstart[f], k = L->gsize[f], r = f - g;
+            double s2 = 0.0;
+            for (int q = 0; q < k; q++) {
+                double d = trans ? L->dinv[(size_t)(g + q) * 4 + r] : L->dinv[(size_t)f * 4 + q];
+                s2 = s2 + d * L->rF[g + q];
+            }
+            L->tF[f] = L->omega * s2;
+        }
+        for (int f = 0; f < nF; f++) L->zF[f] = L->zF[f] + L->tF[f];
+    }
+}
+
+/*
+ * One MGR V-cycle (Algorithm 1) without global relaxation (the paper uses
+ * none): F-relaxation, injection restriction r_C = v_C - A_CF z_F,
+ * recursion, interpolation z_C = e_C, z_F += W e_C.  The final coarse block
+ * takes one AMG V(1,1).
+ */
+static void mgr_vcycle(or_ctx *c, int l, const double *v, double *z) {
+    if (l == c->nlev) { amg_vcycle(&c->amg, 0, v, z, 0); return; }
+    mgr_level *L = &c->lev[l];
+    double *yF = (double *)malloc(((size_t)L->nF + 1) * sizeof(double));
+    for (int f = 0; f < L->nF; f++) yF[f] = v[L->fidx[f]];
+    mgr_frelax(L, yF, 0);
+    csr_matvec(&L->ACF, L->zF, L->vC);
+    for (int t = 0; t < L->nC; t++) L->vC[t] = v[L->cidx[t]] - L->vC[t];
+    double *vC = (double *)malloc(((size_t)L->nC + 1) * sizeof(double));
+    double *eC = (double *)malloc(((size_t)L->nC + 1) * sizeof(double));
+    memcpy(vC, L->vC, (size_t)L->nC * sizeof(double));
+    double *zF = (double *)malloc(((size_t)L->nF + 1) * sizeof(double));
+    memcpy(zF, L->zF, (size_t)L->nF * sizeof(double));
+    mgr_vcycle(c, l + 1, vC, eC);
+    double *we = (double *)malloc(((size_t)L->nF + 1) * sizeof(double));
+    csr_matvec(&L->W, eC, we);
+    for (int t = 0; t < L->nC; t++) z[L->cidx[t]] = eC[t];
+    for (int f = 0; f < L->nF; f++) z[L->fidx[f]] = zF[f] + we[f];
+    free(yF); free(vC); free(eC); free(zF); free(we);
+}
+
+/*
+ * Exact transpose of mgr_vcycle.  With M^{-1} = [K 0; 0 0] + [W; I] B [-A_CF K, I]
+ * (K = the F-relaxation operator, B = the coarse cycle):
+ *   r_C = v_C + W^T v_F;  e_C = B^T r_C;  z_C = e_C;
+ *   z_F = K^T (v_F - A_CF^T e_C), K^T = the same sweeps on A_FF^T with D^{-T}.
+ */
+static void mgr_vcycle_t(or_ctx *c, int l, const double *v, double *z) {
+    if (l == c->nlev) { amg_vcycle(&c->amg, 0, v, z, 1); return; }
+    mgr_level *L = &c->lev[l];
+    double *vF = (double *)malloc(((size_t)L->nF + 1) * sizeof(double));
+    double *rC = (double *)malloc(((size_t)L->nC + 1) * sizeof(double));
+    double *eC = (double *)malloc(((size_t)L->nC + 1) * sizeof(double));
+    double *tF = (double *)malloc(((size_t)L->nF + 1) * sizeof(double));
+    for (int f = 0; f < L->nF; f++) vF[f] = v[L->fidx[f]];
+    csr_matvec(&L->WT, vF, rC);
+    for (int t = 0; t < L->nC; t++) rC[t] = v[L->cidx[t]] + rC[t];
+    mgr_vcycle_t(c, l + 1, rC, eC);
+    csr_matvec(&L->ACFT, eC, tF);
+    for (int f = 0; f < L->nF; f++) tF[f] = vF[f] - tF[f];
+    mgr_frelax(L, tF, 1);
+    for (int t = 0; t < L->nC; t++) z[L->cidx[t]] = eC[t];
+    for (int f = 0; f < L->nF; f++) z[L->fidx[f]] = L->zF[f];
+    free(vF); free(rC); free(eC); free(tF);
+}
+
+int or_apply(or_ctx *c, const double *v, double *z) { mgr_vcycle(c, 0, v, z); return OR_OK; }
+int or_apply_transpose(or_ctx *c, const double *v, double *z) { mgr_vcycle_t(c, 0, v, z); return OR_OK; }
+
+static double dot(int n, const double *x, const double *y) {
+    double s = 0.0;
+    for (int i = 0; i < n; i++) s += x[i] * y[i];
+    return s;
+}
+
+/*
+ * Right-preconditioned flexible GMRES(m) (Sec. 5.1 uses right-preconditioned
+ * GMRES), modified Gram-Schmidt Arnoldi, Givens rotations.  Converged when
+ * the true residual ||b - A x|| <= rtol ||b|| (checked at every restart and
+ * when the rotated estimate |g_{j+1}| <= rtol ||b||).  Happy breakdown when
+ * h_{j+1,j} <= 1e-14 ||A z_j||.  *iters counts preconditioner applications.
+ * precond = 0 uses M = I; trans = 1 solves A^T x = b with M^{-T}.
+ */
+int or_solve(or_ctx *c, const double *b, double *x, double rtol, int maxit, int m, int precond,
+             int trans, int *iters, double *relres, double *hist) {
+    int n = c->n;
+    const csr *A = trans ? &c->AT : &c->A;
+    if (m < 1) m = 1;
+    double *V = (double *)malloc((size_t)(m + 1) * n * sizeof(double));
+    double *Z = (double *)malloc((size_t)m * n * sizeof(double));
+    double *H = (double *)calloc((size_t)(m + 1) * m, sizeof(double));
+    double *cs = (double *)calloc((size_t)m + 1, sizeof(double));
+    double *sn = (double *)calloc((size_t)m + 1, sizeof(double));
+    double *g = (double *)calloc((size_t)m + 2, sizeof(double));
+    double *y = (double *)calloc((size_t)m + 1, sizeof(double));
+    double *r = c->work[0], *w = c->work[1];
+    if (!V || !Z || !H || !cs || !sn || !g || !y) return OR_NOMEM;
+    double bn = sqrt(dot(n, b, b));
+    int it = 0, rc = OR_NOT_CONVERGED;
+    if (bn == 0.0) {
+        for (int i = 0; i < n; i++) x[i] = 0.0;
+        *iters = 0; *relres = 0.0; rc = OR_OK; goto done;
+    }
+    for (;;) {
+        csr_matvec(A, x, r);
+        for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
+        double beta = sqrt(dot(n, r, r));
+        *relres = beta / bn;
+        if (hist && it == 0) hist[0] = *relres;
+        if (beta <= rtol * bn) { rc = OR_OK; break; }
+        if (it >= maxit) break;
+        for (int i = 0; i < n; i++) V[i] = r[i] / beta;
+        for (int t = 0; t <= m; t++) g[t] = 0.0;
+        g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m && it < maxit; j++) {
+            double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
+            if (precond) { if (trans) mgr_vcycle_t(c, 0, vj, zj); else mgr_vcycle(c, 0, vj, zj); }
+            else memcpy(zj, vj, (size_t)n * sizeof(double));
+            csr_matvec(A, zj, w);
+            it++;
+            double w0 = sqrt(dot(n, w, w));
+            for (int i = 0; i <= j; i++) {
+                double *vi = V + (size_t)i * n;
+                double h = dot(n, w, vi);
+                H[(size_t)i * m + j] = h;
+                for (int e = 0; e < n; e++) w[e] -= h * vi[e];
+            }
+            double hn = sqrt(dot(n, w, w));
+            H[(size_t)(j + 1) * m + j] = hn;
+            for (int i = 0; i < j; i++) {
+                double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+            }
+            double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+            double rho = sqrt(a * a + bb * bb);
+            cs[j] = a / rho; sn[j] = bb / rho;
+            H[(size_t)j * m + j] = rho; H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            k = j + 1;
+            if (hist) hist[it] = fabs(g[j + 1]) / bn;
+            if (fabs(g[j + 1]) <= rtol * bn || hn <= 1e-14 * w0) break;
+            double *vn = V + (size_t)(j + 1) * n;
+            for (int e = 0; e < n; e++) vn[e] = w[e] / hn;
+        }
+        for (int i = k - 1; i >= 0; i--) {
+            double s = g[i];
+            for (int t = i + 1; t < k; t++) s -= H[(size_t)i * m + t] * y[t];
+            y[i] = s / H[(size_t)i * m + i];
+        }
+        for (int i = 0; i < k; i++) {
+            double *zi = Z + (size_t)i * n;
+            for (int e = 0; e < n; e++) x[e] += y[i] * zi[e];
+        }
+    }
+    *iters = it;
+done:
+    free(V); free(Z); free(H); free(cs); free(sn); free(g); free(y);
+    return rc;
+}
+
+/* ------------------------------------------------------- inspection */
+int or_n(or_ctx *c) { return c->n; }
+int or_mgr_nlevels(or_ctx *c) { return c->nlev; }
+int or_amg_nlevels(or_ctx *c) { return c->amg.nlev; }
+
+static const csr *mgr_mat(or_ctx *c, int l, int which) {
+    if (l < 0 || l > c->nlev) return NULL;
+    if (l == c->nlev) return which == 0 ? &c->amg.lev[0].A : NULL;
+    mgr_level *L = &c->lev[l];
+    switch (which) {
+        case 0: return &L->A;
+        case 1: return &L->AFF;
+        case 2: return &L->AFC;
+        case 3: return &L->ACF;
+        case 4: return &L->W;
+        default: return NULL;
+    }
+}
+
+static const csr *amg_mat(or_ctx *c, int k, int which) {
+    if (k < 0 || k >= c->amg.nlev) return NULL;
+    amg_level *L = &c->amg.lev[k];
+    switch (which) {
+        case 0: return &L->A;
+        case 1: return L->P.rp ? &L->P : NULL;
+        default: return NULL;
+    }
+}
+
+/* dims[0..2] = rows, cols, nnz of the selected matrix; -1 when absent */
+int or_mat_dims(or_ctx *c, int amg, int lvl, int which, int *dims) {
+    const csr *a = amg ? amg_mat(c, lvl, which) : mgr_mat(c, lvl, which);
+    if (!a) { dims[0] = dims[1] = dims[2] = -1; return OR_INVALID; }
+    dims[0] = a->n; dims[1] = a->m; dims[2] = a->nnz;
+    return OR_OK;
+}
+
+int or_mat_copy(or_ctx *c, int amg, int lvl, int which, int *rp, int *ci, double *v) {
+    const csr *a = amg ? amg_mat(c, lvl, which) : mgr_mat(c, lvl, which);
+    if (!a) return OR_INVALID;
+    memcpy(rp, a->rp, ((size_t)a->n + 1) * sizeof(int));
+    memcpy(ci, a->ci, (size_t)a->nnz * sizeof(int));
+    memcpy(v, a->v, (size_t)a->nnz * sizeof(double));
+    return OR_OK;
+}
+
+/* per-F-point inverse-block rows (4 slots each) and block sizes of MGR level l */
+int or_mgr_dinv(or_ctx *c, int l, double *dinv, int *gsize) {
+    if (l < 0 || l >= c->nlev) return OR_INVALID;
+    mgr_level *L = &c->lev[l];
+    memcpy(dinv, L->dinv, (size_t)L->nF * 4 * sizeof(double));
+    memcpy(gsize, L->gsize, (size_t)L->nF * sizeof(int));
+    return OR_OK;
+}
+
+int or_amg_cf(or_ctx *c, int k, int *cf) {
+    if (k < 0 || k >= c->amg.nlev - 1) return OR_INVALID;
+    memcpy(cf, c->amg.lev[k].cf, (size_t)c->amg.lev[k].A.n * sizeof(int));
+    return OR_OK;
+}
+
+int or_amg_coarse_n(or_ctx *c) { return c->amg.nco; }
+
+/* ---------------------------------------------- standalone AMG pieces */
+/* Strength + PMIS + ext+i on a CSR matrix given by arrays (test hooks). */
+int or_amg_split_interp(int n, const int *rp, const int *ci, const double *v, const int *func,
+                        double theta, int level, int pmax, int *cf, int *p_rp, int *p_ci,
+                        double *p_v, int p_cap, int *nc) {
+    csr A;
+    A.n = n; A.m = n; A.nnz = rp[n];
+    A.rp = (int *)rp; A.ci = (int *)ci; A.v = (double *)v;
+    csr S, P;
+    int rc = amg_strength(&A, func, theta, &S);
+    if (rc) return rc;
+    rc = amg_pmis(&S, level, cf);
+    if (!rc) rc = amg_extpi(&A, &S, cf, func, pmax, &P, nc);
+    csr_free(&S);
+    if (rc) return rc;
+    if (P.nnz > p_cap) { csr_free(&P); return OR_INVALID; }
+    memcpy(p_rp, P.rp, ((size_t)n + 1) * sizeof(int));
+    memcpy(p_ci, P.ci, (size_t)P.nnz * sizeof(int));
+    memcpy(p_v, P.v, (size_t)P.nnz * sizeof(double));
+    csr_free(&P);
+    return OR_OK;
+}
+
+/* Strength matrix pattern only (test hook): s_rp[n+1], s_ci[cap]. */
+int or_amg_strength(int n, const int *rp, const int *ci, const double *v, const int *func,
+                    double theta, int *s_rp, int *s_ci, int cap) {
+    csr A, S;
+    A.n = n; A.m = n; A.nnz = rp[n];
+    A.rp = (int *)rp; A.ci = (int *)ci; A.v = (double *)v;
+    int rc = amg_strength(&A, func, theta, &S);
+    if (rc) return rc;
+    if (S.nnz > cap) { csr_free(&S); return OR_INVALID; }
+    memcpy(s_rp, S.rp, ((size_t)n + 1) * sizeof(int));
+    memcpy(s_ci, S.ci, (size_t)S.nnz * sizeof(int));
+    csr_free(&S);
+    return OR_OK;
+}

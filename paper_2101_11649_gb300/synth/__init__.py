@@ -1,0 +1,23 @@
+"""Seeded synthetic Jacobians shaped like the paper's three applications.
+
+Inputs only: every generator returns a :class:`BlockSystem` and holds none of
+the multigrid-reduction arithmetic.  Both the CUDA path and the CPU oracle
+read these systems.
+"""
+from .bsr import BlockSystem, assemble_bsr
+from .two_phase import make_two_phase
+from .mimetic import make_mimetic
+from .compositional import make_compositional
+from .poromech import make_poromech
+from .batched import make_batch, batch_grids
+
+# The five named workloads at full size (small variants for fast tests).
+CONFIGS = {
+    "two_phase_16x16x8": lambda: make_two_phase(16, 16, 8),
+    "mimetic_64": lambda: make_mimetic(64, 64, 64),
+    "compositional_128x128x32": lambda: make_compositional(128, 128, 32),
+    "poromech_64": lambda: make_poromech(64, 48),
+}
+
+__all__ = ["BlockSystem", "assemble_bsr", "make_two_phase", "make_mimetic",
+           "make_compositional", "make_poromech", "make_batch", "batch_grids", "CONFIGS"]
