@@ -456,6 +456,12 @@ static int amg_extpi(const csr *A, const csr *S, const int *cf, const int *func,
     int pos = 0;
     for (int i = 0; i < n; i++) {
         P->rp[i] = pos;
+        if (pos + 1 > cap) {
+            cap = 2 * (pos + 1);
+            P->ci = (int *)realloc(P->ci, (size_t)cap * sizeof(int));
+            P->v = (double *)realloc(P->v, (size_t)cap * sizeof(double));
+            if (!P->ci || !P->v) return OR_NOMEM;
+        }
         if (cf[i] == 1) { P->ci[pos] = cnum[i]; P->v[pos] = 1.0; pos++; continue; }
         /* Chat_i */
         int cnt = 0;
@@ -471,6 +477,12 @@ static int amg_extpi(const csr *A, const csr *S, const int *cf, const int *func,
             }
         }
         if (cnt == 0) continue;
+        if (pos + cnt > cap) {
+            cap = 2 * (pos + cnt);
+            P->ci = (int *)realloc(P->ci, (size_t)cap * sizeof(int));
+            P->v = (double *)realloc(P->v, (size_t)cap * sizeof(double));
+            if (!P->ci || !P->v) return OR_NOMEM;
+        }
         qsort(list, (size_t)cnt, sizeof(int), cmp_int);
         for (int t = 0; t < cnt; t++) num[list[t]] = 0.0;
         double diag = 0.0;

@@ -221,7 +221,7 @@ def amg_split_interp(rp, ci, v, func=None, theta=0.25, level=0, pmax=4):
     n = rp.size - 1
     func = np.zeros(n, np.int32) if func is None else _i32(func)
     cf = np.zeros(n, np.int32)
-    cap = n * max(pmax, 1) + 1 if pmax > 0 else int(rp[-1]) * 8 + n + 1
+    cap = n * max(pmax, 1) + 1 if pmax > 0 else int(rp[-1]) * 64 + n + 1
     prp = np.zeros(n + 1, np.int32); pci = np.zeros(cap, np.int32); pv = np.zeros(cap)
     nc = np.zeros(1, np.int32)
     rc = lib().or_amg_split_interp(n, _p(rp), _p(ci), _p(v), _p(func), theta, level, pmax,

@@ -1,0 +1,377 @@
+"""Pins of the CPU oracle to what the paper and the mathematics fix.
+
+Each test checks the oracle against an independent fact (a dense definition,
+a closed form, a published test vector, an invariant), never against a
+retyped copy of its own formula.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2101_11649_gb300.synth import (make_compositional, make_mimetic, make_poromech,
+                                          make_two_phase)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense_of(sysm):
+    """Dense matrix of a BlockSystem from its blocks (numpy only)."""
+    n, b = sysm.n, sysm.b
+    A = np.zeros((n, n))
+    for I in range(sysm.nb):
+        for p in range(sysm.row_ptr[I], sysm.row_ptr[I + 1]):
+            J = sysm.col_idx[p]
+            A[I * b:(I + 1) * b, J * b:(J + 1) * b] += sysm.val[p]
+    return A
+
+
+def csr_dense(m):
+    rp, ci, v, (n, mm) = m
+    A = np.zeros((n, mm))
+    for i in range(n):
+        A[i, ci[rp[i]:rp[i + 1]]] += v[rp[i]:rp[i + 1]]
+    return A
+
+
+def random_bsr(nb, b, density, rng, empty_rows=()):
+    rows, cols = [], []
+    for i in range(nb):
+        if i in empty_rows:
+            continue
+        js = np.flatnonzero(rng.random(nb) < density)
+        rows += [i] * len(js); cols += list(js)
+    from paper_2101_11649_gb300.synth.bsr import assemble_bsr
+    blocks = rng.standard_normal((len(rows), b, b))
+    return assemble_bsr(nb, b, np.array(rows, np.int64), np.array(cols, np.int64), blocks)
+
+
+# ---------------------------------------------------------------- SpMV
+@pytest.mark.parametrize("b", [1, 2, 3, 4])
+def test_spmv_matches_dense(b):
+    rng = np.random.default_rng(b)
+    nb = 37
+    rp, ci, val = random_bsr(nb, b, 0.15, rng, empty_rows=(0, 5, 36))
+    x = rng.standard_normal(nb * b)
+    y = O.spmv_bsr(nb, b, rp, ci, val, x)
+    A = np.zeros((nb * b, nb * b))
+    for I in range(nb):
+        for p in range(rp[I], rp[I + 1]):
+            A[I * b:(I + 1) * b, ci[p] * b:(ci[p] + 1) * b] = val[p]
+    ref = A @ x
+    scale = np.abs(A) @ np.abs(x) + 1e-300
+    assert np.max(np.abs(y - ref) / scale) < 1e-14
+    sp = pytest.importorskip("scipy.sparse")
+    Bs = sp.bsr_matrix((val, ci, rp), shape=A.shape)
+    assert np.max(np.abs(y - Bs @ x) / scale) < 1e-14
+
+
+def test_dense_lu_matches_numpy():
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 7, 50, 200):
+        A = rng.standard_normal((n, n)) + n * 0.1 * np.eye(n)
+        bb = rng.standard_normal(n)
+        x = O.dense_solve(A, bb)
+        ref = np.linalg.solve(A, bb)
+        assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref) * max(1, np.linalg.cond(A) / 1e3)
+
+
+# --------------------------------------------------- reduced operator (Eq. 2, 4)
+def test_reduced_operator_is_schur_complement_diagonal_F():
+    """A_FF diagonal (MGR_P on the mimetic system, Eq. 15): the coarse
+    operator A_CC - A_CF D^{-1} A_FC is the exact Schur complement of Eq. 2."""
+    s = make_mimetic(5, 4, 3)
+    o = O.Oracle(s)
+    A = dense_of(s)
+    F = np.flatnonzero(s.dof_level == 0); Cc = np.flatnonzero(s.dof_level == 1)
+    AFF = A[np.ix_(F, F)]
+    assert np.count_nonzero(AFF - np.diag(np.diag(AFF))) == 0
+    S = A[np.ix_(Cc, Cc)] - A[np.ix_(Cc, F)] @ np.linalg.solve(AFF, A[np.ix_(F, Cc)])
+    got = csr_dense(o.mgr_matrix(1, "A"))
+    assert np.max(np.abs(got - S)) <= 1e-13 * np.max(np.abs(S))
+    # W = -D^{-1} A_FC, the Jacobi interpolation block of Eq. 4
+    W = csr_dense(o.mgr_matrix(0, "W"))
+    assert np.max(np.abs(W + np.diag(1 / np.diag(AFF)) @ A[np.ix_(F, Cc)])) < 1e-13 * np.abs(W).max()
+
+
+def test_reduced_operator_block_jacobi_wells_exact():
+    """Level 1 of the compositional system eliminates the wells with exact
+    2x2 block inverses; wells do not couple, so A_FF is block-diagonal and
+    the reduced operator is the exact Schur complement, including the
+    zero-diagonal pressure-controlled wells (Sec. 4.2)."""
+    s = make_compositional(8, 8, 3, nwell_side=2)
+    o = O.Oracle(s)
+    A1 = csr_dense(o.mgr_matrix(1, "A"))
+    lvl1 = s.dof_level[s.dof_level >= 1]
+    F = np.flatnonzero(lvl1 == 1); Cc = np.flatnonzero(lvl1 == 2)
+    AFF = A1[np.ix_(F, F)]
+    assert (np.abs(np.diag(AFF)) == 0).any(), "expected zero diagonals from BHP wells"
+    S = A1[np.ix_(Cc, Cc)] - A1[np.ix_(Cc, F)] @ np.linalg.solve(AFF, A1[np.ix_(F, Cc)])
+    got = csr_dense(o.mgr_matrix(2, "A"))
+    assert np.max(np.abs(got - S)) <= 1e-12 * np.max(np.abs(S))
+
+
+def test_block_jacobi_inverse_blocks():
+    s = make_compositional(4, 4, 2, nwell_side=2)
+    o = O.Oracle(s)
+    d, g = o.mgr_dinv(0)
+    AFF = csr_dense(o.mgr_matrix(0, "AFF"))
+    f = 0
+    while f < g.size:
+        k = g[f]
+        inv = np.linalg.inv(AFF[f:f + k, f:f + k])
+        assert np.allclose(d[f:f + k, :k], inv, rtol=1e-12, atol=1e-14 * np.abs(inv).max())
+        f += k
+
+
+# ------------------------------------------------ MGR as a direct solver
+def test_two_level_mgr_is_direct_solver():
+    """Exact F solve (diagonal A_FF, one Jacobi sweep) + exact coarse solve
+    (dense LU) make the V-cycle equal A^{-1} (LDU of Eq. 2), so FGMRES
+    converges in one iteration."""
+    s = make_mimetic(4, 4, 4)
+    assert (s.dof_level == 1).sum() <= 256
+    o = O.Oracle(s)
+    assert o.amg_nlevels == 1
+    A = dense_of(s)
+    v = np.random.default_rng(0).standard_normal(s.n)
+    z = o.apply(v)
+    ref = np.linalg.solve(A, v)
+    assert np.linalg.norm(z - ref) <= 1e-10 * np.linalg.norm(ref)
+    r = o.solve(s.rhs, rtol=1e-12)
+    assert r["status"] == 0 and r["iters"] == 1 and r["relres"] <= 1e-12
+
+
+def test_extra_sweeps_on_diagonal_F_level_change_nothing():
+    """A diagonal F block is solved exactly by one Jacobi sweep (Sec. 4.2,
+    the rho_2 level); further sweeps leave z unchanged."""
+    s = make_mimetic(4, 3, 3)
+    v = np.random.default_rng(1).standard_normal(s.n)
+    z1 = O.Oracle(s, O.Options(relax=["jacobi"], sweeps=[1])).apply(v)
+    z3 = O.Oracle(s, O.Options(relax=["jacobi"], sweeps=[3])).apply(v)
+    assert np.max(np.abs(z1 - z3)) <= 1e-13 * np.max(np.abs(z1))
+
+
+# ----------------------------------------------------------- FGMRES
+def _ls_residual(A, r0, basis):
+    Q, _ = np.linalg.qr(basis)
+    y, *_ = np.linalg.lstsq(A @ Q, r0, rcond=None)
+    return np.linalg.norm(r0 - A @ Q @ y)
+
+
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_fgmres_minimises_residual_over_krylov_space(k):
+    """Unpreconditioned: x_k minimises ||b - A x|| over x0 + K_k(A, r0)."""
+    rng = np.random.default_rng(k)
+    s = make_two_phase(4, 3, 2)
+    A = dense_of(s)
+    o = O.Oracle(s)
+    b = rng.standard_normal(s.n)
+    r = o.solve(b, rtol=1e-30, maxit=k, precond=False)
+    basis = np.stack([np.linalg.matrix_power(A, t) @ b for t in range(k)], 1)
+    best = _ls_residual(A, b, basis)
+    got = np.linalg.norm(b - A @ r["x"])
+    assert abs(got - best) <= 1e-9 * np.linalg.norm(b)
+
+
+def test_right_preconditioned_fgmres_minimises_over_preconditioned_space():
+    """With the fixed MGR preconditioner M, x_k minimises the residual over
+    span{M^{-1} r0, M^{-1}(A M^{-1}) r0, ...} (right preconditioning)."""
+    s = make_two_phase(6, 5, 2)
+    A = dense_of(s)
+    o = O.Oracle(s)
+    Minv = np.stack([o.apply(e) for e in np.eye(s.n)], 1)
+    b = s.rhs
+    k = 4
+    r = o.solve(b, rtol=1e-30, maxit=k)
+    AM = A @ Minv
+    basis = np.stack([Minv @ np.linalg.matrix_power(AM, t) @ b for t in range(k)], 1)
+    best = _ls_residual(A, b, basis)
+    assert abs(np.linalg.norm(b - A @ r["x"]) - best) <= 1e-9 * np.linalg.norm(b)
+
+
+def test_fgmres_restart_converges_true_residual():
+    s = make_two_phase(8, 8, 4)
+    o = O.Oracle(s)
+    r = o.solve(s.rhs, rtol=1e-10, restart=3, maxit=200)
+    A = dense_of(s)
+    assert r["status"] == 0
+    assert np.linalg.norm(s.rhs - A @ r["x"]) <= 1e-10 * np.linalg.norm(s.rhs)
+
+
+# ---------------------------------------------------------------- AMG
+def poisson(nx, ny=1, nz=1, periodic=False):
+    n = nx * ny * nz
+    idx = np.arange(n).reshape(nz, ny, nx)
+    rows, cols, vals = [], [], []
+    dims = [(nx, 2), (ny, 1), (nz, 0)]
+    for size, ax in dims:
+        if size == 1:
+            continue
+        a = idx; b = np.roll(idx, -1, axis=ax)
+        if not periodic:
+            sl = [slice(None)] * 3; sl[ax] = slice(0, size - 1)
+            a = a[tuple(sl)]; b = b[tuple(sl)]
+        a = a.ravel(); b = b.ravel()
+        rows += [a, b, a, b]; cols += [b, a, a, b]
+        vals += [-np.ones(a.size), -np.ones(a.size), np.ones(a.size), np.ones(a.size)]
+    rows = np.concatenate(rows); cols = np.concatenate(cols); vals = np.concatenate(vals)
+    if not periodic:  # Dirichlet: add the missing neighbours to the diagonal
+        deg = 2 * sum(1 for s_, _ in dims if s_ > 1)
+        cnt = np.bincount(rows[rows != cols], minlength=n)
+        rows = np.concatenate([rows, np.arange(n)]); cols = np.concatenate([cols, np.arange(n)])
+        vals = np.concatenate([vals, (deg - cnt).astype(float)])
+    from paper_2101_11649_gb300.synth.bsr import assemble_bsr
+    rp, ci, v = assemble_bsr(n, 1, rows, cols, vals)
+    return rp, ci, v.ravel()
+
+
+def test_splitmix64_published_vectors():
+    g = json.load(open(os.path.join(GOLDEN, "splitmix64.json")))
+    outs = [int(h, 16) for h in g["outputs_seed0"]]
+    gamma = int(g["golden_gamma"], 16)
+    # output 1: state gamma  <- i = 0, level = 0
+    assert O.pmis_u01(0, 0) == (outs[0] >> 11) * 2.0 ** -53
+    # output 2: state 2*gamma = gamma + gamma -> i + 2^32 level = gamma
+    assert O.pmis_u01(gamma & 0xFFFFFFFF, gamma >> 32) == (outs[1] >> 11) * 2.0 ** -53
+
+
+def test_strength_hand_example():
+    # row 0: a00 = 4, a01 = -1, a02 = -0.2 (0.2 < 0.25 * 1: weak), a03 = +3 (positive: weak)
+    rp = np.array([0, 4, 5, 6, 7]); ci = np.array([0, 1, 2, 3, 1, 2, 3])
+    v = np.array([4.0, -1.0, -0.2, 3.0, 1.0, 1.0, 1.0])
+    srp, sci = O.amg_strength(rp, ci, v)
+    assert list(sci[srp[0]:srp[1]]) == [1]
+    # negative diagonal flips the sign test
+    v2 = v.copy(); v2[0] = -4.0
+    srp, sci = O.amg_strength(rp, ci, v2)
+    assert list(sci[srp[0]:srp[1]]) == [3]
+
+
+def _strength_sets(rp, ci, v):
+    srp, sci = O.amg_strength(rp, ci, v)
+    n = rp.size - 1
+    S = [set(sci[srp[i]:srp[i + 1]]) for i in range(n)]
+    ST = [set() for _ in range(n)]
+    for i in range(n):
+        for j in S[i]:
+            ST[j].add(i)
+    return S, ST
+
+
+@pytest.mark.parametrize("shape", [(30, 1, 1), (12, 11, 1), (7, 6, 5)])
+def test_pmis_independent_and_covering(shape):
+    rp, ci, v = poisson(*shape)
+    cf, P = O.amg_split_interp(rp, ci, v)
+    S, ST = _strength_sets(rp, ci, v)
+    C = set(np.flatnonzero(cf == 1))
+    for i in C:  # independence in the symmetrised strength graph
+        assert not (S[i] | ST[i]) & C
+    for i in np.flatnonzero(cf == -1):  # every F point either influences nobody or depends on a C point
+        assert len(ST[i]) == 0 or (S[i] & C)
+    assert set(np.unique(cf)) <= {-1, 1}
+
+
+def test_extpi_reproduces_constants_zero_row_sum():
+    """Extended+i interpolates constants exactly when rows sum to zero (De
+    Sterck et al. 2008), with truncation rescaled to keep row sums."""
+    for shape in ((9, 8, 1), (6, 5, 4)):
+        rp, ci, v = poisson(*shape, periodic=True)
+        for pmax in (0, 4):
+            cf, P = O.amg_split_interp(rp, ci, v, pmax=pmax)
+            Pd = csr_dense(P)
+            rows = np.flatnonzero(np.diff(P[0]) > 0)
+            assert np.max(np.abs(Pd[rows].sum(1) - 1.0)) < 1e-13
+            # C rows are identity rows
+            for i in np.flatnonzero(cf == 1):
+                nz = np.flatnonzero(Pd[i]); assert nz.size == 1 and Pd[i, nz[0]] == 1.0
+
+
+def test_extpi_linear_in_1d():
+    """1D Laplacian: each F point interpolates linearly between its nearest C
+    points on both sides (weights 1/2, or 2/3 and 1/3 across an F-F pair)."""
+    g = json.load(open(os.path.join(GOLDEN, "extpi_1d_laplacian.json")))
+    rp, ci, v = poisson(40)
+    cf, P = O.amg_split_interp(rp, ci, v, pmax=0)
+    Pd = csr_dense(P)
+    cpts = np.flatnonzero(cf == 1)
+    x = np.arange(40.0)
+    for i in np.flatnonzero(cf == -1):
+        if i < cpts[0] or i > cpts[-1]:
+            continue
+        assert abs(Pd[i] @ x[cpts] - x[i]) < 1e-13
+        left, right = cpts[cpts < i][-1], cpts[cpts > i][0]
+        if right - left == 2:
+            assert np.allclose(Pd[i][Pd[i] != 0], g["weight"])
+
+
+def test_galerkin_product_matches_dense():
+    s = make_two_phase(8, 6, 3)
+    o = O.Oracle(s)
+    for k in range(o.amg_nlevels - 1):
+        A = csr_dense(o.amg_matrix(k, "A")); P = csr_dense(o.amg_matrix(k, "P"))
+        Ac = csr_dense(o.amg_matrix(k + 1, "A"))
+        ref = P.T @ A @ P
+        assert np.max(np.abs(Ac - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_amg_vcycle_convergence_factor_poisson():
+    """Sanity (not exact): AMG V(1,1) with l1-Jacobi on the 7-point Poisson
+    problem contracts the residual by < 0.3 per cycle inside GMRES terms."""
+    from paper_2101_11649_gb300.synth.bsr import BlockSystem
+    rp, ci, v = poisson(14, 13, 12)
+    n = rp.size - 1
+    s = BlockSystem("poisson", 1, rp, ci, v.reshape(-1, 1, 1), np.zeros(n, np.int8), 0,
+                    np.random.default_rng(0).standard_normal(n))
+    o = O.Oracle(s, O.Options(relax=[]))
+    r = o.solve(s.rhs, rtol=1e-8, maxit=100)
+    assert r["status"] == 0
+    rate = (r["relres"]) ** (1.0 / r["iters"])
+    assert rate < 0.3, rate
+
+
+# ------------------------------------------------- transposed cycle (adjoint)
+@pytest.mark.parametrize("make,opts", [
+    (lambda: make_two_phase(6, 5, 3), None),
+    (lambda: make_two_phase(6, 5, 3), O.Options(relax=["l1_jacobi"], sweeps=[3], weights=[0.8])),
+    (lambda: make_compositional(8, 8, 2, nwell_side=2), None),
+    (lambda: make_compositional(8, 8, 2, nwell_side=2),
+     O.Options(relax=["block_jacobi", "block_jacobi"], sweeps=[2, 1])),
+    (lambda: make_poromech(6, 4), None),
+])
+def test_transpose_cycle_is_adjoint(make, opts):
+    s = make()
+    o = O.Oracle(s, opts) if opts else O.Oracle(s)
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal(s.n); v = rng.standard_normal(s.n)
+    lhs = u @ o.apply(v)
+    rhs = o.apply_transpose(u) @ v
+    assert abs(lhs - rhs) <= 1e-11 * (np.abs(u) @ np.abs(o.apply(v)) + 1e-300)
+
+
+def test_transpose_solve_and_gradient_match_dense():
+    """A^T lambda = g solved with the transposed cycle; dL/dA_ij = -lambda_i x_j."""
+    s = make_two_phase(5, 4, 2)
+    A = dense_of(s)
+    o = O.Oracle(s)
+    g = np.random.default_rng(2).standard_normal(s.n)
+    r = o.solve(g, rtol=1e-13, trans=True)
+    lam = np.linalg.solve(A.T, g)
+    assert r["status"] == 0
+    assert np.linalg.norm(r["x"] - lam) <= 1e-10 * np.linalg.norm(lam)
+
+
+# ------------------------------------------------- configs, qualitative
+def test_iteration_counts_mesh_independent_two_phase():
+    """Mesh-independent iteration counts (Sec. 5.2, 5.4): a qualitative pin."""
+    its = [O.Oracle(s).solve(s.rhs, rtol=1e-8)["iters"]
+           for s in (make_two_phase(8, 8, 4), make_two_phase(16, 16, 8), make_two_phase(24, 24, 12))]
+    assert max(its) - min(its) <= 4, its
+
+
+def test_compositional_and_poromech_small_converge():
+    for s in (make_compositional(16, 16, 4), make_poromech(8, 4)):
+        r = O.Oracle(s).solve(s.rhs, rtol=1e-8)
+        assert r["status"] == 0 and r["relres"] <= 1e-8
