@@ -1,0 +1,190 @@
+/*
+ * mgr_gb300.h -- C ABI of the GB300 (sm_103a) multigrid-reduction solver.
+ *
+ * The library solves the block linear systems A x = b of Eq. 1 (arXiv
+ * 2101.11649, Sec. 1) with flexible GMRES(m), right-preconditioned by one
+ * multilevel MGR V-cycle (Algorithm 1, Sec. 3) whose final coarse block is
+ * solved by one algebraic-multigrid V(1,1) cycle (Sec. 5.1).  Every step of
+ * setup and solve runs in CUDA kernels on one GPU.
+ *
+ * Conventions shared by all entry points:
+ *   - Pointers named "device" are CUDA device (or managed) addresses on the
+ *     handle's device; "host" pointers are ordinary host memory.
+ *   - Vectors are FP64, length n = nb * b, in the caller's dof order.
+ *   - All work is enqueued on the handle's stream; entry points that return
+ *     scalars (solve statistics) synchronise that stream before returning.
+ *   - No entry point throws or aborts.  Each returns an mgr_status; the
+ *     message of the last failure is available from mgr_last_error().
+ *   - The caller keeps ownership of everything it passes in.  The handle
+ *     owns its copies of the matrix and the whole hierarchy until mgr_free.
+ */
+#ifndef MGR_GB300_H
+#define MGR_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MGR_OK = 0,
+    MGR_ERR_INVALID = 1,       /* malformed input (sizes, pattern, labels, NaN) */
+    MGR_ERR_NOMEM = 2,         /* device allocation failed */
+    MGR_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    MGR_ERR_SINGULAR = 4,      /* a zero pivot in D_FF, a block inverse or the coarsest solve */
+    MGR_ERR_NOT_CONVERGED = 5, /* maxit reached; x holds the last iterate */
+    MGR_ERR_TIMEOUT = 6,       /* a bounded device wait ran out */
+    MGR_ERR_UNSUPPORTED = 7    /* valid request outside what this build supports */
+} mgr_status;
+
+typedef struct mgr_ctx *mgr_handle;
+
+/*
+ * Square block-CSR matrix (the block system of Eq. 1).  b in 1..4; block
+ * row I holds blocks row_ptr[I]..row_ptr[I+1]-1 with strictly ascending
+ * col_idx; each block is b*b FP64 values, row-major; every block row must
+ * contain its diagonal block.  on_device != 0 means the three arrays are
+ * device pointers, else host pointers.  They are copied by mgr_setup.
+ */
+typedef struct {
+    int32_t nb, b;
+    int64_t nnzb;
+    const int32_t *row_ptr, *col_idx;
+    const double *val;
+    int32_t on_device;
+} mgr_bsr;
+
+/*
+ * MGR C/F labels (the physics-based reduction order of Sec. 3-4).
+ * dof_level[i] (host, int8, length n) is the level at which scalar dof i is
+ * an F-point (0..num_levels-1); num_levels means that dof survives to the
+ * final coarse block solved by AMG.  Level l's F set is {dof_level == l}
+ * and its C set is {dof_level > l}, both in ascending dof order; the coarse
+ * numbering follows ascending dof order.
+ */
+typedef struct {
+    int32_t num_levels;
+    const int8_t *dof_level;
+} mgr_labels;
+
+enum { MGR_RELAX_JACOBI = 0, MGR_RELAX_L1_JACOBI = 1, MGR_RELAX_BLOCK_JACOBI = 2 };
+enum { MGR_PREC_FP64 = 0, MGR_PREC_FP32 = 1 };
+#define MGR_MAX_LEVELS 8
+
+/*
+ * Options.  Per MGR level l: F-relaxation type (D_FF of Eq. 4 is the same
+ * matrix: its diagonal, its l1-row-scaled diagonal, or its per-block-row
+ * F-by-F blocks), number of sweeps (from z = 0) and weight omega.
+ * AMG: strength threshold theta, level and coarse-size limits, max
+ * interpolation entries per row (0 = no truncation), number of functions
+ * of the unknown approach (function of a coarse-block dof = its index mod
+ * num_functions).  precision selects FP64 or FP32 storage and arithmetic of
+ * the whole V-cycle (FGMRES, residuals and the coarsest dense solve stay
+ * FP64).  restart = FGMRES m.  use_graphs != 0 replays the per-iteration
+ * kernel sequence from captured CUDA graphs.
+ */
+typedef struct {
+    int32_t relax_type[MGR_MAX_LEVELS];
+    int32_t relax_sweeps[MGR_MAX_LEVELS];
+    double relax_weight[MGR_MAX_LEVELS];
+    double amg_theta;
+    int32_t amg_max_levels, amg_max_coarse, amg_pmax, amg_num_functions;
+    int32_t precision;
+    int32_t restart;
+    int32_t use_graphs;
+} mgr_options;
+
+/* Solve report.  level_rows/level_nnz list the MGR levels, then the AMG levels. */
+typedef struct {
+    int32_t iterations;        /* preconditioner applications */
+    double rel_residual;       /* true ||b - A x|| / ||b|| at exit */
+    double setup_ms, solve_ms;
+    int32_t mgr_levels, amg_levels;
+    int64_t level_rows[40], level_nnz[40];
+    double operator_complexity;
+} mgr_solve_info;
+
+/* Defaults: Jacobi, 1 sweep, omega 1 on every level; theta 0.25, 25 AMG
+ * levels, coarsest <= 256 rows, P_max 4, 1 function; FP64; m = 30; graphs on. */
+void mgr_options_default(mgr_options *opt);
+
+/*
+ * Build the MGR hierarchy (Sec. 3): per level, the F/C split, D_FF^{-1},
+ * W = -D_FF^{-1} A_FC and the coarse operator A_{l+1} = A_CC + A_CF W (the
+ * product R~ A P~ of Eq. 4 operators); then the AMG hierarchy of the final
+ * block (strength, PMIS, extended+i, Galerkin P^T A P, dense inverse of the
+ * coarsest grid).  stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: INVALID (pattern/labels/sizes, an empty F or C set), SINGULAR
+ * (a zero diagonal or singular block in D_FF), NOMEM, CUDA.
+ */
+mgr_status mgr_setup(const mgr_bsr *A, const mgr_labels *cf, const mgr_options *opt,
+                     void *stream, mgr_handle *out);
+
+/* z = M^{-1} v: one MGR V-cycle (Algorithm 1 without global relaxation). device v, z. */
+mgr_status mgr_apply(mgr_handle h, const double *v, double *z);
+
+/* z = M^{-T} v: the exact transpose of mgr_apply's operator. device v, z. */
+mgr_status mgr_apply_transpose(mgr_handle h, const double *v, double *z);
+
+/* y = A x with the handle's copy of A (device x, y). */
+mgr_status mgr_spmv(mgr_handle h, const double *x, double *y);
+
+/*
+ * Right-preconditioned flexible GMRES(m) (Sec. 5.1) on A x = b from the x
+ * given (device b, x).  Stops when the true residual ||b - A x||_2 <=
+ * rtol ||b||_2 (NOT_CONVERGED after maxit preconditioner applications, with
+ * x the last iterate).  info may be NULL.
+ */
+mgr_status mgr_solve(mgr_handle h, const double *b, double *x, double rtol, int32_t maxit,
+                     mgr_solve_info *info);
+
+/* The same on A^T lambda = g with the transposed cycle (adjoint solve). */
+mgr_status mgr_solve_transpose(mgr_handle h, const double *g, double *lam, double rtol,
+                               int32_t maxit, mgr_solve_info *info);
+
+/* dA_val[p*b*b + r*b + c] = -lam[I*b + r] * x[J*b + c] for block p = (I, J):
+ * the gradient of a scalar loss with respect to the stored values of A when
+ * lam solves A^T lam = dL/dx.  device pointers. */
+mgr_status mgr_grad_values(mgr_handle h, const double *lam, const double *x, double *dA_val);
+
+/*
+ * Standalone block-CSR product y = alpha A x + beta y on device arrays
+ * (b in 1..4) without a handle.  stream as in mgr_setup.
+ */
+mgr_status mgr_bsr_spmv(int32_t nb, int32_t b, const int32_t *row_ptr, const int32_t *col_idx,
+                        const double *val, const double *x, double *y, double alpha, double beta,
+                        void *stream);
+
+/* Release the handle and everything it owns.  NULL is a no-op. */
+void mgr_free(mgr_handle h);
+
+/* Message of the last failure on h (thread-local last failure when h is NULL). */
+const char *mgr_last_error(mgr_handle h);
+
+/* -------------------------------------------------- hierarchy inspection
+ * For parity tests and tooling.  which: 0 = the level matrix; for MGR
+ * levels 1 = A_FF, 2 = A_FC, 3 = A_CF, 4 = W; for AMG levels 1 = P.
+ * amg = 0 selects MGR level `level` (level == mgr levels is the final coarse
+ * block), amg = 1 AMG level `level`.  dims (host int32[3]) receives rows,
+ * cols, nnz; when rp/ci/v (host) are non-NULL they receive the CSR arrays
+ * (rp: rows+1, ci and v: nnz).  INVALID if the matrix does not exist.
+ */
+mgr_status mgr_get_matrix(mgr_handle h, int32_t amg, int32_t level, int32_t which, int32_t *dims,
+                          int32_t *rp, int32_t *ci, double *v);
+
+/* AMG level C/F marks (host int32[rows]: +1 C, -1 F). */
+mgr_status mgr_get_cf(mgr_handle h, int32_t level, int32_t *cf);
+
+/* MGR level D_FF^{-1}: per F point 4 slots (its row of the block inverse)
+ * and its block size (host double[nF*4], int32[nF]). */
+mgr_status mgr_get_dinv(mgr_handle h, int32_t level, double *dinv, int32_t *gsize);
+
+/* Level counts: out[0] = MGR levels, out[1] = AMG levels, out[2] = n. */
+mgr_status mgr_get_info(mgr_handle h, int32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGR_GB300_H */

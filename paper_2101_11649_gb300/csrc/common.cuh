@@ -1,0 +1,145 @@
+// Internal declarations shared by the CUDA translation units of the MGR
+// library.  Nothing here is part of the public C ABI (include/mgr_gb300.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace mgr {
+
+// Scalar CSR on the device.  Columns strictly ascending per row.  v32 is an
+// optional FP32 copy of the values (FP32 V-cycle).
+struct DCSR {
+    int n = 0, m = 0;
+    int nnz = 0;
+    int *rp = nullptr, *ci = nullptr;
+    double *v = nullptr;
+    float *v32 = nullptr;
+};
+
+// Status codes mirror mgr_status.
+enum { ST_OK = 0, ST_INVALID = 1, ST_NOMEM = 2, ST_CUDA = 3, ST_SINGULAR = 4,
+       ST_NOT_CONVERGED = 5, ST_TIMEOUT = 6, ST_UNSUPPORTED = 7 };
+
+// Device error word bits written by setup kernels.
+enum { ERRW_SINGULAR = 1, ERRW_INVALID = 2, ERRW_OVERFLOW = 4 };
+
+// Simple device allocator that remembers what it handed out.
+struct Arena {
+    std::vector<void *> blocks;
+    size_t bytes = 0;
+    int status = ST_OK;
+    void *get(size_t nbytes);
+    template <class T> T *alloc(size_t count) { return (T *)get(count * sizeof(T)); }
+    void release(void *p);
+    void free_all();
+};
+
+// ------------------------------------------------------------- utilities
+int scan_exclusive(const int *in, int *out, int n, cudaStream_t s, Arena &ar, int *total);
+int scan_exclusive_ll(const int *in, long long *out, int n, cudaStream_t s, Arena &ar,
+                      long long *total);
+
+// ------------------------------------------------------------- setup (bit-exact with the CPU reading)
+void launch_bsr_to_csr(int nb, int b, const int *rp, const int *ci, const double *val, DCSR &A,
+                       cudaStream_t s);
+// flags: per local row of level l, 0 = F, 1 = C, 2 = invalid (level < l)
+void launch_level_flags(const int8_t *dof_level_g, const int *gdof, int n, int level, int *isF,
+                        int *isC, int *err, cudaStream_t s);
+void launch_index_maps(const int *isF, const int *isC, const int *fpos_ex, const int *cpos_ex,
+                       int n, int *fidx, int *cidx, int *fmap, int *cmap, cudaStream_t s);
+// Submatrix of A: rows ridx[0..nr), columns remapped through cmap (-1 drops).
+int extract_submatrix(const DCSR &A, const int *ridx, int nr, const int *cmap, int ncols, DCSR &out,
+                      cudaStream_t s, Arena &ar);
+int mgr_dinv(const DCSR &AFF, const int *fidx, const int *gdof, int b, int relax, int *gstart,
+             int *gsize, double *dinv, int *errw, cudaStream_t s);
+int mgr_build_w(const DCSR &AFC, const int *gstart, const int *gsize, const double *dinv, DCSR &W,
+                cudaStream_t s, Arena &ar);
+// C = A*B (+E added last), accumulation order of the CPU reading.
+int spgemm(const DCSR &A, const DCSR &B, const DCSR *E, DCSR &C, cudaStream_t s, Arena &ar);
+int transpose(const DCSR &A, DCSR &T, cudaStream_t s, Arena &ar);
+int amg_strength(const DCSR &A, const int *func, double theta, uint8_t *sflag, DCSR &S,
+                 cudaStream_t s, Arena &ar);
+int amg_pmis(const DCSR &S, const DCSR &ST, int level, int *cf, cudaStream_t s, Arena &ar);
+int amg_extpi(const DCSR &A, const uint8_t *sflag, const int *cf, const int *func, int pmax,
+              DCSR &P, int *nc, cudaStream_t s, Arena &ar);
+int l1_inverse(const DCSR &A, double *dinv, float *dinv32, int *errw, cudaStream_t s);
+void launch_coarse_func(const int *cf, const int *func, const DCSR &P, int *cfunc, int n,
+                        cudaStream_t s);
+void launch_iota_mod(int *func, int n, int nf, cudaStream_t s);
+int dense_inverse(const DCSR &A, double *inv, int *errw, cudaStream_t s, Arena &ar);
+void launch_cast_f32(const double *in, float *out, long long n, cudaStream_t s);
+
+// ------------------------------------------------------------- solve phase
+// BSR y = alpha A x + beta y (b in 1..4) on FP64
+void launch_bsr_spmv(int nb, int b, const int *rp, const int *ci, const double *val,
+                     const double *x, double *y, double alpha, double beta, cudaStream_t s);
+// y = bvec - A x  (residual) or y = A x when bvec == nullptr
+void launch_bsr_residual(int nb, int b, const int *rp, const int *ci, const double *val,
+                         const double *x, const double *bvec, double *y, cudaStream_t s);
+
+// MGR level kernels, T = value/arith type, TV = type of the level's in/out vectors
+template <class T, class TV>
+void launch_frelax_first(int nF, const int *fidx, const int *gstart, const int *gsize,
+                         const T *dinv, T omega, const TV *v, T *zF, cudaStream_t s);
+template <class T, class TV>
+void launch_frelax_residual(const DCSR &AFF, const T *vals, const int *fidx, const TV *v,
+                            const T *zF, T *rF, cudaStream_t s);
+template <class T>
+void launch_frelax_update(int nF, const int *gstart, const int *gsize, const T *dinv, T omega,
+                          const T *rF, T *zF, int transpose, cudaStream_t s);
+template <class T, class TV>
+void launch_mgr_restrict(const DCSR &ACF, const T *vals, const int *cidx, const TV *v,
+                         const T *zF, T *vC, cudaStream_t s);
+template <class T, class TV>
+void launch_mgr_interp(const DCSR &W, const T *wvals, int nC, const int *fidx, const int *cidx,
+                       const T *zF, const T *eC, TV *z, cudaStream_t s);
+// transposed-cycle pieces
+template <class T, class TV>
+void launch_gather(const int *idx, int n, const TV *v, T *out, cudaStream_t s);
+template <class T, class TV>
+void launch_csr_axpy_gather(const DCSR &M, const T *vals, const T *x, const int *idx_b,
+                            const TV *bsrc, T sign, T *y, cudaStream_t s);
+template <class T, class TV>
+void launch_scatter2(int nF, int nC, const int *fidx, const int *cidx, const T *zF, const T *eC,
+                     TV *z, cudaStream_t s);
+
+// AMG level kernels
+template <class T, class TV>
+void launch_amg_smooth0_residual(const DCSR &A, const T *vals, const T *dinv, const TV *r, T *x,
+                                 T *res, cudaStream_t s);
+template <class T>
+void launch_csr_spmv(const DCSR &A, const T *vals, const T *x, T *y, cudaStream_t s);
+template <class T>
+void launch_csr_spmv_add(const DCSR &A, const T *vals, const T *x, T *y, cudaStream_t s);
+template <class T, class TV>
+void launch_amg_post_smooth(const DCSR &A, const T *vals, const T *dinv, const TV *r, const T *x,
+                            TV *xout, cudaStream_t s);
+template <class TV>
+void launch_dense_matvec(int n, const double *inv, const TV *r, TV *x, cudaStream_t s);
+template <class TV>
+void launch_copy_cast(const TV *in, double *out, int n, cudaStream_t s);
+
+// Krylov pieces (FP64)
+struct Krylov;
+void launch_vec_scale(const double *x, double *y, const double *scale_num, const double *scale_den,
+                      int invert, int n, cudaStream_t s);
+void launch_dot_partial(const double *x, const double *y, int n, double *partial, int nblk,
+                        cudaStream_t s);
+void launch_finalize_sum(const double *partial, int nblk, int nvec, double *out, int sqrt_out,
+                         cudaStream_t s);
+void launch_multidot(const double *V, long long ldv, int k, const double *w, int n,
+                     double *partial, int nblk, cudaStream_t s);
+void launch_update_dot(const double *V, long long ldv, int k, const double *h, double *w, int n,
+                       double *partial, int nblk, int mode, cudaStream_t s);
+void launch_multi_axpy(const double *Z, long long ldz, int k, const double *y, double *x, int n,
+                       cudaStream_t s);
+int multidot_blocks(int n);
+
+void launch_grad_values(int nb, int b, const int *rp, const int *ci, const double *lam,
+                        const double *x, double *dA, cudaStream_t s);
+
+}  // namespace mgr

@@ -1,0 +1,1101 @@
+// Setup-phase kernels of the MGR hierarchy and its AMG coarse solver.
+//
+// Compiled with --fmad=false: every product and sum is rounded separately,
+// and each loop below accumulates in the order stated in its comment, so
+// that the hierarchy is reproducible bit for bit (a reading: the paper
+// fixes no summation order).  Work is spread one thread per row; setup is
+// not on the timed path.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mgr {
+
+#define GRID(n, t) (unsigned)(((long long)(n) + (t)-1) / (t) > 0 ? ((long long)(n) + (t)-1) / (t) : 1)
+
+// ------------------------------------------------------------------ arena
+void *Arena::get(size_t nbytes) {
+    if (nbytes == 0) nbytes = 16;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        status = ST_NOMEM;
+        return nullptr;
+    }
+    blocks.push_back(p);
+    bytes += nbytes;
+    return p;
+}
+
+void Arena::release(void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < blocks.size(); i++)
+        if (blocks[i] == p) {
+            cudaFree(p);
+            blocks[i] = blocks.back();
+            blocks.pop_back();
+            return;
+        }
+}
+
+void Arena::free_all() {
+    for (void *p : blocks) cudaFree(p);
+    blocks.clear();
+    bytes = 0;
+}
+
+// ------------------------------------------------------------------ scan
+template <class T>
+__global__ void k_block_sums(const int *in, int n, T *sums, int per_block) {
+    __shared__ T sh[32];
+    long long base = (long long)blockIdx.x * per_block;
+    T s = 0;
+    for (int t = threadIdx.x; t < per_block; t += blockDim.x) {
+        long long i = base + t;
+        if (i < n) s += (T)in[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffff, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        T v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : (T)0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
+        if (threadIdx.x == 0) sums[blockIdx.x] = v;
+    }
+}
+
+// single block: exclusive scan of sums in place, total to sums[nb]
+template <class T>
+__global__ void k_scan_sums(T *sums, int nb) {
+    __shared__ T carry;
+    __shared__ T warp_tot[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        T v = i < nb ? sums[i] : (T)0;
+        T x = v;
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffff, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            T t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : (T)0;
+            for (int o = 1; o < 32; o <<= 1) {
+                T y = __shfl_up_sync(0xffffffff, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        T incl = x + (w > 0 ? warp_tot[w - 1] : (T)0) + carry;
+        if (i < nb) sums[i] = incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+template <class T>
+__global__ void k_scan_blocks(const int *in, int n, const T *sums, T *out, int per_block) {
+    __shared__ T warp_tot[32];
+    __shared__ T carry;
+    long long base = (long long)blockIdx.x * per_block;
+    if (threadIdx.x == 0) carry = sums[blockIdx.x];
+    __syncthreads();
+    for (int off = 0; off < per_block; off += blockDim.x) {
+        long long i = base + off + threadIdx.x;
+        T v = i < n ? (T)in[i] : (T)0;
+        T x = v;
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffff, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            T t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : (T)0;
+            for (int o = 1; o < 32; o <<= 1) {
+                T y = __shfl_up_sync(0xffffffff, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        T incl = x + (w > 0 ? warp_tot[w - 1] : (T)0) + carry;
+        if (i < n) out[i] = incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = incl;
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void k_set_total(T *out, int n, const T *sums, int nb) { out[n] = sums[nb]; }
+
+template <class T>
+static int scan_impl(const int *in, T *out, int n, cudaStream_t s, Arena &ar, T *total) {
+    const int per = 4096, thr = 512;
+    int nb = (n + per - 1) / per;
+    if (nb < 1) nb = 1;
+    T *sums = ar.alloc<T>(nb + 1);
+    if (!sums) return ST_NOMEM;
+    k_block_sums<T><<<nb, thr, 0, s>>>(in, n, sums, per);
+    k_scan_sums<T><<<1, 1024, 0, s>>>(sums, nb);
+    k_scan_blocks<T><<<nb, thr, 0, s>>>(in, n, sums, out, per);
+    k_set_total<T><<<1, 1, 0, s>>>(out, n, sums, nb);
+    if (total) {
+        cudaMemcpyAsync(total, out + n, sizeof(T), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+    }
+    ar.release(sums);
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+// out has n+1 entries; out[n] = total
+int scan_exclusive(const int *in, int *out, int n, cudaStream_t s, Arena &ar, int *total) {
+    return scan_impl<int>(in, out, n, s, ar, total);
+}
+int scan_exclusive_ll(const int *in, long long *out, int n, cudaStream_t s, Arena &ar,
+                      long long *total) {
+    return scan_impl<long long>(in, out, n, s, ar, total);
+}
+
+// ------------------------------------------------------------- BSR -> CSR
+// Scalar row I*b+r: blocks of row I in ascending J, entries (r, 0..b-1).
+__global__ void k_bsr_to_csr(int nb, int b, const int *rp, const int *ci, const double *val,
+                             int *crp, int *cci, double *cv) {
+    long long nrows = (long long)nb * b;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nrows;
+         t += (long long)gridDim.x * blockDim.x) {
+        int I = (int)(t / b), r = (int)(t % b);
+        int p0 = rp[I], p1 = rp[I + 1];
+        long long base = (long long)p0 * b * b + (long long)r * (p1 - p0) * b;
+        crp[t] = (int)base;
+        for (int p = p0; p < p1; p++)
+            for (int c = 0; c < b; c++) {
+                long long q = base + (long long)(p - p0) * b + c;
+                cci[q] = ci[p] * b + c;
+                cv[q] = val[((long long)p * b + r) * b + c];
+            }
+        if (t == 0) crp[nrows] = (int)((long long)rp[nb] * b * b);
+    }
+}
+
+void launch_bsr_to_csr(int nb, int b, const int *rp, const int *ci, const double *val, DCSR &A,
+                       cudaStream_t s) {
+    long long n = (long long)nb * b;
+    k_bsr_to_csr<<<GRID(n, 256), 256, 0, s>>>(nb, b, rp, ci, val, A.rp, A.ci, A.v);
+}
+
+// --------------------------------------------------------------- level split
+__global__ void k_level_flags(const int8_t *lvl, const int *gdof, int n, int level, int *isF,
+                              int *isC, int *err) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int g = gdof ? gdof[i] : i;
+    int lv = lvl[g];
+    isF[i] = lv == level;
+    isC[i] = lv > level;
+    if (lv < level) atomicOr(err, ERRW_INVALID);
+}
+
+void launch_level_flags(const int8_t *dof_level_g, const int *gdof, int n, int level, int *isF,
+                        int *isC, int *err, cudaStream_t s) {
+    k_level_flags<<<GRID(n, 256), 256, 0, s>>>(dof_level_g, gdof, n, level, isF, isC, err);
+}
+
+__global__ void k_index_maps(const int *isF, const int *isC, const int *fpos, const int *cpos,
+                             int n, int *fidx, int *cidx, int *fmap, int *cmap) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (isF[i]) { fidx[fpos[i]] = i; fmap[i] = fpos[i]; } else fmap[i] = -1;
+    if (isC[i]) { cidx[cpos[i]] = i; cmap[i] = cpos[i]; } else cmap[i] = -1;
+}
+
+void launch_index_maps(const int *isF, const int *isC, const int *fpos_ex, const int *cpos_ex,
+                       int n, int *fidx, int *cidx, int *fmap, int *cmap, cudaStream_t s) {
+    k_index_maps<<<GRID(n, 256), 256, 0, s>>>(isF, isC, fpos_ex, cpos_ex, n, fidx, cidx, fmap, cmap);
+}
+
+// ------------------------------------------------------------ submatrix
+__global__ void k_sub_count(const int *rp, const int *ci, const int *ridx, int nr, const int *cmap,
+                            int *cnt) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    int i = ridx[r], c = 0;
+    for (int p = rp[i]; p < rp[i + 1]; p++) c += cmap[ci[p]] >= 0;
+    cnt[r] = c;
+}
+
+__global__ void k_sub_fill(const int *rp, const int *ci, const double *v, const int *ridx, int nr,
+                           const int *cmap, const int *orp, int *oci, double *ov) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    int i = ridx[r], q = orp[r];
+    for (int p = rp[i]; p < rp[i + 1]; p++) {
+        int c = cmap[ci[p]];
+        if (c >= 0) { oci[q] = c; ov[q] = v[p]; q++; }
+    }
+}
+
+int extract_submatrix(const DCSR &A, const int *ridx, int nr, const int *cmap, int ncols, DCSR &out,
+                      cudaStream_t s, Arena &ar) {
+    out.n = nr; out.m = ncols;
+    out.rp = ar.alloc<int>(nr + 1);
+    int *cnt = ar.alloc<int>(nr + 1);
+    if (!out.rp || !cnt) return ST_NOMEM;
+    k_sub_count<<<GRID(nr, 256), 256, 0, s>>>(A.rp, A.ci, ridx, nr, cmap, cnt);
+    int tot = 0;
+    int rc = scan_exclusive(cnt, out.rp, nr, s, ar, &tot);
+    ar.release(cnt);
+    if (rc) return rc;
+    out.nnz = tot;
+    out.ci = ar.alloc<int>(tot + 1);
+    out.v = ar.alloc<double>(tot + 1);
+    if (!out.ci || !out.v) return ST_NOMEM;
+    k_sub_fill<<<GRID(nr, 256), 256, 0, s>>>(A.rp, A.ci, A.v, ridx, nr, cmap, out.rp, out.ci, out.v);
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+// ------------------------------------------------------------ D_FF^{-1}
+__device__ double csr_get(const int *rp, const int *ci, const double *v, int i, int j) {
+    for (int p = rp[i]; p < rp[i + 1]; p++)
+        if (ci[p] == j) return v[p];
+    return 0.0;
+}
+
+// Gauss-Jordan with partial pivoting (first row of largest |pivot|),
+// singular when |pivot| <= 1e-14 ||B||_inf.  Same operation order as the
+// CPU reading.
+__device__ int block_inverse(int k, const double *B, double *inv) {
+    double m[16], x[16];
+    double nrm = 0.0;
+    for (int r = 0; r < k; r++) {
+        double s = 0.0;
+        for (int c = 0; c < k; c++) s = s + fabs(B[r * k + c]);
+        if (s > nrm) nrm = s;
+    }
+    for (int t = 0; t < k * k; t++) { m[t] = B[t]; x[t] = 0.0; }
+    for (int r = 0; r < k; r++) x[r * k + r] = 1.0;
+    for (int c = 0; c < k; c++) {
+        int p = c;
+        for (int r = c + 1; r < k; r++)
+            if (fabs(m[r * k + c]) > fabs(m[p * k + c])) p = r;
+        if (!(fabs(m[p * k + c]) > 1e-14 * nrm)) return 1;
+        if (p != c)
+            for (int t = 0; t < k; t++) {
+                double s = m[c * k + t]; m[c * k + t] = m[p * k + t]; m[p * k + t] = s;
+                s = x[c * k + t]; x[c * k + t] = x[p * k + t]; x[p * k + t] = s;
+            }
+        double piv = m[c * k + c];
+        for (int t = 0; t < k; t++) { m[c * k + t] = m[c * k + t] / piv; x[c * k + t] = x[c * k + t] / piv; }
+        for (int r = 0; r < k; r++) {
+            if (r == c) continue;
+            double f = m[r * k + c];
+            for (int t = 0; t < k; t++) {
+                m[r * k + t] = m[r * k + t] - f * m[c * k + t];
+                x[r * k + t] = x[r * k + t] - f * x[c * k + t];
+            }
+        }
+    }
+    for (int t = 0; t < k * k; t++) inv[t] = x[t];
+    return 0;
+}
+
+__global__ void k_mgr_dinv(int nF, const int *rp, const int *ci, const double *v, const int *fidx,
+                           const int *gdof, int b, int relax, int *gstart, int *gsize,
+                           double *dinv, int *errw) {
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nF) return;
+    if (relax != 2) {
+        double aii = csr_get(rp, ci, v, f, f);
+        double d = aii;
+        if (relax == 1) {
+            double s = 0.0;
+            for (int p = rp[f]; p < rp[f + 1]; p++)
+                if (ci[p] != f) s = s + fabs(v[p]);
+            d = aii < 0.0 ? aii - s : aii + s;
+        }
+        gstart[f] = f; gsize[f] = 1;
+        if (d == 0.0) { atomicOr(errw, ERRW_SINGULAR); dinv[(long long)f * 4] = 0.0; return; }
+        dinv[(long long)f * 4] = 1.0 / d;
+        dinv[(long long)f * 4 + 1] = dinv[(long long)f * 4 + 2] = dinv[(long long)f * 4 + 3] = 0.0;
+        return;
+    }
+    auto blk = [&](int q) { int g = gdof ? gdof[fidx[q]] : fidx[q]; return g / b; };
+    int my = blk(f);
+    int g0 = f;
+    while (g0 > 0 && f - g0 < 3 && blk(g0 - 1) == my) g0--;
+    int k = 0;
+    while (g0 + k < nF && k < 4 && blk(g0 + k) == my) k++;
+    double B[16], inv[16];
+    for (int r = 0; r < k; r++)
+        for (int c = 0; c < k; c++) B[r * k + c] = csr_get(rp, ci, v, g0 + r, g0 + c);
+    gstart[f] = g0; gsize[f] = k;
+    int rr = f - g0;
+    if (block_inverse(k, B, inv)) {
+        atomicOr(errw, ERRW_SINGULAR);
+        for (int c = 0; c < 4; c++) dinv[(long long)f * 4 + c] = 0.0;
+        return;
+    }
+    for (int c = 0; c < 4; c++) dinv[(long long)f * 4 + c] = c < k ? inv[rr * k + c] : 0.0;
+}
+
+int mgr_dinv(const DCSR &AFF, const int *fidx, const int *gdof, int b, int relax, int *gstart,
+             int *gsize, double *dinv, int *errw, cudaStream_t s) {
+    k_mgr_dinv<<<GRID(AFF.n, 128), 128, 0, s>>>(AFF.n, AFF.rp, AFF.ci, AFF.v, fidx, gdof, b, relax,
+                                                 gstart, gsize, dinv, errw);
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+// --------------------------------------------------------------------- W
+// Row f of W = -D^{-1} A_FC: merge of the A_FC rows of f's block (<= 4
+// sorted lists); at each column, acc = sum over block rows q ascending of
+// dinv[f][q] * a_qj (from +0.0), then W = -acc.
+template <bool FILL>
+__global__ void k_build_w(int nF, const int *rp, const int *ci, const double *v, const int *gstart,
+                          const int *gsize, const double *dinv, int *cnt, const int *wrp, int *wci,
+                          double *wv) {
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nF) return;
+    int g0 = gstart[f], k = gsize[f];
+    int head[4], end[4];
+    for (int q = 0; q < k; q++) { head[q] = rp[g0 + q]; end[q] = rp[g0 + q + 1]; }
+    int c = 0;
+    int out = FILL ? wrp[f] : 0;
+    for (;;) {
+        int j = 0x7fffffff;
+        for (int q = 0; q < k; q++)
+            if (head[q] < end[q] && ci[head[q]] < j) j = ci[head[q]];
+        if (j == 0x7fffffff) break;
+        double acc = 0.0;
+        for (int q = 0; q < k; q++)
+            if (head[q] < end[q] && ci[head[q]] == j) {
+                if (FILL) acc = acc + dinv[(long long)f * 4 + q] * v[head[q]];
+                head[q]++;
+            }
+        if (FILL) { wci[out] = j; wv[out] = -acc; out++; }
+        c++;
+    }
+    if (!FILL) cnt[f] = c;
+}
+
+int mgr_build_w(const DCSR &AFC, const int *gstart, const int *gsize, const double *dinv, DCSR &W,
+                cudaStream_t s, Arena &ar) {
+    int nF = AFC.n;
+    W.n = nF; W.m = AFC.m;
+    W.rp = ar.alloc<int>(nF + 1);
+    int *cnt = ar.alloc<int>(nF + 1);
+    if (!W.rp || !cnt) return ST_NOMEM;
+    k_build_w<false><<<GRID(nF, 128), 128, 0, s>>>(nF, AFC.rp, AFC.ci, AFC.v, gstart, gsize, dinv,
+                                                   cnt, nullptr, nullptr, nullptr);
+    int tot = 0;
+    int rc = scan_exclusive(cnt, W.rp, nF, s, ar, &tot);
+    ar.release(cnt);
+    if (rc) return rc;
+    W.nnz = tot;
+    W.ci = ar.alloc<int>(tot + 1);
+    W.v = ar.alloc<double>(tot + 1);
+    if (!W.ci || !W.v) return ST_NOMEM;
+    k_build_w<true><<<GRID(nF, 128), 128, 0, s>>>(nF, AFC.rp, AFC.ci, AFC.v, gstart, gsize, dinv,
+                                                  nullptr, W.rp, W.ci, W.v);
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+// ---------------------------------------------------------------- SpGEMM
+// Row i of C = A*B (+E): for (i,k) in A ascending k, for (k,j) in B
+// ascending j: acc[j] = acc[j] + a_ik*b_kj (acc = +0.0 on first touch);
+// then acc[j] = acc[j] + e_ij.  One thread per row, private open-addressing
+// table in global scratch; the output row is then sorted by column.
+__global__ void k_spgemm_bound(int n, const int *arp, const int *aci, const int *brp,
+                               const int *erp, int *bound) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long long s = 0;
+    for (int p = arp[i]; p < arp[i + 1]; p++) { int k = aci[p]; s += brp[k + 1] - brp[k]; }
+    if (erp) s += erp[i + 1] - erp[i];
+    // hash capacity: power of two >= 2*bound (>= 8)
+    long long cap = 8;
+    while (cap < 2 * s) cap <<= 1;
+    bound[i] = (int)(cap > 0x40000000LL ? 0x40000000LL : cap);
+}
+
+__device__ __forceinline__ unsigned hash_col(int j) { return (unsigned)j * 2654435761u; }
+
+template <bool NUMERIC>
+__global__ void k_spgemm_row(int r0, int r1, const int *arp, const int *aci, const double *av,
+                             const int *brp, const int *bci, const double *bv, const int *erp,
+                             const int *eci, const double *ev, const long long *capoff,
+                             long long base, int *hkey, double *hval, int *cnt, const int *crp,
+                             int *cci, double *cv, int *errw) {
+    int i = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r1) return;
+    long long off = capoff[i] - base;
+    unsigned cap = (unsigned)(capoff[i + 1] - capoff[i]);
+    int *key = hkey + off;
+    double *val = hval + off;
+    for (unsigned t = 0; t < cap; t++) key[t] = -1;
+    int distinct = 0;
+    auto insert = [&](int j, double prod) {
+        unsigned h = hash_col(j) & (cap - 1);
+        for (unsigned probe = 0; probe < cap; probe++) {
+            int kk = key[h];
+            if (kk == j) { if (NUMERIC) val[h] = val[h] + prod; return; }
+            if (kk < 0) {
+                key[h] = j;
+                if (NUMERIC) { val[h] = 0.0; val[h] = val[h] + prod; }
+                distinct++;
+                return;
+            }
+            h = (h + 1) & (cap - 1);
+        }
+        atomicOr(errw, ERRW_OVERFLOW);  // table full: cannot happen when cap >= 2 * distinct
+    };
+    for (int p = arp[i]; p < arp[i + 1]; p++) {
+        int k = aci[p];
+        double a = NUMERIC ? av[p] : 0.0;
+        for (int q = brp[k]; q < brp[k + 1]; q++) insert(bci[q], NUMERIC ? a * bv[q] : 0.0);
+    }
+    if (erp)
+        for (int q = erp[i]; q < erp[i + 1]; q++) insert(eci[q], NUMERIC ? ev[q] : 0.0);
+    if (!NUMERIC) { cnt[i] = distinct; return; }
+    // gather and sort by column (shell sort, Ciura gaps)
+    int o = crp[i], len = 0;
+    for (unsigned t = 0; t < cap; t++)
+        if (key[t] >= 0) { cci[o + len] = key[t]; cv[o + len] = val[t]; len++; }
+    const int gaps[8] = {701, 301, 132, 57, 23, 10, 4, 1};
+    for (int gi = 0; gi < 8; gi++) {
+        int g = gaps[gi];
+        for (int a = g; a < len; a++) {
+            int kc = cci[o + a];
+            double kv = cv[o + a];
+            int b = a;
+            while (b >= g && cci[o + b - g] > kc) {
+                cci[o + b] = cci[o + b - g]; cv[o + b] = cv[o + b - g];
+                b -= g;
+            }
+            cci[o + b] = kc; cv[o + b] = kv;
+        }
+    }
+}
+
+int spgemm(const DCSR &A, const DCSR &B, const DCSR *E, DCSR &C, cudaStream_t s, Arena &ar) {
+    int n = A.n;
+    C.n = n; C.m = B.m;
+    int *capv = ar.alloc<int>(n + 1);
+    long long *capoff = ar.alloc<long long>(n + 1);
+    int *cnt = ar.alloc<int>(n + 1);
+    C.rp = ar.alloc<int>(n + 1);
+    if (!capv || !capoff || !cnt || !C.rp) return ST_NOMEM;
+    k_spgemm_bound<<<GRID(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, E ? E->rp : nullptr, capv);
+    long long totcap = 0;
+    int rc = scan_exclusive_ll(capv, capoff, n, s, ar, &totcap);
+    if (rc) return rc;
+    std::vector<long long> hoff(n + 1);
+    cudaMemcpyAsync(hoff.data(), capoff, sizeof(long long) * (n + 1), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    const long long budget = 1LL << 26;  // hash slots per chunk
+    long long maxchunk = 0;
+    std::vector<int> cuts{0};
+    while (cuts.back() < n) {
+        int r0 = cuts.back(), r1 = r0 + 1;
+        while (r1 < n && hoff[r1 + 1] - hoff[r0] <= budget) r1++;
+        maxchunk = std::max(maxchunk, hoff[r1] - hoff[r0]);
+        cuts.push_back(r1);
+    }
+    int *errw = ar.alloc<int>(1);
+    if (!errw) return ST_NOMEM;
+    cudaMemsetAsync(errw, 0, sizeof(int), s);
+    int *hkey = ar.alloc<int>(maxchunk + 1);
+    double *hval = ar.alloc<double>(maxchunk + 1);
+    if (!hkey || !hval) return ST_NOMEM;
+    const int *erp = E ? E->rp : nullptr, *eci = E ? E->ci : nullptr;
+    const double *ev = E ? E->v : nullptr;
+    for (size_t c = 0; c + 1 < cuts.size(); c++) {
+        int r0 = cuts[c], r1 = cuts[c + 1];
+        k_spgemm_row<false><<<GRID(r1 - r0, 128), 128, 0, s>>>(
+            r0, r1, A.rp, A.ci, A.v, B.rp, B.ci, B.v, erp, eci, ev, capoff, hoff[r0], hkey, hval,
+            cnt, nullptr, nullptr, nullptr, errw);
+    }
+    int tot = 0;
+    rc = scan_exclusive(cnt, C.rp, n, s, ar, &tot);
+    if (rc) return rc;
+    C.nnz = tot;
+    C.ci = ar.alloc<int>(tot + 1);
+    C.v = ar.alloc<double>(tot + 1);
+    if (!C.ci || !C.v) return ST_NOMEM;
+    for (size_t c = 0; c + 1 < cuts.size(); c++) {
+        int r0 = cuts[c], r1 = cuts[c + 1];
+        k_spgemm_row<true><<<GRID(r1 - r0, 128), 128, 0, s>>>(
+            r0, r1, A.rp, A.ci, A.v, B.rp, B.ci, B.v, erp, eci, ev, capoff, hoff[r0], hkey, hval,
+            cnt, C.rp, C.ci, C.v, errw);
+    }
+    int herr = 0;
+    cudaMemcpyAsync(&herr, errw, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    ar.release(hkey); ar.release(hval); ar.release(capv); ar.release(capoff); ar.release(cnt);
+    ar.release(errw);
+    if (herr) return ST_NOMEM;
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+// -------------------------------------------------------------- transpose
+__global__ void k_col_count(int nnz, const int *ci, int *cnt) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nnz;
+         p += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[ci[p]], 1);
+}
+
+__global__ void k_tr_fill(int n, const int *rp, const int *ci, const double *v, const int *trp,
+                          int *cursor, int *tci, double *tv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rp[i]; p < rp[i + 1]; p++) {
+        int j = ci[p];
+        int q = trp[j] + atomicAdd(&cursor[j], 1);
+        tci[q] = i;
+        if (v) tv[q] = v[p];
+    }
+}
+
+// sort each row by column (source row index); insertion sort (rows are short)
+__global__ void k_row_sort(int n, const int *rp, int *ci, double *v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int o = rp[i], len = rp[i + 1] - o;
+    const int gaps[8] = {701, 301, 132, 57, 23, 10, 4, 1};
+    for (int gi = 0; gi < 8; gi++) {
+        int g = gaps[gi];
+        for (int a = g; a < len; a++) {
+            int kc = ci[o + a];
+            double kv = v ? v[o + a] : 0.0;
+            int b = a;
+            while (b >= g && ci[o + b - g] > kc) {
+                ci[o + b] = ci[o + b - g];
+                if (v) v[o + b] = v[o + b - g];
+                b -= g;
+            }
+            ci[o + b] = kc;
+            if (v) v[o + b] = kv;
+        }
+    }
+}
+
+int transpose(const DCSR &A, DCSR &T, cudaStream_t s, Arena &ar) {
+    T.n = A.m; T.m = A.n; T.nnz = A.nnz;
+    T.rp = ar.alloc<int>(A.m + 1);
+    int *cnt = ar.alloc<int>(A.m + 1);
+    T.ci = ar.alloc<int>(A.nnz + 1);
+    T.v = A.v ? ar.alloc<double>(A.nnz + 1) : nullptr;
+    if (!T.rp || !cnt || !T.ci || (A.v && !T.v)) return ST_NOMEM;
+    cudaMemsetAsync(cnt, 0, sizeof(int) * (A.m + 1), s);
+    k_col_count<<<GRID(A.nnz, 256) > 4096 ? 4096 : GRID(A.nnz, 256), 256, 0, s>>>(A.nnz, A.ci, cnt);
+    int rc = scan_exclusive(cnt, T.rp, A.m, s, ar, nullptr);
+    if (rc) return rc;
+    cudaMemsetAsync(cnt, 0, sizeof(int) * (A.m + 1), s);
+    k_tr_fill<<<GRID(A.n, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, T.rp, cnt, T.ci, T.v);
+    k_row_sort<<<GRID(A.m, 128), 128, 0, s>>>(A.m, T.rp, T.ci, T.v);
+    cudaStreamSynchronize(s);
+    ar.release(cnt);
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+// --------------------------------------------------------------- strength
+// s_i = -1 if a_ii < 0 else +1; m_i = max over off-diagonal same-function j
+// of -s_i a_ij (from 0); j strong iff m_i > 0 and -s_i a_ij >= theta m_i.
+__global__ void k_strength(int n, const int *rp, const int *ci, const double *v, const int *func,
+                           double theta, uint8_t *sflag, int *cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double aii = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; p++)
+        if (ci[p] == i) aii = v[p];
+    bool neg = aii < 0.0;
+    double m = 0.0;
+    int fi = func[i];
+    for (int p = rp[i]; p < rp[i + 1]; p++) {
+        int j = ci[p];
+        if (j == i || func[j] != fi) continue;
+        double val = neg ? v[p] : -v[p];
+        if (val > m) m = val;
+    }
+    int c = 0;
+    double thr = theta * m;
+    for (int p = rp[i]; p < rp[i + 1]; p++) {
+        int j = ci[p];
+        uint8_t st = 0;
+        if (m > 0.0 && j != i && func[j] == fi) {
+            double val = neg ? v[p] : -v[p];
+            st = val >= thr;
+        }
+        sflag[p] = st;
+        c += st;
+    }
+    cnt[i] = c;
+}
+
+__global__ void k_strength_fill(int n, const int *rp, const int *ci, const uint8_t *sflag,
+                                const int *srp, int *sci) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int q = srp[i];
+    for (int p = rp[i]; p < rp[i + 1]; p++)
+        if (sflag[p]) sci[q++] = ci[p];
+}
+
+int amg_strength(const DCSR &A, const int *func, double theta, uint8_t *sflag, DCSR &S,
+                 cudaStream_t s, Arena &ar) {
+    int n = A.n;
+    S.n = S.m = n;
+    S.rp = ar.alloc<int>(n + 1);
+    int *cnt = ar.alloc<int>(n + 1);
+    if (!S.rp || !cnt) return ST_NOMEM;
+    k_strength<<<GRID(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, func, theta, sflag, cnt);
+    int tot = 0;
+    int rc = scan_exclusive(cnt, S.rp, n, s, ar, &tot);
+    ar.release(cnt);
+    if (rc) return rc;
+    S.nnz = tot;
+    S.ci = ar.alloc<int>(tot + 1);
+    S.v = nullptr;
+    if (!S.ci) return ST_NOMEM;
+    k_strength_fill<<<GRID(n, 128), 128, 0, s>>>(n, A.rp, A.ci, sflag, S.rp, S.ci);
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+// ------------------------------------------------------------------- PMIS
+// Weight u(i, level): the SplitMix64 output function (Steele, Lea & Flood
+// 2014) of the state i + 2^32 level, top 53 bits times 2^-53.
+__device__ double pmis_u01(unsigned i, unsigned level) {
+    unsigned long long z = (unsigned long long)i + ((unsigned long long)level << 32);
+    z += 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__global__ void k_pmis_init(int n, const int *strp, int level, double *w, int *cf, int *und) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = strp[i + 1] - strp[i];
+    w[i] = (double)c + pmis_u01((unsigned)i, (unsigned)level);
+    cf[i] = c == 0 ? -1 : 0;
+    if (c) atomicAdd(und, 1);
+}
+
+__global__ void k_pmis_select(int n, const int *srp, const int *sci, const int *strp,
+                              const int *stci, const double *w, const int *cf, int *sel) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int best = 0;
+    if (cf[i] == 0) {
+        best = 1;
+        double wi = w[i];
+        for (int p = srp[i]; p < srp[i + 1] && best; p++) {
+            int j = sci[p];
+            if (cf[j] == 0 && (w[j] > wi || (w[j] == wi && j > i))) best = 0;
+        }
+        for (int p = strp[i]; p < strp[i + 1] && best; p++) {
+            int j = stci[p];
+            if (cf[j] == 0 && (w[j] > wi || (w[j] == wi && j > i))) best = 0;
+        }
+    }
+    sel[i] = best;
+}
+
+__global__ void k_pmis_mark_c(int n, const int *sel, int *cf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && sel[i]) cf[i] = 1;
+}
+
+__global__ void k_pmis_mark_f(int n, const int *srp, const int *sci, int *cf, int *und) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (cf[i] != 0) return;
+    for (int p = srp[i]; p < srp[i + 1]; p++)
+        if (cf[sci[p]] == 1) { cf[i] = -1; return; }
+    atomicAdd(und, 1);
+}
+
+int amg_pmis(const DCSR &S, const DCSR &ST, int level, int *cf, cudaStream_t s, Arena &ar) {
+    int n = S.n;
+    double *w = ar.alloc<double>(n + 1);
+    int *sel = ar.alloc<int>(n + 1);
+    int *und = ar.alloc<int>(1);
+    if (!w || !sel || !und) return ST_NOMEM;
+    cudaMemsetAsync(und, 0, sizeof(int), s);
+    k_pmis_init<<<GRID(n, 256), 256, 0, s>>>(n, ST.rp, level, w, cf, und);
+    int hund = 0;
+    cudaMemcpyAsync(&hund, und, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    int rounds = 0;
+    while (hund > 0 && rounds < 10000) {
+        k_pmis_select<<<GRID(n, 256), 256, 0, s>>>(n, S.rp, S.ci, ST.rp, ST.ci, w, cf, sel);
+        k_pmis_mark_c<<<GRID(n, 256), 256, 0, s>>>(n, sel, cf);
+        cudaMemsetAsync(und, 0, sizeof(int), s);
+        k_pmis_mark_f<<<GRID(n, 256), 256, 0, s>>>(n, S.rp, S.ci, cf, und);
+        cudaMemcpyAsync(&hund, und, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        rounds++;
+    }
+    ar.release(w); ar.release(sel); ar.release(und);
+    if (hund > 0) return ST_TIMEOUT;
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+// -------------------------------------------------------- extended+i
+__device__ __forceinline__ double abar(double akk, double akl) {
+    if (akk >= 0.0) return akl < 0.0 ? akl : 0.0;
+    return akl > 0.0 ? akl : 0.0;
+}
+
+__device__ __forceinline__ bool in_sorted(const int *a, int len, int j) {
+    int lo = 0, hi = len - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int x = a[mid];
+        if (x == j) return true;
+        if (x < j) lo = mid + 1; else hi = mid - 1;
+    }
+    return false;
+}
+
+// bound on |Chat_i| candidates: sum over strong j of (C ? 1 : |S_j|)
+__global__ void k_extpi_bound(int n, const int *rp, const int *ci, const uint8_t *sflag,
+                              const int *srp, const int *cf, int *bound) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int b = 0;
+    if (cf[i] != 1)
+        for (int p = rp[i]; p < rp[i + 1]; p++)
+            if (sflag[p]) { int j = ci[p]; b += cf[j] == 1 ? 1 : srp[j + 1] - srp[j]; }
+    bound[i] = b + 1;
+}
+
+// Pass 1: Chat_i (sorted, unique) and the untruncated weights into scratch;
+// final row length into len[i].
+__global__ void k_extpi_weights(int n, const int *rp, const int *ci, const double *v,
+                                const uint8_t *sflag, const int *cf, const int *func,
+                                const long long *boff, int *cand, double *wts, int *chat_len,
+                                int *len, int pmax) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (cf[i] == 1) { len[i] = 1; chat_len[i] = 0; return; }
+    int *L = cand + boff[i];
+    double *num = wts + boff[i];
+    int cnt = 0;
+    for (int p = rp[i]; p < rp[i + 1]; p++) {
+        if (!sflag[p]) continue;
+        int j = ci[p];
+        if (cf[j] == 1) L[cnt++] = j;
+        else
+            for (int q = rp[j]; q < rp[j + 1]; q++)
+                if (sflag[q] && cf[ci[q]] == 1) L[cnt++] = ci[q];
+    }
+    // sort + unique
+    const int gaps[8] = {701, 301, 132, 57, 23, 10, 4, 1};
+    for (int gi = 0; gi < 8; gi++) {
+        int g = gaps[gi];
+        for (int a = g; a < cnt; a++) {
+            int kc = L[a], b = a;
+            while (b >= g && L[b - g] > kc) { L[b] = L[b - g]; b -= g; }
+            L[b] = kc;
+        }
+    }
+    int u = 0;
+    for (int a = 0; a < cnt; a++)
+        if (u == 0 || L[a] != L[u - 1]) L[u++] = L[a];
+    cnt = u;
+    chat_len[i] = cnt;
+    if (cnt == 0) { len[i] = 0; return; }
+    for (int t = 0; t < cnt; t++) num[t] = 0.0;
+    double diag = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; p++)
+        if (ci[p] == i) diag = v[p];
+    int fi = func[i];
+    // phase 1
+    for (int p = rp[i]; p < rp[i + 1]; p++) {
+        int j = ci[p];
+        if (j == i || func[j] != fi) continue;
+        int lo = 0, hi = cnt - 1, at = -1;
+        while (lo <= hi) { int mid = (lo + hi) >> 1; if (L[mid] == j) { at = mid; break; } if (L[mid] < j) lo = mid + 1; else hi = mid - 1; }
+        if (at >= 0) num[at] = num[at] + v[p];
+        else if (!sflag[p]) diag = diag + v[p];
+    }
+    // phase 2
+    for (int p = rp[i]; p < rp[i + 1]; p++) {
+        int k = ci[p];
+        if (k == i || !sflag[p] || cf[k] == 1) continue;
+        double aik = v[p];
+        double akk = 0.0;
+        for (int q = rp[k]; q < rp[k + 1]; q++)
+            if (ci[q] == k) akk = v[q];
+        int fk = func[k];
+        double den = 0.0;
+        for (int q = rp[k]; q < rp[k + 1]; q++) {
+            int l = ci[q];
+            if (l == k || func[l] != fk) continue;
+            if (l == i || in_sorted(L, cnt, l)) den = den + abar(akk, v[q]);
+        }
+        if (den == 0.0) { diag = diag + aik; continue; }
+        double f = aik / den;
+        for (int q = rp[k]; q < rp[k + 1]; q++) {
+            int l = ci[q];
+            if (l == k || func[l] != fk) continue;
+            int lo = 0, hi = cnt - 1, at = -1;
+            while (lo <= hi) { int mid = (lo + hi) >> 1; if (L[mid] == l) { at = mid; break; } if (L[mid] < l) lo = mid + 1; else hi = mid - 1; }
+            if (at >= 0) num[at] = num[at] + f * abar(akk, v[q]);
+            else if (l == i) diag = diag + f * abar(akk, v[q]);
+        }
+    }
+    if (diag == 0.0) { len[i] = 0; return; }
+    for (int t = 0; t < cnt; t++) num[t] = -(num[t] / diag);
+    len[i] = (pmax > 0 && cnt > pmax) ? pmax : cnt;
+}
+
+// Pass 2: truncation (pmax largest |w|, ties to the lower column; rescale by
+// sum(all)/sum(kept) when sum(kept) != 0) and coarse renumbering.
+__global__ void k_extpi_fill(int n, const int *cf, const int *cnum, const long long *boff,
+                             const int *cand, const double *wts, const int *chat_len, const int *prp,
+                             int *pci, double *pv, int pmax) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int o = prp[i], len = prp[i + 1] - o;
+    if (cf[i] == 1) { pci[o] = cnum[i]; pv[o] = 1.0; return; }
+    if (len == 0) return;
+    const int *L = cand + boff[i];
+    const double *w = wts + boff[i];
+    int cnt = chat_len[i];
+    if (!(pmax > 0 && cnt > pmax)) {
+        for (int t = 0; t < cnt; t++) { pci[o + t] = cnum[L[t]]; pv[o + t] = w[t]; }
+        return;
+    }
+    int ord[64];
+    int K = pmax < 64 ? pmax : 64;
+    // the K largest |w| (ties to the lower position), picked one at a time
+    for (int s2 = 0; s2 < K; s2++) {
+        int best = -1;
+        for (int t = 0; t < cnt; t++) {
+            bool used = false;
+            for (int u = 0; u < s2; u++) if (ord[u] == t) { used = true; break; }
+            if (used) continue;
+            if (best < 0) { best = t; continue; }
+            double x = fabs(w[t]), y = fabs(w[best]);
+            if (x > y || (x == y && t < best)) best = t;
+        }
+        ord[s2] = best;
+    }
+    for (int a = 1; a < K; a++) {
+        int kc = ord[a], b = a;
+        while (b > 0 && ord[b - 1] > kc) { ord[b] = ord[b - 1]; b--; }
+        ord[b] = kc;
+    }
+    double sall = 0.0, skept = 0.0;
+    for (int t = 0; t < cnt; t++) sall = sall + w[t];
+    for (int s2 = 0; s2 < K; s2++) skept = skept + w[ord[s2]];
+    double scale = skept != 0.0 ? sall / skept : 1.0;
+    for (int s2 = 0; s2 < K; s2++) {
+        pci[o + s2] = cnum[L[ord[s2]]];
+        pv[o + s2] = skept != 0.0 ? w[ord[s2]] * scale : w[ord[s2]];
+    }
+}
+
+__global__ void k_count_flags(int n, const int *rp, const uint8_t *flag, int *cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = 0;
+    for (int p = rp[i]; p < rp[i + 1]; p++) c += flag[p];
+    cnt[i] = c;
+}
+
+__global__ void k_is_c(int n, const int *cf, int *isc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) isc[i] = cf[i] == 1;
+}
+
+int amg_extpi(const DCSR &A, const uint8_t *sflag, const int *cf, const int *func, int pmax,
+              DCSR &P, int *nc, cudaStream_t s, Arena &ar) {
+    int n = A.n;
+    if (pmax > 64) pmax = 64;
+    int *isc = ar.alloc<int>(n + 1);
+    int *cnum = ar.alloc<int>(n + 1);
+    int *bound = ar.alloc<int>(n + 1);
+    long long *boff = ar.alloc<long long>(n + 1);
+    int *chat = ar.alloc<int>(n + 1);
+    int *len = ar.alloc<int>(n + 1);
+    if (!isc || !cnum || !bound || !boff || !chat || !len) return ST_NOMEM;
+    k_is_c<<<GRID(n, 256), 256, 0, s>>>(n, cf, isc);
+    int rc = scan_exclusive(isc, cnum, n, s, ar, nc);
+    if (rc) return rc;
+    // strength row pointers from sflag (S rows are A rows filtered)
+    int *scnt = ar.alloc<int>(n + 1), *srp = ar.alloc<int>(n + 1);
+    if (!scnt || !srp) return ST_NOMEM;
+    k_count_flags<<<GRID(n, 256), 256, 0, s>>>(n, A.rp, sflag, scnt);
+    rc = scan_exclusive(scnt, srp, n, s, ar, nullptr);
+    if (rc) return rc;
+    k_extpi_bound<<<GRID(n, 128), 128, 0, s>>>(n, A.rp, A.ci, sflag, srp, cf, bound);
+    long long totb = 0;
+    rc = scan_exclusive_ll(bound, boff, n, s, ar, &totb);
+    if (rc) return rc;
+    int *cand = ar.alloc<int>(totb + 1);
+    double *wts = ar.alloc<double>(totb + 1);
+    if (!cand || !wts) return ST_NOMEM;
+    k_extpi_weights<<<GRID(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, sflag, cf, func, boff, cand,
+                                                 wts, chat, len, pmax);
+    P.n = n; P.m = *nc;
+    P.rp = ar.alloc<int>(n + 1);
+    if (!P.rp) return ST_NOMEM;
+    int tot = 0;
+    rc = scan_exclusive(len, P.rp, n, s, ar, &tot);
+    if (rc) return rc;
+    P.nnz = tot;
+    P.ci = ar.alloc<int>(tot + 1);
+    P.v = ar.alloc<double>(tot + 1);
+    if (!P.ci || !P.v) return ST_NOMEM;
+    k_extpi_fill<<<GRID(n, 128), 128, 0, s>>>(n, cf, cnum, boff, cand, wts, chat, P.rp, P.ci, P.v,
+                                              pmax);
+    cudaStreamSynchronize(s);
+    ar.release(cand); ar.release(wts); ar.release(isc); ar.release(cnum); ar.release(bound);
+    ar.release(boff); ar.release(chat); ar.release(len); ar.release(scnt); ar.release(srp);
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+// ------------------------------------------------------------- l1 inverse
+// d_i = a_ii + sign(a_ii) sum_{j != i} |a_ij| (ascending), 1/d_i.
+__global__ void k_l1_inverse(int n, const int *rp, const int *ci, const double *v, double *dinv,
+                             float *dinv32, int *errw) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double aii = 0.0, s = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; p++) {
+        if (ci[p] == i) { aii = v[p]; continue; }
+        s = s + fabs(v[p]);
+    }
+    double d = aii < 0.0 ? aii - s : aii + s;
+    if (d == 0.0) { atomicOr(errw, ERRW_SINGULAR); dinv[i] = 0.0; if (dinv32) dinv32[i] = 0.f; return; }
+    dinv[i] = 1.0 / d;
+    if (dinv32) dinv32[i] = (float)dinv[i];
+}
+
+int l1_inverse(const DCSR &A, double *dinv, float *dinv32, int *errw, cudaStream_t s) {
+    k_l1_inverse<<<GRID(A.n, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, dinv, dinv32, errw);
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+__global__ void k_coarse_func(int n, const int *cf, const int *func, const int *prp, const int *pci,
+                              int *cfunc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && cf[i] == 1) cfunc[pci[prp[i]]] = func[i];
+}
+
+void launch_coarse_func(const int *cf, const int *func, const DCSR &P, int *cfunc, int n,
+                        cudaStream_t s) {
+    k_coarse_func<<<GRID(n, 256), 256, 0, s>>>(n, cf, func, P.rp, P.ci, cfunc);
+}
+
+__global__ void k_iota_mod(int *f, int n, int nf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) f[i] = nf > 1 ? i % nf : 0;
+}
+
+void launch_iota_mod(int *func, int n, int nf, cudaStream_t s) {
+    k_iota_mod<<<GRID(n, 256), 256, 0, s>>>(func, n, nf);
+}
+
+// ------------------------------------------------------- coarsest inverse
+// Gauss-Jordan with partial pivoting on [A | I] (one CTA), n <= 1024.
+__global__ void k_dense_fill(int n, const int *rp, const int *ci, const double *v, double *M) {
+    int i = blockIdx.x;
+    if (i >= n) return;
+    for (int c = threadIdx.x; c < 2 * n; c += blockDim.x) M[(long long)i * 2 * n + c] = (c - n == i) ? 1.0 : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int p = rp[i]; p < rp[i + 1]; p++) M[(long long)i * 2 * n + ci[p]] = v[p];
+}
+
+__global__ void k_gauss_jordan(int n, double *M, double *inv, int *errw) {
+    __shared__ double red_v[1024];
+    __shared__ int red_i[1024];
+    __shared__ int piv_row;
+    __shared__ double piv_val;
+    int tid = threadIdx.x, nt = blockDim.x;
+    long long ld = 2LL * n;
+    for (int c = 0; c < n; c++) {
+        double best = -1.0;
+        int bi = c;
+        for (int r = c + tid; r < n; r += nt) {
+            double x = fabs(M[r * ld + c]);
+            if (x > best || (x == best && r < bi)) { best = x; bi = r; }
+        }
+        red_v[tid] = best; red_i[tid] = bi;
+        __syncthreads();
+        for (int o = nt / 2; o > 0; o >>= 1) {
+            if (tid < o) {
+                double a = red_v[tid], b = red_v[tid + o];
+                int ia = red_i[tid], ib = red_i[tid + o];
+                if (b > a || (b == a && ib < ia)) { red_v[tid] = b; red_i[tid] = ib; }
+            }
+            __syncthreads();
+        }
+        if (tid == 0) { piv_row = red_i[0]; piv_val = M[red_i[0] * ld + c]; }
+        __syncthreads();
+        if (piv_val == 0.0) { if (tid == 0) atomicOr(errw, ERRW_SINGULAR); return; }
+        int p = piv_row;
+        if (p != c)
+            for (int t = tid; t < 2 * n; t += nt) {
+                double a = M[c * ld + t]; M[c * ld + t] = M[p * ld + t]; M[p * ld + t] = a;
+            }
+        __syncthreads();
+        double pv = piv_val;
+        for (int t = tid; t < 2 * n; t += nt) M[c * ld + t] = M[c * ld + t] / pv;
+        __syncthreads();
+        for (long long e = tid; e < (long long)n * 2 * n; e += nt) {
+            int r = (int)(e / (2 * n)), t = (int)(e % (2 * n));
+            if (r == c || t == c) continue;
+            M[r * ld + t] = M[r * ld + t] - M[r * ld + c] * M[c * ld + t];
+        }
+        __syncthreads();
+        for (int r = tid; r < n; r += nt)
+            if (r != c) M[r * ld + c] = 0.0;
+        __syncthreads();
+    }
+    for (long long e = tid; e < (long long)n * n; e += nt) {
+        int r = (int)(e / n), t = (int)(e % n);
+        inv[e] = M[r * ld + n + t];
+    }
+}
+
+int dense_inverse(const DCSR &A, double *inv, int *errw, cudaStream_t s, Arena &ar) {
+    int n = A.n;
+    double *M = ar.alloc<double>((size_t)n * 2 * n + 1);
+    if (!M) return ST_NOMEM;
+    k_dense_fill<<<n, 256, 0, s>>>(n, A.rp, A.ci, A.v, M);
+    k_gauss_jordan<<<1, 1024, 0, s>>>(n, M, inv, errw);
+    cudaStreamSynchronize(s);
+    ar.release(M);
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+__global__ void k_cast_f32(const double *in, float *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+void launch_cast_f32(const double *in, float *out, long long n, cudaStream_t s) {
+    unsigned g = GRID(n, 256);
+    k_cast_f32<<<g > 8192 ? 8192 : g, 256, 0, s>>>(in, out, n);
+}
+
+}  // namespace mgr

@@ -1,0 +1,259 @@
+"""CUDA path vs the CPU oracle, through the C ABI (marked gpu).
+
+Setup is compared bit for bit (both sides follow the same stated operation
+order without fused multiply-add); the solve phase within the tolerances of
+the FP64 arithmetic: SpMV per entry relative to sum_j |a_ij x_j| (1e-13),
+V-cycle 1e-11 relative, FGMRES iterations +-1 and solutions 1e-8 relative
+when both are converged to 1e-12.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2101_11649_gb300.synth import (make_compositional, make_mimetic, make_poromech,
+                                          make_two_phase)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2101_11649_gb300 import mgr as M  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+SMALL = {
+    "two_phase": lambda: make_two_phase(8, 7, 5),
+    "mimetic": lambda: make_mimetic(7, 6, 5),
+    "compositional": lambda: make_compositional(16, 12, 4),
+    "poromech": lambda: make_poromech(8, 4),
+}
+
+
+def t(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device=DEV)
+
+
+def solver(sysm, precision="fp64", **kw):
+    return M.MGRSolver.from_system(sysm, precision=precision, **kw)
+
+
+# ------------------------------------------------------------------ SpMV
+@pytest.mark.parametrize("b", [1, 2, 3, 4])
+@pytest.mark.parametrize("nb", [1, 7, 33, 1000])
+def test_bsr_spmv_parity(b, nb):
+    rng = np.random.default_rng(100 * b + nb)
+    from paper_2101_11649_gb300.synth.bsr import assemble_bsr
+    rows, cols = [], []
+    for i in range(nb):
+        if i % 5 == 3:
+            continue  # empty block rows
+        js = np.unique(rng.integers(0, nb, 1 + rng.integers(0, 9)))
+        rows += [i] * len(js); cols += list(js)
+    rp, ci, val = assemble_bsr(nb, b, np.array(rows, np.int64), np.array(cols, np.int64),
+                               rng.standard_normal((len(rows), b, b)))
+    x = rng.standard_normal(nb * b)
+    y0 = rng.standard_normal(nb * b)
+    ref = O.spmv_bsr(nb, b, rp, ci, val, x)
+    absref = O.spmv_bsr(nb, b, rp, ci, np.abs(val), np.abs(x)) + 1e-300
+    trp = torch.as_tensor(rp, device=DEV); tci = torch.as_tensor(ci, device=DEV)
+    tv = t(val.ravel())
+    y = M.bsr_spmv(trp, tci, tv, b, t(x))
+    torch.cuda.synchronize()
+    err = np.abs(y.cpu().numpy() - ref) / absref
+    assert err.max() <= 1e-13
+    # alpha, beta form
+    y2 = M.bsr_spmv(trp, tci, tv, b, t(x), y=t(y0), alpha=-2.0, beta=0.5)
+    ref2 = -2.0 * ref + 0.5 * y0
+    assert (np.abs(y2.cpu().numpy() - ref2) / (2 * absref + 0.5 * np.abs(y0))).max() <= 1e-13
+
+
+# ------------------------------------------------------ setup, bit-exact
+def _same_csr(a, b, what):
+    assert a is not None and b is not None, what
+    assert a[3] == b[3], (what, a[3], b[3])
+    assert np.array_equal(a[0], b[0]), what + " row_ptr"
+    assert np.array_equal(a[1], b[1]), what + " col_idx"
+    assert np.array_equal(a[2].view(np.int64), b[2].view(np.int64)), \
+        (what + " values", np.max(np.abs(a[2] - b[2])))
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_hierarchy_bit_exact(name):
+    s = SMALL[name]()
+    g = solver(s)
+    o = O.Oracle(s)
+    info = g.info()
+    assert info["mgr_levels"] == o.mgr_nlevels
+    assert info["amg_levels"] == o.amg_nlevels
+    for l in range(s.num_levels + 1):
+        _same_csr(g.matrix(0, l, 0), o.mgr_matrix(l, "A"), f"MGR A_{l}")
+    for l in range(s.num_levels):
+        for w, nm in ((1, "AFF"), (2, "AFC"), (3, "ACF"), (4, "W")):
+            _same_csr(g.matrix(0, l, w), o.mgr_matrix(l, nm), f"MGR {nm}_{l}")
+        gd, gg = g.mgr_dinv(l)
+        od, og = o.mgr_dinv(l)
+        assert np.array_equal(gg, og)
+        assert np.array_equal(gd.view(np.int64), od.view(np.int64)), f"D^-1 level {l}"
+    for k in range(o.amg_nlevels):
+        _same_csr(g.matrix(1, k, 0), o.amg_matrix(k, "A"), f"AMG A_{k}")
+        if k < o.amg_nlevels - 1:
+            _same_csr(g.matrix(1, k, 1), o.amg_matrix(k, "P"), f"AMG P_{k}")
+            assert np.array_equal(g.amg_cf(k), o.amg_cf(k)), f"C/F split level {k}"
+
+
+# -------------------------------------------------------- V-cycle, solve
+@pytest.mark.parametrize("name", list(SMALL))
+def test_vcycle_parity(name):
+    s = SMALL[name]()
+    g = solver(s)
+    o = O.Oracle(s)
+    rng = np.random.default_rng(5)
+    for trans in (False, True):
+        v = rng.standard_normal(s.n)
+        zg = g.apply(t(v), transpose=trans).cpu().numpy()
+        zo = o.apply_transpose(v) if trans else o.apply(v)
+        assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo), (trans, np.linalg.norm(zg - zo) / np.linalg.norm(zo))
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_solve_parity(name):
+    s = SMALL[name]()
+    g = solver(s)
+    o = O.Oracle(s)
+    ro = o.solve(s.rhs, rtol=1e-8)
+    xg, ig = g.solve(t(s.rhs), rtol=1e-8)
+    assert ig["status"] == 0 and ro["status"] == 0
+    assert abs(ig["iterations"] - ro["iters"]) <= 1, (ig["iterations"], ro["iters"])
+    assert ig["rel_residual"] <= 1e-8
+    # solutions when both are converged tightly
+    ro = o.solve(s.rhs, rtol=1e-12, maxit=1000)
+    xg, ig = g.solve(t(s.rhs), rtol=1e-12, maxit=1000)
+    xo = ro["x"]
+    assert np.linalg.norm(xg.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_fp32_preconditioner_reaches_fp64_tolerance(name):
+    s = SMALL[name]()
+    g = solver(s, precision="fp32")
+    o = O.Oracle(s)
+    xg, ig = g.solve(t(s.rhs), rtol=1e-8)
+    assert ig["status"] == 0 and ig["rel_residual"] <= 1e-8
+    ro = o.solve(s.rhs, rtol=1e-8)
+    assert ig["iterations"] <= ro["iters"] + 3
+    # error against the FP64 oracle solution (both at 1e-8 residual)
+    xo = ro["x"]
+    rel = np.linalg.norm(xg.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert rel <= 1e-5, rel
+
+
+def test_transpose_solve_and_gradient():
+    s = make_two_phase(6, 5, 4)
+    g = solver(s)
+    o = O.Oracle(s)
+    gvec = np.random.default_rng(9).standard_normal(s.n)
+    lam, info = g.solve(t(gvec), rtol=1e-12, transpose=True)
+    ro = o.solve(gvec, rtol=1e-12, trans=True)
+    assert info["status"] == 0
+    assert np.linalg.norm(lam.cpu().numpy() - ro["x"]) <= 1e-8 * np.linalg.norm(ro["x"])
+    x, _ = g.solve(t(s.rhs), rtol=1e-12)
+    dA = g.grad_values(lam, x).cpu().numpy()
+    lam_n, x_n = lam.cpu().numpy(), x.cpu().numpy()
+    b = s.b
+    for p in range(0, s.nnzb, 7):
+        I = np.searchsorted(s.row_ptr, p, side="right") - 1
+        J = s.col_idx[p]
+        ref = -np.outer(lam_n[I * b:(I + 1) * b], x_n[J * b:(J + 1) * b])
+        assert np.array_equal(dA[p], ref)
+
+
+# ------------------------------------------------------------ edge cases
+def test_invalid_inputs_are_rejected():
+    s = make_two_phase(3, 3, 2)
+    # unsorted columns
+    ci = s.col_idx.copy(); ci[[0, 1]] = ci[[1, 0]]
+    with pytest.raises(M.MGRError) as e:
+        M.MGRSolver(s.row_ptr, ci, s.val, s.b, s.dof_level, s.num_levels)
+    assert e.value.status == M.MGR_ERR_INVALID
+    # NaN value
+    v = s.val.copy(); v[3, 0, 1] = np.nan
+    with pytest.raises(M.MGRError) as e:
+        M.MGRSolver(s.row_ptr, s.col_idx, v, s.b, s.dof_level, s.num_levels)
+    assert e.value.status == M.MGR_ERR_INVALID
+    # empty C set
+    with pytest.raises(M.MGRError) as e:
+        M.MGRSolver(s.row_ptr, s.col_idx, s.val, s.b, np.zeros(s.n, np.int8), 1)
+    assert e.value.status == M.MGR_ERR_INVALID
+    # label out of range
+    with pytest.raises(M.MGRError) as e:
+        M.MGRSolver(s.row_ptr, s.col_idx, s.val, s.b, np.full(s.n, 3, np.int8), 1)
+    assert e.value.status == M.MGR_ERR_INVALID
+
+
+def test_singular_f_block_reports_singular():
+    s = make_two_phase(3, 3, 2)
+    v = s.val.copy()
+    # zero the saturation diagonal of block row 4 (an F point under Jacobi)
+    diag = [p for p in range(s.row_ptr[4], s.row_ptr[5]) if s.col_idx[p] == 4][0]
+    v[diag, 1, 1] = 0.0
+    with pytest.raises(M.MGRError) as e:
+        M.MGRSolver(s.row_ptr, s.col_idx, v, s.b, s.dof_level, s.num_levels,
+                    M.options(relax=("jacobi",)))
+    assert e.value.status == M.MGR_ERR_SINGULAR
+
+
+def test_maxit_and_zero_rhs():
+    s = make_two_phase(6, 6, 3)
+    g = solver(s)
+    x, info = g.solve(t(s.rhs), rtol=1e-12, maxit=2)
+    assert info["status"] == M.MGR_ERR_NOT_CONVERGED and info["iterations"] == 2
+    x, info = g.solve(torch.zeros(s.n, dtype=torch.float64, device=DEV), rtol=1e-8)
+    assert info["status"] == 0 and info["iterations"] == 0 and float(x.abs().max()) == 0.0
+
+
+def test_single_block_system():
+    from paper_2101_11649_gb300.synth.bsr import BlockSystem
+    val = np.array([[[4.0, 1.0], [2.0, 3.0]]])
+    s = BlockSystem("one", 2, np.array([0, 1], np.int32), np.array([0], np.int32), val,
+                    np.array([1, 0], np.int8), 1, np.array([1.0, 2.0]), relax=["jacobi"])
+    g = solver(s)
+    x, info = g.solve(t(s.rhs), rtol=1e-12)
+    assert info["status"] == 0
+    assert np.allclose(x.cpu().numpy(), np.linalg.solve(val[0], s.rhs), rtol=1e-12)
+
+
+def test_repeat_solves_bitwise_identical():
+    s = SMALL["mimetic"]()
+    g = solver(s)
+    x1, i1 = g.solve(t(s.rhs), rtol=1e-10)
+    x2, i2 = g.solve(t(s.rhs), rtol=1e-10)
+    assert i1["iterations"] == i2["iterations"]
+    assert torch.equal(x1, x2)
+
+
+# ------------------------------------------------ full-size bench workload
+@pytest.mark.slow
+def test_mimetic_64_full_size():
+    """The 64^3 hybrid mimetic system (1,060,864 unknowns) as the benchmark
+    runs it: bit-exact hierarchy on every level, sampled V-cycle entries,
+    iteration parity and the true residual of both precisions."""
+    s = make_mimetic(64, 64, 64)
+    g = solver(s)
+    o = O.Oracle(s)
+    for l in range(2):
+        _same_csr(g.matrix(0, l, 0), o.mgr_matrix(l, "A"), f"MGR A_{l}")
+    for k in range(o.amg_nlevels):
+        _same_csr(g.matrix(1, k, 0), o.amg_matrix(k, "A"), f"AMG A_{k}")
+    v = np.random.default_rng(1).standard_normal(s.n)
+    zg = g.apply(t(v)).cpu().numpy()
+    zo = o.apply(v)
+    assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo)
+    ro = o.solve(s.rhs, rtol=1e-8)
+    for prec in ("fp64", "fp32"):
+        gp = g if prec == "fp64" else solver(s, precision="fp32")
+        x, info = gp.solve(t(s.rhs), rtol=1e-8)
+        assert info["status"] == 0 and info["rel_residual"] <= 1e-8
+        if prec == "fp64":
+            assert abs(info["iterations"] - ro["iters"]) <= 1
