@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark: time to a 1e-8 relative residual of MGR-preconditioned FGMRES.
+
+Workload: the statically condensed hybrid mimetic single-phase system on a
+64^3 hexahedral grid (262,144 cell pressures + 798,720 face multipliers =
+1,060,864 unknowns, 12,070,912 nonzeros), MGR_P (cells F, Jacobi; faces C,
+AMG V(1,1)), FGMRES(30), x0 = 0.  A step is one complete solve to
+||b - A x|| <= 1e-8 ||b|| with the inputs resident in HBM; setup is timed
+separately.  `value` is the plain FP64 form; the FP32-preconditioner form
+(V-cycle stored and run in FP32 inside FP64 FGMRES) is measured in the same
+run.  L2 (129 MB) is flushed by a 256 MB write before every timed step.
+
+`--impl reference` times the CPU oracle (single-threaded plain C) on the
+same system, one full solve per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-8 rel. residual, FP64 vs FP32-MGR; V-cycle HBM GB/s vs 8 TB/s"
+WORKLOAD = "hybrid mimetic single-phase 64^3 (1,060,864 unknowns), MGR_P + AMG V(1,1), FGMRES(30)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--grid", type=int, default=64)
+    p.add_argument("--rtol", type=float, default=1e-8)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-profile", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.f:
+            return None
+        self.f.flush()
+        rows = []
+        try:
+            for line in open(self.f.name):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            return None
+        finally:
+            try:
+                os.unlink(self.f.name)
+            except Exception:
+                pass
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "gb300" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v, dev):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_system(grid):
+    from paper_2101_11649_gb300.synth import make_mimetic
+    return make_mimetic(grid, grid, grid)
+
+
+def oracle_solve_ms(sysm, rtol, steps, warmup):
+    """CPU oracle: setup once (untimed), then `warmup` + `steps` full solves."""
+    from oracle import oracle as O
+    o = O.Oracle(sysm)
+    for _ in range(warmup):
+        o.solve(sysm.rhs, rtol=rtol)
+    ts, its = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        r = o.solve(sysm.rhs, rtol=rtol)
+        ts.append((time.perf_counter() - t0) * 1e3)
+        its.append(r["iters"])
+    return statistics.mean(ts), its
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    sysm = make_system(args.grid)
+    ms, its = oracle_solve_ms(sysm, args.rtol, args.steps, args.warmup)
+    sample = (f"{args.warmup} warm-up + {args.steps} timed full solves to {args.rtol:g} of the "
+              f"whole workload (setup untimed), single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": round(ms, 3), "unit": "ms",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": args.grid, "rtol": args.rtol},
+            "iterations": its[-1] if its else None,
+            "cpu_baseline": {"value": round(ms, 3), "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(ms, 3), "unit": "ms", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    from paper_2101_11649_gb300 import mgr as M
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peak_gbs, peak_kind = peaks()
+    sysm = make_system(args.grid)
+    n = sysm.n
+
+    t0 = time.perf_counter()
+    s64 = M.MGRSolver.from_system(sysm, precision="fp64")
+    torch.cuda.synchronize()
+    setup64_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    s32 = M.MGRSolver.from_system(sysm, precision="fp32")
+    torch.cuda.synchronize()
+    setup32_ms = (time.perf_counter() - t0) * 1e3
+
+    b = torch.as_tensor(sysm.rhs, device=dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def solve(sv):
+        x.zero_()
+        _, info = sv.solve(b, x, rtol=args.rtol, maxit=1000)
+        if info["status"] != 0:
+            raise RuntimeError(f"solve failed: {info}")
+        return info
+
+    def timed(sv, k):
+        """k solves, each bracketed by CUDA events on the current stream, L2
+        flushed before each; returns per-step ms and the last info."""
+        times, info = [], None
+        st = torch.cuda.current_stream()
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            info = solve(sv)
+            e1.record(st)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times, info
+
+    for _ in range(args.warmup):
+        solve(s64)
+        solve(s32)
+
+    # ---- timed region (FP64 headline), clocks sampled during it
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = M.launch_count()
+    with ClockSampler(local) as cs:
+        t64, info64 = timed(s64, args.steps)
+        torch.cuda.synchronize()
+        barrier(world)
+        t32, info32 = timed(s32, args.steps)
+        torch.cuda.synchronize()
+    launches = M.launch_count() - l0
+    clocks = cs.summary()
+    ms64 = max_over_ranks(world, statistics.mean(t64), dev)
+    ms32 = max_over_ranks(world, statistics.mean(t32), dev)
+
+    # ---- per-kernel-class event timing over a second timed pass
+    roofline, kernels, vcycle = None, [], {}
+    if not args.no_profile:
+        s64.profile(True)
+        timed(s64, args.steps)
+        kernels = s64.profile_table()
+        s64.profile(False)
+        kernels.sort(key=lambda r: -r["ms"])
+        top = kernels[0]
+        avg_s = top["ms"] / top["launches"] / 1e3
+        ach = top["bytes_per_launch"] / avg_s / 1e9
+        roofline = {"bound": "hbm", "kernel": top["name"], "achieved": round(ach, 1),
+                    "peak": peak_gbs, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": round(ach / peak_gbs, 4), "traffic": None,
+                    "avg_launch_us": round(avg_s * 1e6, 2),
+                    "bytes_per_launch": top["bytes_per_launch"],
+                    "share_of_solve": round(top["ms"] / sum(k["ms"] for k in kernels), 4)}
+        # the V-cycle as a unit: one profiled apply gives its algorithmic bytes,
+        # event-timed applies its duration
+        for name, sv in (("fp64", s64), ("fp32", s32)):
+            v = torch.randn(n, dtype=torch.float64, device=dev)
+            z = torch.empty_like(v)
+            sv.profile(True)
+            sv.apply(v, z)
+            tab = sv.profile_table()
+            sv.profile(False)
+            vbytes = sum(r["bytes_per_launch"] * r["launches"] for r in tab)
+            st = torch.cuda.current_stream()
+            reps = 20
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st); sv.apply(v, z); e1.record(st)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            vms = statistics.median(ts)
+            vcycle[name] = {"ms": round(vms, 4), "bytes": vbytes, "kernels": len(tab),
+                            "gbs": round(vbytes / (vms / 1e3) / 1e9, 1),
+                            "frac": round(vbytes / (vms / 1e3) / 1e9 / peak_gbs, 4)}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        bh = torch.as_tensor(sysm.rhs).pin_memory()
+        xh = torch.empty(n, dtype=torch.float64).pin_memory()
+        bd = torch.empty(n, dtype=torch.float64, device=dev)
+        xd = torch.empty(n, dtype=torch.float64, device=dev)
+        ts = []
+        for k in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bd.copy_(bh, non_blocking=True)
+            xd.zero_()
+            _, info = s64.solve(bd, xd, rtol=args.rtol, maxit=1000)
+            xh.copy_(xd, non_blocking=True)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ts.append((time.perf_counter() - t0) * 1e3)
+        e2e = {"value": round(max_over_ranks(world, statistics.mean(ts), dev), 3), "unit": "ms",
+               "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ms, its = oracle_solve_ms(sysm, args.rtol, 1, 0)
+        cpu = {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"one full solve of the same system to {args.rtol:g} (setup untimed), "
+                         f"single thread, {its[0]} iterations"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(ms64, 3), "unit": "ms", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms64, 3),
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": args.grid, "rtol": args.rtol,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "256 MB write before every timed step",
+                           "solves_per_s_job": round(world * 1e3 / ms64, 2)},
+                "iterations": info64["iterations"], "rel_residual": info64["rel_residual"],
+                "fp32_mgr": {"ms": round(ms32, 3), "iterations": info32["iterations"],
+                             "rel_residual": info32["rel_residual"],
+                             "speedup_vs_fp64": round(ms64 / ms32, 3)},
+                "setup_ms": {"fp64": round(setup64_ms, 1), "fp32": round(setup32_ms, 1)},
+                "levels": {"mgr": info64["mgr_levels"], "amg": info64["amg_levels"],
+                           "rows": info64["level_rows"], "nnz": info64["level_nnz"],
+                           "operator_complexity": round(info64["operator_complexity"], 3)},
+                "vcycle": vcycle, "roofline": roofline,
+                "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
+                            for r in kernels[:12]],
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": int(launches)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -183,6 +183,25 @@ mgr_status mgr_get_dinv(mgr_handle h, int32_t level, double *dinv, int32_t *gsiz
 /* Level counts: out[0] = MGR levels, out[1] = AMG levels, out[2] = n. */
 mgr_status mgr_get_info(mgr_handle h, int32_t *out);
 
+/* ------------------------------------------------------- instrumentation
+ * Kernel launches this library has made (all handles, solve-phase kernels,
+ * counted on the host when enqueued).  */
+int64_t mgr_launch_count(void);
+
+/* Enable (on != 0) or disable per-kernel-class timing on h and reset the
+ * table.  While on, every solve-phase launch is bracketed by a CUDA event
+ * pair on the handle's stream, tagged with the kernel class (and level) and
+ * the algorithmic bytes one launch moves (each operand read or written once).  */
+mgr_status mgr_profile(mgr_handle h, int32_t on);
+
+/* Number of kernel classes recorded so far (synchronises the stream). */
+int32_t mgr_profile_entries(mgr_handle h);
+
+/* Entry i: name (host buffer of name_cap bytes), summed device time, number
+ * of launches and algorithmic bytes per launch.  */
+mgr_status mgr_profile_entry(mgr_handle h, int32_t i, char *name, int32_t name_cap,
+                             double *total_ms, int64_t *launches, double *bytes_per_launch);
+
 #ifdef __cplusplus
 }
 #endif

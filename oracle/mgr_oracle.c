@@ -729,7 +729,7 @@ static int mgr_dinv(mgr_level *L, int b) {
     int nF = L->nF;
     L->gstart = (int *)malloc(((size_t)nF + 1) * sizeof(int));
     L->gsize = (int *)malloc(((size_t)nF + 1) * sizeof(int));
-    L->dinv = (double *)malloc(((size_t)nF * 4 + 1) * sizeof(double));
+    L->dinv = (double *)calloc((size_t)nF * 4 + 1, sizeof(double));
     if (!L->gstart || !L->gsize || !L->dinv) return OR_NOMEM;
     if (L->relax != OR_BLOCK_JACOBI) {
         for (int f = 0; f < nF; f++) {

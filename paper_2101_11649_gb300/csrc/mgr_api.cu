@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <string>
 #include <vector>
@@ -61,6 +62,21 @@ struct Krylov {
     std::vector<cudaGraphExec_t> graphs[2];
 };
 
+// Per-kernel-class timing: a CUDA event pair around each launch on the
+// handle's stream, tagged with the algorithmic bytes that launch moves
+// (every array read or written once).
+struct Prof {
+    int on = 0;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<int> ptag;
+    std::vector<std::string> names;
+    std::vector<double> ms, bytes;
+    std::vector<long long> cnt;
+};
+
+static std::atomic<long long> g_launches{0};
+
 }  // namespace mgr
 
 using namespace mgr;
@@ -84,6 +100,7 @@ struct mgr_ctx {
     double *coinv = nullptr, *coinvT = nullptr;
     int *errw = nullptr;
     Krylov kr;
+    Prof prof;
     double setup_ms = 0.0;
     std::string err;
 };
@@ -101,6 +118,53 @@ static mgr_status cuda_fail(mgr_handle h, const char *where) {
     char buf[256];
     snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
     return fail(h, e == cudaErrorMemoryAllocation ? MGR_ERR_NOMEM : MGR_ERR_CUDA, buf);
+}
+
+// RAII scope around one kernel launch: counts it, and when profiling is on
+// records an event pair tagged by name and algorithmic bytes.
+struct KScope {
+    mgr_handle h;
+    long long idx = -1;
+    KScope(mgr_handle hh, const char *name, int level, double bytes) : h(hh) {
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        Prof &P = h->prof;
+        if (!P.on) return;
+        char buf[96];
+        if (level >= 0) snprintf(buf, sizeof buf, "%s[L%d]", name, level);
+        else snprintf(buf, sizeof buf, "%s", name);
+        int tag = -1;
+        for (size_t t = 0; t < P.names.size(); t++)
+            if (P.names[t] == buf) { tag = (int)t; break; }
+        if (tag < 0) {
+            tag = (int)P.names.size();
+            P.names.push_back(buf); P.ms.push_back(0.0); P.bytes.push_back(bytes); P.cnt.push_back(0);
+        }
+        if (P.pool.size() < 2 * (P.used + 1)) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a); cudaEventCreate(&b);
+            P.pool.push_back(a); P.pool.push_back(b);
+        }
+        idx = (long long)P.used++;
+        P.ptag.resize(P.used);
+        P.ptag[idx] = tag;
+        cudaEventRecord(P.pool[2 * idx], h->s);
+    }
+    ~KScope() {
+        if (idx >= 0) cudaEventRecord(h->prof.pool[2 * idx + 1], h->s);
+    }
+};
+
+static void prof_resolve(mgr_handle h) {
+    Prof &P = h->prof;
+    if (!P.used) return;
+    cudaStreamSynchronize(h->s);
+    for (size_t i = 0; i < P.used; i++) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, P.pool[2 * i], P.pool[2 * i + 1]);
+        P.ms[P.ptag[i]] += ms;
+        P.cnt[P.ptag[i]] += 1;
+    }
+    P.used = 0;
 }
 
 extern "C" void mgr_options_default(mgr_options *o) {
@@ -424,6 +488,7 @@ static void amg_cycle(mgr_handle h, int k, const TV *r, TV *x, int trans) {
     cudaStream_t s = h->s;
     AmgLevel &L = h->amg[k];
     if (k == h->namg - 1) {
+        KScope ks(h, "coarsest_dense_solve", k, (double)h->nco * h->nco * 8 + 2.0 * h->nco * sizeof(TV));
         launch_dense_matvec<TV>(h->nco, trans ? h->coinvT : h->coinv, r, x, s);
         return;
     }
@@ -432,11 +497,25 @@ static void amg_cycle(mgr_handle h, int k, const TV *r, TV *x, int trans) {
     const T *d = Sel<T>::dinv(L);
     T *xw = Sel<T>::xw(L), *res = Sel<T>::res(L);
     AmgLevel &C = h->amg[k + 1];
-    launch_amg_smooth0_residual<T, TV>(A, av, d, r, xw, res, s);
-    launch_csr_spmv<T>(L.R, Sel<T>::v(L.R), res, Sel<T>::r(C), s);
+    const double ts = sizeof(T), tv = sizeof(TV);
+    double an = A.n, annz = A.nnz, nc = C.A.n;
+    {
+        KScope ks(h, "amg_smooth0_residual", k, annz * (ts + 4) + (an + 1) * 4 + an * (ts + tv) + 2 * an * ts);
+        launch_amg_smooth0_residual<T, TV>(A, av, d, r, xw, res, s);
+    }
+    {
+        KScope ks(h, "amg_restrict", k, (double)L.R.nnz * (ts + 4) + (nc + 1) * 4 + an * ts + nc * ts);
+        launch_csr_spmv<T>(L.R, Sel<T>::v(L.R), res, Sel<T>::r(C), s);
+    }
     amg_cycle<T, T>(h, k + 1, Sel<T>::r(C), Sel<T>::x(C), trans);
-    launch_csr_spmv_add<T>(L.P, Sel<T>::v(L.P), Sel<T>::x(C), xw, s);
-    launch_amg_post_smooth<T, TV>(A, av, d, r, xw, x, s);
+    {
+        KScope ks(h, "amg_prolong", k, (double)L.P.nnz * (ts + 4) + (an + 1) * 4 + nc * ts + 2 * an * ts);
+        launch_csr_spmv_add<T>(L.P, Sel<T>::v(L.P), Sel<T>::x(C), xw, s);
+    }
+    {
+        KScope ks(h, "amg_post_smooth", k, annz * (ts + 4) + (an + 1) * 4 + an * (2 * ts + 2 * tv));
+        launch_amg_post_smooth<T, TV>(A, av, d, r, xw, x, s);
+    }
 }
 
 // MGR level l forward cycle (Algorithm 1): v (TV) -> z (TV)
@@ -448,14 +527,29 @@ static void mgr_cycle(mgr_handle h, int l, const TV *v, TV *z) {
     T *zF = Sel<T>::zF(L), *rF = Sel<T>::rF(L), *vC = Sel<T>::vC(L), *eC = Sel<T>::eC(L);
     const T *dinv = Sel<T>::dinv(L);
     T om = (T)L.omega;
-    launch_frelax_first<T, TV>(L.nF, L.fidx, L.gstart, L.gsize, dinv, om, v, zF, s);
+    const double ts = sizeof(T), tv = sizeof(TV);
+    double nF = L.nF, nC = L.nC, gs = L.relax == 2 ? 4.0 : 1.0;
+    {
+        KScope ks(h, "mgr_frelax_first", l, nF * (gs * ts + 4 + tv + ts + (L.relax == 2 ? 8 : 0)));
+        launch_frelax_first<T, TV>(L.nF, L.fidx, L.gstart, L.gsize, dinv, om, v, zF, s);
+    }
     for (int sw = 1; sw < L.sweeps; sw++) {
-        launch_frelax_residual<T, TV>(L.AFF, Sel<T>::v(L.AFF), L.fidx, v, zF, rF, s);
+        {
+            KScope ks(h, "mgr_frelax_residual", l, (double)L.AFF.nnz * (ts + 4) + (nF + 1) * 4 + nF * (4 + tv + 2 * ts));
+            launch_frelax_residual<T, TV>(L.AFF, Sel<T>::v(L.AFF), L.fidx, v, zF, rF, s);
+        }
+        KScope ks(h, "mgr_frelax_update", l, nF * (gs * ts + 3 * ts + 8));
         launch_frelax_update<T>(L.nF, L.gstart, L.gsize, dinv, om, rF, zF, 0, s);
     }
-    launch_mgr_restrict<T, TV>(L.ACF, Sel<T>::v(L.ACF), L.cidx, v, zF, vC, s);
+    {
+        KScope ks(h, "mgr_restrict", l, (double)L.ACF.nnz * (ts + 4) + (nC + 1) * 4 + nF * ts + nC * (4 + tv + ts));
+        launch_mgr_restrict<T, TV>(L.ACF, Sel<T>::v(L.ACF), L.cidx, v, zF, vC, s);
+    }
     mgr_cycle<T, T>(h, l + 1, vC, eC);
-    launch_mgr_interp<T, TV>(L.W, Sel<T>::v(L.W), L.nC, L.fidx, L.cidx, zF, eC, z, s);
+    {
+        KScope ks(h, "mgr_interp", l, (double)L.W.nnz * (ts + 4) + (nF + 1) * 4 + nC * (ts + 4 + tv) + nF * (ts + 4 + tv));
+        launch_mgr_interp<T, TV>(L.W, Sel<T>::v(L.W), L.nC, L.fidx, L.cidx, zF, eC, z, s);
+    }
 }
 
 // exact transpose of mgr_cycle:
@@ -468,24 +562,34 @@ static void mgr_cycle_t(mgr_handle h, int l, const TV *v, TV *z) {
     T *zF = Sel<T>::zF(L), *rF = Sel<T>::rF(L), *vC = Sel<T>::vC(L), *eC = Sel<T>::eC(L);
     const T *dinv = Sel<T>::dinv(L);
     T om = (T)L.omega;
-    launch_gather<T, TV>(L.fidx, L.nF, v, zF, s);                 // zF <- v_F (scratch)
-    launch_csr_axpy_gather<T, TV>(L.WT, Sel<T>::v(L.WT), zF, L.cidx, v, (T)1, vC, s);
+    const double ts = sizeof(T), tv = sizeof(TV);
+    double nF = L.nF, nC = L.nC, gs = L.relax == 2 ? 4.0 : 1.0;
+    { KScope ks(h, "mgrT_gather", l, nF * (4 + tv + ts));
+      launch_gather<T, TV>(L.fidx, L.nF, v, zF, s); }               // zF <- v_F (scratch)
+    { KScope ks(h, "mgrT_restrict", l, (double)L.WT.nnz * (ts + 4) + (nC + 1) * 4 + nF * ts + nC * (4 + tv + ts));
+      launch_csr_axpy_gather<T, TV>(L.WT, Sel<T>::v(L.WT), zF, L.cidx, v, (T)1, vC, s); }
     mgr_cycle_t<T, T>(h, l + 1, vC, eC);
-    launch_csr_axpy_gather<T, TV>(L.ACFT, Sel<T>::v(L.ACFT), eC, L.fidx, v, (T)-1, rF, s);  // y_F
+    { KScope ks(h, "mgrT_interp", l, (double)L.ACFT.nnz * (ts + 4) + (nF + 1) * 4 + nC * ts + nF * (4 + tv + ts));
+      launch_csr_axpy_gather<T, TV>(L.ACFT, Sel<T>::v(L.ACFT), eC, L.fidx, v, (T)-1, rF, s); }  // y_F
     // K^T y_F: sweeps of z += omega D^{-T} (y - A_FF^T z) from z = 0
     cudaMemsetAsync(zF, 0, sizeof(T) * L.nF, s);
-    launch_frelax_update<T>(L.nF, L.gstart, L.gsize, dinv, om, rF, zF, 1, s);
+    { KScope ks(h, "mgrT_frelax_update", l, nF * (gs * ts + 3 * ts + 8));
+      launch_frelax_update<T>(L.nF, L.gstart, L.gsize, dinv, om, rF, zF, 1, s); }
     if (L.sweeps > 1) {
         // keep y_F in vC's tail is unsafe; y_F must survive: copy to eC-sized scratch is not
         // possible (sizes differ), so rebuild it from v each sweep.
         for (int sw = 1; sw < L.sweeps; sw++) {
             // rF <- y_F - A_FF^T z  with y_F = v_F - A_CF^T e_C
-            launch_csr_axpy_gather<T, TV>(L.ACFT, Sel<T>::v(L.ACFT), eC, L.fidx, v, (T)-1, rF, s);
-            launch_csr_axpy_gather<T, T>(L.AFFT, Sel<T>::v(L.AFFT), zF, L.fiota, rF, (T)-1, rF, s);
-            launch_frelax_update<T>(L.nF, L.gstart, L.gsize, dinv, om, rF, zF, 1, s);
+            { KScope ks(h, "mgrT_interp", l, (double)L.ACFT.nnz * (ts + 4) + (nF + 1) * 4 + nC * ts + nF * (4 + tv + ts));
+              launch_csr_axpy_gather<T, TV>(L.ACFT, Sel<T>::v(L.ACFT), eC, L.fidx, v, (T)-1, rF, s); }
+            { KScope ks(h, "mgrT_frelax_residual", l, (double)L.AFFT.nnz * (ts + 4) + (nF + 1) * 4 + nF * (4 + 3 * ts));
+              launch_csr_axpy_gather<T, T>(L.AFFT, Sel<T>::v(L.AFFT), zF, L.fiota, rF, (T)-1, rF, s); }
+            { KScope ks(h, "mgrT_frelax_update", l, nF * (gs * ts + 3 * ts + 8));
+              launch_frelax_update<T>(L.nF, L.gstart, L.gsize, dinv, om, rF, zF, 1, s); }
         }
     }
-    launch_scatter2<T, TV>(L.nF, L.nC, L.fidx, L.cidx, zF, eC, z, s);
+    { KScope ks(h, "mgrT_scatter", l, (nF + nC) * (4 + ts + tv));
+      launch_scatter2<T, TV>(L.nF, L.nC, L.fidx, L.cidx, zF, eC, z, s); }
 }
 
 static void vcycle(mgr_handle h, const double *v, double *z, int trans) {
@@ -498,12 +602,19 @@ static void vcycle(mgr_handle h, const double *v, double *z, int trans) {
     }
 }
 
+static double outer_bytes(mgr_handle h) {
+    double b = h->b;
+    return (double)h->nnzb * (b * b * 8 + 4) + (h->nb + 1.0) * 4 + 2.0 * h->n * 8;
+}
+
 static void outer_spmv(mgr_handle h, const double *x, double *y, int trans) {
+    KScope ks(h, trans ? "spmv_AT" : "spmv_A", -1, outer_bytes(h));
     if (trans) launch_csr_spmv<double>(h->A0T, h->A0T.v, x, y, h->s);
     else launch_bsr_spmv(h->nb, h->b, h->brp, h->bci, h->bval, x, y, 1.0, 0.0, h->s);
 }
 
 static void outer_residual(mgr_handle h, const double *x, const double *bvec, double *y, int trans) {
+    KScope ks(h, trans ? "residual_AT" : "residual_A", -1, outer_bytes(h) + h->n * 8.0);
     if (trans) launch_csr_residual(h->A0T, x, bvec, y, h->s);
     else launch_bsr_residual(h->nb, h->b, h->brp, h->bci, h->bval, x, bvec, y, h->s);
 }
@@ -540,13 +651,21 @@ static void arnoldi_step(mgr_handle h, int j, int trans, double tol_abs) {
     double *vj = K.V + j * n, *zj = K.Z + j * n, *w = K.V + (j + 1) * n;
     vcycle(h, vj, zj, trans);
     outer_spmv(h, zj, w, trans);
-    launch_multidot(K.V, n, j + 2, w, (int)n, K.partial, K.nblk, s);
-    launch_finalize_sum(K.partial, K.nblk, j + 2, K.h1, 0, s);
-    launch_update_dot(K.V, n, j + 1, K.h1, w, (int)n, K.partial, K.nblk, 0, s);
-    launch_finalize_sum(K.partial, K.nblk, j + 1, K.h2, 0, s);
-    launch_update_dot(K.V, n, j + 1, K.h2, w, (int)n, K.partial, K.nblk, 1, s);
-    launch_finalize_sum(K.partial, K.nblk, 1, K.nrm2, 0, s);
-    launch_arnoldi_finish(j, K.m, K.h1, K.h2, K.nrm2, K.H, K.cs, K.sn, K.g, K.hn, K.stat, tol_abs, s);
+    double nd = (double)n;
+    { KScope ks(h, "arnoldi_multidot", -1, (j + 2) * nd * 8);
+      launch_multidot(K.V, n, j + 2, w, (int)n, K.partial, K.nblk, s); }
+    { KScope ks(h, "arnoldi_reduce", -1, (double)K.nblk * (j + 2) * 8);
+      launch_finalize_sum(K.partial, K.nblk, j + 2, K.h1, 0, s); }
+    { KScope ks(h, "arnoldi_update_dot", -1, (j + 1) * nd * 8 + 2 * nd * 8);
+      launch_update_dot(K.V, n, j + 1, K.h1, w, (int)n, K.partial, K.nblk, 0, s); }
+    { KScope ks(h, "arnoldi_reduce", -1, (double)K.nblk * (j + 1) * 8);
+      launch_finalize_sum(K.partial, K.nblk, j + 1, K.h2, 0, s); }
+    { KScope ks(h, "arnoldi_update_norm", -1, (j + 1) * nd * 8 + 2 * nd * 8);
+      launch_update_dot(K.V, n, j + 1, K.h2, w, (int)n, K.partial, K.nblk, 1, s); }
+    { KScope ks(h, "arnoldi_reduce", -1, (double)K.nblk * 8);
+      launch_finalize_sum(K.partial, K.nblk, 1, K.nrm2, 0, s); }
+    { KScope ks(h, "givens", -1, 0.0);
+      launch_arnoldi_finish(j, K.m, K.h1, K.h2, K.nrm2, K.H, K.cs, K.sn, K.g, K.hn, K.stat, tol_abs, s); }
     cudaMemcpyAsync(K.hstat, K.stat, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
 }
 
@@ -559,8 +678,10 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
     cudaStream_t s = h->s;
     long long n = K.n;
     int m = K.m;
-    launch_dot_partial(b, b, (int)n, K.partial, K.nblk, s);
-    launch_finalize_sum(K.partial, K.nblk, 1, K.beta, 1, s);
+    { KScope ks(h, "norm", -1, n * 8.0);
+      launch_dot_partial(b, b, (int)n, K.partial, K.nblk, s); }
+    { KScope ks(h, "arnoldi_reduce", -1, (double)K.nblk * 8);
+      launch_finalize_sum(K.partial, K.nblk, 1, K.beta, 1, s); }
     double bn = 0.0;
     cudaMemcpyAsync(&bn, K.beta, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
@@ -578,8 +699,10 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
         double tol_abs = rtol * bn;
         for (;;) {
             outer_residual(h, x, b, K.r, trans);
-            launch_dot_partial(K.r, K.r, (int)n, K.partial, K.nblk, s);
-            launch_finalize_sum(K.partial, K.nblk, 1, K.beta, 1, s);
+            { KScope ks(h, "norm", -1, n * 8.0);
+              launch_dot_partial(K.r, K.r, (int)n, K.partial, K.nblk, s); }
+            { KScope ks(h, "arnoldi_reduce", -1, (double)K.nblk * 8);
+              launch_finalize_sum(K.partial, K.nblk, 1, K.beta, 1, s); }
             double beta = 0.0;
             cudaMemcpyAsync(&beta, K.beta, sizeof(double), cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
@@ -588,8 +711,10 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
             if (!isfinite(beta)) { st = MGR_ERR_INVALID; h->err = "residual is not finite"; break; }
             if (beta <= tol_abs) { st = MGR_OK; break; }
             if (it >= maxit) break;
-            launch_vec_scale(K.r, K.V, K.beta, nullptr, 1, (int)n, s);
-            launch_init_g(K.g, m, K.beta, s);
+            { KScope ks(h, "vec_scale", -1, n * 16.0);
+              launch_vec_scale(K.r, K.V, K.beta, nullptr, 1, (int)n, s); }
+            { KScope ks(h, "givens", -1, 0.0);
+              launch_init_g(K.g, m, K.beta, s); }
             int k = 0;
             for (int j = 0; j < m && it < maxit; j++) {
                 arnoldi_step(h, j, trans, tol_abs);
@@ -601,11 +726,14 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
                 int conv = K.hstat[1] != 0.0, brk = K.hstat[2] != 0.0;
                 if (!isfinite(est)) { st = MGR_ERR_INVALID; break; }
                 if (conv || brk) break;
+                KScope ks(h, "vec_scale", -1, n * 16.0);
                 launch_vec_scale(K.V + (j + 1) * n, K.V + (j + 1) * n, K.hn, nullptr, 1, (int)n, s);
             }
             if (st == MGR_ERR_INVALID) { h->err = "preconditioned residual is not finite"; break; }
-            launch_solve_upper(k, m, K.H, K.g, K.y, s);
-            launch_multi_axpy(K.Z, n, k, K.y, x, (int)n, s);
+            { KScope ks(h, "givens", -1, 0.0);
+              launch_solve_upper(k, m, K.H, K.g, K.y, s); }
+            { KScope ks(h, "update_x", -1, (k + 2.0) * n * 8);
+              launch_multi_axpy(K.Z, n, k, K.y, x, (int)n, s); }
         }
     }
     cudaStreamSynchronize(s);
@@ -667,6 +795,7 @@ extern "C" void mgr_free(mgr_handle h) {
     for (int d = 0; d < 2; d++)
         for (auto g : h->kr.graphs[d]) if (g) cudaGraphExecDestroy(g);
     if (h->kr.hstat) cudaFreeHost(h->kr.hstat);
+    for (auto e : h->prof.pool) cudaEventDestroy(e);
     h->ar.free_all();
     delete h;
 }
@@ -731,5 +860,36 @@ extern "C" mgr_status mgr_get_dinv(mgr_handle h, int32_t level, double *dinv, in
 extern "C" mgr_status mgr_get_info(mgr_handle h, int32_t *out) {
     if (!h || !out) return fail(h, MGR_ERR_INVALID, "NULL argument");
     out[0] = h->nlev; out[1] = h->namg; out[2] = h->n;
+    return MGR_OK;
+}
+
+extern "C" int64_t mgr_launch_count(void) { return g_launches.load(); }
+
+extern "C" mgr_status mgr_profile(mgr_handle h, int32_t on) {
+    if (!h) return fail(h, MGR_ERR_INVALID, "NULL handle");
+    prof_resolve(h);
+    Prof &P = h->prof;
+    P.names.clear(); P.ms.clear(); P.bytes.clear(); P.cnt.clear(); P.ptag.clear(); P.used = 0;
+    P.on = on != 0;
+    return MGR_OK;
+}
+
+extern "C" int32_t mgr_profile_entries(mgr_handle h) {
+    if (!h) return 0;
+    prof_resolve(h);
+    return (int32_t)h->prof.names.size();
+}
+
+extern "C" mgr_status mgr_profile_entry(mgr_handle h, int32_t i, char *name, int32_t name_cap,
+                                        double *total_ms, int64_t *launches,
+                                        double *bytes_per_launch) {
+    if (!h) return fail(h, MGR_ERR_INVALID, "NULL handle");
+    prof_resolve(h);
+    Prof &P = h->prof;
+    if (i < 0 || i >= (int32_t)P.names.size()) return fail(h, MGR_ERR_INVALID, "no such entry");
+    if (name && name_cap > 0) { strncpy(name, P.names[i].c_str(), name_cap - 1); name[name_cap - 1] = 0; }
+    if (total_ms) *total_ms = P.ms[i];
+    if (launches) *launches = P.cnt[i];
+    if (bytes_per_launch) *bytes_per_launch = P.bytes[i];
     return MGR_OK;
 }

@@ -94,6 +94,13 @@ def lib(build_if_missing: bool = True):
     L.mgr_get_cf.argtypes = [vp, i32, vp]
     L.mgr_get_dinv.argtypes = [vp, i32, vp, vp]
     L.mgr_get_info.argtypes = [vp, vp]
+    L.mgr_launch_count.argtypes = []
+    L.mgr_launch_count.restype = C.c_int64
+    L.mgr_profile.argtypes = [vp, i32]
+    L.mgr_profile_entries.argtypes = [vp]
+    L.mgr_profile_entries.restype = i32
+    L.mgr_profile_entry.argtypes = [vp, i32, C.c_char_p, i32, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_double)]
     _lib = L
     return L
 
@@ -233,6 +240,24 @@ class MGRSolver:
         _check(lib().mgr_grad_values(self.h, self._vec(lam), self._vec(x), _ptr(dA)), self.h)
         return dA.view(self.nnzb, self.b, self.b)
 
+    # ---------------------------------------------------- instrumentation
+    def profile(self, on=True):
+        """Start (and reset) or stop per-kernel-class event timing."""
+        _check(lib().mgr_profile(self.h, int(bool(on))), self.h)
+
+    def profile_table(self):
+        """[{name, ms, launches, bytes_per_launch}] recorded since profile(True)."""
+        L = lib()
+        out = []
+        for i in range(L.mgr_profile_entries(self.h)):
+            buf = C.create_string_buffer(96)
+            ms, cnt, by = C.c_double(), C.c_int64(), C.c_double()
+            _check(L.mgr_profile_entry(self.h, i, buf, 96, C.byref(ms), C.byref(cnt),
+                                       C.byref(by)), self.h)
+            out.append(dict(name=buf.value.decode(), ms=ms.value, launches=cnt.value,
+                            bytes_per_launch=by.value))
+        return out
+
     # -------------------------------------------------------- inspection
     def info(self):
         out = np.zeros(3, np.int32)
@@ -276,3 +301,8 @@ def bsr_spmv(row_ptr, col_idx, val, b, x, y=None, alpha=1.0, beta=0.0, stream=No
     _check(lib().mgr_bsr_spmv(nb, int(b), _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x), _ptr(y),
                               float(alpha), float(beta), _stream_ptr(stream)))
     return y
+
+
+def launch_count() -> int:
+    """Kernel launches made by the library so far (all handles)."""
+    return int(lib().mgr_launch_count())
