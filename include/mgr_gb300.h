@@ -103,6 +103,7 @@ typedef struct {
     int32_t mgr_levels, amg_levels;
     int64_t level_rows[40], level_nnz[40];
     double operator_complexity;
+    int32_t reorth_steps;      /* Arnoldi steps that needed the second Gram-Schmidt pass */
 } mgr_solve_info;
 
 /* Defaults: Jacobi, 1 sweep, omega 1 on every level; theta 0.25, 25 AMG
@@ -114,7 +115,9 @@ void mgr_options_default(mgr_options *opt);
  * W = -D_FF^{-1} A_FC and the coarse operator A_{l+1} = A_CC + A_CF W (the
  * product R~ A P~ of Eq. 4 operators); then the AMG hierarchy of the final
  * block (strength, PMIS, extended+i, Galerkin P^T A P, dense inverse of the
- * coarsest grid).  stream: a cudaStream_t (NULL = legacy default stream).
+ * coarsest grid).  stream: a cudaStream_t for all of the handle's work; NULL
+ * makes the handle create its own blocking stream, which the legacy default
+ * stream orders against implicitly.
  * Errors: INVALID (pattern/labels/sizes, an empty F or C set), SINGULAR
  * (a zero diagonal or singular block in D_FF), NOMEM, CUDA.
  */

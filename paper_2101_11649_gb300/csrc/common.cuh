@@ -76,10 +76,12 @@ void launch_cast_f32(const double *in, float *out, long long n, cudaStream_t s);
 // ------------------------------------------------------------- solve phase
 // BSR y = alpha A x + beta y (b in 1..4) on FP64
 void launch_bsr_spmv(int nb, int b, const int *rp, const int *ci, const double *val,
-                     const double *x, double *y, double alpha, double beta, cudaStream_t s);
+                     const double *x, double *y, double alpha, double beta, cudaStream_t s,
+                     long long nnzb = 0);
 // y = bvec - A x  (residual) or y = A x when bvec == nullptr
 void launch_bsr_residual(int nb, int b, const int *rp, const int *ci, const double *val,
-                         const double *x, const double *bvec, double *y, cudaStream_t s);
+                         const double *x, const double *bvec, double *y, cudaStream_t s,
+                         long long nnzb = 0);
 
 // MGR level kernels, T = value/arith type, TV = type of the level's in/out vectors
 template <class T, class TV>
@@ -118,23 +120,32 @@ void launch_csr_spmv_add(const DCSR &A, const T *vals, const T *x, T *y, cudaStr
 template <class T, class TV>
 void launch_amg_post_smooth(const DCSR &A, const T *vals, const T *dinv, const TV *r, const T *x,
                             TV *xout, cudaStream_t s);
+template <class T, class TV>
+void launch_amg_residual(const DCSR &A, const T *vals, const T *x, const TV *r, T *res,
+                         cudaStream_t s);
+template <class T>
+void launch_restrict_scaled(const DCSR &R, const T *vals, const T *res, T *rc, const T *dc, T *xc,
+                            cudaStream_t s);
+template <class T, class TV>
+void launch_mgr_restrict_scaled(const DCSR &ACF, const T *vals, const int *cidx, const TV *v,
+                                const T *zF, T *vC, const T *d, T *x, cudaStream_t s);
+template <class T, class TV>
+void launch_scale(int n, const T *d, const TV *r, T *x, cudaStream_t s);
 template <class TV>
 void launch_dense_matvec(int n, const double *inv, const TV *r, TV *x, cudaStream_t s);
 template <class TV>
 void launch_copy_cast(const TV *in, double *out, int n, cudaStream_t s);
 
-// Krylov pieces (FP64)
-struct Krylov;
+// Krylov pieces (FP64); reductions finish in their last block (ticket)
 void launch_vec_scale(const double *x, double *y, const double *scale_num, const double *scale_den,
                       int invert, int n, cudaStream_t s);
-void launch_dot_partial(const double *x, const double *y, int n, double *partial, int nblk,
-                        cudaStream_t s);
-void launch_finalize_sum(const double *partial, int nblk, int nvec, double *out, int sqrt_out,
-                         cudaStream_t s);
-void launch_multidot(const double *V, long long ldv, int k, const double *w, int n,
-                     double *partial, int nblk, cudaStream_t s);
-void launch_update_dot(const double *V, long long ldv, int k, const double *h, double *w, int n,
-                       double *partial, int nblk, int mode, cudaStream_t s);
+void launch_dot(const double *x, const double *y, int n, double *partial, double *out,
+                unsigned *ticket, int sqrt_out, int nblk, cudaStream_t s);
+void launch_dots(const double *V, long long ldv, int k, const double *w, int n, double *partial,
+                 double *h, unsigned *ticket, const int *flag, int nblk, cudaStream_t s);
+void launch_update_norm(const double *V, long long ldv, int k, const double *h, double *w, int n,
+                        double *partial, double *nrm2, unsigned *ticket, int *flag, int mode,
+                        int nblk, cudaStream_t s);
 void launch_multi_axpy(const double *Z, long long ldz, int k, const double *y, double *x, int n,
                        cudaStream_t s);
 int multidot_blocks(int n);

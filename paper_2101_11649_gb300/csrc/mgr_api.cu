@@ -20,9 +20,9 @@ void launch_validate_bsr(int nb, int b, const int *rp, const int *ci, const doub
 void launch_csr_residual(const DCSR &A, const double *x, const double *bvec, double *y,
                          cudaStream_t s);
 void launch_transpose_dense(int n, const double *in, double *out, cudaStream_t s);
-void launch_arnoldi_finish(int j, int m, const double *h1, const double *h2, const double *nrm2,
-                           double *H, double *cs, double *sn, double *g, double *hn, double *stat,
-                           double tol_abs, cudaStream_t s);
+void launch_arnoldi_finish(int j, int m, const double *h1, const double *h2, const double *nrmA,
+                           const double *nrmB, const int *flag, double *H, double *cs, double *sn,
+                           double *g, double *hn, double *stat, const double *tol, cudaStream_t s);
 void launch_init_g(double *g, int m, const double *beta, cudaStream_t s);
 void launch_solve_upper(int k, int m, const double *H, const double *g, double *y, cudaStream_t s);
 void launch_iota(int *a, int n, cudaStream_t s);
@@ -57,7 +57,11 @@ struct Krylov {
     double *V = nullptr, *Z = nullptr, *r = nullptr;
     double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
     double *h1 = nullptr, *h2 = nullptr, *nrm2 = nullptr, *hn = nullptr, *beta = nullptr;
-    double *partial = nullptr, *stat = nullptr;
+    double *partial = nullptr, *stat = nullptr, *nrmB = nullptr;
+    unsigned *ticket = nullptr;
+    int *flag = nullptr;
+    double *tol = nullptr;     // device copy of rtol * |b|
+    long long graph_kernels[2][32] = {};
     double *hstat = nullptr;  // pinned host mirror of stat
     std::vector<cudaGraphExec_t> graphs[2];
 };
@@ -84,6 +88,7 @@ using namespace mgr;
 struct mgr_ctx {
     int dev = 0;
     cudaStream_t s = nullptr;
+    bool own_stream = false;  // created here when the caller passed the legacy default stream
     Arena ar;
     mgr_options opt;
     int nb = 0, b = 0, n = 0;
@@ -294,6 +299,12 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
     mgr_handle h = new mgr_ctx();
     cudaGetDevice(&h->dev);
     h->s = (cudaStream_t)stream;
+    if (!h->s) {
+        // the legacy default stream cannot be captured into graphs: use a
+        // blocking stream of our own, which it orders against implicitly
+        if (cudaStreamCreate(&h->s) != cudaSuccess) { delete h; return cuda_fail(nullptr, "stream"); }
+        h->own_stream = true;
+    }
     if (opt) h->opt = *opt; else mgr_options_default(&h->opt);
     if (h->opt.restart < 1) h->opt.restart = 1;
     if (h->opt.restart > 30) h->opt.restart = 30;
@@ -441,6 +452,13 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
     K.nrm2 = ar.alloc<double>(4); K.hn = ar.alloc<double>(4); K.beta = ar.alloc<double>(4);
     K.partial = ar.alloc<double>((size_t)K.nblk * 33 + 33);
     K.stat = ar.alloc<double>(8);
+    K.nrmB = ar.alloc<double>(4);
+    K.ticket = ar.alloc<unsigned>(4);
+    K.flag = ar.alloc<int>(4);
+    K.tol = ar.alloc<double>(2);
+    if (!K.nrmB || !K.ticket || !K.flag || !K.tol) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "Krylov workspace"); }
+    cudaMemsetAsync(K.ticket, 0, 4 * sizeof(unsigned), s);
+    cudaMemsetAsync(K.flag, 0, 4 * sizeof(int), s);
     cudaMallocHost(&K.hstat, 8 * sizeof(double));
     if (!K.V || !K.Z || !K.r || !K.H || !K.partial || !K.stat || !K.hstat) {
         mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "Krylov workspace");
@@ -481,8 +499,10 @@ template <> struct Sel<float> {
     static float *res(AmgLevel &L) { return L.res32; }
 };
 
-// AMG V(1,1) on level k: r (TV) -> x (TV).  trans uses A_k^T and the
-// transposed coarsest inverse (the exact transpose of the cycle).
+// AMG V(1,1) on level k: r (TV) -> x (TV).  On entry L.xw already holds the
+// pre-smoothed iterate D_k r (l1-Jacobi from zero), written by whoever
+// produced r.  trans uses A_k^T and the transposed coarsest inverse (the
+// exact transpose of the cycle).
 template <class T, class TV>
 static void amg_cycle(mgr_handle h, int k, const TV *r, TV *x, int trans) {
     cudaStream_t s = h->s;
@@ -497,15 +517,17 @@ static void amg_cycle(mgr_handle h, int k, const TV *r, TV *x, int trans) {
     const T *d = Sel<T>::dinv(L);
     T *xw = Sel<T>::xw(L), *res = Sel<T>::res(L);
     AmgLevel &C = h->amg[k + 1];
+    const bool c_coarsest = (k + 1 == h->namg - 1);
     const double ts = sizeof(T), tv = sizeof(TV);
     double an = A.n, annz = A.nnz, nc = C.A.n;
     {
-        KScope ks(h, "amg_smooth0_residual", k, annz * (ts + 4) + (an + 1) * 4 + an * (ts + tv) + 2 * an * ts);
-        launch_amg_smooth0_residual<T, TV>(A, av, d, r, xw, res, s);
+        KScope ks(h, "amg_residual", k, annz * (ts + 4) + (an + 1) * 4 + an * (2 * ts + tv));
+        launch_amg_residual<T, TV>(A, av, xw, r, res, s);
     }
     {
-        KScope ks(h, "amg_restrict", k, (double)L.R.nnz * (ts + 4) + (nc + 1) * 4 + an * ts + nc * ts);
-        launch_csr_spmv<T>(L.R, Sel<T>::v(L.R), res, Sel<T>::r(C), s);
+        KScope ks(h, "amg_restrict", k, (double)L.R.nnz * (ts + 4) + (nc + 1) * 4 + an * ts + nc * ts * (c_coarsest ? 1 : 3));
+        if (c_coarsest) launch_csr_spmv<T>(L.R, Sel<T>::v(L.R), res, Sel<T>::r(C), s);
+        else launch_restrict_scaled<T>(L.R, Sel<T>::v(L.R), res, Sel<T>::r(C), Sel<T>::dinv(C), Sel<T>::xw(C), s);
     }
     amg_cycle<T, T>(h, k + 1, Sel<T>::r(C), Sel<T>::x(C), trans);
     {
@@ -518,11 +540,24 @@ static void amg_cycle(mgr_handle h, int k, const TV *r, TV *x, int trans) {
     }
 }
 
+// x_0 = D_0 r for the AMG entry when r is not produced by a fused epilogue
+template <class T, class TV>
+static void amg_prepare(mgr_handle h, const TV *r) {
+    if (h->namg < 2) return;
+    AmgLevel &L = h->amg[0];
+    KScope ks(h, "amg_scale", 0, (double)L.A.n * (2 * sizeof(T) + sizeof(TV)));
+    launch_scale<T, TV>(L.A.n, Sel<T>::dinv(L), r, Sel<T>::xw(L), h->s);
+}
+
 // MGR level l forward cycle (Algorithm 1): v (TV) -> z (TV)
 template <class T, class TV>
 static void mgr_cycle(mgr_handle h, int l, const TV *v, TV *z) {
     cudaStream_t s = h->s;
-    if (l == h->nlev) { amg_cycle<T, TV>(h, 0, v, z, 0); return; }
+    if (l == h->nlev) {
+        if (l == 0) amg_prepare<T, TV>(h, v);
+        amg_cycle<T, TV>(h, 0, v, z, 0);
+        return;
+    }
     MgrLevel &L = h->lev[l];
     T *zF = Sel<T>::zF(L), *rF = Sel<T>::rF(L), *vC = Sel<T>::vC(L), *eC = Sel<T>::eC(L);
     const T *dinv = Sel<T>::dinv(L);
@@ -542,8 +577,11 @@ static void mgr_cycle(mgr_handle h, int l, const TV *v, TV *z) {
         launch_frelax_update<T>(L.nF, L.gstart, L.gsize, dinv, om, rF, zF, 0, s);
     }
     {
-        KScope ks(h, "mgr_restrict", l, (double)L.ACF.nnz * (ts + 4) + (nC + 1) * 4 + nF * ts + nC * (4 + tv + ts));
-        launch_mgr_restrict<T, TV>(L.ACF, Sel<T>::v(L.ACF), L.cidx, v, zF, vC, s);
+        const bool fuse = (l + 1 == h->nlev) && h->namg > 1;
+        KScope ks(h, "mgr_restrict", l, (double)L.ACF.nnz * (ts + 4) + (nC + 1) * 4 + nF * ts + nC * (4 + tv + ts + (fuse ? 2 * ts : 0)));
+        if (fuse) launch_mgr_restrict_scaled<T, TV>(L.ACF, Sel<T>::v(L.ACF), L.cidx, v, zF, vC,
+                                                    Sel<T>::dinv(h->amg[0]), Sel<T>::xw(h->amg[0]), s);
+        else launch_mgr_restrict<T, TV>(L.ACF, Sel<T>::v(L.ACF), L.cidx, v, zF, vC, s);
     }
     mgr_cycle<T, T>(h, l + 1, vC, eC);
     {
@@ -557,7 +595,11 @@ static void mgr_cycle(mgr_handle h, int l, const TV *v, TV *z) {
 template <class T, class TV>
 static void mgr_cycle_t(mgr_handle h, int l, const TV *v, TV *z) {
     cudaStream_t s = h->s;
-    if (l == h->nlev) { amg_cycle<T, TV>(h, 0, v, z, 1); return; }
+    if (l == h->nlev) {
+        amg_prepare<T, TV>(h, v);
+        amg_cycle<T, TV>(h, 0, v, z, 1);
+        return;
+    }
     MgrLevel &L = h->lev[l];
     T *zF = Sel<T>::zF(L), *rF = Sel<T>::rF(L), *vC = Sel<T>::vC(L), *eC = Sel<T>::eC(L);
     const T *dinv = Sel<T>::dinv(L);
@@ -610,13 +652,13 @@ static double outer_bytes(mgr_handle h) {
 static void outer_spmv(mgr_handle h, const double *x, double *y, int trans) {
     KScope ks(h, trans ? "spmv_AT" : "spmv_A", -1, outer_bytes(h));
     if (trans) launch_csr_spmv<double>(h->A0T, h->A0T.v, x, y, h->s);
-    else launch_bsr_spmv(h->nb, h->b, h->brp, h->bci, h->bval, x, y, 1.0, 0.0, h->s);
+    else launch_bsr_spmv(h->nb, h->b, h->brp, h->bci, h->bval, x, y, 1.0, 0.0, h->s, h->nnzb);
 }
 
 static void outer_residual(mgr_handle h, const double *x, const double *bvec, double *y, int trans) {
     KScope ks(h, trans ? "residual_AT" : "residual_A", -1, outer_bytes(h) + h->n * 8.0);
     if (trans) launch_csr_residual(h->A0T, x, bvec, y, h->s);
-    else launch_bsr_residual(h->nb, h->b, h->brp, h->bci, h->bval, x, bvec, y, h->s);
+    else launch_bsr_residual(h->nb, h->b, h->brp, h->bci, h->bval, x, bvec, y, h->s, h->nnzb);
 }
 
 extern "C" mgr_status mgr_apply(mgr_handle h, const double *v, double *z) {
@@ -641,10 +683,11 @@ extern "C" mgr_status mgr_spmv(mgr_handle h, const double *x, double *y) {
 }
 
 // ----------------------------------------------------------------- FGMRES
-// One Arnoldi step j: z_j = M^{-1} v_j, w = A z_j (stored in V_{j+1}), CGS2
-// against V_0..V_j with the norm of w taken in the first pass, Givens update,
-// status to the pinned host mirror.
-static void arnoldi_step(mgr_handle h, int j, int trans, double tol_abs) {
+// One Arnoldi step j: z_j = M^{-1} v_j, w = A z_j (stored in V_{j+1}),
+// classical Gram-Schmidt against V_0..V_j with the norm of w taken in the
+// same pass and a conditional second pass, Givens update, status to the
+// pinned host mirror, then v_{j+1} = w / h_{j+1,j}.
+static void arnoldi_step(mgr_handle h, int j, int trans) {
     Krylov &K = h->kr;
     cudaStream_t s = h->s;
     long long n = K.n;
@@ -652,21 +695,54 @@ static void arnoldi_step(mgr_handle h, int j, int trans, double tol_abs) {
     vcycle(h, vj, zj, trans);
     outer_spmv(h, zj, w, trans);
     double nd = (double)n;
-    { KScope ks(h, "arnoldi_multidot", -1, (j + 2) * nd * 8);
-      launch_multidot(K.V, n, j + 2, w, (int)n, K.partial, K.nblk, s); }
-    { KScope ks(h, "arnoldi_reduce", -1, (double)K.nblk * (j + 2) * 8);
-      launch_finalize_sum(K.partial, K.nblk, j + 2, K.h1, 0, s); }
-    { KScope ks(h, "arnoldi_update_dot", -1, (j + 1) * nd * 8 + 2 * nd * 8);
-      launch_update_dot(K.V, n, j + 1, K.h1, w, (int)n, K.partial, K.nblk, 0, s); }
-    { KScope ks(h, "arnoldi_reduce", -1, (double)K.nblk * (j + 1) * 8);
-      launch_finalize_sum(K.partial, K.nblk, j + 1, K.h2, 0, s); }
-    { KScope ks(h, "arnoldi_update_norm", -1, (j + 1) * nd * 8 + 2 * nd * 8);
-      launch_update_dot(K.V, n, j + 1, K.h2, w, (int)n, K.partial, K.nblk, 1, s); }
-    { KScope ks(h, "arnoldi_reduce", -1, (double)K.nblk * 8);
-      launch_finalize_sum(K.partial, K.nblk, 1, K.nrm2, 0, s); }
+    int k = j + 1;
+    // first pass: projections on V_0..V_j and |w|^2 (w = V_{j+1} itself)
+    { KScope ks(h, "arnoldi_dots", -1, (k + 1) * nd * 8);
+      launch_dots(K.V, n, k + 1, w, (int)n, K.partial, K.h1, K.ticket, nullptr, K.nblk, s); }
+    { KScope ks(h, "arnoldi_update_norm", -1, k * nd * 8 + 2 * nd * 8);
+      launch_update_norm(K.V, n, k, K.h1, w, (int)n, K.partial, K.nrm2, K.ticket, K.flag, 1, K.nblk, s); }
+    // second pass only when the first cancelled most of w (device flag)
+    { KScope ks(h, "arnoldi_reorth", -1, 0.0);
+      launch_dots(K.V, n, k, w, (int)n, K.partial, K.h2, K.ticket, K.flag, K.nblk, s); }
+    { KScope ks(h, "arnoldi_reorth", -1, 0.0);
+      launch_update_norm(K.V, n, k, K.h2, w, (int)n, K.partial, K.nrmB, K.ticket, K.flag, 2, K.nblk, s); }
     { KScope ks(h, "givens", -1, 0.0);
-      launch_arnoldi_finish(j, K.m, K.h1, K.h2, K.nrm2, K.H, K.cs, K.sn, K.g, K.hn, K.stat, tol_abs, s); }
-    cudaMemcpyAsync(K.hstat, K.stat, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+      launch_arnoldi_finish(j, K.m, K.h1, K.h2, K.nrm2, K.nrmB, K.flag, K.H, K.cs, K.sn, K.g, K.hn, K.stat, K.tol, s); }
+    cudaMemcpyAsync(K.hstat, K.stat, 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    { KScope ks(h, "vec_scale", -1, nd * 16);
+      launch_vec_scale(w, w, K.hn, nullptr, 1, (int)n, s); }
+}
+
+// Run step j, from a captured CUDA graph when enabled (one graph per
+// (direction, j), captured on first use and replayed afterwards; the
+// kernels read every per-solve scalar from device memory).
+static cudaError_t run_step(mgr_handle h, int j, int trans) {
+    Krylov &K = h->kr;
+    if (!h->opt.use_graphs || h->prof.on) {
+        arnoldi_step(h, j, trans);
+        return cudaGetLastError();
+    }
+    auto &gv = K.graphs[trans];
+    if ((int)gv.size() < K.m) gv.resize(K.m, nullptr);
+    if (!gv[j]) {
+        cudaGraph_t g = nullptr;
+        long long before = g_launches.load();
+        cudaError_t e = cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        arnoldi_step(h, j, trans);
+        e = cudaStreamEndCapture(h->s, &g);
+        if (e != cudaSuccess) return e;
+        // the launches recorded during capture execute at replay time
+        K.graph_kernels[trans][j] = g_launches.load() - before;
+        g_launches.fetch_sub(K.graph_kernels[trans][j]);
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        gv[j] = ex;
+    }
+    g_launches.fetch_add(K.graph_kernels[trans][j]);
+    return cudaGraphLaunch(gv[j], h->s);
 }
 
 static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, int maxit, int trans,
@@ -679,15 +755,13 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
     long long n = K.n;
     int m = K.m;
     { KScope ks(h, "norm", -1, n * 8.0);
-      launch_dot_partial(b, b, (int)n, K.partial, K.nblk, s); }
-    { KScope ks(h, "arnoldi_reduce", -1, (double)K.nblk * 8);
-      launch_finalize_sum(K.partial, K.nblk, 1, K.beta, 1, s); }
+      launch_dot(b, b, (int)n, K.partial, K.beta, K.ticket, 1, K.nblk, s); }
     double bn = 0.0;
     cudaMemcpyAsync(&bn, K.beta, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     if (cudaGetLastError() != cudaSuccess) return cuda_fail(h, "solve");
     if (!isfinite(bn)) return fail(h, MGR_ERR_INVALID, "right-hand side is not finite");
-    int it = 0;
+    int it = 0, reorth = 0;
     double relres = 0.0;
     mgr_status st = MGR_ERR_NOT_CONVERGED;
     if (bn == 0.0) {
@@ -697,12 +771,11 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
         st = MGR_OK;
     } else {
         double tol_abs = rtol * bn;
+        cudaMemcpyAsync(K.tol, &tol_abs, sizeof(double), cudaMemcpyHostToDevice, s);
         for (;;) {
             outer_residual(h, x, b, K.r, trans);
             { KScope ks(h, "norm", -1, n * 8.0);
-              launch_dot_partial(K.r, K.r, (int)n, K.partial, K.nblk, s); }
-            { KScope ks(h, "arnoldi_reduce", -1, (double)K.nblk * 8);
-              launch_finalize_sum(K.partial, K.nblk, 1, K.beta, 1, s); }
+              launch_dot(K.r, K.r, (int)n, K.partial, K.beta, K.ticket, 1, K.nblk, s); }
             double beta = 0.0;
             cudaMemcpyAsync(&beta, K.beta, sizeof(double), cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
@@ -717,17 +790,16 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
               launch_init_g(K.g, m, K.beta, s); }
             int k = 0;
             for (int j = 0; j < m && it < maxit; j++) {
-                arnoldi_step(h, j, trans, tol_abs);
+                cudaError_t ge = run_step(h, j, trans);
                 cudaStreamSynchronize(s);
-                if (cudaGetLastError() != cudaSuccess) return cuda_fail(h, "Arnoldi step");
+                if (ge != cudaSuccess || cudaGetLastError() != cudaSuccess) return cuda_fail(h, "Arnoldi step");
                 it++;
                 k = j + 1;
                 double est = K.hstat[0];
                 int conv = K.hstat[1] != 0.0, brk = K.hstat[2] != 0.0;
                 if (!isfinite(est)) { st = MGR_ERR_INVALID; break; }
+                if (K.hstat[4] != 0.0) reorth++;
                 if (conv || brk) break;
-                KScope ks(h, "vec_scale", -1, n * 16.0);
-                launch_vec_scale(K.V + (j + 1) * n, K.V + (j + 1) * n, K.hn, nullptr, 1, (int)n, s);
             }
             if (st == MGR_ERR_INVALID) { h->err = "preconditioned residual is not finite"; break; }
             { KScope ks(h, "givens", -1, 0.0);
@@ -755,6 +827,7 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
             if (k == 0) base = h->amg[k].A.nnz;
         }
         info->operator_complexity = base > 0 ? tot / base : 0.0;
+        info->reorth_steps = reorth;
     }
     if (st == MGR_ERR_NOT_CONVERGED) return fail(h, st, "maximum iterations reached");
     if (st != MGR_OK) return fail(h, st, h->err);
@@ -797,6 +870,7 @@ extern "C" void mgr_free(mgr_handle h) {
     if (h->kr.hstat) cudaFreeHost(h->kr.hstat);
     for (auto e : h->prof.pool) cudaEventDestroy(e);
     h->ar.free_all();
+    if (h->own_stream) cudaStreamDestroy(h->s);
     delete h;
 }
 

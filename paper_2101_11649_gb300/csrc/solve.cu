@@ -1,8 +1,13 @@
 // Solve-phase kernels: sparse products, the MGR and AMG cycle steps, and
-// the FGMRES reductions.  All are bandwidth-bound gathers over CSR/BSR
-// rows; a row is owned by a group of G lanes (G from the mean row length),
-// partial sums are combined with warp shuffles, and every reduction uses a
-// fixed tree so repeated runs give identical bits.
+// the FGMRES reductions.  All are HBM-bandwidth-bound.
+//
+// CSR rows are processed by a chunk engine: a warp owns R consecutive rows
+// (R chosen per matrix so that a chunk holds ~192 nonzeros), loads the
+// chunk's nonzeros with CU independent coalesced loads per lane, keeps the
+// products in shared memory, and each lane then sums one row in order.
+// Gathers and epilogues are functors, so every cycle step (residual,
+// smoothing, restriction, interpolation) is one pass over its matrix.
+// Every reduction uses a fixed order, so repeated runs give identical bits.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -11,13 +16,7 @@ namespace mgr {
 
 #define GRIDN(n, t) (unsigned)((((long long)(n)) + (t)-1) / (t) > 0 ? (((long long)(n)) + (t)-1) / (t) : 1)
 
-static inline int pick_group(long long nnz, int n) {
-    double avg = n > 0 ? (double)nnz / n : 0.0;
-    if (avg <= 5.0) return 4;
-    if (avg <= 12.5) return 8;
-    if (avg <= 24.0) return 16;
-    return 32;
-}
+static const int NUM_SMS = 152;
 
 template <int G, class T>
 __device__ __forceinline__ T group_sum(T s) {
@@ -26,84 +25,226 @@ __device__ __forceinline__ T group_sum(T s) {
     return s;
 }
 
-// sum_p v[p] * x[ci[p]] over row `row`, lanes of the group stride the row
-template <int G, class T, class XT>
-__device__ __forceinline__ T row_dot(const int *__restrict__ rp, const int *__restrict__ ci,
-                                     const T *__restrict__ v, const XT *__restrict__ x, int row,
-                                     bool valid, int lane) {
-    T s = (T)0;
-    if (valid) {
-        int p1 = __ldg(rp + row + 1);
-        for (int p = __ldg(rp + row) + lane; p < p1; p += G) s += __ldg(v + p) * (T)__ldg(x + __ldg(ci + p));
-    }
-    return group_sum<G, T>(s);
+// ----------------------------------------------------------- chunk engine
+// A warp owns R consecutive rows (R a power of two, ~192 nonzeros per
+// chunk).  Phase 1 stages the chunk's values and column indices in shared
+// memory with CU independent coalesced loads per lane.  Phase 2 gives each
+// row G = 32/R lanes; lane j of a group runs one fused multiply-add chain
+// over a contiguous slice of its row, and the group combines its G partial
+// sums with a fixed shuffle tree.  This keeps the FP64 work at one FMA per
+// nonzero plus log2(G) adds per row (FP64 issue rate, not HBM, bounds FP64
+// sparse products on this part).
+constexpr int CU = 8;          // independent loads per lane per batch
+constexpr int CCAP = 384;      // nonzeros a warp stages in shared memory
+constexpr int CWARPS = 8;      // warps per block
+
+static inline int rows_per_warp(long long nnz, int n) {
+    double avg = n > 0 ? (double)nnz / n : 1.0;
+    if (avg < 1.0) avg = 1.0;
+    int r = 1;
+    while (r < 32 && (r * 2) * avg <= 192.0) r *= 2;
+    return r;
 }
 
-#define ROW_SETUP(G)                                                   \
-    int gtid = blockIdx.x * blockDim.x + threadIdx.x;                  \
-    int row = gtid / G;                                                \
-    int lane = threadIdx.x & (G - 1);                                  \
-    bool valid = row < n;
+template <int G, class T>
+__device__ __forceinline__ T group_tree(T s) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, G);
+    return s;
+}
+
+template <int R, class T, class XF, class EPI>
+__device__ __forceinline__ void chunk_rows(int r0, int r1, int p0, int cnt, const int *__restrict__ rp,
+                                           const int *__restrict__ ci, const T *__restrict__ v,
+                                           const XF &xf, const EPI &epi, T *sv, int *sc, int lane) {
+    constexpr int G = 32 / R;
+    // phase 1: stage values and columns
+#pragma unroll
+    for (int t = 0; t < CCAP / 32; t++) {
+        const int q = lane + 32 * t;
+        if (q < cnt) { sv[q] = __ldg(v + p0 + q); sc[q] = __ldg(ci + p0 + q); }
+    }
+    __syncwarp();
+    // phase 2: G lanes per row, contiguous slices
+    const int grp = lane / G, j = lane % G;
+    const int row = r0 + grp;
+    T s = (T)0;
+    if (row < r1) {
+        const int a = __ldg(rp + row) - p0, b = __ldg(rp + row + 1) - p0;
+        const int len = b - a, Lr = (len + G - 1) / G;
+        const int q0 = a + j * Lr, q1 = min(q0 + Lr, b);
+        for (int q = q0; q < q1; q++) s = fma(sv[q], xf(sc[q]), s);
+    }
+    s = group_tree<G, T>(s);
+    if (row < r1 && j == 0) epi(row, s);
+    __syncwarp();
+}
+
+template <int R, class T, class XF, class EPI>
+__global__ void __launch_bounds__(CWARPS * 32) k_csr_chunk(int n, const int *__restrict__ rp,
+                                                           const int *__restrict__ ci,
+                                                           const T *__restrict__ v, XF xf, EPI epi) {
+    __shared__ T sv[CWARPS][CCAP];
+    __shared__ int sc[CWARPS][CCAP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nchunk = (n + R - 1) / R;
+    for (int c = blockIdx.x * CWARPS + warp; c < nchunk; c += gridDim.x * CWARPS) {
+        const int r0 = c * R, r1 = min(r0 + R, n);
+        const int p0 = __ldg(rp + r0), p1 = __ldg(rp + r1);
+        const int cnt = p1 - p0;
+        if (cnt <= CCAP) {
+            chunk_rows<R, T, XF, EPI>(r0, r1, p0, cnt, rp, ci, v, xf, epi, sv[warp], sc[warp], lane);
+        } else {
+            for (int row = r0; row < r1; row++) {
+                const int a = __ldg(rp + row), b = __ldg(rp + row + 1);
+                T s = (T)0;
+                for (int p = a + lane; p < b; p += 32) s = fma(__ldg(v + p), xf(__ldg(ci + p)), s);
+                s = group_tree<32, T>(s);
+                if (lane == 0) epi(row, s);
+            }
+        }
+    }
+}
+
+template <class T, class XF, class EPI>
+static void csr_chunk(int n, long long nnz, const int *rp, const int *ci, const T *v, XF xf, EPI epi,
+                      cudaStream_t s) {
+    if (n <= 0) return;
+    int R = rows_per_warp(nnz, n);
+    long long nchunk = (n + R - 1) / R;
+    long long blocks = (nchunk + CWARPS - 1) / CWARPS;
+    if (blocks > NUM_SMS * 8) blocks = NUM_SMS * 8;
+    if (blocks < 1) blocks = 1;
+    unsigned g = (unsigned)blocks;
+    switch (R) {
+        case 1: k_csr_chunk<1, T, XF, EPI><<<g, CWARPS * 32, 0, s>>>(n, rp, ci, v, xf, epi); break;
+        case 2: k_csr_chunk<2, T, XF, EPI><<<g, CWARPS * 32, 0, s>>>(n, rp, ci, v, xf, epi); break;
+        case 4: k_csr_chunk<4, T, XF, EPI><<<g, CWARPS * 32, 0, s>>>(n, rp, ci, v, xf, epi); break;
+        case 8: k_csr_chunk<8, T, XF, EPI><<<g, CWARPS * 32, 0, s>>>(n, rp, ci, v, xf, epi); break;
+        case 16: k_csr_chunk<16, T, XF, EPI><<<g, CWARPS * 32, 0, s>>>(n, rp, ci, v, xf, epi); break;
+        default: k_csr_chunk<32, T, XF, EPI><<<g, CWARPS * 32, 0, s>>>(n, rp, ci, v, xf, epi); break;
+    }
+}
+
+// gathers
+template <class T, class XT>
+struct XPlain {
+    const XT *x;
+    __device__ __forceinline__ T operator()(int j) const { return (T)__ldg(x + j); }
+};
+template <class T, class TV>
+struct XScaled {  // x_j = d_j r_j (pre-smoothing from zero)
+    const T *d;
+    const TV *r;
+    __device__ __forceinline__ T operator()(int j) const { return __ldg(d + j) * (T)__ldg(r + j); }
+};
+
+// epilogues
+template <class T, class TO>
+struct EStore {
+    TO *y;
+    __device__ __forceinline__ void operator()(int row, T s) const { y[row] = (TO)s; }
+};
+template <class T>
+struct EAdd {
+    T *y;
+    __device__ __forceinline__ void operator()(int row, T s) const { y[row] += s; }
+};
+struct EAxpby {
+    double alpha, beta;
+    const double *b;  // residual mode when non-null: y = b - s
+    double *y;
+    __device__ __forceinline__ void operator()(int row, double s) const {
+        if (b) y[row] = b[row] - s;
+        else y[row] = beta == 0.0 ? alpha * s : alpha * s + beta * y[row];
+    }
+};
+template <class T>
+struct EStoreScaled {  // y = s ; x = d s  (restriction that also seeds the next pre-smoothing)
+    T *y;
+    const T *d;
+    T *x;
+    __device__ __forceinline__ void operator()(int row, T s) const {
+        y[row] = s;
+        x[row] = d[row] * s;
+    }
+};
+template <class T, class TV>
+struct EGatherMinusScaled {  // y = b[idx] - s ; x = d y
+    const int *idx;
+    const TV *b;
+    T *y;
+    const T *d;
+    T *x;
+    __device__ __forceinline__ void operator()(int row, T s) const {
+        T t = (T)b[idx[row]] - s;
+        y[row] = t;
+        x[row] = d[row] * t;
+    }
+};
+template <class T, class TV>
+struct EResid {  // res = r - s
+    const TV *r;
+    T *res;
+    __device__ __forceinline__ void operator()(int row, T s) const { res[row] = (T)r[row] - s; }
+};
+template <class T, class TV>
+struct ESmooth0 {  // x = d r ; res = r - A (d r)
+    const TV *r;
+    const T *d;
+    T *x, *res;
+    __device__ __forceinline__ void operator()(int row, T s) const {
+        T ri = (T)r[row];
+        x[row] = d[row] * ri;
+        res[row] = ri - s;
+    }
+};
+template <class T, class TV>
+struct EPost {  // xout = x + d (r - A x)
+    const TV *r;
+    const T *d;
+    const T *x;
+    TV *xout;
+    __device__ __forceinline__ void operator()(int row, T s) const {
+        xout[row] = (TV)(x[row] + d[row] * ((T)r[row] - s));
+    }
+};
+template <class T, class TV>
+struct EGatherMinus {  // y = b[idx[row]] + sign * s
+    const int *idx;
+    const TV *b;
+    T sign;
+    T *y;
+    __device__ __forceinline__ void operator()(int row, T s) const { y[row] = (T)b[idx[row]] + sign * s; }
+};
+template <class T, class TV>
+struct EInterp {  // z[fidx] = zF + s
+    const int *fidx;
+    const T *zF;
+    TV *z;
+    __device__ __forceinline__ void operator()(int row, T s) const { z[fidx[row]] = (TV)(zF[row] + s); }
+};
 
 // --------------------------------------------------------------- CSR y = A x
-template <int G, class T>
-__global__ void k_csr_spmv(int n, const int *rp, const int *ci, const T *v, const T *x, T *y) {
-    ROW_SETUP(G)
-    T s = row_dot<G, T, T>(rp, ci, v, x, row, valid, lane);
-    if (valid && lane == 0) y[row] = s;
-}
-
-template <int G, class T>
-__global__ void k_csr_spmv_add(int n, const int *rp, const int *ci, const T *v, const T *x, T *y) {
-    ROW_SETUP(G)
-    T s = row_dot<G, T, T>(rp, ci, v, x, row, valid, lane);
-    if (valid && lane == 0) y[row] += s;
-}
-
-#define LAUNCH_G(G, KER, n, ...)                                                       \
-    do {                                                                               \
-        const int thr = 256;                                                           \
-        unsigned grid = GRIDN((long long)(n) * (G), thr);                              \
-        switch (G) {                                                                   \
-            case 4: KER(4)<<<grid, thr, 0, s>>>(__VA_ARGS__); break;                   \
-            case 8: KER(8)<<<grid, thr, 0, s>>>(__VA_ARGS__); break;                   \
-            case 16: KER(16)<<<grid, thr, 0, s>>>(__VA_ARGS__); break;                 \
-            default: KER(32)<<<grid, thr, 0, s>>>(__VA_ARGS__); break;                 \
-        }                                                                              \
-    } while (0)
-
 template <class T>
 void launch_csr_spmv(const DCSR &A, const T *vals, const T *x, T *y, cudaStream_t s) {
-    if (A.n == 0) return;
-    int G = pick_group(A.nnz, A.n);
-#define K(g) k_csr_spmv<g, T>
-    LAUNCH_G(G, K, A.n, A.n, A.rp, A.ci, vals, x, y);
-#undef K
+    csr_chunk<T>(A.n, A.nnz, A.rp, A.ci, vals, XPlain<T, T>{x}, EStore<T, T>{y}, s);
 }
 
 template <class T>
 void launch_csr_spmv_add(const DCSR &A, const T *vals, const T *x, T *y, cudaStream_t s) {
-    if (A.n == 0) return;
-    int G = pick_group(A.nnz, A.n);
-#define K(g) k_csr_spmv_add<g, T>
-    LAUNCH_G(G, K, A.n, A.n, A.rp, A.ci, vals, x, y);
-#undef K
+    csr_chunk<T>(A.n, A.nnz, A.rp, A.ci, vals, XPlain<T, T>{x}, EAdd<T>{y}, s);
+}
+
+void launch_csr_residual(const DCSR &A, const double *x, const double *bvec, double *y,
+                         cudaStream_t s) {
+    csr_chunk<double>(A.n, A.nnz, A.rp, A.ci, A.v, XPlain<double, double>{x},
+                      EAxpby{1.0, 0.0, bvec, y}, s);
 }
 
 // -------------------------------------------------------------- BSR (FP64)
-// b == 1 is CSR.  b > 1: one thread per scalar row (I, r); the b values of
-// row r of each block are contiguous.
-template <int G>
-__global__ void k_bsr1(int n, const int *rp, const int *ci, const double *v, const double *x,
-                       const double *bvec, double *y, double alpha, double beta, int mode) {
-    ROW_SETUP(G)
-    double s = row_dot<G, double, double>(rp, ci, v, x, row, valid, lane);
-    if (valid && lane == 0) {
-        if (mode == 1) y[row] = bvec[row] - s;
-        else y[row] = beta == 0.0 ? alpha * s : alpha * s + beta * y[row];
-    }
-}
-
+// b == 1 is CSR (chunk engine).  b > 1: one thread per scalar row (I, r);
+// the b values of row r of each block are contiguous.
 template <int B>
 __global__ void k_bsrB(int nb, const int *__restrict__ rp, const int *__restrict__ ci,
                        const double *__restrict__ val, const double *__restrict__ x,
@@ -124,17 +265,13 @@ __global__ void k_bsrB(int nb, const int *__restrict__ rp, const int *__restrict
     else y[t] = beta == 0.0 ? alpha * s : alpha * s + beta * y[t];
 }
 
-static void bsr_dispatch(int nb, int b, const int *rp, const int *ci, const double *val,
-                         const double *x, const double *bvec, double *y, double alpha, double beta,
-                         int mode, cudaStream_t s) {
+static void bsr_dispatch(int nb, int b, long long nnzb, const int *rp, const int *ci,
+                         const double *val, const double *x, const double *bvec, double *y,
+                         double alpha, double beta, int mode, cudaStream_t s) {
     if (nb <= 0) return;
     if (b == 1) {
-        // nnz unknown on the host without a copy: read it from a cached guess is
-        // unsafe; use the average supplied through rp on the device instead.
-        int G = 8;
-#define K(g) k_bsr1<g>
-        LAUNCH_G(G, K, nb, nb, rp, ci, val, x, bvec, y, alpha, beta, mode);
-#undef K
+        csr_chunk<double>(nb, nnzb > 0 ? nnzb : 8LL * nb, rp, ci, val, XPlain<double, double>{x},
+                          EAxpby{alpha, beta, mode == 1 ? bvec : nullptr, y}, s);
         return;
     }
     long long n = (long long)nb * b;
@@ -147,14 +284,15 @@ static void bsr_dispatch(int nb, int b, const int *rp, const int *ci, const doub
 }
 
 void launch_bsr_spmv(int nb, int b, const int *rp, const int *ci, const double *val,
-                     const double *x, double *y, double alpha, double beta, cudaStream_t s) {
-    bsr_dispatch(nb, b, rp, ci, val, x, nullptr, y, alpha, beta, 0, s);
+                     const double *x, double *y, double alpha, double beta, cudaStream_t s,
+                     long long nnzb) {
+    bsr_dispatch(nb, b, nnzb, rp, ci, val, x, nullptr, y, alpha, beta, 0, s);
 }
 
 void launch_bsr_residual(int nb, int b, const int *rp, const int *ci, const double *val,
-                         const double *x, const double *bvec, double *y, cudaStream_t s) {
-    if (bvec) bsr_dispatch(nb, b, rp, ci, val, x, bvec, y, 1.0, 0.0, 1, s);
-    else bsr_dispatch(nb, b, rp, ci, val, x, nullptr, y, 1.0, 0.0, 0, s);
+                         const double *x, const double *bvec, double *y, cudaStream_t s,
+                         long long nnzb) {
+    bsr_dispatch(nb, b, nnzb, rp, ci, val, x, bvec, y, 1.0, 0.0, bvec ? 1 : 0, s);
 }
 
 // ---------------------------------------------------------------- MGR level
@@ -178,22 +316,11 @@ void launch_frelax_first(int nF, const int *fidx, const int *gstart, const int *
 }
 
 // r_F = v_F - A_FF z_F
-template <int G, class T, class TV>
-__global__ void k_frelax_residual(int n, const int *rp, const int *ci, const T *vals,
-                                  const int *fidx, const TV *v, const T *zF, T *rF) {
-    ROW_SETUP(G)
-    T s = row_dot<G, T, T>(rp, ci, vals, zF, row, valid, lane);
-    if (valid && lane == 0) rF[row] = (T)v[fidx[row]] - s;
-}
-
 template <class T, class TV>
 void launch_frelax_residual(const DCSR &AFF, const T *vals, const int *fidx, const TV *v,
                             const T *zF, T *rF, cudaStream_t s) {
-    if (AFF.n == 0) return;
-    int G = pick_group(AFF.nnz, AFF.n);
-#define K(g) k_frelax_residual<g, T, TV>
-    LAUNCH_G(G, K, AFF.n, AFF.n, AFF.rp, AFF.ci, vals, fidx, v, zF, rF);
-#undef K
+    csr_chunk<T>(AFF.n, AFF.nnz, AFF.rp, AFF.ci, vals, XPlain<T, T>{zF},
+                 EGatherMinus<T, TV>{fidx, v, (T)-1, rF}, s);
 }
 
 // z_F += omega D^{-1} r_F (transpose: D^{-T})
@@ -219,43 +346,25 @@ void launch_frelax_update(int nF, const int *gstart, const int *gsize, const T *
 }
 
 // injection restriction of the residual: v_C = v[C] - A_CF z_F
-template <int G, class T, class TV>
-__global__ void k_mgr_restrict(int n, const int *rp, const int *ci, const T *vals,
-                               const int *cidx, const TV *v, const T *zF, T *vC) {
-    ROW_SETUP(G)
-    T s = row_dot<G, T, T>(rp, ci, vals, zF, row, valid, lane);
-    if (valid && lane == 0) vC[row] = (T)v[cidx[row]] - s;
-}
-
 template <class T, class TV>
 void launch_mgr_restrict(const DCSR &ACF, const T *vals, const int *cidx, const TV *v,
                          const T *zF, T *vC, cudaStream_t s) {
-    if (ACF.n == 0) return;
-    int G = pick_group(ACF.nnz, ACF.n);
-#define K(g) k_mgr_restrict<g, T, TV>
-    LAUNCH_G(G, K, ACF.n, ACF.n, ACF.rp, ACF.ci, vals, cidx, v, zF, vC);
-#undef K
-}
-
-// interpolation + correction: z[F] = z_F + W e_C, z[C] = e_C
-template <int G, class T, class TV>
-__global__ void k_mgr_interp(int n, const int *rp, const int *ci, const T *wv, const int *fidx,
-                             const T *zF, const T *eC, TV *z, int nC, const int *cidx) {
-    ROW_SETUP(G)
-    T s = row_dot<G, T, T>(rp, ci, wv, eC, row, valid, lane);
-    if (valid && lane == 0) z[fidx[row]] = (TV)(zF[row] + s);
-    // the C part: one element per launched thread
-    for (int i = gtid; i < nC; i += gridDim.x * blockDim.x) z[cidx[i]] = (TV)eC[i];
+    csr_chunk<T>(ACF.n, ACF.nnz, ACF.rp, ACF.ci, vals, XPlain<T, T>{zF},
+                 EGatherMinus<T, TV>{cidx, v, (T)-1, vC}, s);
 }
 
 template <class T, class TV>
+__global__ void k_scatter_c(int nC, const int *cidx, const T *eC, TV *z) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nC) z[cidx[i]] = (TV)eC[i];
+}
+
+// interpolation + correction: z[F] = z_F + W e_C, z[C] = e_C
+template <class T, class TV>
 void launch_mgr_interp(const DCSR &W, const T *wvals, int nC, const int *fidx, const int *cidx,
                        const T *zF, const T *eC, TV *z, cudaStream_t s) {
-    int G = pick_group(W.nnz, W.n > 0 ? W.n : 1);
-    long long rows = W.n > nC / G ? W.n : (nC + G - 1) / G;
-#define K(g) k_mgr_interp<g, T, TV>
-    LAUNCH_G(G, K, rows, W.n, W.rp, W.ci, wvals, fidx, zF, eC, z, nC, cidx);
-#undef K
+    csr_chunk<T>(W.n, W.nnz, W.rp, W.ci, wvals, XPlain<T, T>{eC}, EInterp<T, TV>{fidx, zF, z}, s);
+    if (nC > 0) k_scatter_c<T, TV><<<GRIDN(nC, 256), 256, 0, s>>>(nC, cidx, eC, z);
 }
 
 // transposed-cycle pieces
@@ -272,22 +381,11 @@ void launch_gather(const int *idx, int n, const TV *v, T *out, cudaStream_t s) {
 }
 
 // y[i] = bsrc[idx_b[i]] + sign * (M x)_i
-template <int G, class T, class TV>
-__global__ void k_csr_axpy_gather(int n, const int *rp, const int *ci, const T *vals, const T *x,
-                                  const int *idx_b, const TV *bsrc, T sign, T *y) {
-    ROW_SETUP(G)
-    T s = row_dot<G, T, T>(rp, ci, vals, x, row, valid, lane);
-    if (valid && lane == 0) y[row] = (T)bsrc[idx_b[row]] + sign * s;
-}
-
 template <class T, class TV>
 void launch_csr_axpy_gather(const DCSR &M, const T *vals, const T *x, const int *idx_b,
                             const TV *bsrc, T sign, T *y, cudaStream_t s) {
-    if (M.n == 0) return;
-    int G = pick_group(M.nnz, M.n);
-#define K(g) k_csr_axpy_gather<g, T, TV>
-    LAUNCH_G(G, K, M.n, M.n, M.rp, M.ci, vals, x, idx_b, bsrc, sign, y);
-#undef K
+    csr_chunk<T>(M.n, M.nnz, M.rp, M.ci, vals, XPlain<T, T>{x},
+                 EGatherMinus<T, TV>{idx_b, bsrc, sign, y}, s);
 }
 
 template <class T, class TV>
@@ -307,54 +405,52 @@ void launch_scatter2(int nF, int nC, const int *fidx, const int *cidx, const T *
 // ---------------------------------------------------------------- AMG level
 // pre-smoothing from x = 0 fused with the residual:
 //   x_i = dinv_i r_i ;  res_i = r_i - sum_j a_ij dinv_j r_j
-template <int G, class T, class TV>
-__global__ void k_amg_smooth0_residual(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                       const T *__restrict__ vals, const T *__restrict__ dinv,
-                                       const TV *__restrict__ r, T *x, T *res) {
-    ROW_SETUP(G)
-    T s = (T)0;
-    if (valid) {
-        int p1 = __ldg(rp + row + 1);
-        for (int p = __ldg(rp + row) + lane; p < p1; p += G) {
-            int j = __ldg(ci + p);
-            s += __ldg(vals + p) * (__ldg(dinv + j) * (T)__ldg(r + j));
-        }
-    }
-    s = group_sum<G, T>(s);
-    if (valid && lane == 0) {
-        T ri = (T)r[row];
-        x[row] = dinv[row] * ri;
-        res[row] = ri - s;
-    }
-}
-
 template <class T, class TV>
 void launch_amg_smooth0_residual(const DCSR &A, const T *vals, const T *dinv, const TV *r, T *x,
                                  T *res, cudaStream_t s) {
-    if (A.n == 0) return;
-    int G = pick_group(A.nnz, A.n);
-#define K(g) k_amg_smooth0_residual<g, T, TV>
-    LAUNCH_G(G, K, A.n, A.n, A.rp, A.ci, vals, dinv, r, x, res);
-#undef K
+    csr_chunk<T>(A.n, A.nnz, A.rp, A.ci, vals, XScaled<T, TV>{dinv, r},
+                 ESmooth0<T, TV>{r, dinv, x, res}, s);
 }
 
-// post-smoothing: xout_i = x_i + dinv_i (r_i - sum_j a_ij x_j)
-template <int G, class T, class TV>
-__global__ void k_amg_post_smooth(int n, const int *rp, const int *ci, const T *vals, const T *dinv,
-                                  const TV *r, const T *x, TV *xout) {
-    ROW_SETUP(G)
-    T s = row_dot<G, T, T>(rp, ci, vals, x, row, valid, lane);
-    if (valid && lane == 0) xout[row] = (TV)(x[row] + dinv[row] * ((T)r[row] - s));
+// residual of the pre-smoothed iterate x = D r computed by the producer of r:
+//   res_i = r_i - sum_j a_ij x_j
+template <class T, class TV>
+void launch_amg_residual(const DCSR &A, const T *vals, const T *x, const TV *r, T *res,
+                         cudaStream_t s) {
+    csr_chunk<T>(A.n, A.nnz, A.rp, A.ci, vals, XPlain<T, T>{x}, EResid<T, TV>{r, res}, s);
+}
+
+// restriction r_c = R res that also writes x_c = D_c r_c for the next level
+template <class T>
+void launch_restrict_scaled(const DCSR &R, const T *vals, const T *res, T *rc, const T *dc, T *xc,
+                            cudaStream_t s) {
+    csr_chunk<T>(R.n, R.nnz, R.rp, R.ci, vals, XPlain<T, T>{res}, EStoreScaled<T>{rc, dc, xc}, s);
+}
+
+// MGR injection restriction that also writes x = D v_C for the AMG below
+template <class T, class TV>
+void launch_mgr_restrict_scaled(const DCSR &ACF, const T *vals, const int *cidx, const TV *v,
+                                const T *zF, T *vC, const T *d, T *x, cudaStream_t s) {
+    csr_chunk<T>(ACF.n, ACF.nnz, ACF.rp, ACF.ci, vals, XPlain<T, T>{zF},
+                 EGatherMinusScaled<T, TV>{cidx, v, vC, d, x}, s);
 }
 
 template <class T, class TV>
+__global__ void k_scale(int n, const T *d, const TV *r, T *x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = d[i] * (T)r[i];
+}
+
+template <class T, class TV>
+void launch_scale(int n, const T *d, const TV *r, T *x, cudaStream_t s) {
+    if (n > 0) k_scale<T, TV><<<GRIDN(n, 256), 256, 0, s>>>(n, d, r, x);
+}
+
+// post-smoothing: xout_i = x_i + dinv_i (r_i - sum_j a_ij x_j)
+template <class T, class TV>
 void launch_amg_post_smooth(const DCSR &A, const T *vals, const T *dinv, const TV *r, const T *x,
                             TV *xout, cudaStream_t s) {
-    if (A.n == 0) return;
-    int G = pick_group(A.nnz, A.n);
-#define K(g) k_amg_post_smooth<g, T, TV>
-    LAUNCH_G(G, K, A.n, A.n, A.rp, A.ci, vals, dinv, r, x, xout);
-#undef K
+    csr_chunk<T>(A.n, A.nnz, A.rp, A.ci, vals, XPlain<T, T>{x}, EPost<T, TV>{r, dinv, x, xout}, s);
 }
 
 // coarsest grid: x = A^{-1} r with the explicit FP64 inverse; one warp per row
@@ -388,139 +484,206 @@ void launch_copy_cast(const TV *in, double *out, int n, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------- Krylov (FP64)
+// Reductions over n with a fixed grid: each block accumulates a fixed
+// element set, writes its partial, and the last block to finish (ticket)
+// sums the partials in block order, one warp per output.
 static const int RED_THREADS = 256;
+static const int RED_EPT = 2;
 
 int multidot_blocks(int n) {
-    int b = (n + RED_THREADS * 8 - 1) / (RED_THREADS * 8);
-    if (b < 1) b = 1;
-    if (b > 152 * 8) b = 152 * 8;
-    return b;
+    long long b = ((long long)n + RED_THREADS * RED_EPT - 1) / (RED_THREADS * RED_EPT);
+    if (b > NUM_SMS * 2) b = NUM_SMS * 2;
+    return (int)(b < 1 ? 1 : b);
 }
 
 template <int K>
-__device__ __forceinline__ void block_reduce_store(double (&acc)[K], int k, double *out) {
-    __shared__ double sh[RED_THREADS / 32][33];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__device__ __forceinline__ void block_partials(double (&acc)[K], double *partial) {
+    __shared__ double sh[RED_THREADS / 32][K > 0 ? K : 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < K; i++) {
-        if (i < k) {
-            double v = group_sum<32, double>(acc[i]);
-            if (lane == 0) sh[w][i] = v;
-        }
+        double v = group_sum<32, double>(acc[i]);
+        if (lane == 0) sh[w][i] = v;
     }
     __syncthreads();
-    if (threadIdx.x < k) {
+    if (threadIdx.x < K) {
         double t = 0.0;
+#pragma unroll
         for (int ww = 0; ww < RED_THREADS / 32; ww++) t += sh[ww][threadIdx.x];
-        out[threadIdx.x] = t;
+        partial[(long long)blockIdx.x * K + threadIdx.x] = t;
     }
 }
 
-// partial[blk*k + i] = sum over the block's elements of V_i . w  (k <= 32)
-__global__ void __launch_bounds__(RED_THREADS) k_multidot(const double *__restrict__ V, long long ldv,
-                                                          int k, const double *__restrict__ w, int n,
-                                                          double *partial) {
-    double acc[32];
-#pragma unroll
-    for (int i = 0; i < 32; i++) acc[i] = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-        double we = w[e];
-#pragma unroll
-        for (int i = 0; i < 32; i++)
-            if (i < k) acc[i] += __ldg(V + i * ldv + e) * we;
-    }
-    block_reduce_store<32>(acc, k, partial + (long long)blockIdx.x * k);
-}
-
-void launch_multidot(const double *V, long long ldv, int k, const double *w, int n,
-                     double *partial, int nblk, cudaStream_t s) {
-    k_multidot<<<nblk, RED_THREADS, 0, s>>>(V, ldv, k, w, n, partial);
-}
-
-// w <- w - sum_i V_i h_i, then mode 0: partial dots V_i . w ; mode 1: partial |w|^2
-__global__ void __launch_bounds__(RED_THREADS) k_update_dot(const double *__restrict__ V, long long ldv,
-                                                            int k, const double *__restrict__ h,
-                                                            double *w, int n, double *partial,
-                                                            int mode) {
-    __shared__ double hs[32];
-    if (threadIdx.x < k) hs[threadIdx.x] = h[threadIdx.x];
+// true in the last block to arrive (all partials visible to it)
+__device__ __forceinline__ bool last_block(unsigned *ticket) {
+    __shared__ bool am_last;
+    __threadfence();
     __syncthreads();
-    double acc[32];
-#pragma unroll
-    for (int i = 0; i < 32; i++) acc[i] = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-        double vv[32];
-        double we = w[e];
-#pragma unroll
-        for (int i = 0; i < 32; i++)
-            if (i < k) { vv[i] = __ldg(V + i * ldv + e); we -= vv[i] * hs[i]; }
-        w[e] = we;
-        if (mode == 0) {
-#pragma unroll
-            for (int i = 0; i < 32; i++)
-                if (i < k) acc[i] += vv[i] * we;
-        } else {
-            acc[0] += we * we;
-        }
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(ticket, 1u);
+        am_last = (t == gridDim.x - 1);
     }
-    block_reduce_store<32>(acc, mode == 0 ? k : 1, partial + (long long)blockIdx.x * (mode == 0 ? k : 1));
+    __syncthreads();
+    return am_last;
 }
 
-void launch_update_dot(const double *V, long long ldv, int k, const double *h, double *w, int n,
-                       double *partial, int nblk, int mode, cudaStream_t s) {
-    k_update_dot<<<nblk, RED_THREADS, 0, s>>>(V, ldv, k, h, w, n, partial, mode);
-}
-
-// out[v] = sum_b partial[b*nvec + v] in a fixed order (sqrt if asked)
-__global__ void k_finalize_sum(const double *partial, int nblk, int nvec, double *out, int sqrt_out) {
-    __shared__ double sh[256];
-    for (int v = 0; v < nvec; v++) {
+// out[i] = sum over blocks of partial[b*K + i], warp per output, fixed tree
+template <int K>
+__device__ __forceinline__ void sum_partials(const double *partial, double *out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = w; i < K; i += RED_THREADS / 32) {
         double t = 0.0;
-        for (int b = threadIdx.x; b < nblk; b += blockDim.x) t += partial[(long long)b * nvec + v];
-        sh[threadIdx.x] = t;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[v] = sqrt_out ? sqrt(sh[0]) : sh[0];
-        __syncthreads();
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partial + (long long)b * K + i);
+        t = group_sum<32, double>(t);
+        if (lane == 0) out[i] = t;
     }
 }
 
-void launch_finalize_sum(const double *partial, int nblk, int nvec, double *out, int sqrt_out,
-                         cudaStream_t s) {
-    k_finalize_sum<<<1, 256, 0, s>>>(partial, nblk, nvec, out, sqrt_out);
+// h[i] = V_i . w for i < K (w may be V_{K-1} itself).  Skipped when
+// *flag == 0 (flag != nullptr): the conditional reorthogonalisation pass.
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS) k_dots(const double *__restrict__ V, long long ldv,
+                                                      const double *__restrict__ w, int n,
+                                                      double *partial, double *h, unsigned *ticket,
+                                                      const int *flag) {
+    if (flag && *flag == 0) return;
+    double acc[K];
+#pragma unroll
+    for (int i = 0; i < K; i++) acc[i] = 0.0;
+    const long long stride = (long long)gridDim.x * RED_THREADS * RED_EPT;
+    for (long long e0 = (long long)blockIdx.x * RED_THREADS * RED_EPT + threadIdx.x; e0 < n; e0 += stride) {
+        double wv[RED_EPT];
+#pragma unroll
+        for (int u = 0; u < RED_EPT; u++) {
+            long long e = e0 + (long long)u * RED_THREADS;
+            wv[u] = e < n ? __ldg(w + e) : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < K; i++)
+#pragma unroll
+            for (int u = 0; u < RED_EPT; u++) {
+                long long e = e0 + (long long)u * RED_THREADS;
+                if (e < n) acc[i] += __ldg(V + i * ldv + e) * wv[u];
+            }
+    }
+    block_partials<K>(acc, partial);
+    if (last_block(ticket)) {
+        sum_partials<K>(partial, h);
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
 }
 
-__global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const double *x, const double *y, int n,
-                                                             double *partial) {
+// Classical Gram-Schmidt with a rescue pass: the second projection runs
+// only when the first removed more than 99% of |w| (|w'| < 0.1 |w|), the
+// cancellation that costs orthogonality (a DGKS-type test with eta = 0.1).
+static constexpr double REORTH_ETA2 = 1e-2;
+
+// w <- w - sum_{i<K} V_i h_i ; nrm2 = |w|^2.  mode 1 (first pass) also
+// decides reorthogonalisation (|w'|^2 < eta^2 |w|^2, with |w|^2 = h[K]) and
+// writes it to *flag; mode 2 (the second pass) is skipped when *flag == 0.
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS) k_update_norm(const double *__restrict__ V, long long ldv,
+                                                             const double *__restrict__ h, double *w,
+                                                             int n, double *partial, double *nrm2,
+                                                             unsigned *ticket, int *flag, int mode) {
+    if (mode == 2 && *flag == 0) return;
+    double hs[K];
+#pragma unroll
+    for (int i = 0; i < K; i++) hs[i] = h[i];
     double acc[1] = {0.0};
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x)
-        acc[0] += x[e] * y[e];
-    block_reduce_store<1>(acc, 1, partial + blockIdx.x);
+    const long long stride = (long long)gridDim.x * RED_THREADS * RED_EPT;
+    for (long long e0 = (long long)blockIdx.x * RED_THREADS * RED_EPT + threadIdx.x; e0 < n; e0 += stride) {
+        double wv[RED_EPT];
+#pragma unroll
+        for (int u = 0; u < RED_EPT; u++) {
+            long long e = e0 + (long long)u * RED_THREADS;
+            wv[u] = e < n ? w[e] : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < K; i++)
+#pragma unroll
+            for (int u = 0; u < RED_EPT; u++) {
+                long long e = e0 + (long long)u * RED_THREADS;
+                if (e < n) wv[u] -= __ldg(V + i * ldv + e) * hs[i];
+            }
+#pragma unroll
+        for (int u = 0; u < RED_EPT; u++) {
+            long long e = e0 + (long long)u * RED_THREADS;
+            if (e < n) { w[e] = wv[u]; acc[0] += wv[u] * wv[u]; }
+        }
+    }
+    block_partials<1>(acc, partial);
+    if (last_block(ticket)) {
+        sum_partials<1>(partial, nrm2);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (mode == 1) *flag = (*nrm2 < REORTH_ETA2 * h[K]) ? 1 : 0;
+            *ticket = 0u;
+        }
+    }
 }
 
-void launch_dot_partial(const double *x, const double *y, int n, double *partial, int nblk,
-                        cudaStream_t s) {
-    k_dot_partial<<<nblk, RED_THREADS, 0, s>>>(x, y, n, partial);
+#define K_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) \
+    X(15) X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) \
+    X(30) X(31) X(32)
+
+void launch_dots(const double *V, long long ldv, int k, const double *w, int n, double *partial,
+                 double *h, unsigned *ticket, const int *flag, int nblk, cudaStream_t s) {
+    switch (k) {
+#define X(K) case K: k_dots<K><<<nblk, RED_THREADS, 0, s>>>(V, ldv, w, n, partial, h, ticket, flag); break;
+        K_CASES(X)
+#undef X
+        default: break;
+    }
+}
+
+void launch_update_norm(const double *V, long long ldv, int k, const double *h, double *w, int n,
+                        double *partial, double *nrm2, unsigned *ticket, int *flag, int mode,
+                        int nblk, cudaStream_t s) {
+    switch (k) {
+#define X(K) case K: k_update_norm<K><<<nblk, RED_THREADS, 0, s>>>(V, ldv, h, w, n, partial, nrm2, ticket, flag, mode); break;
+        K_CASES(X)
+#undef X
+        default: break;
+    }
+}
+
+// x . y (sqrt when asked) with the ticketed reduction
+__global__ void __launch_bounds__(RED_THREADS) k_dot2(const double *x, const double *y, int n,
+                                                      double *partial, double *out, unsigned *ticket,
+                                                      int sqrt_out) {
+    double acc[1] = {0.0};
+    const long long stride = (long long)gridDim.x * RED_THREADS;
+    for (long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x; e < n; e += stride)
+        acc[0] += x[e] * y[e];
+    block_partials<1>(acc, partial);
+    if (last_block(ticket)) {
+        sum_partials<1>(partial, out);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (sqrt_out) *out = sqrt(*out);
+            *ticket = 0u;
+        }
+    }
+}
+
+void launch_dot(const double *x, const double *y, int n, double *partial, double *out,
+                unsigned *ticket, int sqrt_out, int nblk, cudaStream_t s) {
+    k_dot2<<<nblk, RED_THREADS, 0, s>>>(x, y, n, partial, out, ticket, sqrt_out);
 }
 
 // y = x * s  or  y = x / s  (s a device scalar)
 __global__ void k_vec_scale(const double *x, double *y, const double *sc, int invert, int n) {
-    double f = *sc;
+    const double f = invert ? 1.0 / *sc : *sc;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x)
-        y[e] = invert ? x[e] / f : x[e] * f;
+        y[e] = x[e] * f;
 }
 
 void launch_vec_scale(const double *x, double *y, const double *scale_num, const double *,
                       int invert, int n, cudaStream_t s) {
     unsigned g = GRIDN(n, 256);
-    k_vec_scale<<<g > 4096 ? 4096 : g, 256, 0, s>>>(x, y, scale_num, invert, n);
+    k_vec_scale<<<g > NUM_SMS * 8 ? NUM_SMS * 8 : g, 256, 0, s>>>(x, y, scale_num, invert, n);
 }
 
 // x += sum_i y_i Z_i
@@ -540,7 +703,7 @@ __global__ void k_multi_axpy(const double *__restrict__ Z, long long ldz, int k,
 void launch_multi_axpy(const double *Z, long long ldz, int k, const double *y, double *x, int n,
                        cudaStream_t s) {
     unsigned g = GRIDN(n, 256);
-    k_multi_axpy<<<g > 4096 ? 4096 : g, 256, 0, s>>>(Z, ldz, k, y, x, n);
+    k_multi_axpy<<<g > NUM_SMS * 8 ? NUM_SMS * 8 : g, 256, 0, s>>>(Z, ldz, k, y, x, n);
 }
 
 // dA[p, r, c] = -lam[I*b + r] * x[J*b + c]
@@ -587,23 +750,6 @@ void launch_validate_bsr(int nb, int b, const int *rp, const int *ci, const doub
     k_validate_bsr<<<GRIDN(nb, 256), 256, 0, s>>>(nb, b, rp, ci, val, err);
 }
 
-template <int G>
-__global__ void k_csr_residual(int n, const int *rp, const int *ci, const double *v, const double *x,
-                               const double *bvec, double *y) {
-    ROW_SETUP(G)
-    double s = row_dot<G, double, double>(rp, ci, v, x, row, valid, lane);
-    if (valid && lane == 0) y[row] = bvec ? bvec[row] - s : s;
-}
-
-void launch_csr_residual(const DCSR &A, const double *x, const double *bvec, double *y,
-                         cudaStream_t s) {
-    if (A.n == 0) return;
-    int G = pick_group(A.nnz, A.n);
-#define K(g) k_csr_residual<g>
-    LAUNCH_G(G, K, A.n, A.n, A.rp, A.ci, A.v, x, bvec, y);
-#undef K
-}
-
 __global__ void k_transpose_dense(int n, const double *in, double *out) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= (long long)n * n) return;
@@ -617,16 +763,20 @@ void launch_transpose_dense(int n, const double *in, double *out, cudaStream_t s
 }
 
 // H is (m+1) x m row-major.  h1[0..j] first-pass projections and h1[j+1] =
-// |w|^2 before orthogonalisation; h2 second-pass projections; nrm2 = |w|^2
-// after.  Applies the previous Givens rotations to column j, forms the new
-// one, and writes stat = {|g_{j+1}|, converged, breakdown, h_{j+1,j}}.
-__global__ void k_arnoldi_finish(int j, int m, const double *h1, const double *h2, const double *nrm2,
+// |w|^2 before orthogonalisation; when *flag (reorthogonalised) h2 holds the
+// second-pass projections and nrmB the final |w|^2, else nrmA.  Applies the
+// previous Givens rotations to column j, forms the new one, and writes
+// stat = {|g_{j+1}|, converged, breakdown, h_{j+1,j}}.
+__global__ void k_arnoldi_finish(int j, int m, const double *h1, const double *h2,
+                                 const double *nrmA, const double *nrmB, const int *flag,
                                  double *H, double *cs, double *sn, double *g, double *hn_out,
-                                 double *stat, double tol_abs) {
+                                 double *stat, const double *tol) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double tol_abs = *tol;
+    const int re = *flag;
     double w0 = sqrt(h1[j + 1]);
-    for (int i = 0; i <= j; i++) H[i * m + j] = h1[i] + h2[i];
-    double hn = sqrt(*nrm2);
+    for (int i = 0; i <= j; i++) H[i * m + j] = re ? h1[i] + h2[i] : h1[i];
+    double hn = sqrt(re ? *nrmB : *nrmA);
     for (int i = 0; i < j; i++) {
         double a = H[i * m + j], b = H[(i + 1) * m + j];
         H[i * m + j] = cs[i] * a + sn[i] * b;
@@ -646,12 +796,13 @@ __global__ void k_arnoldi_finish(int j, int m, const double *h1, const double *h
     stat[1] = est <= tol_abs ? 1.0 : 0.0;
     stat[2] = hn <= 1e-14 * w0 ? 1.0 : 0.0;
     stat[3] = hn;
+    stat[4] = re;
 }
 
-void launch_arnoldi_finish(int j, int m, const double *h1, const double *h2, const double *nrm2,
-                           double *H, double *cs, double *sn, double *g, double *hn, double *stat,
-                           double tol_abs, cudaStream_t s) {
-    k_arnoldi_finish<<<1, 32, 0, s>>>(j, m, h1, h2, nrm2, H, cs, sn, g, hn, stat, tol_abs);
+void launch_arnoldi_finish(int j, int m, const double *h1, const double *h2, const double *nrmA,
+                           const double *nrmB, const int *flag, double *H, double *cs, double *sn,
+                           double *g, double *hn, double *stat, const double *tol, cudaStream_t s) {
+    k_arnoldi_finish<<<1, 32, 0, s>>>(j, m, h1, h2, nrmA, nrmB, flag, H, cs, sn, g, hn, stat, tol);
 }
 
 __global__ void k_init_g(double *g, int m, const double *beta) {
@@ -694,6 +845,7 @@ void launch_gather_int(const int *idx, int n, const int *v, int *out, cudaStream
     if (n > 0) k_gather_int<<<GRIDN(n, 256), 256, 0, s>>>(idx, n, v, out);
 }
 
+
 // ------------------------------------------------------- instantiations
 #define INST_T_TV(T, TV)                                                                          \
     template void launch_frelax_first<T, TV>(int, const int *, const int *, const int *,          \
@@ -712,7 +864,13 @@ void launch_gather_int(const int *idx, int n, const int *v, int *out, cudaStream
     template void launch_amg_smooth0_residual<T, TV>(const DCSR &, const T *, const T *,          \
                                                      const TV *, T *, T *, cudaStream_t);         \
     template void launch_amg_post_smooth<T, TV>(const DCSR &, const T *, const T *, const TV *,   \
-                                                const T *, TV *, cudaStream_t);
+                                                const T *, TV *, cudaStream_t);                   \
+    template void launch_amg_residual<T, TV>(const DCSR &, const T *, const T *, const TV *, T *, \
+                                             cudaStream_t);                                       \
+    template void launch_mgr_restrict_scaled<T, TV>(const DCSR &, const T *, const int *,         \
+                                                    const TV *, const T *, T *, const T *, T *,   \
+                                                    cudaStream_t);                                \
+    template void launch_scale<T, TV>(int, const T *, const TV *, T *, cudaStream_t);
 
 INST_T_TV(double, double)
 INST_T_TV(float, float)
@@ -726,6 +884,10 @@ template void launch_csr_spmv<double>(const DCSR &, const double *, const double
                                       cudaStream_t);
 template void launch_csr_spmv<float>(const DCSR &, const float *, const float *, float *,
                                      cudaStream_t);
+template void launch_restrict_scaled<double>(const DCSR &, const double *, const double *, double *,
+                                             const double *, double *, cudaStream_t);
+template void launch_restrict_scaled<float>(const DCSR &, const float *, const float *, float *,
+                                            const float *, float *, cudaStream_t);
 template void launch_csr_spmv_add<double>(const DCSR &, const double *, const double *, double *,
                                           cudaStream_t);
 template void launch_csr_spmv_add<float>(const DCSR &, const float *, const float *, float *,

@@ -51,7 +51,7 @@ class mgr_solve_info(C.Structure):
                 ("setup_ms", C.c_double), ("solve_ms", C.c_double),
                 ("mgr_levels", C.c_int32), ("amg_levels", C.c_int32),
                 ("level_rows", C.c_int64 * 40), ("level_nnz", C.c_int64 * 40),
-                ("operator_complexity", C.c_double)]
+                ("operator_complexity", C.c_double), ("reorth_steps", C.c_int32)]
 
     def as_dict(self):
         nl = self.mgr_levels + self.amg_levels
@@ -59,7 +59,8 @@ class mgr_solve_info(C.Structure):
                     setup_ms=self.setup_ms, solve_ms=self.solve_ms, mgr_levels=self.mgr_levels,
                     amg_levels=self.amg_levels, level_rows=list(self.level_rows[:nl]),
                     level_nnz=list(self.level_nnz[:nl]),
-                    operator_complexity=self.operator_complexity)
+                    operator_complexity=self.operator_complexity,
+                    reorth_steps=self.reorth_steps)
 
 
 _lib = None
