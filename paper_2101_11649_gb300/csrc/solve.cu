@@ -27,15 +27,15 @@ __device__ __forceinline__ T group_sum(T s) {
 
 // ----------------------------------------------------------- chunk engine
 // A warp owns R consecutive rows (R a power of two, ~192 nonzeros per
-// chunk).  Phase 1 stages the chunk in shared memory: each lane loads up to
-// CCAP/32 values and column indices (coalesced) and gathers the matching
-// x entries, so a lane has many independent loads in flight.  Phase 2 gives
-// each row G = 32/R lanes; lane j of a group runs one fused multiply-add
-// chain over a contiguous slice of its row from shared memory, and the group
-// combines its G partial sums with a fixed shuffle tree.  FP64 work stays at
-// one FMA per nonzero plus log2(G) adds per row (FP64 issue rate, not HBM,
-// bounds FP64 sparse products on this part).
-constexpr int CCAP = 320;      // nonzeros a warp stages in shared memory
+// chunk).  Phase 1 stages the chunk's values and column indices in shared
+// memory with CU independent coalesced loads per lane.  Phase 2 gives each
+// row G = 32/R lanes; lane j of a group runs one fused multiply-add chain
+// over a contiguous slice of its row, and the group combines its G partial
+// sums with a fixed shuffle tree.  This keeps the FP64 work at one FMA per
+// nonzero plus log2(G) adds per row (FP64 issue rate, not HBM, bounds FP64
+// sparse products on this part).
+constexpr int CU = 8;          // independent loads per lane per batch
+constexpr int CCAP = 384;      // nonzeros a warp stages in shared memory
 constexpr int CWARPS = 8;      // warps per block
 
 static inline int rows_per_warp(long long nnz, int n) {
@@ -56,29 +56,13 @@ __device__ __forceinline__ T group_tree(T s) {
 template <int R, class T, class XF, class EPI>
 __device__ __forceinline__ void chunk_rows(int r0, int r1, int p0, int cnt, const int *__restrict__ rp,
                                            const int *__restrict__ ci, const T *__restrict__ v,
-                                           const XF &xf, const EPI &epi, T *sv, T *sx, int lane) {
+                                           const XF &xf, const EPI &epi, T *sv, int *sc, int lane) {
     constexpr int G = 32 / R;
-    // phase 1: stage values and gathered x entries; the loads of all slots
-    // issue before the first use (independent loads in flight per lane)
-    constexpr int NT = CCAP / 32;
-    int cj[NT];
-    T vv[NT], xv[NT];
+    // phase 1: stage values and columns
 #pragma unroll
-    for (int t = 0; t < NT; t++) {
+    for (int t = 0; t < CCAP / 32; t++) {
         const int q = lane + 32 * t;
-        cj[t] = q < cnt ? __ldg(ci + p0 + q) : -1;
-    }
-#pragma unroll
-    for (int t = 0; t < NT; t++) {
-        const int q = lane + 32 * t;
-        vv[t] = q < cnt ? __ldg(v + p0 + q) : (T)0;
-    }
-#pragma unroll
-    for (int t = 0; t < NT; t++) xv[t] = cj[t] >= 0 ? xf(cj[t]) : (T)0;
-#pragma unroll
-    for (int t = 0; t < NT; t++) {
-        const int q = lane + 32 * t;
-        if (q < cnt) { sv[q] = vv[t]; sx[q] = xv[t]; }
+        if (q < cnt) { sv[q] = __ldg(v + p0 + q); sc[q] = __ldg(ci + p0 + q); }
     }
     __syncwarp();
     // phase 2: G lanes per row, contiguous slices
@@ -89,7 +73,7 @@ __device__ __forceinline__ void chunk_rows(int r0, int r1, int p0, int cnt, cons
         const int a = __ldg(rp + row) - p0, b = __ldg(rp + row + 1) - p0;
         const int len = b - a, Lr = (len + G - 1) / G;
         const int q0 = a + j * Lr, q1 = min(q0 + Lr, b);
-        for (int q = q0; q < q1; q++) s = fma(sv[q], sx[q], s);
+        for (int q = q0; q < q1; q++) s = fma(sv[q], xf(sc[q]), s);
     }
     s = group_tree<G, T>(s);
     if (row < r1 && j == 0) epi(row, s);
@@ -101,7 +85,7 @@ __global__ void __launch_bounds__(CWARPS * 32) k_csr_chunk(int n, const int *__r
                                                            const int *__restrict__ ci,
                                                            const T *__restrict__ v, XF xf, EPI epi) {
     __shared__ T sv[CWARPS][CCAP];
-    __shared__ T sx[CWARPS][CCAP];
+    __shared__ int sc[CWARPS][CCAP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nchunk = (n + R - 1) / R;
     for (int c = blockIdx.x * CWARPS + warp; c < nchunk; c += gridDim.x * CWARPS) {
@@ -109,7 +93,7 @@ __global__ void __launch_bounds__(CWARPS * 32) k_csr_chunk(int n, const int *__r
         const int p0 = __ldg(rp + r0), p1 = __ldg(rp + r1);
         const int cnt = p1 - p0;
         if (cnt <= CCAP) {
-            chunk_rows<R, T, XF, EPI>(r0, r1, p0, cnt, rp, ci, v, xf, epi, sv[warp], sx[warp], lane);
+            chunk_rows<R, T, XF, EPI>(r0, r1, p0, cnt, rp, ci, v, xf, epi, sv[warp], sc[warp], lane);
         } else {
             for (int row = r0; row < r1; row++) {
                 const int a = __ldg(rp + row), b = __ldg(rp + row + 1);
