@@ -1,4 +1,4 @@
-"""Compositional flow with wells (4x4 BSR), shaped like Sec. 4.2 / Eq. 9.
+"""Compositional flow with wells (4x4 BSR), shaped like Sec. 4.2 / Eq. 12.
 
 Recipe (a synthetic stand-in; the paper's EOS-based model is App. B):
   * nx*ny*nz unit cells, ln K ~ N(0, 1.5^2), harmonic transmissibility.

@@ -12,15 +12,15 @@ Recipe:
     X = face-centroid offsets from the cell centroid, N = outward vector
     areas, Q = orthonormal basis of range(N).  Consistency M_c N K = X holds
     when X^T N = |c| I.
-  * Saddle point of Eq. 12 with A_ww = blockdiag(M_c), A_wp = -D,
+  * Saddle point of Eq. 6 with A_ww = blockdiag(M_c), A_wp = -D,
     A_wpi = C (= -1 one-sided-face-to-face incidence), incompressible
-    A_pw = D^T, A_pp = 1e-3 mean(kappa) I; statically condensed as in Eq. 13:
+    A_pw = D^T, A_pp = 1e-3 mean(kappa) I; statically condensed as in Eq. 7:
       Abar_pp = A_pp + D^T M^{-1} D            (diagonal)
       Abar_ppi = D^T M^{-1} C,  Abar_pip = C^T M^{-1} D,
       Abar_pipi = C^T M^{-1} C.
   * Unknown order: cell pressures, then x-, y-, z-face multipliers.
   * Labels: cells -> level 0 (F, Jacobi; Abar_pp diagonal, inverted
-    exactly), faces -> level 1 (C, AMG).  This is MGR_P, Eq. 15.
+    exactly), faces -> level 1 (C, AMG).  This is MGR_P, Eq. 9.
   * rhs ~ N(0,1).
 """
 from __future__ import annotations

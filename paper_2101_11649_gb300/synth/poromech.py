@@ -1,4 +1,4 @@
-"""Poromechanics with a planar hydraulic fracture (3x3 BSR), Sec. 4.3 / Eq. 10.
+"""Poromechanics with a planar hydraulic fracture (3x3 BSR), Sec. 4.3 / Eq. 13.
 
 Recipe (a synthetic stand-in for the paper's GEOSX fracture model, App. C):
   * ne^3 trilinear hexahedra of side h = 4 m, (ne+1)^3 nodes, 3 displacement

@@ -80,7 +80,7 @@ def test_dense_lu_matches_numpy():
 
 # --------------------------------------------------- reduced operator (Eq. 2, 4)
 def test_reduced_operator_is_schur_complement_diagonal_F():
-    """A_FF diagonal (MGR_P on the mimetic system, Eq. 15): the coarse
+    """A_FF diagonal (MGR_P on the mimetic system, Eq. 9): the coarse
     operator A_CC - A_CF D^{-1} A_FC is the exact Schur complement of Eq. 2."""
     s = make_mimetic(5, 4, 3)
     o = O.Oracle(s)
