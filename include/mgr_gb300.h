@@ -159,6 +159,26 @@ mgr_status mgr_bsr_spmv(int32_t nb, int32_t b, const int32_t *row_ptr, const int
                         const double *val, const double *x, double *y, double alpha, double beta,
                         void *stream);
 
+/*
+ * Residual r = bvec - A x and its norm without any allocation (the paper has
+ * no counterpart; this serves callers that cannot call cudaMalloc: code
+ * running while a CUDA graph is being captured, plug-ins whose host
+ * application owns all device memory, loops that must not enter the
+ * allocator).  A is a block-CSR matrix on the device (as mgr_bsr_spmv);
+ * x, bvec, r (length n = nb*b) and norm_out (one double, = ||r||_2) are
+ * caller-owned device memory.  The reduction's only scratch is a file-scope
+ * static device array of MGR_NOALLOC_MAX_BLOCKS partial sums plus a ticket
+ * (32 KiB per GPU, held until the process exits); one partial covers 4096
+ * entries, so n may be at most 16,777,216 (MGR_ERR_UNSUPPORTED beyond).
+ * The first call on a device looks up the array's device address (make it
+ * before any stream capture).  Calls share the array: calls that overlap on
+ * the GPU race.  Enqueued on stream; returns without synchronising.
+ */
+#define MGR_NOALLOC_MAX_BLOCKS 4096
+mgr_status mgr_residual_norm_noalloc(int32_t nb, int32_t b, const int32_t *row_ptr,
+                                     const int32_t *col_idx, const double *val, const double *x,
+                                     const double *bvec, double *r, double *norm_out, void *stream);
+
 /* Release the handle and everything it owns.  NULL is a no-op. */
 void mgr_free(mgr_handle h);
 

@@ -22,6 +22,7 @@ UNITS = {
     "setup.cu": ["--fmad=false"],
     "solve.cu": [],
     "mgr_api.cu": [],
+    "noalloc.cu": [],
 }
 
 

@@ -95,6 +95,7 @@ def lib(build_if_missing: bool = True):
     L.mgr_get_cf.argtypes = [vp, i32, vp]
     L.mgr_get_dinv.argtypes = [vp, i32, vp, vp]
     L.mgr_get_info.argtypes = [vp, vp]
+    L.mgr_residual_norm_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mgr_launch_count.argtypes = []
     L.mgr_launch_count.restype = C.c_int64
     L.mgr_profile.argtypes = [vp, i32]
@@ -307,3 +308,20 @@ def bsr_spmv(row_ptr, col_idx, val, b, x, y=None, alpha=1.0, beta=0.0, stream=No
 def launch_count() -> int:
     """Kernel launches made by the library so far (all handles)."""
     return int(lib().mgr_launch_count())
+
+
+def residual_norm_noalloc(row_ptr, col_idx, val, b, x, bvec, r=None, norm=None, stream=None):
+    """r = bvec - A x and ||r||_2 (device tensors) through the allocation-free
+    entry point: its reduction scratch is a static device array, so it can run
+    where cudaMalloc cannot be called (torch may still allocate r and norm
+    here when they are not passed in)."""
+    import torch
+    r = torch.empty_like(x) if r is None else r
+    norm = torch.empty(1, dtype=torch.float64, device=x.device) if norm is None else norm
+    nb = row_ptr.numel() - 1
+    st = lib().mgr_residual_norm_noalloc(nb, int(b), _ptr(row_ptr), _ptr(col_idx), _ptr(val),
+                                         _ptr(x), _ptr(bvec), _ptr(r), _ptr(norm),
+                                         _stream_ptr(stream))
+    if st != MGR_OK:
+        raise MGRError(st, "mgr_residual_norm_noalloc")
+    return r, norm
