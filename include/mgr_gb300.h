@@ -221,9 +221,11 @@ mgr_status mgr_profile(mgr_handle h, int32_t on);
 int32_t mgr_profile_entries(mgr_handle h);
 
 /* Entry i: name (host buffer of name_cap bytes), summed device time, number
- * of launches and algorithmic bytes per launch.  */
+ * of launches, and per launch (averaged over launches) the algorithmic bytes
+ * and FP64 fused multiply-adds.  */
 mgr_status mgr_profile_entry(mgr_handle h, int32_t i, char *name, int32_t name_cap,
-                             double *total_ms, int64_t *launches, double *bytes_per_launch);
+                             double *total_ms, int64_t *launches, double *bytes_per_launch,
+                             double *fp64_fma_per_launch);
 
 #ifdef __cplusplus
 }

@@ -75,7 +75,7 @@ struct Prof {
     size_t used = 0;
     std::vector<int> ptag;
     std::vector<std::string> names;
-    std::vector<double> ms, bytes;
+    std::vector<double> ms, bytes, fma;
     std::vector<long long> cnt;
 };
 
@@ -130,7 +130,7 @@ static mgr_status cuda_fail(mgr_handle h, const char *where) {
 struct KScope {
     mgr_handle h;
     long long idx = -1;
-    KScope(mgr_handle hh, const char *name, int level, double bytes) : h(hh) {
+    KScope(mgr_handle hh, const char *name, int level, double bytes, double fma64 = 0.0) : h(hh) {
         g_launches.fetch_add(1, std::memory_order_relaxed);
         Prof &P = h->prof;
         if (!P.on) return;
@@ -142,8 +142,11 @@ struct KScope {
             if (P.names[t] == buf) { tag = (int)t; break; }
         if (tag < 0) {
             tag = (int)P.names.size();
-            P.names.push_back(buf); P.ms.push_back(0.0); P.bytes.push_back(bytes); P.cnt.push_back(0);
+            P.names.push_back(buf); P.ms.push_back(0.0); P.bytes.push_back(0.0); P.cnt.push_back(0);
+            P.fma.push_back(0.0);
         }
+        P.bytes[tag] += bytes;
+        P.fma[tag] += fma64;
         if (P.pool.size() < 2 * (P.used + 1)) {
             cudaEvent_t a, b;
             cudaEventCreate(&a); cudaEventCreate(&b);
@@ -508,7 +511,8 @@ static void amg_cycle(mgr_handle h, int k, const TV *r, TV *x, int trans) {
     cudaStream_t s = h->s;
     AmgLevel &L = h->amg[k];
     if (k == h->namg - 1) {
-        KScope ks(h, "coarsest_dense_solve", k, (double)h->nco * h->nco * 8 + 2.0 * h->nco * sizeof(TV));
+        KScope ks(h, "coarsest_dense_solve", k, (double)h->nco * h->nco * 8 + 2.0 * h->nco * sizeof(TV),
+                  (double)h->nco * h->nco);
         launch_dense_matvec<TV>(h->nco, trans ? h->coinvT : h->coinv, r, x, s);
         return;
     }
@@ -519,23 +523,25 @@ static void amg_cycle(mgr_handle h, int k, const TV *r, TV *x, int trans) {
     AmgLevel &C = h->amg[k + 1];
     const bool c_coarsest = (k + 1 == h->namg - 1);
     const double ts = sizeof(T), tv = sizeof(TV);
+    const double f64 = sizeof(T) == 8 ? 1.0 : 0.0;  // FP64 FMAs only in the FP64 form
     double an = A.n, annz = A.nnz, nc = C.A.n;
     {
-        KScope ks(h, "amg_residual", k, annz * (ts + 4) + (an + 1) * 4 + an * (2 * ts + tv));
+        KScope ks(h, "amg_residual", k, annz * (ts + 4) + (an + 1) * 4 + an * (2 * ts + tv), f64 * annz);
         launch_amg_residual<T, TV>(A, av, xw, r, res, s);
     }
     {
-        KScope ks(h, "amg_restrict", k, (double)L.R.nnz * (ts + 4) + (nc + 1) * 4 + an * ts + nc * ts * (c_coarsest ? 1 : 3));
+        KScope ks(h, "amg_restrict", k, (double)L.R.nnz * (ts + 4) + (nc + 1) * 4 + an * ts + nc * ts * (c_coarsest ? 1 : 3),
+                  f64 * L.R.nnz);
         if (c_coarsest) launch_csr_spmv<T>(L.R, Sel<T>::v(L.R), res, Sel<T>::r(C), s);
         else launch_restrict_scaled<T>(L.R, Sel<T>::v(L.R), res, Sel<T>::r(C), Sel<T>::dinv(C), Sel<T>::xw(C), s);
     }
     amg_cycle<T, T>(h, k + 1, Sel<T>::r(C), Sel<T>::x(C), trans);
     {
-        KScope ks(h, "amg_prolong", k, (double)L.P.nnz * (ts + 4) + (an + 1) * 4 + nc * ts + 2 * an * ts);
+        KScope ks(h, "amg_prolong", k, (double)L.P.nnz * (ts + 4) + (an + 1) * 4 + nc * ts + 2 * an * ts, f64 * L.P.nnz);
         launch_csr_spmv_add<T>(L.P, Sel<T>::v(L.P), Sel<T>::x(C), xw, s);
     }
     {
-        KScope ks(h, "amg_post_smooth", k, annz * (ts + 4) + (an + 1) * 4 + an * (2 * ts + 2 * tv));
+        KScope ks(h, "amg_post_smooth", k, annz * (ts + 4) + (an + 1) * 4 + an * (2 * ts + 2 * tv), f64 * (annz + an));
         launch_amg_post_smooth<T, TV>(A, av, d, r, xw, x, s);
     }
 }
@@ -563,6 +569,7 @@ static void mgr_cycle(mgr_handle h, int l, const TV *v, TV *z) {
     const T *dinv = Sel<T>::dinv(L);
     T om = (T)L.omega;
     const double ts = sizeof(T), tv = sizeof(TV);
+    const double f64 = sizeof(T) == 8 ? 1.0 : 0.0;
     double nF = L.nF, nC = L.nC, gs = L.relax == 2 ? 4.0 : 1.0;
     {
         KScope ks(h, "mgr_frelax_first", l, nF * (gs * ts + 4 + tv + ts + (L.relax == 2 ? 8 : 0)));
@@ -578,14 +585,16 @@ static void mgr_cycle(mgr_handle h, int l, const TV *v, TV *z) {
     }
     {
         const bool fuse = (l + 1 == h->nlev) && h->namg > 1;
-        KScope ks(h, "mgr_restrict", l, (double)L.ACF.nnz * (ts + 4) + (nC + 1) * 4 + nF * ts + nC * (4 + tv + ts + (fuse ? 2 * ts : 0)));
+        KScope ks(h, "mgr_restrict", l, (double)L.ACF.nnz * (ts + 4) + (nC + 1) * 4 + nF * ts + nC * (4 + tv + ts + (fuse ? 2 * ts : 0)),
+                  f64 * L.ACF.nnz);
         if (fuse) launch_mgr_restrict_scaled<T, TV>(L.ACF, Sel<T>::v(L.ACF), L.cidx, v, zF, vC,
                                                     Sel<T>::dinv(h->amg[0]), Sel<T>::xw(h->amg[0]), s);
         else launch_mgr_restrict<T, TV>(L.ACF, Sel<T>::v(L.ACF), L.cidx, v, zF, vC, s);
     }
     mgr_cycle<T, T>(h, l + 1, vC, eC);
     {
-        KScope ks(h, "mgr_interp", l, (double)L.W.nnz * (ts + 4) + (nF + 1) * 4 + nC * (ts + 4 + tv) + nF * (ts + 4 + tv));
+        KScope ks(h, "mgr_interp", l, (double)L.W.nnz * (ts + 4) + (nF + 1) * 4 + nC * (ts + 4 + tv) + nF * (ts + 4 + tv),
+                  f64 * L.W.nnz);
         launch_mgr_interp<T, TV>(L.W, Sel<T>::v(L.W), L.nC, L.fidx, L.cidx, zF, eC, z, s);
     }
 }
@@ -650,13 +659,13 @@ static double outer_bytes(mgr_handle h) {
 }
 
 static void outer_spmv(mgr_handle h, const double *x, double *y, int trans) {
-    KScope ks(h, trans ? "spmv_AT" : "spmv_A", -1, outer_bytes(h));
+    KScope ks(h, trans ? "spmv_AT" : "spmv_A", -1, outer_bytes(h), (double)h->nnzb * h->b * h->b);
     if (trans) launch_csr_spmv<double>(h->A0T, h->A0T.v, x, y, h->s);
     else launch_bsr_spmv(h->nb, h->b, h->brp, h->bci, h->bval, x, y, 1.0, 0.0, h->s, h->nnzb);
 }
 
 static void outer_residual(mgr_handle h, const double *x, const double *bvec, double *y, int trans) {
-    KScope ks(h, trans ? "residual_AT" : "residual_A", -1, outer_bytes(h) + h->n * 8.0);
+    KScope ks(h, trans ? "residual_AT" : "residual_A", -1, outer_bytes(h) + h->n * 8.0, (double)h->nnzb * h->b * h->b);
     if (trans) launch_csr_residual(h->A0T, x, bvec, y, h->s);
     else launch_bsr_residual(h->nb, h->b, h->brp, h->bci, h->bval, x, bvec, y, h->s, h->nnzb);
 }
@@ -697,9 +706,9 @@ static void arnoldi_step(mgr_handle h, int j, int trans) {
     double nd = (double)n;
     int k = j + 1;
     // first pass: projections on V_0..V_j and |w|^2 (w = V_{j+1} itself)
-    { KScope ks(h, "arnoldi_dots", -1, (k + 1) * nd * 8);
+    { KScope ks(h, "arnoldi_dots", -1, (k + 1) * nd * 8, (k + 1) * nd);
       launch_dots(K.V, n, k + 1, w, (int)n, K.partial, K.h1, K.ticket, nullptr, K.nblk, s); }
-    { KScope ks(h, "arnoldi_update_norm", -1, k * nd * 8 + 2 * nd * 8);
+    { KScope ks(h, "arnoldi_update_norm", -1, k * nd * 8 + 2 * nd * 8, (k + 1) * nd);
       launch_update_norm(K.V, n, k, K.h1, w, (int)n, K.partial, K.nrm2, K.ticket, K.flag, 1, K.nblk, s); }
     // second pass only when the first cancelled most of w (device flag)
     { KScope ks(h, "arnoldi_reorth", -1, 0.0);
@@ -804,7 +813,7 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
             if (st == MGR_ERR_INVALID) { h->err = "preconditioned residual is not finite"; break; }
             { KScope ks(h, "givens", -1, 0.0);
               launch_solve_upper(k, m, K.H, K.g, K.y, s); }
-            { KScope ks(h, "update_x", -1, (k + 2.0) * n * 8);
+            { KScope ks(h, "update_x", -1, (k + 2.0) * n * 8, (double)k * n);
               launch_multi_axpy(K.Z, n, k, K.y, x, (int)n, s); }
         }
     }
@@ -943,7 +952,7 @@ extern "C" mgr_status mgr_profile(mgr_handle h, int32_t on) {
     if (!h) return fail(h, MGR_ERR_INVALID, "NULL handle");
     prof_resolve(h);
     Prof &P = h->prof;
-    P.names.clear(); P.ms.clear(); P.bytes.clear(); P.cnt.clear(); P.ptag.clear(); P.used = 0;
+    P.names.clear(); P.ms.clear(); P.bytes.clear(); P.fma.clear(); P.cnt.clear(); P.ptag.clear(); P.used = 0;
     P.on = on != 0;
     return MGR_OK;
 }
@@ -956,7 +965,7 @@ extern "C" int32_t mgr_profile_entries(mgr_handle h) {
 
 extern "C" mgr_status mgr_profile_entry(mgr_handle h, int32_t i, char *name, int32_t name_cap,
                                         double *total_ms, int64_t *launches,
-                                        double *bytes_per_launch) {
+                                        double *bytes_per_launch, double *fp64_fma_per_launch) {
     if (!h) return fail(h, MGR_ERR_INVALID, "NULL handle");
     prof_resolve(h);
     Prof &P = h->prof;
@@ -964,6 +973,10 @@ extern "C" mgr_status mgr_profile_entry(mgr_handle h, int32_t i, char *name, int
     if (name && name_cap > 0) { strncpy(name, P.names[i].c_str(), name_cap - 1); name[name_cap - 1] = 0; }
     if (total_ms) *total_ms = P.ms[i];
     if (launches) *launches = P.cnt[i];
-    if (bytes_per_launch) *bytes_per_launch = P.bytes[i];
+    // per-launch figures averaged over the recorded launches (they vary with
+    // the Arnoldi step)
+    double nrec = P.cnt[i] > 0 ? (double)P.cnt[i] : 1.0;
+    if (bytes_per_launch) *bytes_per_launch = P.bytes[i] / nrec;
+    if (fp64_fma_per_launch) *fp64_fma_per_launch = P.fma[i] / nrec;
     return MGR_OK;
 }

@@ -102,7 +102,8 @@ def lib(build_if_missing: bool = True):
     L.mgr_profile_entries.argtypes = [vp]
     L.mgr_profile_entries.restype = i32
     L.mgr_profile_entry.argtypes = [vp, i32, C.c_char_p, i32, C.POINTER(C.c_double),
-                                    C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]
     _lib = L
     return L
 
@@ -248,16 +249,16 @@ class MGRSolver:
         _check(lib().mgr_profile(self.h, int(bool(on))), self.h)
 
     def profile_table(self):
-        """[{name, ms, launches, bytes_per_launch}] recorded since profile(True)."""
+        """[{name, ms, launches, bytes_per_launch, fp64_fma_per_launch}] since profile(True)."""
         L = lib()
         out = []
         for i in range(L.mgr_profile_entries(self.h)):
             buf = C.create_string_buffer(96)
-            ms, cnt, by = C.c_double(), C.c_int64(), C.c_double()
+            ms, cnt, by, fm = C.c_double(), C.c_int64(), C.c_double(), C.c_double()
             _check(L.mgr_profile_entry(self.h, i, buf, 96, C.byref(ms), C.byref(cnt),
-                                       C.byref(by)), self.h)
+                                       C.byref(by), C.byref(fm)), self.h)
             out.append(dict(name=buf.value.decode(), ms=ms.value, launches=cnt.value,
-                            bytes_per_launch=by.value))
+                            bytes_per_launch=by.value, fp64_fma_per_launch=fm.value))
         return out
 
     # -------------------------------------------------------- inspection
