@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-profile", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
     return p.parse_args()
 
 
@@ -350,6 +351,54 @@ def main():
         e2e = {"value": round(max_over_ranks(world, statistics.mean(ts), dev), 3), "unit": "ms",
                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
 
+    # ---- batched form: 48 uneven two-phase systems, one launch per kernel class
+    batched = None
+    if not args.no_batched:
+        from paper_2101_11649_gb300.synth import make_batch
+        systems, _ = make_batch(48)
+        nunk = sum(s.n for s in systems)
+        rhs = [torch.as_tensor(s.rhs, device=dev) for s in systems]
+        batched = {"workload": f"48 two-phase TPFA systems, grids 16^3..96x96x48, {nunk} unknowns",
+                   "rtol": args.rtol}
+        st = torch.cuda.current_stream()
+        for prec in ("fp64", "fp32"):
+            t0 = time.perf_counter()
+            bt = M.MGRBatch(systems, precision=prec)
+            torch.cuda.synchronize()
+            setup_ms = (time.perf_counter() - t0) * 1e3
+            for _ in range(max(1, args.warmup)):
+                bt.solve(rhs, rtol=args.rtol)
+            ts, infos = [], None
+            for _ in range(max(1, min(args.steps, 5))):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                _, infos = bt.solve(rhs, rtol=args.rtol)
+                e1.record(st)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            its = [i["iterations"] for i in infos]
+            ms = statistics.mean(ts)
+            batched[prec] = {"ms": round(ms, 3), "setup_ms": round(setup_ms, 1),
+                             "iterations_max": max(its), "iterations_mean": round(sum(its) / len(its), 2),
+                             "all_converged": all(i["status"] == 0 for i in infos),
+                             "unknowns_per_s": round(nunk / (ms / 1e3), 1)}
+            if prec == "fp64":
+                # the same systems one after another through their single-system handles
+                seq = 0.0
+                for i, s in enumerate(systems):
+                    sv = bt.system(i)
+                    x1 = torch.zeros_like(rhs[i])
+                    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    sv.solve(rhs[i], x1, rtol=args.rtol)
+                    e1.record(st)
+                    e1.synchronize()
+                    seq += e0.elapsed_time(e1)
+                batched["sequential_fp64_ms"] = round(seq, 3)
+                batched["speedup_vs_sequential_fp64"] = round(seq / ms, 3)
+            bt.close()
+
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -375,7 +424,7 @@ def main():
                 "levels": {"mgr": info64["mgr_levels"], "amg": info64["amg_levels"],
                            "rows": info64["level_rows"], "nnz": info64["level_nnz"],
                            "operator_complexity": round(info64["operator_complexity"], 3)},
-                "vcycle": vcycle, "roofline": roofline,
+                "vcycle": vcycle, "roofline": roofline, "batched": batched,
                 "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
                             for r in kernels[:12]],
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

@@ -146,6 +146,13 @@ mgr_status mgr_solve(mgr_handle h, const double *b, double *x, double rtol, int3
 mgr_status mgr_solve_transpose(mgr_handle h, const double *g, double *lam, double rtol,
                                int32_t maxit, mgr_solve_info *info);
 
+/* Replace the stored values of A (same pattern; val as in mgr_bsr, host or
+ * device) in the operator that mgr_spmv, mgr_solve and mgr_solve_transpose
+ * apply, keeping the MGR/AMG hierarchy built by mgr_setup as the
+ * preconditioner: the reuse of a hierarchy across Newton steps (Sec. 5.3).
+ * Synchronises the stream.  INVALID on a non-finite value. */
+mgr_status mgr_update_values(mgr_handle h, const double *val, int32_t on_device);
+
 /* dA_val[p*b*b + r*b + c] = -lam[I*b + r] * x[J*b + c] for block p = (I, J):
  * the gradient of a scalar loss with respect to the stored values of A when
  * lam solves A^T lam = dL/dx.  device pointers. */
@@ -178,6 +185,33 @@ mgr_status mgr_bsr_spmv(int32_t nb, int32_t b, const int32_t *row_ptr, const int
 mgr_status mgr_residual_norm_noalloc(int32_t nb, int32_t b, const int32_t *row_ptr,
                                      const int32_t *col_idx, const double *val, const double *x,
                                      const double *bvec, double *r, double *norm_out, void *stream);
+
+/* --------------------------------------------------------------- batched
+ * Many systems of uneven sizes (different time steps or models) solved
+ * together.  Each system keeps its own hierarchy, and every kernel class of
+ * the V-cycle, the outer product and the Arnoldi reductions runs as one
+ * launch over all systems (a job table of per-system operands; per-system
+ * convergence flags drop finished systems).  Chunk shapes of the sparse
+ * products are picked at setup by timing candidates (autotuner).  All
+ * systems need the same block size, MGR level count and options, at least
+ * one MGR level, and one F-relaxation sweep (MGR_ERR_UNSUPPORTED otherwise).
+ */
+typedef struct mgr_batch_ctx *mgr_batch;
+
+/* A[nsys], cf[nsys] as for mgr_setup; stream as for mgr_setup. */
+mgr_status mgr_setup_batched(int32_t nsys, const mgr_bsr *A, const mgr_labels *cf,
+                             const mgr_options *opt, void *stream, mgr_batch *out);
+
+/* FGMRES(m) for every system: b[i], x[i] device vectors (x[i] in: x0, out: x);
+ * info[nsys] may be NULL.  NOT_CONVERGED if any system hit maxit. */
+mgr_status mgr_solve_batched(mgr_batch h, const double *const *b, double *const *x, double rtol,
+                             int32_t maxit, mgr_solve_info *info);
+
+/* The single-system handle of system i (owned by the batch): for
+ * mgr_solve_transpose, mgr_grad_values and inspection. */
+mgr_status mgr_batch_handle(mgr_batch h, int32_t i, mgr_handle *out);
+
+void mgr_free_batched(mgr_batch h);
 
 /* Release the handle and everything it owns.  NULL is a no-op. */
 void mgr_free(mgr_handle h);

@@ -150,6 +150,56 @@ void launch_multi_axpy(const double *Z, long long ldz, int k, const double *y, d
                        cudaStream_t s);
 int multidot_blocks(int n);
 
+// ---------------------------------------------------------------- batched
+// One system's operands for one kernel class.  Vectors that walk the Krylov
+// basis (the top-level input/output of the V-cycle, the outer product's
+// operands) are addressed as base + jsel * stride, jsel a launch argument.
+struct BJob {
+    int n = 0;                       // rows / elements / block rows
+    const int *rp = nullptr, *ci = nullptr;
+    const void *v = nullptr;         // matrix values (or dense inverse)
+    const void *x = nullptr;         // gathered vector
+    const void *r = nullptr;         // per-row input
+    const void *d = nullptr;         // per-row diagonal inverse (may be null)
+    void *o1 = nullptr, *o2 = nullptr;
+    const int *idx = nullptr;        // index map
+    const int *gs = nullptr, *gz = nullptr;  // block-Jacobi group start / size
+    const void *zF = nullptr;
+    const int *active = nullptr;     // system still iterating (null = always)
+    long long sx = 0, sr = 0, so1 = 0;  // strides per jsel
+    // Krylov reductions
+    double *partial = nullptr;
+    unsigned *ticket = nullptr;
+    int *flag = nullptr;
+    int nblk = 0;
+};
+
+// batched table launches (T = value type, TV = top-level vector type)
+enum BOp { BOP_RESID, BOP_RESTRICT, BOP_PROLONG, BOP_POST, BOP_MGR_RESTRICT, BOP_MGR_INTERP,
+           BOP_OUTER_CSR };
+template <class T, class TV>
+void launch_bchunk(int op, const BJob *jobs, const long long *prefix, int njobs, long long total,
+                   int R, int jsel, cudaStream_t s);
+template <class T, class TV>
+void launch_bfrelax_first(const BJob *jobs, const long long *prefix, int njobs, long long total,
+                          T omega, int jsel, cudaStream_t s);
+template <class T, class TV>
+void launch_bscatter(const BJob *jobs, const long long *prefix, int njobs, long long total,
+                     int jsel, cudaStream_t s);
+template <class TV>
+void launch_bdense(const BJob *jobs, const long long *prefix, int njobs, long long total, int jsel,
+                   cudaStream_t s);
+void launch_bbsr(int b, const BJob *jobs, const long long *prefix, int njobs, long long total,
+                 int jsel, cudaStream_t s);
+void launch_bdots(int k, const BJob *jobs, const long long *bprefix, int njobs, long long nblocks,
+                  int jsel, int conditional, int sqrt_out, cudaStream_t s);
+void launch_bupdate_norm(int k, const BJob *jobs, const long long *bprefix, int njobs,
+                         long long nblocks, int jsel, int mode, cudaStream_t s);
+void launch_bscale(const BJob *jobs, const long long *prefix, int njobs, long long total, int jsel,
+                   int invert, cudaStream_t s);
+void launch_bmulti_axpy(const BJob *jobs, const long long *prefix, int njobs, long long total,
+                        cudaStream_t s);
+
 void launch_grad_values(int nb, int b, const int *rp, const int *ci, const double *lam,
                         const double *x, double *dA, cudaStream_t s);
 

@@ -853,6 +853,32 @@ extern "C" mgr_status mgr_solve_transpose(mgr_handle h, const double *g, double 
     return fgmres(h, g, lam, rtol, maxit, 1, info);
 }
 
+extern "C" mgr_status mgr_update_values(mgr_handle h, const double *val, int32_t on_device) {
+    if (!h || !val) return fail(h, MGR_ERR_INVALID, "NULL argument");
+    cudaStream_t s = h->s;
+    const long long nv = h->nnzb * h->b * h->b;
+    cudaMemcpyAsync(h->bval, val, sizeof(double) * nv,
+                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+    launch_validate_bsr(h->nb, h->b, h->brp, h->bci, h->bval, h->errw, s);
+    if (read_errw(h)) return fail(h, MGR_ERR_INVALID, "non-finite matrix value");
+    // the transposed outer operator: same pattern, positions unchanged
+    Arena tmp;
+    DCSR A0, T;
+    A0.n = A0.m = h->n;
+    A0.nnz = (int)nv;
+    A0.rp = tmp.alloc<int>(h->n + 1);
+    A0.ci = tmp.alloc<int>(nv + 1);
+    A0.v = tmp.alloc<double>(nv + 1);
+    if (!A0.rp || !A0.ci || !A0.v) { tmp.free_all(); return fail(h, MGR_ERR_NOMEM, "update scratch"); }
+    launch_bsr_to_csr(h->nb, h->b, h->brp, h->bci, h->bval, A0, s);
+    if (transpose(A0, T, s, tmp)) { tmp.free_all(); return fail(h, MGR_ERR_NOMEM, "update transpose"); }
+    cudaMemcpyAsync(h->A0T.v, T.v, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+    tmp.free_all();
+    if (cudaGetLastError() != cudaSuccess) return cuda_fail(h, "mgr_update_values");
+    return MGR_OK;
+}
+
 extern "C" mgr_status mgr_grad_values(mgr_handle h, const double *lam, const double *x,
                                       double *dA_val) {
     if (!h || !lam || !x || !dA_val) return fail(h, MGR_ERR_INVALID, "NULL argument");
@@ -979,4 +1005,635 @@ extern "C" mgr_status mgr_profile_entry(mgr_handle h, int32_t i, char *name, int
     if (bytes_per_launch) *bytes_per_launch = P.bytes[i] / nrec;
     if (fp64_fma_per_launch) *fp64_fma_per_launch = P.fma[i] / nrec;
     return MGR_OK;
+}
+
+// ================================================================ batched
+// Many systems of uneven sizes solved together: each keeps its own hierarchy
+// (built by mgr_setup), and every kernel class runs as ONE launch over all
+// systems through a job table (per-system operands + a prefix of work items).
+// The V-cycle is level-synchronous across systems; FGMRES reductions are
+// segmented per system; converged systems drop out through device flags.
+
+namespace mgr {
+
+struct BTable {
+    BJob *jobs = nullptr;
+    long long *prefix = nullptr;
+    int njobs = 0;
+    long long total = 0;
+    int R = 1;
+    int kind = 0;  // 0 chunk (warp-chunks of R rows), 1 elements, 2 reduction blocks
+    std::vector<BJob> host;
+};
+
+struct BKry {  // one system's Krylov scalars for the per-system bookkeeping kernels
+    double *h1, *h2, *nrm2, *nrmB, *H, *cs, *sn, *g, *hn, *stat, *beta, *y;
+    const double *tol;
+    int *flag, *active, *kk;
+};
+
+__global__ void k_bgivens(BKry *kr, int nsys, int j, int m) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    BKry K = kr[s];
+    if (!*K.active) return;
+    const int re = *K.flag;
+    double w0 = sqrt(K.h1[j + 1]);
+    for (int i = 0; i <= j; i++) K.H[i * m + j] = re ? K.h1[i] + K.h2[i] : K.h1[i];
+    double hn = sqrt(re ? *K.nrmB : *K.nrm2);
+    for (int i = 0; i < j; i++) {
+        double a = K.H[i * m + j], b = K.H[(i + 1) * m + j];
+        K.H[i * m + j] = K.cs[i] * a + K.sn[i] * b;
+        K.H[(i + 1) * m + j] = -K.sn[i] * a + K.cs[i] * b;
+    }
+    double a = K.H[j * m + j], b = hn;
+    double rho = sqrt(a * a + b * b);
+    K.cs[j] = a / rho;
+    K.sn[j] = b / rho;
+    K.H[j * m + j] = rho;
+    K.H[(j + 1) * m + j] = 0.0;
+    K.g[j + 1] = -K.sn[j] * K.g[j];
+    K.g[j] = K.cs[j] * K.g[j];
+    double est = fabs(K.g[j + 1]);
+    *K.hn = hn;
+    K.stat[0] = est;
+    K.stat[1] = est <= *K.tol ? 1.0 : 0.0;
+    K.stat[2] = hn <= 1e-14 * w0 ? 1.0 : 0.0;
+    K.stat[3] = hn;
+    K.stat[4] = re;
+}
+
+__global__ void k_binit_g(BKry *kr, int nsys, int m) {
+    int s = blockIdx.x;
+    if (s >= nsys) return;
+    BKry K = kr[s];
+    if (!*K.active) return;
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) K.g[i] = i == 0 ? *K.beta : 0.0;
+}
+
+__global__ void k_bsolve_upper(BKry *kr, int nsys, int m) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    BKry K = kr[s];
+    int k = *K.kk;
+    for (int i = k - 1; i >= 0; i--) {
+        double t = K.g[i];
+        for (int c = i + 1; c < k; c++) t -= K.H[i * m + c] * K.y[c];
+        K.y[i] = t / K.H[i * m + i];
+    }
+}
+
+}  // namespace mgr
+
+struct mgr_batch_ctx {
+    int nsys = 0;
+    std::vector<mgr_handle> hs;
+    cudaStream_t s = nullptr;
+    bool own_stream = false;
+    Arena ar;
+    int prec = 0, nlev = 0, kmax = 0, b = 1, m = 30;
+    int *active = nullptr, *kk = nullptr;
+    double *tol = nullptr, *stat = nullptr, *hstat = nullptr;
+    BKry *kry = nullptr;
+    // tables
+    std::vector<BTable> mgr_first, mgr_restrict, mgr_interp, mgr_scatter;
+    std::vector<BTable> amg_resid, amg_restrict, amg_prolong, amg_post;
+    BTable coarse, outer, dots1, dots2, upd1, upd2, vnorm, rnorm, v0scale;
+    BTable resid_user, xupd;
+    std::vector<cudaGraphExec_t> graphs;
+    std::vector<long long> graph_kernels;
+    std::string err;
+};
+
+static mgr_status bfail(mgr_batch bh, mgr_status st, const std::string &msg) {
+    if (bh) bh->err = msg;
+    g_last_error = msg;
+    return st;
+}
+
+// work items of one job: chunks of R rows, elements, or reduction blocks
+static long long job_items(const BTable &t, const BJob &j, int R) {
+    if (t.kind == 0) return (j.n + R - 1) / R;
+    if (t.kind == 2) return j.nblk;
+    return j.n;
+}
+
+static int upload_table(mgr_batch bh, BTable &t) {
+    t.njobs = (int)t.host.size();
+    if (!t.jobs) t.jobs = bh->ar.alloc<BJob>(t.njobs + 1);
+    if (!t.prefix) t.prefix = bh->ar.alloc<long long>(t.njobs + 2);
+    if (!t.jobs || !t.prefix) return ST_NOMEM;
+    std::vector<long long> pre(t.njobs + 1, 0);
+    for (int i = 0; i < t.njobs; i++) pre[i + 1] = pre[i] + job_items(t, t.host[i], t.R);
+    t.total = pre[t.njobs];
+    if (t.njobs) cudaMemcpyAsync(t.jobs, t.host.data(), sizeof(BJob) * t.njobs, cudaMemcpyHostToDevice, bh->s);
+    cudaMemcpyAsync(t.prefix, pre.data(), sizeof(long long) * (t.njobs + 1), cudaMemcpyHostToDevice, bh->s);
+    cudaStreamSynchronize(bh->s);
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+template <class T>
+static const void *vals_of(const DCSR &M) {
+    return sizeof(T) == 8 ? (const void *)M.v : (const void *)M.v32;
+}
+template <class T>
+static void *sel(double *d, float *f) { return sizeof(T) == 8 ? (void *)d : (void *)f; }
+
+// The AMG input/output buffers of system s at AMG level k (T precision)
+template <class T>
+static void amg_io(mgr_handle h, int k, void **r, void **x) {
+    if (k == 0) {
+        MgrLevel &L = h->lev[h->nlev - 1];
+        *r = sel<T>(L.vC, L.vC32);
+        *x = sel<T>(L.eC, L.eC32);
+    } else {
+        AmgLevel &A = h->amg[k];
+        *r = sel<T>(A.r, A.r32);
+        *x = sel<T>(A.x, A.x32);
+    }
+}
+
+template <class T>
+static int build_tables(mgr_batch bh) {
+    const int L = bh->nlev;
+    bh->mgr_first.assign(L, BTable()); bh->mgr_restrict.assign(L, BTable());
+    bh->mgr_interp.assign(L, BTable()); bh->mgr_scatter.assign(L, BTable());
+    bh->amg_resid.assign(bh->kmax, BTable()); bh->amg_restrict.assign(bh->kmax, BTable());
+    bh->amg_prolong.assign(bh->kmax, BTable()); bh->amg_post.assign(bh->kmax, BTable());
+    for (int s = 0; s < bh->nsys; s++) {
+        mgr_handle h = bh->hs[s];
+        Krylov &K = h->kr;
+        const int n = h->n;
+        int *act = bh->active + s;
+        for (int l = 0; l < L; l++) {
+            MgrLevel &M = h->lev[l];
+            const void *vin = l == 0 ? (const void *)K.V : sel<T>(h->lev[l - 1].vC, h->lev[l - 1].vC32);
+            void *zout = l == 0 ? (void *)K.Z : sel<T>(h->lev[l - 1].eC, h->lev[l - 1].eC32);
+            long long st = l == 0 ? n : 0;
+            BJob f; f.n = M.nF; f.r = vin; f.sr = st; f.d = sel<T>(M.dinv, M.dinv32); f.gs = M.gstart;
+            f.gz = M.gsize; f.idx = M.fidx; f.o1 = sel<T>(M.zF, M.zF32); f.active = act;
+            bh->mgr_first[l].host.push_back(f);
+            BJob r; r.n = M.nC; r.rp = M.ACF.rp; r.ci = M.ACF.ci; r.v = vals_of<T>(M.ACF);
+            r.x = sel<T>(M.zF, M.zF32); r.idx = M.cidx; r.r = vin; r.sr = st;
+            r.o1 = sel<T>(M.vC, M.vC32); r.active = act;
+            if (l + 1 == L && h->namg > 1) {
+                r.d = sel<T>(h->amg[0].dinv, h->amg[0].dinv32);
+                r.o2 = sel<T>(h->amg[0].xw, h->amg[0].xw32);
+            }
+            bh->mgr_restrict[l].host.push_back(r);
+            BJob w; w.n = M.nF; w.rp = M.W.rp; w.ci = M.W.ci; w.v = vals_of<T>(M.W);
+            w.x = sel<T>(M.eC, M.eC32); w.idx = M.fidx; w.zF = sel<T>(M.zF, M.zF32);
+            w.o1 = zout; w.so1 = st; w.active = act;
+            bh->mgr_interp[l].host.push_back(w);
+            BJob c; c.n = M.nC; c.idx = M.cidx; c.x = sel<T>(M.eC, M.eC32); c.o1 = zout; c.so1 = st;
+            c.active = act;
+            bh->mgr_scatter[l].host.push_back(c);
+        }
+        const int cl = h->namg - 1;  // this system's coarsest AMG level
+        for (int k = 0; k < cl; k++) {
+            AmgLevel &A = h->amg[k];
+            AmgLevel &C = h->amg[k + 1];
+            void *rk, *xk;
+            amg_io<T>(h, k, &rk, &xk);
+            void *rc, *xc;
+            amg_io<T>(h, k + 1, &rc, &xc);
+            BJob e; e.n = A.A.n; e.rp = A.A.rp; e.ci = A.A.ci; e.v = vals_of<T>(A.A);
+            e.x = sel<T>(A.xw, A.xw32); e.r = rk; e.o1 = sel<T>(A.res, A.res32); e.active = act;
+            bh->amg_resid[k].host.push_back(e);
+            BJob q; q.n = A.R.n; q.rp = A.R.rp; q.ci = A.R.ci; q.v = vals_of<T>(A.R);
+            q.x = sel<T>(A.res, A.res32); q.o1 = rc; q.active = act;
+            if (k + 1 < cl) { q.d = sel<T>(C.dinv, C.dinv32); q.o2 = sel<T>(C.xw, C.xw32); }
+            bh->amg_restrict[k].host.push_back(q);
+            BJob pr; pr.n = A.P.n; pr.rp = A.P.rp; pr.ci = A.P.ci; pr.v = vals_of<T>(A.P);
+            pr.x = xc; pr.o1 = sel<T>(A.xw, A.xw32); pr.active = act;
+            bh->amg_prolong[k].host.push_back(pr);
+            BJob po; po.n = A.A.n; po.rp = A.A.rp; po.ci = A.A.ci; po.v = vals_of<T>(A.A);
+            po.x = sel<T>(A.xw, A.xw32); po.r = rk; po.d = sel<T>(A.dinv, A.dinv32); po.o1 = xk;
+            po.active = act;
+            bh->amg_post[k].host.push_back(po);
+        }
+        {
+            void *rc, *xc;
+            amg_io<T>(h, cl, &rc, &xc);
+            BJob c; c.n = h->nco; c.v = h->coinv; c.r = rc; c.o1 = xc; c.active = act;
+            bh->coarse.host.push_back(c);
+        }
+        // outer product w = A z_j -> V_{j+1}
+        BJob o; o.n = bh->b == 1 ? n : n; o.rp = h->brp; o.ci = h->bci; o.v = h->bval;
+        o.x = K.Z; o.sx = n; o.o1 = K.V + n; o.so1 = n; o.active = act;
+        bh->outer.host.push_back(o);
+        // Arnoldi: w = V_{j+1} = V + n + j n
+        BJob d1; d1.n = n; d1.v = K.V; d1.x = K.V + n; d1.sx = n; d1.partial = K.partial;
+        d1.ticket = K.ticket; d1.flag = K.flag; d1.nblk = K.nblk; d1.o1 = K.h1; d1.active = act;
+        bh->dots1.host.push_back(d1);
+        BJob d2 = d1; d2.o1 = K.h2;
+        bh->dots2.host.push_back(d2);
+        BJob u1 = d1; u1.r = K.h1; u1.o2 = K.nrm2;
+        bh->upd1.host.push_back(u1);
+        BJob u2 = d1; u2.r = K.h2; u2.o2 = K.nrmB;
+        bh->upd2.host.push_back(u2);
+        BJob vn; vn.n = n; vn.x = K.V + n; vn.sx = n; vn.o1 = K.V + n; vn.so1 = n; vn.d = K.hn;
+        vn.active = act;
+        bh->vnorm.host.push_back(vn);
+        BJob rn; rn.n = n; rn.v = K.r; rn.x = K.r; rn.partial = K.partial; rn.ticket = K.ticket;
+        rn.flag = K.flag; rn.nblk = K.nblk; rn.o1 = K.beta; rn.active = act;
+        bh->rnorm.host.push_back(rn);
+        BJob v0; v0.n = n; v0.x = K.r; v0.o1 = K.V; v0.d = K.beta; v0.active = act;
+        bh->v0scale.host.push_back(v0);
+    }
+    auto setR = [](std::vector<BTable> &v, int kind) { for (auto &t : v) t.kind = kind; };
+    setR(bh->mgr_first, 1); setR(bh->mgr_scatter, 1);
+    setR(bh->mgr_restrict, 0); setR(bh->mgr_interp, 0);
+    setR(bh->amg_resid, 0); setR(bh->amg_restrict, 0); setR(bh->amg_prolong, 0); setR(bh->amg_post, 0);
+    bh->coarse.kind = 1;
+    bh->outer.kind = bh->b == 1 ? 0 : 1;
+    bh->dots1.kind = bh->dots2.kind = bh->upd1.kind = bh->upd2.kind = bh->rnorm.kind = 2;
+    bh->vnorm.kind = bh->v0scale.kind = 1;
+    if (bh->b > 1)  // one item per scalar row of the block product
+        for (auto &j : bh->outer.host) j.n = j.n;
+    auto initR = [](BTable &t) {
+        if (t.kind != 0) { t.R = 1; return; }
+        long long nnz = 0, n = 0;
+        for (auto &j : t.host) { n += j.n; }
+        (void)nnz;
+        t.R = 1;
+    };
+    (void)initR;
+    return ST_OK;
+}
+
+// rows-per-warp from the table's aggregate density (the autotuner refines it)
+static int table_R0(mgr_batch bh, BTable &t) {
+    long long n = 0, nnz = 0;
+    std::vector<int> hrp;
+    for (auto &j : t.host) {
+        if (j.n <= 0) continue;
+        int last = 0, first = 0;
+        cudaMemcpyAsync(&first, j.rp, sizeof(int), cudaMemcpyDeviceToHost, bh->s);
+        cudaMemcpyAsync(&last, j.rp + j.n, sizeof(int), cudaMemcpyDeviceToHost, bh->s);
+        cudaStreamSynchronize(bh->s);
+        n += j.n;
+        nnz += last - first;
+    }
+    double avg = n > 0 ? (double)nnz / n : 1.0;
+    if (avg < 1.0) avg = 1.0;
+    int r = 1;
+    while (r < 32 && (r * 2) * avg <= 192.0) r *= 2;
+    return r;
+}
+
+template <class T>
+static void run_chunk(mgr_batch bh, BTable &t, int op, int js, bool top) {
+    if (!t.total) return;
+    KScope ks(bh->hs[0], "batched_chunk", op, 0.0);
+    if (top) launch_bchunk<T, double>(op, t.jobs, t.prefix, t.njobs, t.total, t.R, js, bh->s);
+    else launch_bchunk<T, T>(op, t.jobs, t.prefix, t.njobs, t.total, t.R, js, bh->s);
+}
+
+// Autotuner: for every chunk table try R0/2, R0, 2 R0 (within 1..32), time
+// three launches of each (the first discarded) and keep the fastest; the
+// buffers hold no solve state yet, so the trial launches are harmless.
+template <class T>
+static int autotune(mgr_batch bh, BTable &t, int op, bool top) {
+    if (t.kind != 0 || t.host.empty()) return upload_table(bh, t);
+    int R0 = table_R0(bh, t);
+    int cands[3] = {R0 / 2, R0, R0 * 2};
+    float best = 1e30f;
+    int bestR = R0;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a); cudaEventCreate(&b);
+    for (int c = 0; c < 3; c++) {
+        int R = cands[c];
+        if (R < 1 || R > 32) continue;
+        t.R = R;
+        if (upload_table(bh, t)) { cudaEventDestroy(a); cudaEventDestroy(b); return ST_NOMEM; }
+        float ms = 0.f;
+        for (int rep = 0; rep < 3; rep++) {
+            cudaEventRecord(a, bh->s);
+            run_chunk<T>(bh, t, op, 0, top);
+            cudaEventRecord(b, bh->s);
+            cudaEventSynchronize(b);
+            float e = 0.f;
+            cudaEventElapsedTime(&e, a, b);
+            if (rep > 0) ms += e;
+        }
+        if (ms < best) { best = ms; bestR = R; }
+    }
+    cudaEventDestroy(a); cudaEventDestroy(b);
+    t.R = bestR;
+    return upload_table(bh, t);
+}
+
+template <class T>
+static int finish_tables(mgr_batch bh) {
+    int rc = 0;
+    for (int l = 0; l < bh->nlev && !rc; l++) {
+        rc |= upload_table(bh, bh->mgr_first[l]);
+        rc |= upload_table(bh, bh->mgr_scatter[l]);
+        rc |= autotune<T>(bh, bh->mgr_restrict[l], BOP_MGR_RESTRICT, l == 0);
+        rc |= autotune<T>(bh, bh->mgr_interp[l], BOP_MGR_INTERP, l == 0);
+    }
+    for (int k = 0; k < bh->kmax && !rc; k++) {
+        rc |= autotune<T>(bh, bh->amg_resid[k], BOP_RESID, false);
+        rc |= autotune<T>(bh, bh->amg_restrict[k], BOP_RESTRICT, false);
+        rc |= autotune<T>(bh, bh->amg_prolong[k], BOP_PROLONG, false);
+        rc |= autotune<T>(bh, bh->amg_post[k], BOP_POST, false);
+    }
+    rc |= upload_table(bh, bh->coarse);
+    if (bh->b == 1) rc |= autotune<double>(bh, bh->outer, BOP_OUTER_CSR, true);
+    else rc |= upload_table(bh, bh->outer);
+    rc |= upload_table(bh, bh->dots1); rc |= upload_table(bh, bh->dots2);
+    rc |= upload_table(bh, bh->upd1); rc |= upload_table(bh, bh->upd2);
+    rc |= upload_table(bh, bh->vnorm); rc |= upload_table(bh, bh->rnorm);
+    rc |= upload_table(bh, bh->v0scale);
+    return rc;
+}
+
+// One batched MGR V-cycle on V_j -> Z_j of every active system.
+template <class T>
+static void bvcycle(mgr_batch bh, int j) {
+    cudaStream_t s = bh->s;
+    const int L = bh->nlev;
+    for (int l = 0; l < L; l++) {
+        BTable &f = bh->mgr_first[l];
+        { KScope ks(bh->hs[0], "batched_frelax_first", l, 0.0);
+          if (l == 0) launch_bfrelax_first<T, double>(f.jobs, f.prefix, f.njobs, f.total, (T)bh->hs[0]->lev[l].omega, j, s);
+          else launch_bfrelax_first<T, T>(f.jobs, f.prefix, f.njobs, f.total, (T)bh->hs[0]->lev[l].omega, j, s); }
+        run_chunk<T>(bh, bh->mgr_restrict[l], BOP_MGR_RESTRICT, j, l == 0);
+    }
+    for (int k = 0; k < bh->kmax; k++) {
+        run_chunk<T>(bh, bh->amg_resid[k], BOP_RESID, j, false);
+        run_chunk<T>(bh, bh->amg_restrict[k], BOP_RESTRICT, j, false);
+    }
+    { KScope ks(bh->hs[0], "batched_coarsest", -1, 0.0);
+      launch_bdense<T>(bh->coarse.jobs, bh->coarse.prefix, bh->coarse.njobs, bh->coarse.total, j, s); }
+    for (int k = bh->kmax - 1; k >= 0; k--) {
+        run_chunk<T>(bh, bh->amg_prolong[k], BOP_PROLONG, j, false);
+        run_chunk<T>(bh, bh->amg_post[k], BOP_POST, j, false);
+    }
+    for (int l = L - 1; l >= 0; l--) {
+        run_chunk<T>(bh, bh->mgr_interp[l], BOP_MGR_INTERP, j, l == 0);
+        BTable &c = bh->mgr_scatter[l];
+        KScope ks(bh->hs[0], "batched_scatter", l, 0.0);
+        if (l == 0) launch_bscatter<T, double>(c.jobs, c.prefix, c.njobs, c.total, j, s);
+        else launch_bscatter<T, T>(c.jobs, c.prefix, c.njobs, c.total, j, s);
+    }
+}
+
+static void bstep(mgr_batch bh, int j) {
+    cudaStream_t s = bh->s;
+    if (bh->prec == MGR_PREC_FP32) bvcycle<float>(bh, j);
+    else bvcycle<double>(bh, j);
+    {
+        KScope ks(bh->hs[0], "batched_spmv_A", -1, 0.0);
+        if (bh->b == 1) launch_bchunk<double, double>(BOP_OUTER_CSR, bh->outer.jobs, bh->outer.prefix, bh->outer.njobs, bh->outer.total, bh->outer.R, j, s);
+        else launch_bbsr(bh->b, bh->outer.jobs, bh->outer.prefix, bh->outer.njobs, bh->outer.total, j, s);
+    }
+    const int k = j + 1;
+    { KScope ks(bh->hs[0], "batched_arnoldi", -1, 0.0);
+      launch_bdots(k + 1, bh->dots1.jobs, bh->dots1.prefix, bh->dots1.njobs, bh->dots1.total, j, 0, 0, s); }
+    { KScope ks(bh->hs[0], "batched_arnoldi", -1, 0.0);
+      launch_bupdate_norm(k, bh->upd1.jobs, bh->upd1.prefix, bh->upd1.njobs, bh->upd1.total, j, 1, s); }
+    { KScope ks(bh->hs[0], "batched_arnoldi", -1, 0.0);
+      launch_bdots(k, bh->dots2.jobs, bh->dots2.prefix, bh->dots2.njobs, bh->dots2.total, j, 1, 0, s); }
+    { KScope ks(bh->hs[0], "batched_arnoldi", -1, 0.0);
+      launch_bupdate_norm(k, bh->upd2.jobs, bh->upd2.prefix, bh->upd2.njobs, bh->upd2.total, j, 2, s); }
+    { KScope ks(bh->hs[0], "batched_givens", -1, 0.0);
+      k_bgivens<<<(bh->nsys + 31) / 32, 32, 0, s>>>(bh->kry, bh->nsys, j, bh->m); }
+    cudaMemcpyAsync(bh->hstat, bh->stat, sizeof(double) * 8 * bh->nsys, cudaMemcpyDeviceToHost, s);
+    { KScope ks(bh->hs[0], "batched_vec_scale", -1, 0.0);
+      launch_bscale(bh->vnorm.jobs, bh->vnorm.prefix, bh->vnorm.njobs, bh->vnorm.total, j, 1, s); }
+}
+
+static cudaError_t brun_step(mgr_batch bh, int j, bool graphs) {
+    if (!graphs) { bstep(bh, j); return cudaGetLastError(); }
+    if ((int)bh->graphs.size() < bh->m) { bh->graphs.resize(bh->m, nullptr); bh->graph_kernels.resize(bh->m, 0); }
+    if (!bh->graphs[j]) {
+        cudaGraph_t g = nullptr;
+        long long before = g_launches.load();
+        cudaError_t e = cudaStreamBeginCapture(bh->s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        bstep(bh, j);
+        e = cudaStreamEndCapture(bh->s, &g);
+        if (e != cudaSuccess) return e;
+        bh->graph_kernels[j] = g_launches.load() - before;
+        g_launches.fetch_sub(bh->graph_kernels[j]);
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        bh->graphs[j] = ex;
+    }
+    g_launches.fetch_add(bh->graph_kernels[j]);
+    return cudaGraphLaunch(bh->graphs[j], bh->s);
+}
+
+extern "C" void mgr_free_batched(mgr_batch bh) {
+    if (!bh) return;
+    cudaStreamSynchronize(bh->s);
+    for (auto g : bh->graphs) if (g) cudaGraphExecDestroy(g);
+    for (auto h : bh->hs) mgr_free(h);
+    if (bh->hstat) cudaFreeHost(bh->hstat);
+    bh->ar.free_all();
+    if (bh->own_stream) cudaStreamDestroy(bh->s);
+    delete bh;
+}
+
+extern "C" mgr_status mgr_setup_batched(int32_t nsys, const mgr_bsr *A, const mgr_labels *cf,
+                                        const mgr_options *opt, void *stream, mgr_batch *out) {
+    if (!out || nsys < 1 || !A || !cf) return bfail(nullptr, MGR_ERR_INVALID, "bad batched arguments");
+    *out = nullptr;
+    mgr_batch bh = new mgr_batch_ctx();
+    bh->nsys = nsys;
+    bh->s = (cudaStream_t)stream;
+    if (!bh->s) {
+        if (cudaStreamCreate(&bh->s) != cudaSuccess) { delete bh; return bfail(nullptr, MGR_ERR_CUDA, "stream"); }
+        bh->own_stream = true;
+    }
+    mgr_options o;
+    if (opt) o = *opt; else mgr_options_default(&o);
+    bh->prec = o.precision;
+    bh->nlev = cf[0].num_levels;
+    bh->b = A[0].b;
+    if (bh->nlev < 1) { mgr_free_batched(bh); return bfail(nullptr, MGR_ERR_UNSUPPORTED, "batched solves need at least one MGR level"); }
+    for (int l = 0; l < bh->nlev; l++)
+        if (o.relax_sweeps[l] > 1) { mgr_free_batched(bh); return bfail(nullptr, MGR_ERR_UNSUPPORTED, "batched solves use one F-relaxation sweep"); }
+    for (int s = 0; s < nsys; s++) {
+        if (A[s].b != bh->b || cf[s].num_levels != bh->nlev) {
+            mgr_free_batched(bh);
+            return bfail(nullptr, MGR_ERR_INVALID, "all systems of a batch need the same block size and MGR level count");
+        }
+        mgr_handle h = nullptr;
+        mgr_status st = mgr_setup(&A[s], &cf[s], &o, bh->s, &h);
+        if (st != MGR_OK) {
+            std::string m = g_last_error;
+            mgr_free_batched(bh);
+            char buf[64];
+            snprintf(buf, sizeof buf, "system %d: ", s);
+            return bfail(nullptr, st, buf + m);
+        }
+        bh->hs.push_back(h);
+        bh->kmax = std::max(bh->kmax, h->namg - 1);
+    }
+    bh->m = bh->hs[0]->kr.m;
+    Arena &ar = bh->ar;
+    bh->active = ar.alloc<int>(nsys);
+    bh->kk = ar.alloc<int>(nsys);
+    bh->tol = ar.alloc<double>(nsys);
+    bh->stat = ar.alloc<double>(8 * nsys);
+    bh->kry = ar.alloc<BKry>(nsys);
+    cudaMallocHost(&bh->hstat, sizeof(double) * 8 * nsys);
+    if (!bh->active || !bh->kk || !bh->tol || !bh->stat || !bh->kry || !bh->hstat) {
+        mgr_free_batched(bh);
+        return bfail(nullptr, MGR_ERR_NOMEM, "batch workspace");
+    }
+    std::vector<BKry> hk(nsys);
+    for (int s = 0; s < nsys; s++) {
+        Krylov &K = bh->hs[s]->kr;
+        hk[s] = BKry{K.h1, K.h2, K.nrm2, K.nrmB, K.H, K.cs, K.sn, K.g, K.hn, bh->stat + 8 * s,
+                     K.beta, K.y, bh->tol + s, K.flag, bh->active + s, bh->kk + s};
+    }
+    cudaMemcpyAsync(bh->kry, hk.data(), sizeof(BKry) * nsys, cudaMemcpyHostToDevice, bh->s);
+    std::vector<int> ones(nsys, 1);
+    cudaMemcpyAsync(bh->active, ones.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, bh->s);
+    int rc = bh->prec == MGR_PREC_FP32 ? build_tables<float>(bh) : build_tables<double>(bh);
+    if (!rc) rc = bh->prec == MGR_PREC_FP32 ? finish_tables<float>(bh) : finish_tables<double>(bh);
+    // the residual/update tables point at per-solve user vectors: filled per call
+    bh->resid_user.kind = bh->b == 1 ? 0 : 1;
+    bh->xupd.kind = 1;
+    cudaStreamSynchronize(bh->s);
+    if (rc || cudaGetLastError() != cudaSuccess) {
+        mgr_free_batched(bh);
+        return bfail(nullptr, rc == ST_NOMEM ? MGR_ERR_NOMEM : MGR_ERR_CUDA, "batched tables");
+    }
+    *out = bh;
+    return MGR_OK;
+}
+
+extern "C" mgr_status mgr_batch_handle(mgr_batch bh, int32_t i, mgr_handle *out) {
+    if (!bh || !out || i < 0 || i >= bh->nsys) return bfail(bh, MGR_ERR_INVALID, "no such system");
+    *out = bh->hs[i];
+    return MGR_OK;
+}
+
+extern "C" mgr_status mgr_solve_batched(mgr_batch bh, const double *const *bvec, double *const *xvec,
+                                        double rtol, int32_t maxit, mgr_solve_info *info) {
+    if (!bh || !bvec || !xvec) return bfail(bh, MGR_ERR_INVALID, "NULL argument");
+    auto t0 = std::chrono::steady_clock::now();
+    const int ns = bh->nsys, m = bh->m;
+    cudaStream_t s = bh->s;
+    // per-call tables over the user's vectors
+    bh->resid_user.host.clear();
+    bh->xupd.host.clear();
+    for (int i = 0; i < ns; i++) {
+        mgr_handle h = bh->hs[i];
+        BJob r; r.n = h->n; r.rp = h->brp; r.ci = h->bci; r.v = h->bval; r.x = xvec[i]; r.r = bvec[i];
+        r.o1 = h->kr.r; r.active = bh->active + i;
+        bh->resid_user.host.push_back(r);
+        BJob u; u.n = h->n; u.v = h->kr.Z; u.r = h->kr.y; u.o1 = xvec[i]; u.gz = bh->kk + i;
+        bh->xupd.host.push_back(u);
+    }
+    bh->resid_user.R = bh->outer.R;
+    if (upload_table(bh, bh->resid_user) || upload_table(bh, bh->xupd)) return bfail(bh, MGR_ERR_NOMEM, "tables");
+    std::vector<int> act(ns, 1), done(ns, 0), iters(ns, 0), kk(ns, 0);
+    std::vector<double> bn(ns, 0.0), relres(ns, 0.0);
+    // |b| per system (the residual table with x = 0 is not needed: norms of b)
+    {
+        BTable bt; bt.kind = 2;
+        for (int i = 0; i < ns; i++) {
+            Krylov &K = bh->hs[i]->kr;
+            BJob d; d.n = bh->hs[i]->n; d.v = bvec[i]; d.x = bvec[i]; d.partial = K.partial;
+            d.ticket = K.ticket; d.flag = K.flag; d.nblk = K.nblk; d.o1 = K.beta;
+            bt.host.push_back(d);
+        }
+        if (upload_table(bh, bt)) return bfail(bh, MGR_ERR_NOMEM, "tables");
+        launch_bdots(1, bt.jobs, bt.prefix, bt.njobs, bt.total, 0, 0, 1, s);
+        for (int i = 0; i < ns; i++)
+            cudaMemcpyAsync(&bn[i], bh->hs[i]->kr.beta, sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        bh->ar.release(bt.jobs); bh->ar.release(bt.prefix);
+    }
+    std::vector<double> tol(ns);
+    for (int i = 0; i < ns; i++) {
+        if (!std::isfinite(bn[i])) return bfail(bh, MGR_ERR_INVALID, "right-hand side is not finite");
+        tol[i] = rtol * bn[i];
+        if (bn[i] == 0.0) { act[i] = 0; done[i] = 1; cudaMemsetAsync(xvec[i], 0, sizeof(double) * bh->hs[i]->n, s); }
+    }
+    cudaMemcpyAsync(bh->tol, tol.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s);
+    const bool graphs = bh->hs[0]->opt.use_graphs && !bh->hs[0]->prof.on;
+    mgr_status st = MGR_OK;
+    for (;;) {
+        // true residuals of the systems still open
+        cudaMemcpyAsync(bh->active, act.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s);
+        {
+            KScope ks(bh->hs[0], "batched_residual", -1, 0.0);
+            BTable &t = bh->resid_user;
+            if (bh->b == 1) launch_bchunk<double, double>(BOP_OUTER_CSR, t.jobs, t.prefix, t.njobs, t.total, t.R, 0, s);
+            else launch_bbsr(bh->b, t.jobs, t.prefix, t.njobs, t.total, 0, s);
+        }
+        launch_bdots(1, bh->rnorm.jobs, bh->rnorm.prefix, bh->rnorm.njobs, bh->rnorm.total, 0, 0, 1, s);
+        std::vector<double> beta(ns, 0.0);
+        for (int i = 0; i < ns; i++)
+            if (act[i]) cudaMemcpyAsync(&beta[i], bh->hs[i]->kr.beta, sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        if (cudaGetLastError() != cudaSuccess) return cuda_fail(nullptr, "batched residual");
+        bool any = false;
+        for (int i = 0; i < ns; i++) {
+            if (!act[i]) continue;
+            relres[i] = beta[i] / bn[i];
+            if (!std::isfinite(beta[i])) { act[i] = 0; done[i] = 2; continue; }
+            if (beta[i] <= tol[i]) { act[i] = 0; done[i] = 1; continue; }
+            if (iters[i] >= maxit) { act[i] = 0; continue; }
+            any = true;
+        }
+        if (!any) break;
+        cudaMemcpyAsync(bh->active, act.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s);
+        launch_bscale(bh->v0scale.jobs, bh->v0scale.prefix, bh->v0scale.njobs, bh->v0scale.total, 0, 1, s);
+        k_binit_g<<<ns, 32, 0, s>>>(bh->kry, ns, m);
+        std::vector<int> cyc(act);  // systems in this restart cycle
+        std::fill(kk.begin(), kk.end(), 0);
+        for (int j = 0; j < m; j++) {
+            cudaError_t ge = brun_step(bh, j, graphs);
+            cudaStreamSynchronize(s);
+            if (ge != cudaSuccess || cudaGetLastError() != cudaSuccess) return cuda_fail(nullptr, "batched step");
+            bool changed = false, open = false;
+            for (int i = 0; i < ns; i++) {
+                if (!act[i]) continue;
+                iters[i]++;
+                kk[i] = j + 1;
+                const double *st8 = bh->hstat + 8 * i;
+                if (!std::isfinite(st8[0])) { act[i] = 0; done[i] = 2; changed = true; continue; }
+                if (st8[1] != 0.0 || st8[2] != 0.0 || iters[i] >= maxit) { act[i] = 0; changed = true; continue; }
+                open = true;
+            }
+            if (changed) cudaMemcpyAsync(bh->active, act.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s);
+            if (!open) break;
+        }
+        // x += Z y for every system of this cycle
+        for (int i = 0; i < ns; i++) if (!cyc[i]) kk[i] = 0;
+        cudaMemcpyAsync(bh->kk, kk.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s);
+        k_bsolve_upper<<<(ns + 31) / 32, 32, 0, s>>>(bh->kry, ns, m);
+        launch_bmulti_axpy(bh->xupd.jobs, bh->xupd.prefix, bh->xupd.njobs, bh->xupd.total, s);
+        // every system of the cycle gets its true residual checked next
+        for (int i = 0; i < ns; i++) if (cyc[i] && done[i] == 0) act[i] = 1;
+    }
+    cudaStreamSynchronize(s);
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    bool all = true, bad = false;
+    for (int i = 0; i < ns; i++) {
+        if (done[i] != 1) all = false;
+        if (done[i] == 2) bad = true;
+        if (info) {
+            memset(&info[i], 0, sizeof(mgr_solve_info));
+            info[i].iterations = iters[i];
+            info[i].rel_residual = relres[i];
+            info[i].setup_ms = bh->hs[i]->setup_ms;
+            info[i].solve_ms = ms;
+            info[i].mgr_levels = bh->hs[i]->nlev;
+            info[i].amg_levels = bh->hs[i]->namg;
+        }
+    }
+    if (bad) return bfail(bh, MGR_ERR_INVALID, "a residual became non-finite");
+    if (!all) return bfail(bh, MGR_ERR_NOT_CONVERGED, "maximum iterations reached for some system");
+    return st;
 }

@@ -86,6 +86,7 @@ def lib(build_if_missing: bool = True):
     L.mgr_solve.argtypes = [vp, vp, vp, dp, i32, C.POINTER(mgr_solve_info)]
     L.mgr_solve_transpose.argtypes = [vp, vp, vp, dp, i32, C.POINTER(mgr_solve_info)]
     L.mgr_grad_values.argtypes = [vp, vp, vp, vp]
+    L.mgr_update_values.argtypes = [vp, vp, i32]
     L.mgr_bsr_spmv.argtypes = [i32, i32, vp, vp, vp, vp, vp, dp, dp, vp]
     L.mgr_free.argtypes = [vp]
     L.mgr_free.restype = None
@@ -237,6 +238,17 @@ class MGRSolver:
         d["status"] = int(st)
         return x, d
 
+    def update_values(self, val):
+        """New values of A (same pattern) for the outer operator; the
+        hierarchy from setup stays the preconditioner."""
+        import torch
+        if isinstance(val, torch.Tensor) and val.is_cuda:
+            v = val.to(torch.float64).contiguous()
+            _check(lib().mgr_update_values(self.h, _ptr(v), 1), self.h)
+        else:
+            v = np.ascontiguousarray(val, np.float64)
+            _check(lib().mgr_update_values(self.h, v.ctypes.data, 0), self.h)
+
     def grad_values(self, lam, x):
         import torch
         dA = torch.empty(self.nnzb * self.b * self.b, dtype=torch.float64, device=lam.device)
@@ -326,3 +338,95 @@ def residual_norm_noalloc(row_ptr, col_idx, val, b, x, bvec, r=None, norm=None, 
     if st != MGR_OK:
         raise MGRError(st, "mgr_residual_norm_noalloc")
     return r, norm
+
+
+class _BorrowedSolver(MGRSolver):
+    """A system handle owned by a batch (not freed by this object)."""
+
+    def __init__(self, h, n, nb, b, nnzb, device):
+        self.h = h
+        self.n, self.nb, self.b, self.nnzb = n, nb, b, nnzb
+        self.device = device
+
+    def close(self):
+        self.h = C.c_void_p()
+
+
+class MGRBatch:
+    """Many systems solved together: one launch per kernel class for all."""
+
+    def __init__(self, systems, precision="fp64", device=None, **kw):
+        import torch
+        L = lib()
+        L.mgr_setup_batched.argtypes = [C.c_int32, C.POINTER(mgr_bsr), C.POINTER(mgr_labels),
+                                        C.POINTER(mgr_options), C.c_void_p, C.POINTER(C.c_void_p)]
+        L.mgr_solve_batched.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
+                                        C.POINTER(mgr_solve_info)]
+        L.mgr_batch_handle.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]
+        L.mgr_free_batched.argtypes = [C.c_void_p]
+        L.mgr_free_batched.restype = None
+        self.device = torch.device(device or "cuda")
+        ns = len(systems)
+        s0 = systems[0]
+        self.opts = options(relax=tuple(s0.relax), num_functions=s0.num_functions,
+                            precision=precision, **kw)
+        keep = []
+        As = (mgr_bsr * ns)()
+        Ls = (mgr_labels * ns)()
+        for i, s in enumerate(systems):
+            rp = np.ascontiguousarray(s.row_ptr, np.int32)
+            ci = np.ascontiguousarray(s.col_idx, np.int32)
+            vv = np.ascontiguousarray(s.val, np.float64)
+            lv = np.ascontiguousarray(s.dof_level, np.int8)
+            keep += [rp, ci, vv, lv]
+            As[i] = mgr_bsr(rp.size - 1, s.b, ci.size, rp.ctypes.data, ci.ctypes.data,
+                            vv.ctypes.data, 0)
+            Ls[i] = mgr_labels(s.num_levels, lv.ctypes.data)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = L.mgr_setup_batched(ns, As, Ls, C.byref(self.opts),
+                                     C.c_void_p(torch.cuda.current_stream().cuda_stream), C.byref(h))
+        if st != MGR_OK:
+            raise MGRError(st, L.mgr_last_error(None).decode(errors="replace"))
+        self.h = h
+        self.nsys = ns
+        self.sizes = [s.n for s in systems]
+        self._meta = [(s.n, s.nb, s.b, s.nnzb) for s in systems]
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().mgr_free_batched(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def system(self, i):
+        """The borrowed single-system solver of member i (transpose solves,
+        gradients, inspection); valid while the batch lives."""
+        hh = C.c_void_p()
+        _check(lib().mgr_batch_handle(self.h, int(i), C.byref(hh)))
+        n, nb, b, nnzb = self._meta[i]
+        return _BorrowedSolver(hh, n, nb, b, nnzb, self.device)
+
+    def solve(self, rhs, xs=None, rtol=1e-8, maxit=500, check=True):
+        import torch
+        xs = [torch.zeros_like(r) for r in rhs] if xs is None else xs
+        for r, x, n in zip(rhs, xs, self.sizes):
+            assert r.is_cuda and r.dtype == torch.float64 and r.numel() == n and r.is_contiguous()
+            assert x.is_cuda and x.dtype == torch.float64 and x.numel() == n and x.is_contiguous()
+        bp = (C.c_void_p * self.nsys)(*[r.data_ptr() for r in rhs])
+        xp = (C.c_void_p * self.nsys)(*[x.data_ptr() for x in xs])
+        infos = (mgr_solve_info * self.nsys)()
+        st = lib().mgr_solve_batched(self.h, bp, xp, float(rtol), int(maxit), infos)
+        if check and st not in (MGR_OK, MGR_ERR_NOT_CONVERGED):
+            _check(st)
+        out = []
+        for i in range(self.nsys):
+            d = infos[i].as_dict()
+            d["status"] = int(st)
+            out.append(d)
+        return xs, out
