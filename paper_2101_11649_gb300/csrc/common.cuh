@@ -18,7 +18,19 @@ struct DCSR {
     int *rp = nullptr, *ci = nullptr;
     double *v = nullptr;
     float *v32 = nullptr;
+    // SELL-32-sigma copy for the solve phase (null when not built): slices of
+    // 32 rows (rows sorted by length inside windows of 1024), column-major
+    // within a slice, padded to the slice's longest row with zero values.
+    int nsl = 0;
+    long long *sptr = nullptr;   // [nsl+1] slice offsets
+    int *slen = nullptr;         // [nsl] slice widths
+    int *perm = nullptr;         // [nsl*32] row of each slice lane (-1: none)
+    int *sci = nullptr;          // padded column indices
+    double *sv = nullptr;        // padded values (FP64)
+    float *sv32 = nullptr;       // padded values (FP32)
+    long long sell_stored = 0;   // stored entries including padding
 };
+
 
 // Status codes mirror mgr_status.
 enum { ST_OK = 0, ST_INVALID = 1, ST_NOMEM = 2, ST_CUDA = 3, ST_SINGULAR = 4,
@@ -37,6 +49,11 @@ struct Arena {
     void release(void *p);
     void free_all();
 };
+
+// SELL-32 build from the CSR arrays (values of both precisions when present)
+int build_sell(DCSR &M, cudaStream_t s, Arena &ar);
+// re-copy the values of a built SELL layout after the CSR values changed
+void refresh_sell(DCSR &M, cudaStream_t s);
 
 // ------------------------------------------------------------- utilities
 int scan_exclusive(const int *in, int *out, int n, cudaStream_t s, Arena &ar, int *total);

@@ -96,6 +96,7 @@ struct mgr_ctx {
     int *brp = nullptr, *bci = nullptr;
     double *bval = nullptr;
     DCSR A0T;  // scalar transpose of A (adjoint outer products)
+    DCSR Aout; // CSR view of A when b == 1 (the outer product runs on its SELL copy)
     int8_t *dlevel = nullptr;
     int nlev = 0;
     MgrLevel lev[MGR_MAX_LEVELS];
@@ -466,6 +467,28 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
     if (!K.V || !K.Z || !K.r || !K.H || !K.partial || !K.stat || !K.hstat) {
         mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "Krylov workspace");
     }
+    // SELL-32 copies of every matrix the solve phase multiplies with
+    {
+        int rc2 = 0;
+        for (int l = 0; l < h->nlev && !rc2; l++) {
+            MgrLevel &L = h->lev[l];
+            DCSR *ms[] = {&L.AFF, &L.ACF, &L.W, &L.AFFT, &L.ACFT, &L.WT};
+            for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
+        }
+        for (int k = 0; k + 1 < h->namg && !rc2; k++) {
+            AmgLevel &A = h->amg[k];
+            DCSR *ms[] = {&A.A, &A.AT, &A.P, &A.R};
+            for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
+        }
+        if (b == 1) {
+            h->Aout.n = h->Aout.m = n;
+            h->Aout.nnz = (int)nnzb;
+            h->Aout.rp = h->brp; h->Aout.ci = h->bci; h->Aout.v = h->bval;
+            rc2 |= build_sell(h->Aout, s, ar);
+        }
+        rc2 |= build_sell(h->A0T, s, ar);
+        if (rc2) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "SELL copies"); }
+    }
     cudaStreamSynchronize(s);
     if (cudaGetLastError() != cudaSuccess) { mgr_free(h); return cuda_fail(nullptr, "setup"); }
     h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -661,12 +684,14 @@ static double outer_bytes(mgr_handle h) {
 static void outer_spmv(mgr_handle h, const double *x, double *y, int trans) {
     KScope ks(h, trans ? "spmv_AT" : "spmv_A", -1, outer_bytes(h), (double)h->nnzb * h->b * h->b);
     if (trans) launch_csr_spmv<double>(h->A0T, h->A0T.v, x, y, h->s);
+    else if (h->b == 1) launch_csr_spmv<double>(h->Aout, h->Aout.v, x, y, h->s);
     else launch_bsr_spmv(h->nb, h->b, h->brp, h->bci, h->bval, x, y, 1.0, 0.0, h->s, h->nnzb);
 }
 
 static void outer_residual(mgr_handle h, const double *x, const double *bvec, double *y, int trans) {
     KScope ks(h, trans ? "residual_AT" : "residual_A", -1, outer_bytes(h) + h->n * 8.0, (double)h->nnzb * h->b * h->b);
     if (trans) launch_csr_residual(h->A0T, x, bvec, y, h->s);
+    else if (h->b == 1) launch_csr_residual(h->Aout, x, bvec, y, h->s);
     else launch_bsr_residual(h->nb, h->b, h->brp, h->bci, h->bval, x, bvec, y, h->s, h->nnzb);
 }
 
@@ -873,6 +898,8 @@ extern "C" mgr_status mgr_update_values(mgr_handle h, const double *val, int32_t
     launch_bsr_to_csr(h->nb, h->b, h->brp, h->bci, h->bval, A0, s);
     if (transpose(A0, T, s, tmp)) { tmp.free_all(); return fail(h, MGR_ERR_NOMEM, "update transpose"); }
     cudaMemcpyAsync(h->A0T.v, T.v, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s);
+    if (h->Aout.sptr) refresh_sell(h->Aout, s);
+    if (h->A0T.sptr) refresh_sell(h->A0T, s);
     cudaStreamSynchronize(s);
     tmp.free_all();
     if (cudaGetLastError() != cudaSuccess) return cuda_fail(h, "mgr_update_values");

@@ -1099,3 +1099,117 @@ void launch_cast_f32(const double *in, float *out, long long n, cudaStream_t s) 
 }
 
 }  // namespace mgr
+
+namespace mgr {
+
+// ------------------------------------------------------------ SELL-32-sigma
+// Rows are sorted by decreasing length (ties: ascending row) inside windows
+// of SELL_WIN rows, then cut into slices of 32; a slice stores its entries
+// column-major (entry t of lane l at offset t*32 + l) padded to its widest row.
+static const int SELL_WIN = 1024;
+
+__global__ void k_sell_sort(int n, const int *rp, int *perm) {
+    __shared__ unsigned long long key[SELL_WIN];
+    const int w0 = blockIdx.x * SELL_WIN;
+    for (int t = threadIdx.x; t < SELL_WIN; t += blockDim.x) {
+        int row = w0 + t;
+        if (row < n) {
+            unsigned len = (unsigned)(rp[row + 1] - rp[row]);
+            key[t] = ((unsigned long long)(0x7fffffffu - len) << 32) | (unsigned)row;
+        } else {
+            key[t] = ~0ULL;
+        }
+    }
+    __syncthreads();
+    // bitonic sort, ascending
+    for (int k = 2; k <= SELL_WIN; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < SELL_WIN; t += blockDim.x) {
+                int q = t ^ j;
+                if (q > t) {
+                    bool up = (t & k) == 0;
+                    unsigned long long a = key[t], b = key[q];
+                    if ((a > b) == up) { key[t] = b; key[q] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < SELL_WIN; t += blockDim.x) {
+        unsigned long long k2 = key[t];
+        perm[w0 + t] = k2 == ~0ULL ? -1 : (int)(k2 & 0xffffffffu);
+    }
+}
+
+__global__ void k_sell_width(int nsl, const int *rp, const int *perm, int *slen) {
+    int s2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s2 >= nsl) return;
+    int row = perm[s2 * 32];  // the longest row of the slice comes first
+    slen[s2] = row >= 0 ? rp[row + 1] - rp[row] : 0;
+}
+
+__global__ void k_sell_scale32(const int *slen, int nsl, int *w32) {
+    int s2 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s2 < nsl) w32[s2] = slen[s2] * 32;
+}
+
+__global__ void k_sell_fill(int nsl, const int *rp, const int *ci, const double *v, const float *v32,
+                            const int *perm, const long long *sptr, const int *slen, int *sci,
+                            double *sv, float *sv32) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= (long long)nsl * 32) return;
+    int s2 = (int)(p >> 5), lane = (int)(p & 31);
+    int row = perm[p];
+    int len = row >= 0 ? rp[row + 1] - rp[row] : 0;
+    int base = row >= 0 ? rp[row] : 0;
+    int padc = len > 0 ? ci[base + len - 1] : 0;
+    long long o = sptr[s2] + lane;
+    for (int t = 0; t < slen[s2]; t++, o += 32) {
+        if (t < len) {
+            sci[o] = ci[base + t];
+            if (sv) sv[o] = v[base + t];
+            if (sv32) sv32[o] = v32[base + t];
+        } else {
+            sci[o] = padc;
+            if (sv) sv[o] = 0.0;
+            if (sv32) sv32[o] = 0.0f;
+        }
+    }
+}
+
+int build_sell(DCSR &M, cudaStream_t s, Arena &ar) {
+    if (M.n <= 0) return ST_OK;
+    const int nwin = (M.n + SELL_WIN - 1) / SELL_WIN;
+    const int nsl = nwin * (SELL_WIN / 32);
+    M.nsl = nsl;
+    M.perm = ar.alloc<int>((size_t)nwin * SELL_WIN);
+    M.slen = ar.alloc<int>(nsl + 1);
+    M.sptr = ar.alloc<long long>(nsl + 1);
+    int *w32 = ar.alloc<int>(nsl + 1);
+    if (!M.perm || !M.slen || !M.sptr || !w32) return ST_NOMEM;
+    k_sell_sort<<<nwin, 512, 0, s>>>(M.n, M.rp, M.perm);
+    k_sell_width<<<(nsl + 255) / 256, 256, 0, s>>>(nsl, M.rp, M.perm, M.slen);
+    k_sell_scale32<<<(nsl + 255) / 256, 256, 0, s>>>(M.slen, nsl, w32);
+    long long tot = 0;
+    int rc = scan_exclusive_ll(w32, M.sptr, nsl, s, ar, &tot);
+    ar.release(w32);
+    if (rc) return rc;
+    M.sell_stored = tot;
+    M.sci = ar.alloc<int>(tot + 1);
+    M.sv = M.v ? ar.alloc<double>(tot + 1) : nullptr;
+    M.sv32 = M.v32 ? ar.alloc<float>(tot + 1) : nullptr;
+    if (!M.sci || (M.v && !M.sv) || (M.v32 && !M.sv32)) return ST_NOMEM;
+    long long np = (long long)nsl * 32;
+    k_sell_fill<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(nsl, M.rp, M.ci, M.v, M.v32, M.perm, M.sptr,
+                                                          M.slen, M.sci, M.sv, M.sv32);
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+void refresh_sell(DCSR &M, cudaStream_t s) {
+    if (!M.sptr) return;
+    long long np = (long long)M.nsl * 32;
+    k_sell_fill<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(M.nsl, M.rp, M.ci, M.v, M.v32, M.perm, M.sptr,
+                                                          M.slen, M.sci, M.sv, M.sv32);
+}
+
+}  // namespace mgr

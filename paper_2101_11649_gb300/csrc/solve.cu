@@ -126,6 +126,64 @@ static void csr_chunk(int n, long long nnz, const int *rp, const int *ci, const 
     }
 }
 
+// --------------------------------------------------------------- SELL-32
+// One warp per slice of 32 rows, one lane per row: a single FMA chain over
+// the lane's column of the slice (loads of values and columns coalesced,
+// four entries in flight per lane), no cross-lane reduction.  Padding
+// entries carry zero values and a column of the same row.
+template <class T, class XF, class EPI>
+__global__ void __launch_bounds__(256) k_sell(int nsl, const long long *__restrict__ sptr,
+                                              const int *__restrict__ slen,
+                                              const int *__restrict__ perm,
+                                              const int *__restrict__ sci,
+                                              const T *__restrict__ sv, XF xf, EPI epi) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nsl; sl += nw) {
+        const int L = __ldg(slen + sl);
+        const long long base = __ldg(sptr + sl) + lane;
+        T acc = (T)0;
+        int t = 0;
+        for (; t + 4 <= L; t += 4) {
+            const long long o = base + (long long)t * 32;
+            const T v0 = __ldg(sv + o), v1 = __ldg(sv + o + 32), v2 = __ldg(sv + o + 64), v3 = __ldg(sv + o + 96);
+            const int c0 = __ldg(sci + o), c1 = __ldg(sci + o + 32), c2 = __ldg(sci + o + 64), c3 = __ldg(sci + o + 96);
+            const T x0 = xf(c0), x1 = xf(c1), x2 = xf(c2), x3 = xf(c3);
+            acc = fma(v0, x0, acc);
+            acc = fma(v1, x1, acc);
+            acc = fma(v2, x2, acc);
+            acc = fma(v3, x3, acc);
+        }
+        for (; t < L; t++) {
+            const long long o = base + (long long)t * 32;
+            acc = fma(__ldg(sv + o), xf(__ldg(sci + o)), acc);
+        }
+        const int row = __ldg(perm + (long long)sl * 32 + lane);
+        if (row >= 0) epi(row, acc);
+    }
+}
+
+template <class T>
+__host__ __device__ inline const T *sell_vals(const DCSR &M);
+template <>
+inline const double *sell_vals<double>(const DCSR &M) { return M.sv; }
+template <>
+inline const float *sell_vals<float>(const DCSR &M) { return M.sv32; }
+
+// Row products over a matrix: SELL-32 when built, else the chunk engine.
+template <class T, class XF, class EPI>
+static void spmv_rows(const DCSR &M, const T *csr_vals, XF xf, EPI epi, cudaStream_t s) {
+    if (M.n <= 0) return;
+    if (M.sptr && sell_vals<T>(M)) {
+        long long blocks = ((long long)M.nsl * 32 + 255) / 256;
+        if (blocks > NUM_SMS * 8) blocks = NUM_SMS * 8;
+        k_sell<T, XF, EPI><<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(
+            M.nsl, M.sptr, M.slen, M.perm, M.sci, sell_vals<T>(M), xf, epi);
+        return;
+    }
+    csr_chunk<T>(M.n, M.nnz, M.rp, M.ci, csr_vals, xf, epi, s);
+}
+
 // gathers
 template <class T, class XT>
 struct XPlain {
@@ -228,18 +286,17 @@ struct EInterp {  // z[fidx] = zF + s
 // --------------------------------------------------------------- CSR y = A x
 template <class T>
 void launch_csr_spmv(const DCSR &A, const T *vals, const T *x, T *y, cudaStream_t s) {
-    csr_chunk<T>(A.n, A.nnz, A.rp, A.ci, vals, XPlain<T, T>{x}, EStore<T, T>{y}, s);
+    spmv_rows<T>(A, vals, XPlain<T, T>{x}, EStore<T, T>{y}, s);
 }
 
 template <class T>
 void launch_csr_spmv_add(const DCSR &A, const T *vals, const T *x, T *y, cudaStream_t s) {
-    csr_chunk<T>(A.n, A.nnz, A.rp, A.ci, vals, XPlain<T, T>{x}, EAdd<T>{y}, s);
+    spmv_rows<T>(A, vals, XPlain<T, T>{x}, EAdd<T>{y}, s);
 }
 
 void launch_csr_residual(const DCSR &A, const double *x, const double *bvec, double *y,
                          cudaStream_t s) {
-    csr_chunk<double>(A.n, A.nnz, A.rp, A.ci, A.v, XPlain<double, double>{x},
-                      EAxpby{1.0, 0.0, bvec, y}, s);
+    spmv_rows<double>(A, A.v, XPlain<double, double>{x}, EAxpby{1.0, 0.0, bvec, y}, s);
 }
 
 // -------------------------------------------------------------- BSR (FP64)
@@ -319,8 +376,7 @@ void launch_frelax_first(int nF, const int *fidx, const int *gstart, const int *
 template <class T, class TV>
 void launch_frelax_residual(const DCSR &AFF, const T *vals, const int *fidx, const TV *v,
                             const T *zF, T *rF, cudaStream_t s) {
-    csr_chunk<T>(AFF.n, AFF.nnz, AFF.rp, AFF.ci, vals, XPlain<T, T>{zF},
-                 EGatherMinus<T, TV>{fidx, v, (T)-1, rF}, s);
+    spmv_rows<T>(AFF, vals, XPlain<T, T>{zF}, EGatherMinus<T, TV>{fidx, v, (T)-1, rF}, s);
 }
 
 // z_F += omega D^{-1} r_F (transpose: D^{-T})
@@ -349,8 +405,7 @@ void launch_frelax_update(int nF, const int *gstart, const int *gsize, const T *
 template <class T, class TV>
 void launch_mgr_restrict(const DCSR &ACF, const T *vals, const int *cidx, const TV *v,
                          const T *zF, T *vC, cudaStream_t s) {
-    csr_chunk<T>(ACF.n, ACF.nnz, ACF.rp, ACF.ci, vals, XPlain<T, T>{zF},
-                 EGatherMinus<T, TV>{cidx, v, (T)-1, vC}, s);
+    spmv_rows<T>(ACF, vals, XPlain<T, T>{zF}, EGatherMinus<T, TV>{cidx, v, (T)-1, vC}, s);
 }
 
 template <class T, class TV>
@@ -363,7 +418,7 @@ __global__ void k_scatter_c(int nC, const int *cidx, const T *eC, TV *z) {
 template <class T, class TV>
 void launch_mgr_interp(const DCSR &W, const T *wvals, int nC, const int *fidx, const int *cidx,
                        const T *zF, const T *eC, TV *z, cudaStream_t s) {
-    csr_chunk<T>(W.n, W.nnz, W.rp, W.ci, wvals, XPlain<T, T>{eC}, EInterp<T, TV>{fidx, zF, z}, s);
+    spmv_rows<T>(W, wvals, XPlain<T, T>{eC}, EInterp<T, TV>{fidx, zF, z}, s);
     if (nC > 0) k_scatter_c<T, TV><<<GRIDN(nC, 256), 256, 0, s>>>(nC, cidx, eC, z);
 }
 
@@ -384,8 +439,7 @@ void launch_gather(const int *idx, int n, const TV *v, T *out, cudaStream_t s) {
 template <class T, class TV>
 void launch_csr_axpy_gather(const DCSR &M, const T *vals, const T *x, const int *idx_b,
                             const TV *bsrc, T sign, T *y, cudaStream_t s) {
-    csr_chunk<T>(M.n, M.nnz, M.rp, M.ci, vals, XPlain<T, T>{x},
-                 EGatherMinus<T, TV>{idx_b, bsrc, sign, y}, s);
+    spmv_rows<T>(M, vals, XPlain<T, T>{x}, EGatherMinus<T, TV>{idx_b, bsrc, sign, y}, s);
 }
 
 template <class T, class TV>
@@ -408,8 +462,7 @@ void launch_scatter2(int nF, int nC, const int *fidx, const int *cidx, const T *
 template <class T, class TV>
 void launch_amg_smooth0_residual(const DCSR &A, const T *vals, const T *dinv, const TV *r, T *x,
                                  T *res, cudaStream_t s) {
-    csr_chunk<T>(A.n, A.nnz, A.rp, A.ci, vals, XScaled<T, TV>{dinv, r},
-                 ESmooth0<T, TV>{r, dinv, x, res}, s);
+    spmv_rows<T>(A, vals, XScaled<T, TV>{dinv, r}, ESmooth0<T, TV>{r, dinv, x, res}, s);
 }
 
 // residual of the pre-smoothed iterate x = D r computed by the producer of r:
@@ -417,22 +470,21 @@ void launch_amg_smooth0_residual(const DCSR &A, const T *vals, const T *dinv, co
 template <class T, class TV>
 void launch_amg_residual(const DCSR &A, const T *vals, const T *x, const TV *r, T *res,
                          cudaStream_t s) {
-    csr_chunk<T>(A.n, A.nnz, A.rp, A.ci, vals, XPlain<T, T>{x}, EResid<T, TV>{r, res}, s);
+    spmv_rows<T>(A, vals, XPlain<T, T>{x}, EResid<T, TV>{r, res}, s);
 }
 
 // restriction r_c = R res that also writes x_c = D_c r_c for the next level
 template <class T>
 void launch_restrict_scaled(const DCSR &R, const T *vals, const T *res, T *rc, const T *dc, T *xc,
                             cudaStream_t s) {
-    csr_chunk<T>(R.n, R.nnz, R.rp, R.ci, vals, XPlain<T, T>{res}, EStoreScaled<T>{rc, dc, xc}, s);
+    spmv_rows<T>(R, vals, XPlain<T, T>{res}, EStoreScaled<T>{rc, dc, xc}, s);
 }
 
 // MGR injection restriction that also writes x = D v_C for the AMG below
 template <class T, class TV>
 void launch_mgr_restrict_scaled(const DCSR &ACF, const T *vals, const int *cidx, const TV *v,
                                 const T *zF, T *vC, const T *d, T *x, cudaStream_t s) {
-    csr_chunk<T>(ACF.n, ACF.nnz, ACF.rp, ACF.ci, vals, XPlain<T, T>{zF},
-                 EGatherMinusScaled<T, TV>{cidx, v, vC, d, x}, s);
+    spmv_rows<T>(ACF, vals, XPlain<T, T>{zF}, EGatherMinusScaled<T, TV>{cidx, v, vC, d, x}, s);
 }
 
 template <class T, class TV>
@@ -450,7 +502,7 @@ void launch_scale(int n, const T *d, const TV *r, T *x, cudaStream_t s) {
 template <class T, class TV>
 void launch_amg_post_smooth(const DCSR &A, const T *vals, const T *dinv, const TV *r, const T *x,
                             TV *xout, cudaStream_t s) {
-    csr_chunk<T>(A.n, A.nnz, A.rp, A.ci, vals, XPlain<T, T>{x}, EPost<T, TV>{r, dinv, x, xout}, s);
+    spmv_rows<T>(A, vals, XPlain<T, T>{x}, EPost<T, TV>{r, dinv, x, xout}, s);
 }
 
 // coarsest grid: x = A^{-1} r with the explicit FP64 inverse; one warp per row
