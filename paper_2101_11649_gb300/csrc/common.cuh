@@ -18,13 +18,17 @@ struct DCSR {
     int *rp = nullptr, *ci = nullptr;
     double *v = nullptr;
     float *v32 = nullptr;
-    // SELL-32-sigma copy for the solve phase (null when not built): slices of
-    // 32 rows (rows sorted by length inside windows of 1024), column-major
-    // within a slice, padded to the slice's longest row with zero values.
+    // SELL-C-sigma copy for the solve phase (null when not built): rows
+    // sorted by length inside windows of 1024, cut into slices of C = 32/sg
+    // rows; each row gets sg lanes of a warp.  A slice is stored as steps of
+    // 32 contiguous entries: entry t*sg + g of the slice's row r sits at
+    // step t, position r*sg + g; rows are padded with zero values to the
+    // slice's longest row.
     int nsl = 0;
+    int sg = 1;                  // lanes per row (power of two, <= 32)
     long long *sptr = nullptr;   // [nsl+1] slice offsets
-    int *slen = nullptr;         // [nsl] slice widths
-    int *perm = nullptr;         // [nsl*32] row of each slice lane (-1: none)
+    int *slen = nullptr;         // [nsl] slice widths in steps of 32 entries
+    int *perm = nullptr;         // [nsl*32/sg] row of each slice row (-1: none)
     int *sci = nullptr;          // padded column indices
     double *sv = nullptr;        // padded values (FP64)
     float *sv32 = nullptr;       // padded values (FP32)
@@ -50,7 +54,7 @@ struct Arena {
     void free_all();
 };
 
-// SELL-32 build from the CSR arrays (values of both precisions when present)
+// SELL-C-sigma build from the CSR arrays (values of both precisions when present)
 int build_sell(DCSR &M, cudaStream_t s, Arena &ar);
 // re-copy the values of a built SELL layout after the CSR values changed
 void refresh_sell(DCSR &M, cudaStream_t s);

@@ -467,7 +467,7 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
     if (!K.V || !K.Z || !K.r || !K.H || !K.partial || !K.stat || !K.hstat) {
         mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "Krylov workspace");
     }
-    // SELL-32 copies of every matrix the solve phase multiplies with
+    // SELL-C-sigma copies of every matrix the solve phase multiplies with
     {
         int rc2 = 0;
         for (int l = 0; l < h->nlev && !rc2; l++) {

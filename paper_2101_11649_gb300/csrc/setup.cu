@@ -1102,10 +1102,11 @@ void launch_cast_f32(const double *in, float *out, long long n, cudaStream_t s) 
 
 namespace mgr {
 
-// ------------------------------------------------------------ SELL-32-sigma
+// ----------------------------------------------------------- SELL-C-sigma
 // Rows are sorted by decreasing length (ties: ascending row) inside windows
-// of SELL_WIN rows, then cut into slices of 32; a slice stores its entries
-// column-major (entry t of lane l at offset t*32 + l) padded to its widest row.
+// of SELL_WIN rows, then cut into slices of C = 32/G rows with G lanes per
+// row.  Step t of a slice holds 32 consecutive entries: position r*G + g
+// carries entry t*G + g of the slice's row r.
 static const int SELL_WIN = 1024;
 
 __global__ void k_sell_sort(int n, const int *rp, int *perm) {
@@ -1141,34 +1142,44 @@ __global__ void k_sell_sort(int n, const int *rp, int *perm) {
     }
 }
 
-__global__ void k_sell_width(int nsl, const int *rp, const int *perm, int *slen) {
+// longest row (the first row of each sorted window)
+__global__ void k_sell_maxlen(int nwin, const int *rp, const int *perm, int *out) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwin) return;
+    int row = perm[(long long)w * SELL_WIN];
+    if (row >= 0) atomicMax(out, rp[row + 1] - rp[row]);
+}
+
+// slice width in steps (the longest row of the slice comes first); w32 =
+// stored entries of the slice
+__global__ void k_sell_width(int nsl, int G, const int *rp, const int *perm, int *slen, int *w32) {
     int s2 = blockIdx.x * blockDim.x + threadIdx.x;
     if (s2 >= nsl) return;
-    int row = perm[s2 * 32];  // the longest row of the slice comes first
-    slen[s2] = row >= 0 ? rp[row + 1] - rp[row] : 0;
+    int row = perm[(long long)s2 * (32 / G)];
+    int len = row >= 0 ? rp[row + 1] - rp[row] : 0;
+    int w = (len + G - 1) / G;
+    slen[s2] = w;
+    w32[s2] = w * 32;
 }
 
-__global__ void k_sell_scale32(const int *slen, int nsl, int *w32) {
-    int s2 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s2 < nsl) w32[s2] = slen[s2] * 32;
-}
-
-__global__ void k_sell_fill(int nsl, const int *rp, const int *ci, const double *v, const float *v32,
+__global__ void k_sell_fill(int nsl, int G, const int *rp, const int *ci, const double *v, const float *v32,
                             const int *perm, const long long *sptr, const int *slen, int *sci,
                             double *sv, float *sv32) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= (long long)nsl * 32) return;
     int s2 = (int)(p >> 5), lane = (int)(p & 31);
-    int row = perm[p];
+    int r = lane / G, g = lane % G;
+    int row = perm[(long long)s2 * (32 / G) + r];
     int len = row >= 0 ? rp[row + 1] - rp[row] : 0;
     int base = row >= 0 ? rp[row] : 0;
     int padc = len > 0 ? ci[base + len - 1] : 0;
     long long o = sptr[s2] + lane;
     for (int t = 0; t < slen[s2]; t++, o += 32) {
-        if (t < len) {
-            sci[o] = ci[base + t];
-            if (sv) sv[o] = v[base + t];
-            if (sv32) sv32[o] = v32[base + t];
+        int k = t * G + g;
+        if (k < len) {
+            sci[o] = ci[base + k];
+            if (sv) sv[o] = v[base + k];
+            if (sv32) sv32[o] = v32[base + k];
         } else {
             sci[o] = padc;
             if (sv) sv[o] = 0.0;
@@ -1177,28 +1188,49 @@ __global__ void k_sell_fill(int nsl, const int *rp, const int *ci, const double 
     }
 }
 
-// SELL pays off for short rows spread over enough slices to fill the GPU
-// (measured on GB300: 1.6x faster than the chunk engine on the reduced
-// operator and the first coarse AMG level); long rows in few slices leave
-// it latency-bound, and those matrices keep the chunk engine.
-static bool sell_suits(const DCSR &M) {
-    if (M.n < 152 * 32 * 4) return false;
-    return (double)M.nnz / M.n <= 40.0;
+// Lanes per row (rules fitted to timings of the solve-phase kernels on
+// GB300 over the AMG levels of a 1M-unknown system).  A lane's chain should
+// hold <= 24 entries on average and, while lanes keep >= 4 entries, <= 64 in
+// the longest row; a matrix with fewer than 64 warps per SM spreads rows
+// over more lanes while chains keep >= 16 entries; and a matrix too small
+// to give every SM 8 warps is bound by the dependent load-then-gather
+// rounds of its longest row, which are cut to <= 8 entries.
+static int sell_lanes(double avg, int maxlen, long long n) {
+    int G = 1;
+    while (G < 32) {
+        const double steps = avg / G, longest = (double)maxlen / G;
+        const long long warps = n * G / 32;
+        const bool more = steps > 24.0 || (steps >= 4.0 && longest > 64.0) ||
+                          (warps < 152LL * 64 && steps >= 16.0) || (warps < 152LL * 8 && longest > 8.0);
+        if (!more) break;
+        G *= 2;
+    }
+    return G;
 }
 
 int build_sell(DCSR &M, cudaStream_t s, Arena &ar) {
-    if (M.n <= 0 || !sell_suits(M)) return ST_OK;
+    if (M.n <= 0) return ST_OK;
     const int nwin = (M.n + SELL_WIN - 1) / SELL_WIN;
-    const int nsl = nwin * (SELL_WIN / 32);
-    M.nsl = nsl;
     M.perm = ar.alloc<int>((size_t)nwin * SELL_WIN);
+    int *dmax = ar.alloc<int>(1);
+    if (!M.perm || !dmax) return ST_NOMEM;
+    k_sell_sort<<<nwin, 512, 0, s>>>(M.n, M.rp, M.perm);
+    cudaMemsetAsync(dmax, 0, sizeof(int), s);
+    k_sell_maxlen<<<(nwin + 255) / 256, 256, 0, s>>>(nwin, M.rp, M.perm, dmax);
+    int maxlen = 0;
+    if (cudaMemcpyAsync(&maxlen, dmax, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return ST_CUDA;
+    ar.release(dmax);
+    const int G = sell_lanes((double)M.nnz / M.n, maxlen, M.n);
+    const int nsl = nwin * (SELL_WIN / (32 / G));
+    M.sg = G;
+    M.nsl = nsl;
     M.slen = ar.alloc<int>(nsl + 1);
     M.sptr = ar.alloc<long long>(nsl + 1);
     int *w32 = ar.alloc<int>(nsl + 1);
-    if (!M.perm || !M.slen || !M.sptr || !w32) return ST_NOMEM;
-    k_sell_sort<<<nwin, 512, 0, s>>>(M.n, M.rp, M.perm);
-    k_sell_width<<<(nsl + 255) / 256, 256, 0, s>>>(nsl, M.rp, M.perm, M.slen);
-    k_sell_scale32<<<(nsl + 255) / 256, 256, 0, s>>>(M.slen, nsl, w32);
+    if (!M.slen || !M.sptr || !w32) return ST_NOMEM;
+    k_sell_width<<<(nsl + 255) / 256, 256, 0, s>>>(nsl, G, M.rp, M.perm, M.slen, w32);
     long long tot = 0;
     int rc = scan_exclusive_ll(w32, M.sptr, nsl, s, ar, &tot);
     ar.release(w32);
@@ -1208,17 +1240,15 @@ int build_sell(DCSR &M, cudaStream_t s, Arena &ar) {
     M.sv = M.v ? ar.alloc<double>(tot + 1) : nullptr;
     M.sv32 = M.v32 ? ar.alloc<float>(tot + 1) : nullptr;
     if (!M.sci || (M.v && !M.sv) || (M.v32 && !M.sv32)) return ST_NOMEM;
-    long long np = (long long)nsl * 32;
-    k_sell_fill<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(nsl, M.rp, M.ci, M.v, M.v32, M.perm, M.sptr,
-                                                          M.slen, M.sci, M.sv, M.sv32);
+    refresh_sell(M, s);
     return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
 }
 
 void refresh_sell(DCSR &M, cudaStream_t s) {
     if (!M.sptr) return;
     long long np = (long long)M.nsl * 32;
-    k_sell_fill<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(M.nsl, M.rp, M.ci, M.v, M.v32, M.perm, M.sptr,
-                                                          M.slen, M.sci, M.sv, M.sv32);
+    k_sell_fill<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(M.nsl, M.sg, M.rp, M.ci, M.v, M.v32, M.perm,
+                                                          M.sptr, M.slen, M.sci, M.sv, M.sv32);
 }
 
 }  // namespace mgr

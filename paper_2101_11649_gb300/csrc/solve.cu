@@ -34,7 +34,6 @@ __device__ __forceinline__ T group_sum(T s) {
 // sums with a fixed shuffle tree.  This keeps the FP64 work at one FMA per
 // nonzero plus log2(G) adds per row (FP64 issue rate, not HBM, bounds FP64
 // sparse products on this part).
-constexpr int CU = 8;          // independent loads per lane per batch
 constexpr int CCAP = 384;      // nonzeros a warp stages in shared memory
 constexpr int CWARPS = 8;      // warps per block
 
@@ -126,40 +125,84 @@ static void csr_chunk(int n, long long nnz, const int *rp, const int *ci, const 
     }
 }
 
-// --------------------------------------------------------------- SELL-32
-// One warp per slice of 32 rows, one lane per row: a single FMA chain over
-// the lane's column of the slice (loads of values and columns coalesced,
-// four entries in flight per lane), no cross-lane reduction.  Padding
-// entries carry zero values and a column of the same row.
-template <class T, class XF, class EPI>
-__global__ void __launch_bounds__(256) k_sell(int nsl, const long long *__restrict__ sptr,
-                                              const int *__restrict__ slen,
-                                              const int *__restrict__ perm,
-                                              const int *__restrict__ sci,
-                                              const T *__restrict__ sv, XF xf, EPI epi) {
+// ---------------------------------------------------------- SELL-C-sigma
+// One warp per slice of C = 32/G rows, G lanes per row.  Each step of the
+// slice is 32 contiguous entries (coalesced value and column loads); a lane
+// runs one FMA chain over its entries t*G + g and the row's G partial sums
+// meet in a fixed shuffle tree.  The slice width L is warp-uniform, so each
+// round issues U independent value/column loads, then U gathers, then U
+// FMAs without divergence: the longest slice costs ceil(L/U) dependent
+// load-gather rounds.  Padding entries carry zero values and a column of
+// the same row.
+//
+// Per precision (fitted to GB300 timings of every AMG level's products):
+// FP64 issues U = 4 loads per round and loads the epilogue's row values
+// after the products, so registers go to more resident warps; FP32 issues
+// U = 8 and (PF) starts the epilogue's row loads and the next slice's
+// offsets before the products, so they overlap them.  Both stay within 48
+// registers (5 blocks, 40 warps per SM).
+template <class T>
+struct SellCfg { static constexpr int U = 4, PF = 0; };
+template <>
+struct SellCfg<float> { static constexpr int U = 8, PF = 1; };
+constexpr int SELL_BLOCKS = 5;
+
+template <int G, class T, class XF, class EPI>
+__global__ void __launch_bounds__(256, SELL_BLOCKS)
+    k_sell(int nsl, const long long *__restrict__ sptr, const int *__restrict__ slen,
+           const int *__restrict__ perm, const int *__restrict__ sci, const T *__restrict__ sv, XF xf,
+           EPI epi) {
+    constexpr int U = SellCfg<T>::U, PF = SellCfg<T>::PF;
+    constexpr int C = 32 / G;
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nsl; sl += nw) {
-        const int L = __ldg(slen + sl);
-        const long long base = __ldg(sptr + sl) + lane;
+    int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (sl >= nsl) return;
+    int L = __ldg(slen + sl);
+    long long base = __ldg(sptr + sl) + lane;
+    int row = __ldg(perm + (long long)sl * C + lane / G);
+    for (;;) {
+        const bool own = (lane % G == 0) && row >= 0;
+        typename EPI::Pre pre{};
+        if (PF && own) pre = epi.pre(row);
+        const int nx = sl + nw;
+        int L2 = 0, row2 = -1;
+        long long base2 = 0;
+        if (PF && nx < nsl) {
+            L2 = __ldg(slen + nx);
+            base2 = __ldg(sptr + nx) + lane;
+            row2 = __ldg(perm + (long long)nx * C + lane / G);
+        }
         T acc = (T)0;
-        int t = 0;
-        for (; t + 4 <= L; t += 4) {
-            const long long o = base + (long long)t * 32;
-            const T v0 = __ldg(sv + o), v1 = __ldg(sv + o + 32), v2 = __ldg(sv + o + 64), v3 = __ldg(sv + o + 96);
-            const int c0 = __ldg(sci + o), c1 = __ldg(sci + o + 32), c2 = __ldg(sci + o + 64), c3 = __ldg(sci + o + 96);
-            const T x0 = xf(c0), x1 = xf(c1), x2 = xf(c2), x3 = xf(c3);
-            acc = fma(v0, x0, acc);
-            acc = fma(v1, x1, acc);
-            acc = fma(v2, x2, acc);
-            acc = fma(v3, x3, acc);
+        for (int t = 0; t < L; t += U) {
+            T vv[U], xx[U];
+            int cc[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (t + u < L) {
+                    const long long o = base + (long long)(t + u) * 32;
+                    vv[u] = __ldg(sv + o);
+                    cc[u] = __ldg(sci + o);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (t + u < L) xx[u] = xf(cc[u]);
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (t + u < L) acc = fma(vv[u], xx[u], acc);
         }
-        for (; t < L; t++) {
-            const long long o = base + (long long)t * 32;
-            acc = fma(__ldg(sv + o), xf(__ldg(sci + o)), acc);
+        if (G > 1) acc = group_sum<G, T>(acc);
+        if (own) epi.put(row, acc, PF ? pre : epi.pre(row));
+        if (nx >= nsl) break;
+        sl = nx;
+        if (PF) {
+            L = L2; base = base2; row = row2;
+        } else {
+            L = __ldg(slen + sl);
+            base = __ldg(sptr + sl) + lane;
+            row = __ldg(perm + (long long)sl * C + lane / G);
         }
-        const int row = __ldg(perm + (long long)sl * 32 + lane);
-        if (row >= 0) epi(row, acc);
     }
 }
 
@@ -170,15 +213,29 @@ inline const double *sell_vals<double>(const DCSR &M) { return M.sv; }
 template <>
 inline const float *sell_vals<float>(const DCSR &M) { return M.sv32; }
 
-// Row products over a matrix: SELL-32 when built, else the chunk engine.
+template <int G, class T, class XF, class EPI>
+static void sell_launch(const DCSR &M, const T *vals, XF xf, EPI epi, cudaStream_t s) {
+    long long blocks = ((long long)M.nsl * 32 + 255) / 256;
+    const long long cap = (long long)NUM_SMS * SELL_BLOCKS * 2;
+    if (blocks > cap) blocks = cap;
+    k_sell<G, T, XF, EPI><<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(M.nsl, M.sptr, M.slen, M.perm,
+                                                                            M.sci, vals, xf, epi);
+}
+
+// Row products over a matrix: SELL-C-sigma when built, else the chunk engine.
 template <class T, class XF, class EPI>
 static void spmv_rows(const DCSR &M, const T *csr_vals, XF xf, EPI epi, cudaStream_t s) {
     if (M.n <= 0) return;
-    if (M.sptr && sell_vals<T>(M)) {
-        long long blocks = ((long long)M.nsl * 32 + 255) / 256;
-        if (blocks > NUM_SMS * 8) blocks = NUM_SMS * 8;
-        k_sell<T, XF, EPI><<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(
-            M.nsl, M.sptr, M.slen, M.perm, M.sci, sell_vals<T>(M), xf, epi);
+    const T *sv = sell_vals<T>(M);
+    if (M.sptr && sv) {
+        switch (M.sg) {
+            case 1: sell_launch<1, T>(M, sv, xf, epi, s); break;
+            case 2: sell_launch<2, T>(M, sv, xf, epi, s); break;
+            case 4: sell_launch<4, T>(M, sv, xf, epi, s); break;
+            case 8: sell_launch<8, T>(M, sv, xf, epi, s); break;
+            case 16: sell_launch<16, T>(M, sv, xf, epi, s); break;
+            default: sell_launch<32, T>(M, sv, xf, epi, s); break;
+        }
         return;
     }
     csr_chunk<T>(M.n, M.nnz, M.rp, M.ci, csr_vals, xf, epi, s);
@@ -197,35 +254,56 @@ struct XScaled {  // x_j = d_j r_j (pre-smoothing from zero)
     __device__ __forceinline__ T operator()(int j) const { return __ldg(d + j) * (T)__ldg(r + j); }
 };
 
-// epilogues
+// epilogues.  pre(row) issues the loads an epilogue needs from its row
+// alone (so the SELL kernel can start them before the row's products);
+// put(row, s, p) finishes the row.  Every row is finished by one lane and
+// no epilogue reads what another row writes.
+#define EPI_CALL \
+    __device__ __forceinline__ void operator()(int row, T s) const { put(row, s, pre(row)); }
+struct PreNone {};
 template <class T, class TO>
 struct EStore {
     TO *y;
-    __device__ __forceinline__ void operator()(int row, T s) const { y[row] = (TO)s; }
+    using Pre = PreNone;
+    __device__ __forceinline__ Pre pre(int) const { return {}; }
+    __device__ __forceinline__ void put(int row, T s, const Pre &) const { y[row] = (TO)s; }
+    EPI_CALL
 };
 template <class T>
 struct EAdd {
     T *y;
-    __device__ __forceinline__ void operator()(int row, T s) const { y[row] += s; }
+    struct Pre { T y; };
+    __device__ __forceinline__ Pre pre(int row) const { return {y[row]}; }
+    __device__ __forceinline__ void put(int row, T s, const Pre &p) const { y[row] = p.y + s; }
+    EPI_CALL
 };
 struct EAxpby {
     double alpha, beta;
     const double *b;  // residual mode when non-null: y = b - s
     double *y;
-    __device__ __forceinline__ void operator()(int row, double s) const {
-        if (b) y[row] = b[row] - s;
-        else y[row] = beta == 0.0 ? alpha * s : alpha * s + beta * y[row];
+    using T = double;
+    struct Pre { double u; };
+    __device__ __forceinline__ Pre pre(int row) const {
+        return {b ? b[row] : (beta == 0.0 ? 0.0 : y[row])};
     }
+    __device__ __forceinline__ void put(int row, double s, const Pre &p) const {
+        if (b) y[row] = p.u - s;
+        else y[row] = beta == 0.0 ? alpha * s : alpha * s + beta * p.u;
+    }
+    EPI_CALL
 };
 template <class T>
 struct EStoreScaled {  // y = s ; x = d s  (restriction that also seeds the next pre-smoothing)
     T *y;
     const T *d;
     T *x;
-    __device__ __forceinline__ void operator()(int row, T s) const {
+    struct Pre { T d; };
+    __device__ __forceinline__ Pre pre(int row) const { return {d[row]}; }
+    __device__ __forceinline__ void put(int row, T s, const Pre &p) const {
         y[row] = s;
-        x[row] = d[row] * s;
+        x[row] = p.d * s;
     }
+    EPI_CALL
 };
 template <class T, class TV>
 struct EGatherMinusScaled {  // y = b[idx] - s ; x = d y
@@ -234,28 +312,36 @@ struct EGatherMinusScaled {  // y = b[idx] - s ; x = d y
     T *y;
     const T *d;
     T *x;
-    __device__ __forceinline__ void operator()(int row, T s) const {
-        T t = (T)b[idx[row]] - s;
+    struct Pre { T b, d; };
+    __device__ __forceinline__ Pre pre(int row) const { return {(T)b[idx[row]], d[row]}; }
+    __device__ __forceinline__ void put(int row, T s, const Pre &p) const {
+        T t = p.b - s;
         y[row] = t;
-        x[row] = d[row] * t;
+        x[row] = p.d * t;
     }
+    EPI_CALL
 };
 template <class T, class TV>
 struct EResid {  // res = r - s
     const TV *r;
     T *res;
-    __device__ __forceinline__ void operator()(int row, T s) const { res[row] = (T)r[row] - s; }
+    struct Pre { T r; };
+    __device__ __forceinline__ Pre pre(int row) const { return {(T)r[row]}; }
+    __device__ __forceinline__ void put(int row, T s, const Pre &p) const { res[row] = p.r - s; }
+    EPI_CALL
 };
 template <class T, class TV>
 struct ESmooth0 {  // x = d r ; res = r - A (d r)
     const TV *r;
     const T *d;
     T *x, *res;
-    __device__ __forceinline__ void operator()(int row, T s) const {
-        T ri = (T)r[row];
-        x[row] = d[row] * ri;
-        res[row] = ri - s;
+    struct Pre { T r, d; };
+    __device__ __forceinline__ Pre pre(int row) const { return {(T)r[row], d[row]}; }
+    __device__ __forceinline__ void put(int row, T s, const Pre &p) const {
+        x[row] = p.d * p.r;
+        res[row] = p.r - s;
     }
+    EPI_CALL
 };
 template <class T, class TV>
 struct EPost {  // xout = x + d (r - A x)
@@ -263,9 +349,12 @@ struct EPost {  // xout = x + d (r - A x)
     const T *d;
     const T *x;
     TV *xout;
-    __device__ __forceinline__ void operator()(int row, T s) const {
-        xout[row] = (TV)(x[row] + d[row] * ((T)r[row] - s));
+    struct Pre { T r, d, x; };
+    __device__ __forceinline__ Pre pre(int row) const { return {(T)r[row], d[row], x[row]}; }
+    __device__ __forceinline__ void put(int row, T s, const Pre &p) const {
+        xout[row] = (TV)(p.x + p.d * (p.r - s));
     }
+    EPI_CALL
 };
 template <class T, class TV>
 struct EGatherMinus {  // y = b[idx[row]] + sign * s
@@ -273,15 +362,22 @@ struct EGatherMinus {  // y = b[idx[row]] + sign * s
     const TV *b;
     T sign;
     T *y;
-    __device__ __forceinline__ void operator()(int row, T s) const { y[row] = (T)b[idx[row]] + sign * s; }
+    struct Pre { T b; };
+    __device__ __forceinline__ Pre pre(int row) const { return {(T)b[idx[row]]}; }
+    __device__ __forceinline__ void put(int row, T s, const Pre &p) const { y[row] = p.b + sign * s; }
+    EPI_CALL
 };
 template <class T, class TV>
 struct EInterp {  // z[fidx] = zF + s
     const int *fidx;
     const T *zF;
     TV *z;
-    __device__ __forceinline__ void operator()(int row, T s) const { z[fidx[row]] = (TV)(zF[row] + s); }
+    struct Pre { int f; T zF; };
+    __device__ __forceinline__ Pre pre(int row) const { return {fidx[row], zF[row]}; }
+    __device__ __forceinline__ void put(int, T s, const Pre &p) const { z[p.f] = (TV)(p.zF + s); }
+    EPI_CALL
 };
+#undef EPI_CALL
 
 // --------------------------------------------------------------- CSR y = A x
 template <class T>
@@ -548,15 +644,49 @@ int multidot_blocks(int n) {
     return (int)(b < 1 ? 1 : b);
 }
 
+__host__ __device__ constexpr int pow2_at_least(int k) { return k <= 1 ? 1 : 2 * pow2_at_least((k + 1) / 2); }
+__host__ __device__ constexpr int log2_of(int p) { return p <= 1 ? 0 : 1 + log2_of(p / 2); }
+
+// Warp sum of K values per lane by recursive halving: at the level with
+// lane distance o, a lane keeps half of its values and adds the partner's
+// copies of them, so after log2 K' levels (K' = K rounded up to a power of
+// two) each lane holds one partial sum, of value index lane >> (5 - log2 K'),
+// and plain shuffle levels finish it.  K' - 1 + 5 - log2 K' adds per lane
+// instead of 5 K; the order is fixed, so results are reproducible.
+template <int K>
+__device__ __forceinline__ double warp_sum_many(const double (&acc)[K], int lane, int &index) {
+    constexpr int KP = pow2_at_least(K);
+    constexpr int LK = log2_of(KP);
+    static_assert(KP <= 32, "at most 32 values");
+    double v[KP];
+#pragma unroll
+    for (int i = 0; i < KP; i++) v[i] = i < K ? acc[i] : 0.0;
+#pragma unroll
+    for (int lev = 0; lev < LK; lev++) {
+        const int o = 16 >> lev, m = KP >> (lev + 1);
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < m; i++) {
+            const double send = upper ? v[i] : v[i + m];
+            const double keep = upper ? v[i + m] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    double t = v[0];
+#pragma unroll
+    for (int o = (16 >> LK); o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    index = lane >> (5 - LK);
+    return t;
+}
+
 template <int K>
 __device__ __forceinline__ void block_partials(double (&acc)[K], double *partial) {
     __shared__ double sh[RED_THREADS / 32][K > 0 ? K : 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < K; i++) {
-        double v = group_sum<32, double>(acc[i]);
-        if (lane == 0) sh[w][i] = v;
-    }
+    constexpr int LK = log2_of(pow2_at_least(K));
+    int idx;
+    const double t0 = warp_sum_many<K>(acc, lane, idx);
+    if ((lane & ((1 << (5 - LK)) - 1)) == 0 && idx < K) sh[w][idx] = t0;
     __syncthreads();
     if (threadIdx.x < K) {
         double t = 0.0;

@@ -69,6 +69,52 @@ def test_bsr_spmv_parity(b, nb):
     assert (np.abs(y2.cpu().numpy() - ref2) / (2 * absref + 0.5 * np.abs(y0))).max() <= 1e-13
 
 
+# ------------------------------------------- SELL-C-sigma over row shapes
+def _banded_m_matrix(n, K, keep, seed):
+    """Scalar symmetric M-matrix (AMG only, no MGR level): the pair (i, i+d),
+    d = 1..K, is kept with probability ``keep`` (ragged rows of up to 2K+1
+    entries); off-diagonals -U(0.1, 1), diagonal = sum of the row's
+    off-diagonal magnitudes + U(0.1, 1)."""
+    from paper_2101_11649_gb300.synth.bsr import BlockSystem, assemble_bsr
+    rng = np.random.default_rng(seed)
+    ii = [np.flatnonzero(rng.random(n - d) < keep) for d in range(1, K + 1)]
+    jj = np.concatenate([i + d for d, i in zip(range(1, K + 1), ii)])
+    ii = np.concatenate(ii)
+    w = rng.uniform(0.1, 1.0, ii.size)
+    diag = np.bincount(ii, w, n) + np.bincount(jj, w, n) + rng.uniform(0.1, 1.0, n)
+    rows = np.concatenate([ii, jj, np.arange(n)])
+    cols = np.concatenate([jj, ii, np.arange(n)])
+    rp, ci, val = assemble_bsr(n, 1, rows, cols, np.concatenate([-w, -w, diag]))
+    return BlockSystem(f"band{n}x{K}", 1, rp, ci, val, np.zeros(n, np.int8), 0,
+                       rng.standard_normal(n))
+
+
+# (rows, half band, kept fraction): average row lengths 7 .. 200 at row
+# counts 3k .. 300k, so the layout's lanes per row range over 1 .. 32; none
+# of the row counts is a multiple of 32
+BANDS = [(300007, 3, 1.0), (120001, 20, 0.95), (60007, 40, 0.95), (40009, 75, 1.0),
+         (10007, 60, 1.0), (3001, 100, 1.0), (50021, 30, 0.3)]
+
+
+@pytest.mark.parametrize("n,K,keep", BANDS)
+def test_sell_products_over_row_shapes(n, K, keep):
+    s = _banded_m_matrix(n, K, keep, seed=n)
+    g = solver(s)
+    x = np.random.default_rng(7).standard_normal(n)
+    y = g.spmv(t(x)).cpu().numpy()
+    ref = O.spmv_bsr(n, 1, s.row_ptr, s.col_idx, s.val, x)
+    absref = O.spmv_bsr(n, 1, s.row_ptr, s.col_idx, np.abs(s.val), np.abs(x)) + 1e-300
+    assert (np.abs(y - ref) / absref).max() <= 1e-13
+    if n <= 10007:
+        # every coarse level's product, both precisions, through the V-cycle
+        o = O.Oracle(s)
+        zo = o.apply(x)
+        zg = g.apply(t(x)).cpu().numpy()
+        assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo)
+        z32 = solver(s, precision="fp32").apply(t(x)).cpu().numpy()
+        assert np.linalg.norm(z32 - zo) <= 1e-4 * np.linalg.norm(zo)
+
+
 # ------------------------------------------------------ setup, bit-exact
 def _same_csr(a, b, what):
     assert a is not None and b is not None, what
