@@ -723,12 +723,16 @@ __device__ __forceinline__ void sum_partials(const double *partial, double *out)
 
 // h[i] = V_i . w for i < K (w may be V_{K-1} itself).  Skipped when
 // *flag == 0 (flag != nullptr): the conditional reorthogonalisation pass.
+// The K basis vectors are read in chunks of KB: a chunk's loads are all
+// issued before its FMAs, so every thread keeps 2 KB loads in flight
+// whatever schedule the compiler picks for a given K.
 template <int K>
-__global__ void __launch_bounds__(RED_THREADS) k_dots(const double *__restrict__ V, long long ldv,
-                                                      const double *__restrict__ w, int n,
-                                                      double *partial, double *h, unsigned *ticket,
-                                                      const int *flag) {
+__global__ void __launch_bounds__(RED_THREADS, 2) k_dots(const double *__restrict__ V, long long ldv,
+                                                         const double *__restrict__ w, int n,
+                                                         double *partial, double *h, unsigned *ticket,
+                                                         const int *flag) {
     if (flag && *flag == 0) return;
+    constexpr int KB = K < 8 ? K : 8;
     double acc[K];
 #pragma unroll
     for (int i = 0; i < K; i++) acc[i] = 0.0;
@@ -737,16 +741,25 @@ __global__ void __launch_bounds__(RED_THREADS) k_dots(const double *__restrict__
         double wv[RED_EPT];
 #pragma unroll
         for (int u = 0; u < RED_EPT; u++) {
-            long long e = e0 + (long long)u * RED_THREADS;
+            const long long e = e0 + (long long)u * RED_THREADS;
             wv[u] = e < n ? __ldg(w + e) : 0.0;
         }
 #pragma unroll
-        for (int i = 0; i < K; i++)
+        for (int i0 = 0; i0 < K; i0 += KB) {
+            double vv[KB][RED_EPT];
 #pragma unroll
-            for (int u = 0; u < RED_EPT; u++) {
-                long long e = e0 + (long long)u * RED_THREADS;
-                if (e < n) acc[i] += __ldg(V + i * ldv + e) * wv[u];
-            }
+            for (int i = 0; i < KB; i++)
+#pragma unroll
+                for (int u = 0; u < RED_EPT; u++) {
+                    const long long e = e0 + (long long)u * RED_THREADS;
+                    vv[i][u] = (i0 + i < K && e < n) ? __ldg(V + (i0 + i) * ldv + e) : 0.0;
+                }
+#pragma unroll
+            for (int i = 0; i < KB; i++)
+                if (i0 + i < K)
+#pragma unroll
+                    for (int u = 0; u < RED_EPT; u++) acc[i0 + i] = fma(vv[i][u], wv[u], acc[i0 + i]);
+        }
     }
     block_partials<K>(acc, partial);
     if (last_block(ticket)) {
@@ -763,35 +776,48 @@ static constexpr double REORTH_ETA2 = 1e-2;
 // w <- w - sum_{i<K} V_i h_i ; nrm2 = |w|^2.  mode 1 (first pass) also
 // decides reorthogonalisation (|w'|^2 < eta^2 |w|^2, with |w|^2 = h[K]) and
 // writes it to *flag; mode 2 (the second pass) is skipped when *flag == 0.
+// Chunked loads as in k_dots; h is read from shared memory.
 template <int K>
-__global__ void __launch_bounds__(RED_THREADS) k_update_norm(const double *__restrict__ V, long long ldv,
-                                                             const double *__restrict__ h, double *w,
-                                                             int n, double *partial, double *nrm2,
-                                                             unsigned *ticket, int *flag, int mode) {
+__global__ void __launch_bounds__(RED_THREADS, 2) k_update_norm(const double *__restrict__ V, long long ldv,
+                                                                const double *__restrict__ h, double *w,
+                                                                int n, double *partial, double *nrm2,
+                                                                unsigned *ticket, int *flag, int mode) {
     if (mode == 2 && *flag == 0) return;
-    double hs[K];
-#pragma unroll
-    for (int i = 0; i < K; i++) hs[i] = h[i];
+    constexpr int KB = K < 16 ? K : 16;
+    __shared__ double hs[K];
+    if (threadIdx.x < K) hs[threadIdx.x] = h[threadIdx.x];
+    __syncthreads();
     double acc[1] = {0.0};
     const long long stride = (long long)gridDim.x * RED_THREADS * RED_EPT;
     for (long long e0 = (long long)blockIdx.x * RED_THREADS * RED_EPT + threadIdx.x; e0 < n; e0 += stride) {
         double wv[RED_EPT];
 #pragma unroll
         for (int u = 0; u < RED_EPT; u++) {
-            long long e = e0 + (long long)u * RED_THREADS;
+            const long long e = e0 + (long long)u * RED_THREADS;
             wv[u] = e < n ? w[e] : 0.0;
         }
 #pragma unroll
-        for (int i = 0; i < K; i++)
+        for (int i0 = 0; i0 < K; i0 += KB) {
+            double vv[KB][RED_EPT];
 #pragma unroll
-            for (int u = 0; u < RED_EPT; u++) {
-                long long e = e0 + (long long)u * RED_THREADS;
-                if (e < n) wv[u] -= __ldg(V + i * ldv + e) * hs[i];
-            }
+            for (int i = 0; i < KB; i++)
+#pragma unroll
+                for (int u = 0; u < RED_EPT; u++) {
+                    const long long e = e0 + (long long)u * RED_THREADS;
+                    vv[i][u] = (i0 + i < K && e < n) ? __ldg(V + (i0 + i) * ldv + e) : 0.0;
+                }
+#pragma unroll
+            for (int i = 0; i < KB; i++)
+                if (i0 + i < K) {
+                    const double hi = hs[i0 + i];
+#pragma unroll
+                    for (int u = 0; u < RED_EPT; u++) wv[u] = fma(-vv[i][u], hi, wv[u]);
+                }
+        }
 #pragma unroll
         for (int u = 0; u < RED_EPT; u++) {
-            long long e = e0 + (long long)u * RED_THREADS;
-            if (e < n) { w[e] = wv[u]; acc[0] += wv[u] * wv[u]; }
+            const long long e = e0 + (long long)u * RED_THREADS;
+            if (e < n) { w[e] = wv[u]; acc[0] = fma(wv[u], wv[u], acc[0]); }
         }
     }
     block_partials<1>(acc, partial);
