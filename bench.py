@@ -39,7 +39,7 @@ WORKLOAD = "hybrid mimetic single-phase 64^3 (1,060,864 unknowns), MGR_P + AMG V
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--grid", type=int, default=64)
@@ -60,9 +60,10 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """nvidia-smi samples (every 50 ms) of SM clock and throttle reasons; only
+    samples stamped inside the marked region count."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -70,17 +71,28 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.f = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
+            # wait for the first sample so the region is covered from its start
+            deadline = time.time() + 5.0
+            while time.time() < deadline and os.path.getsize(self.f.name) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
+
+    def start(self):
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
 
     def __exit__(self, *a):
         if self.proc:
@@ -90,6 +102,16 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(text, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
     def summary(self):
         if not self.f:
             return None
@@ -98,7 +120,7 @@ class ClockSampler:
         try:
             for line in open(self.f.name):
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
+                if len(parts) >= 10:
                     rows.append(parts)
         except Exception:
             return None
@@ -107,14 +129,20 @@ class ClockSampler:
                 os.unlink(self.f.name)
             except Exception:
                 pass
-        if not rows:
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows
+                      if (lambda ts: ts is not None and self.t0 - 0.05 <= ts <= self.t1 + 0.05)(self._stamp(r[0]))]
+        else:
+            inside = rows
+        if not inside:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in inside if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[6 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(inside),
+                "interval_ms": 50}
 
 
 def dist_init(args):
@@ -210,9 +238,17 @@ def main():
         run_reference(args, world, rank)
         return
     import torch
+    torch.cuda.set_device(local)
+    # every launch and every timing event of this arm on one (non-legacy) stream:
+    # the solvers take the current stream at construction
+    with torch.cuda.stream(torch.cuda.Stream()):
+        run_gb300(args, world, rank, local)
+
+
+def run_gb300(args, world, rank, local):
+    import torch
     from paper_2101_11649_gb300 import mgr as M
 
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     peak_gbs, peak_kind = peaks()
     sysm = make_system(args.grid)
@@ -263,11 +299,13 @@ def main():
     torch.cuda.synchronize()
     l0 = M.launch_count()
     with ClockSampler(local) as cs:
+        cs.start()
         t64, info64 = timed(s64, args.steps)
         torch.cuda.synchronize()
         barrier(world)
         t32, info32 = timed(s32, args.steps)
         torch.cuda.synchronize()
+        cs.stop()
     launches = M.launch_count() - l0
     clocks = cs.summary()
     ms64 = max_over_ranks(world, statistics.mean(t64), dev)
