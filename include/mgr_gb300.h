@@ -82,7 +82,12 @@ enum { MGR_PREC_FP64 = 0, MGR_PREC_FP32 = 1 };
  * num_functions).  precision selects FP64 or FP32 storage and arithmetic of
  * the whole V-cycle (FGMRES, residuals and the coarsest dense solve stay
  * FP64).  restart = FGMRES m.  use_graphs != 0 replays the per-iteration
- * kernel sequence from captured CUDA graphs.
+ * kernel sequence from captured CUDA graphs.  amg_tail_nnz: the AMG levels
+ * from the first level k >= 1 whose operator has at most this many nonzeros
+ * down to the coarsest run as one launch of one thread-block cluster (same
+ * arithmetic, bitwise the same result as one launch per step); 0 (the
+ * default) runs every step as its own launch, which measured faster on
+ * GB300 for the workloads here.  Devices without cluster launches ignore it.
  */
 typedef struct {
     int32_t relax_type[MGR_MAX_LEVELS];
@@ -93,6 +98,7 @@ typedef struct {
     int32_t precision;
     int32_t restart;
     int32_t use_graphs;
+    int32_t amg_tail_nnz;
 } mgr_options;
 
 /* Solve report.  level_rows/level_nnz list the MGR levels, then the AMG levels. */
@@ -107,7 +113,8 @@ typedef struct {
 } mgr_solve_info;
 
 /* Defaults: Jacobi, 1 sweep, omega 1 on every level; theta 0.25, 25 AMG
- * levels, coarsest <= 256 rows, P_max 4, 1 function; FP64; m = 30; graphs on. */
+ * levels, coarsest <= 256 rows, P_max 4, 1 function; FP64; m = 30; graphs on;
+ * no fused AMG tail. */
 void mgr_options_default(mgr_options *opt);
 
 /*

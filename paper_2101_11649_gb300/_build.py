@@ -23,6 +23,7 @@ UNITS = {
     "solve.cu": [],
     "mgr_api.cu": [],
     "noalloc.cu": [],
+    "tail.cu": [],
 }
 
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace mgr {
@@ -36,6 +37,31 @@ struct DCSR {
 };
 
 
+// Programmatic dependent launch.  Solve-phase kernels are launched with
+// programmatic stream serialisation: a kernel may be scheduled while its
+// predecessor drains; it waits (griddepcontrol.wait) before it reads or
+// writes memory that earlier kernels touch, then lets its own successor be
+// scheduled.  A kernel started without the attribute passes both at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+bool pdl_on();  // false when the environment sets MGR_PDL=0
+template <class... KArgs, class... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_on() ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Status codes mirror mgr_status.
 enum { ST_OK = 0, ST_INVALID = 1, ST_NOMEM = 2, ST_CUDA = 3, ST_SINGULAR = 4,
        ST_NOT_CONVERGED = 5, ST_TIMEOUT = 6, ST_UNSUPPORTED = 7 };
@@ -53,6 +79,44 @@ struct Arena {
     void release(void *p);
     void free_all();
 };
+
+// A SELL-C-sigma matrix as the fused coarse-level kernel reads it (values of
+// that kernel's precision).
+struct SellView {
+    int nsl = 0, sg = 1;
+    const long long *sptr = nullptr;
+    const int *slen = nullptr, *perm = nullptr, *sci = nullptr;
+    const void *sv = nullptr;
+};
+
+// Fused AMG tail: levels k_t .. k_c - 1 of an AMG V(1,1) cycle (residual,
+// restriction, then after the coarsest solve prolongation and post-smoothing)
+// plus the coarsest dense solve, in one launch of one thread-block cluster.
+// The launch walks a list of phases built at setup; consecutive phases meet
+// at a cluster barrier.  Vectors are of the kernel's precision T (void here).
+enum { TAIL_RESID = 0, TAIL_RESTRICT_SCALED = 1, TAIL_RESTRICT = 2, TAIL_DENSE = 3, TAIL_PROLONG = 4,
+       TAIL_POST = 5 };
+constexpr int TAIL_MAX_PHASES = 64;
+struct TailPhase {
+    int kind = 0;
+    int n = 0;                  // TAIL_DENSE: order of the coarsest inverse
+    SellView M;                 // the phase's matrix (not TAIL_DENSE)
+    const void *x = nullptr;    // gathered vector (TAIL_DENSE: r of the coarsest level)
+    void *y = nullptr;          // output: res, r_c, xw (read-modify-write), x
+    void *y2 = nullptr;         // TAIL_RESTRICT_SCALED: xw_c = d_c r_c
+    const void *r = nullptr;    // TAIL_RESID, TAIL_POST: the level's right-hand side
+    const void *d = nullptr;    // TAIL_RESTRICT_SCALED: d_c; TAIL_POST: d
+    const double *inv = nullptr;  // TAIL_DENSE: coarsest inverse, row-major
+};
+struct TailPlan {
+    int nphase = 0;
+    TailPhase ph[TAIL_MAX_PHASES];
+};
+template <class T>
+int launch_amg_tail(const TailPlan *plan_device, int cluster, cudaStream_t s);
+// Cluster size (16, else 8) the device can run the fused tail with; 0 when
+// it cannot (the cycle then launches the levels one kernel at a time).
+int amg_tail_cluster(void);
 
 // SELL-C-sigma build from the CSR arrays (values of both precisions when present)
 int build_sell(DCSR &M, cudaStream_t s, Arena &ar);

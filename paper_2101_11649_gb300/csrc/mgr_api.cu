@@ -6,12 +6,14 @@
 #include <string.h>
 
 #include <atomic>
+#include <type_traits>
 #include <chrono>
 #include <string>
 #include <vector>
 
 #include "../../include/mgr_gb300.h"
 #include "common.cuh"
+#include "sell.cuh"
 
 namespace mgr {
 
@@ -104,6 +106,9 @@ struct mgr_ctx {
     AmgLevel amg[32];
     int nco = 0;
     double *coinv = nullptr, *coinvT = nullptr;
+    // fused AMG tail (levels tail_k .. namg-1 in one cluster launch), -1: off
+    int tail_k = -1, tail_cl = 0;
+    TailPlan *tail_plan[2] = {nullptr, nullptr};  // device phase lists [trans]
     int *errw = nullptr;
     Krylov kr;
     Prof prof;
@@ -112,6 +117,8 @@ struct mgr_ctx {
 };
 
 static thread_local std::string g_last_error;
+
+static int setup_tail(mgr_handle h, int tail_nnz, cudaStream_t s, Arena &ar);
 
 static mgr_status fail(mgr_handle h, mgr_status st, const std::string &msg) {
     if (h) h->err = msg;
@@ -192,6 +199,7 @@ extern "C" void mgr_options_default(mgr_options *o) {
     o->precision = MGR_PREC_FP64;
     o->restart = 30;
     o->use_graphs = 1;
+    o->amg_tail_nnz = 0;
 }
 
 // ---------------------------------------------------------------- helpers
@@ -489,6 +497,13 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
         rc2 |= build_sell(h->A0T, s, ar);
         if (rc2) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "SELL copies"); }
     }
+    {
+        const int rc3 = setup_tail(h, h->opt.amg_tail_nnz, s, ar);
+        if (rc3) {
+            mgr_free(h);
+            return fail(nullptr, rc3 == ST_NOMEM ? MGR_ERR_NOMEM : MGR_ERR_CUDA, "fused AMG tail");
+        }
+    }
     cudaStreamSynchronize(s);
     if (cudaGetLastError() != cudaSuccess) { mgr_free(h); return cuda_fail(nullptr, "setup"); }
     h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -525,6 +540,130 @@ template <> struct Sel<float> {
     static float *res(AmgLevel &L) { return L.res32; }
 };
 
+// ------------------------------------------------------- fused AMG tail
+template <class T>
+static SellView sell_view(const DCSR &M) {
+    SellView v;
+    v.nsl = M.nsl;
+    v.sg = M.sg;
+    v.sptr = M.sptr;
+    v.slen = M.slen;
+    v.perm = M.perm;
+    v.sci = M.sci;
+    v.sv = sell_vals<T>(M);
+    return v;
+}
+
+// The phase list of levels tail_k .. namg-1 (the order of amg_cycle below).
+// false when a matrix of the tail has no SELL copy of this precision.
+template <class T>
+static bool build_tail_plan(mgr_handle h, int trans, TailPlan &P) {
+    const int kt = h->tail_k, kc = h->namg - 1;
+    P.nphase = 0;
+    auto add = [&](int kind) -> TailPhase & {
+        TailPhase &q = P.ph[P.nphase++];
+        q = TailPhase();
+        q.kind = kind;
+        return q;
+    };
+    for (int k = kt; k < kc; k++) {
+        AmgLevel &L = h->amg[k];
+        const DCSR &A = trans ? L.AT : L.A;
+        if (!A.sptr || !sell_vals<T>(A) || !L.R.sptr || !sell_vals<T>(L.R) || !L.P.sptr || !sell_vals<T>(L.P))
+            return false;
+        TailPhase &q = add(TAIL_RESID);
+        q.M = sell_view<T>(A);
+        q.x = Sel<T>::xw(L);
+        q.r = Sel<T>::r(L);
+        q.y = Sel<T>::res(L);
+        AmgLevel &C = h->amg[k + 1];
+        TailPhase &q2 = add(k + 1 < kc ? TAIL_RESTRICT_SCALED : TAIL_RESTRICT);
+        q2.M = sell_view<T>(L.R);
+        q2.x = Sel<T>::res(L);
+        q2.y = Sel<T>::r(C);
+        if (k + 1 < kc) {
+            q2.y2 = Sel<T>::xw(C);
+            q2.d = Sel<T>::dinv(C);
+        }
+    }
+    TailPhase &qd = add(TAIL_DENSE);
+    qd.n = h->nco;
+    qd.inv = trans ? h->coinvT : h->coinv;
+    qd.x = Sel<T>::r(h->amg[kc]);
+    qd.y = Sel<T>::x(h->amg[kc]);
+    for (int k = kc - 1; k >= kt; k--) {
+        AmgLevel &L = h->amg[k];
+        const DCSR &A = trans ? L.AT : L.A;
+        TailPhase &q = add(TAIL_PROLONG);
+        q.M = sell_view<T>(L.P);
+        q.x = Sel<T>::x(h->amg[k + 1]);
+        q.y = Sel<T>::xw(L);
+        TailPhase &q2 = add(TAIL_POST);
+        q2.M = sell_view<T>(A);
+        q2.x = Sel<T>::xw(L);
+        q2.r = Sel<T>::r(L);
+        q2.d = Sel<T>::dinv(L);
+        q2.y = Sel<T>::x(L);
+    }
+    return true;
+}
+
+// Choose the tail's first level and upload its phase lists (both
+// orientations).  Leaves the tail off when the option, the hierarchy or the
+// device does not allow it.
+static int setup_tail(mgr_handle h, int tail_nnz, cudaStream_t s, Arena &ar) {
+    h->tail_k = -1;
+    if (tail_nnz <= 0 || h->namg < 3) return ST_OK;
+    int kt = -1;
+    for (int k = 1; k < h->namg - 1; k++)
+        if (h->amg[k].A.nnz <= tail_nnz) {
+            kt = k;
+            break;
+        }
+    if (kt < 0) return ST_OK;
+    if (h->namg - 1 - kt > TAIL_MAX_PHASES / 4 - 1) kt = h->namg - 1 - (TAIL_MAX_PHASES / 4 - 1);
+    const int cl = amg_tail_cluster();
+    if (cl <= 0) return ST_OK;
+    h->tail_k = kt;
+    for (int trans = 0; trans < 2; trans++) {
+        TailPlan plan;
+        const bool ok = h->opt.precision == MGR_PREC_FP32 ? build_tail_plan<float>(h, trans, plan)
+                                                          : build_tail_plan<double>(h, trans, plan);
+        if (!ok) {
+            h->tail_k = -1;
+            return ST_OK;
+        }
+        h->tail_plan[trans] = ar.alloc<TailPlan>(1);
+        if (!h->tail_plan[trans]) return ST_NOMEM;
+        if (cudaMemcpyAsync(h->tail_plan[trans], &plan, sizeof(TailPlan), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return ST_CUDA;
+    }
+    h->tail_cl = cl;
+    return ST_OK;
+}
+
+// Algorithmic bytes and FP64 FMAs of one tail launch: the sums of the
+// per-step kernel classes it replaces.
+static void tail_cost(mgr_handle h, double ts, double &bytes, double &fma) {
+    const int kt = h->tail_k, kc = h->namg - 1;
+    const double f64 = ts == 8 ? 1.0 : 0.0;
+    bytes = 0;
+    fma = 0;
+    for (int k = kt; k < kc; k++) {
+        AmgLevel &L = h->amg[k];
+        const double an = L.A.n, annz = L.A.nnz, nc = h->amg[k + 1].A.n;
+        const bool cc = (k + 1 == kc);
+        bytes += annz * (ts + 4) + (an + 1) * 4 + an * (3 * ts);
+        bytes += (double)L.R.nnz * (ts + 4) + (nc + 1) * 4 + an * ts + nc * ts * (cc ? 1 : 3);
+        bytes += (double)L.P.nnz * (ts + 4) + (an + 1) * 4 + nc * ts + 2 * an * ts;
+        bytes += annz * (ts + 4) + (an + 1) * 4 + an * (4 * ts);
+        fma += f64 * (2 * annz + L.R.nnz + L.P.nnz + an);
+    }
+    bytes += (double)h->nco * h->nco * 8 + 2.0 * h->nco * ts;
+    fma += (double)h->nco * h->nco;
+}
+
 // AMG V(1,1) on level k: r (TV) -> x (TV).  On entry L.xw already holds the
 // pre-smoothed iterate D_k r (l1-Jacobi from zero), written by whoever
 // produced r.  trans uses A_k^T and the transposed coarsest inverse (the
@@ -533,6 +672,22 @@ template <class T, class TV>
 static void amg_cycle(mgr_handle h, int k, const TV *r, TV *x, int trans) {
     cudaStream_t s = h->s;
     AmgLevel &L = h->amg[k];
+    if constexpr (std::is_same<T, TV>::value) {
+        if (k == h->tail_k && h->tail_cl > 0 && (const void *)r == (const void *)Sel<T>::r(L) &&
+            (void *)x == (void *)Sel<T>::x(L)) {
+            double by, fm;
+            tail_cost(h, sizeof(T), by, fm);
+            int rc;
+            {
+                KScope ks(h, "amg_tail", k, by, fm);
+                rc = launch_amg_tail<T>(h->tail_plan[trans ? 1 : 0], h->tail_cl, s);
+            }
+            if (rc == cudaSuccess) return;
+            // a refused cluster launch: clear it, keep to one launch per step
+            cudaGetLastError();
+            h->tail_cl = 0;
+        }
+    }
     if (k == h->namg - 1) {
         KScope ks(h, "coarsest_dense_solve", k, (double)h->nco * h->nco * 8 + 2.0 * h->nco * sizeof(TV),
                   (double)h->nco * h->nco);

@@ -1,0 +1,95 @@
+// SELL-C-sigma row products shared by the solve-phase kernels (solve.cu)
+// and the fused coarse-level kernel (tail.cu): one routine, so a row's sum
+// has the same operation order, and the same bits, wherever it is formed.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mgr {
+
+template <int G, class T>
+__device__ __forceinline__ T group_sum(T s) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, G);
+    return s;
+}
+
+// ---------------------------------------------------------- SELL-C-sigma
+// One warp per slice of C = 32/G rows, G lanes per row.  Each step of the
+// slice is 32 contiguous entries (coalesced value and column loads); a lane
+// runs one FMA chain over its entries t*G + g and the row's G partial sums
+// meet in a fixed shuffle tree.  The slice width L is warp-uniform, so each
+// round issues U independent value/column loads, then U gathers, then U
+// FMAs without divergence: the longest slice costs ceil(L/U) dependent
+// load-gather rounds.  Padding entries carry zero values and a column of
+// the same row.
+//
+// Per precision (fitted to GB300 timings of every AMG level's products):
+// FP64 issues U = 4 loads per round and loads the epilogue's row values
+// after the products, so registers go to more resident warps; FP32 issues
+// U = 8 and (PF) starts the epilogue's row loads and the next slice's
+// offsets before the products, so they overlap them.  Both stay within 48
+// registers (5 blocks, 40 warps per SM).
+template <class T>
+struct SellCfg { static constexpr int U = 4, PF = 0; };
+template <>
+struct SellCfg<float> { static constexpr int U = 8, PF = 1; };
+constexpr int SELL_BLOCKS = 5;
+
+template <class T>
+__host__ __device__ inline const T *sell_vals(const DCSR &M);
+template <>
+inline const double *sell_vals<double>(const DCSR &M) { return M.sv; }
+template <>
+inline const float *sell_vals<float>(const DCSR &M) { return M.sv32; }
+
+
+// The calling lane's share of a slice row: lane r*G + g runs the FMA chain
+// over the row's entries t*G + g, t ascending, U loads in flight per round.
+// The chain does not depend on G (the layout places the entries).
+template <class T, class XF>
+__device__ __forceinline__ T sell_chain(int L, long long base, const int *__restrict__ sci,
+                                        const T *__restrict__ sv, const XF &xf) {
+    constexpr int U = SellCfg<T>::U;
+    T acc = (T)0;
+    for (int t = 0; t < L; t += U) {
+        T vv[U], xx[U];
+        int cc[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (t + u < L) {
+                const long long o = base + (long long)(t + u) * 32;
+                vv[u] = __ldg(sv + o);
+                cc[u] = __ldg(sci + o);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (t + u < L) xx[u] = xf(cc[u]);
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (t + u < L) acc = fma(vv[u], xx[u], acc);
+    }
+    return acc;
+}
+
+// The G partial sums of a row meet in a fixed shuffle tree (lane distances
+// G/2, G/4, .., 1); every lane of the group ends with the row's sum.  The
+// run-time-G form performs the same additions in the same order.
+template <int G, class T, class XF>
+__device__ __forceinline__ T sell_rows(int L, long long base, const int *__restrict__ sci,
+                                       const T *__restrict__ sv, const XF &xf) {
+    T acc = sell_chain<T>(L, base, sci, sv, xf);
+    if (G > 1) acc = group_sum<G, T>(acc);
+    return acc;
+}
+
+template <class T>
+__device__ __forceinline__ T group_sum_rt(T s, int G) {
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, G);
+    return s;
+}
+
+}  // namespace mgr

@@ -9,8 +9,10 @@
 // smoothing, restriction, interpolation) is one pass over its matrix.
 // Every reduction uses a fixed order, so repeated runs give identical bits.
 #include <cuda_runtime.h>
+#include <stdlib.h>
 
 #include "common.cuh"
+#include "sell.cuh"
 
 namespace mgr {
 
@@ -18,11 +20,12 @@ namespace mgr {
 
 static const int NUM_SMS = 152;
 
-template <int G, class T>
-__device__ __forceinline__ T group_sum(T s) {
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, G);
-    return s;
+bool pdl_on() {
+    static const bool on = [] {
+        const char *e = getenv("MGR_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
 }
 
 // ----------------------------------------------------------- chunk engine
@@ -83,6 +86,8 @@ template <int R, class T, class XF, class EPI>
 __global__ void __launch_bounds__(CWARPS * 32) k_csr_chunk(int n, const int *__restrict__ rp,
                                                            const int *__restrict__ ci,
                                                            const T *__restrict__ v, XF xf, EPI epi) {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ T sv[CWARPS][CCAP];
     __shared__ int sc[CWARPS][CCAP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -116,43 +121,25 @@ static void csr_chunk(int n, long long nnz, const int *rp, const int *ci, const 
     if (blocks < 1) blocks = 1;
     unsigned g = (unsigned)blocks;
     switch (R) {
-        case 1: k_csr_chunk<1, T, XF, EPI><<<g, CWARPS * 32, 0, s>>>(n, rp, ci, v, xf, epi); break;
-        case 2: k_csr_chunk<2, T, XF, EPI><<<g, CWARPS * 32, 0, s>>>(n, rp, ci, v, xf, epi); break;
-        case 4: k_csr_chunk<4, T, XF, EPI><<<g, CWARPS * 32, 0, s>>>(n, rp, ci, v, xf, epi); break;
-        case 8: k_csr_chunk<8, T, XF, EPI><<<g, CWARPS * 32, 0, s>>>(n, rp, ci, v, xf, epi); break;
-        case 16: k_csr_chunk<16, T, XF, EPI><<<g, CWARPS * 32, 0, s>>>(n, rp, ci, v, xf, epi); break;
-        default: k_csr_chunk<32, T, XF, EPI><<<g, CWARPS * 32, 0, s>>>(n, rp, ci, v, xf, epi); break;
+        case 1: launch_k(k_csr_chunk<1, T, XF, EPI>, dim3(g), dim3(CWARPS * 32), s, n, rp, ci, v, xf, epi); break;
+        case 2: launch_k(k_csr_chunk<2, T, XF, EPI>, dim3(g), dim3(CWARPS * 32), s, n, rp, ci, v, xf, epi); break;
+        case 4: launch_k(k_csr_chunk<4, T, XF, EPI>, dim3(g), dim3(CWARPS * 32), s, n, rp, ci, v, xf, epi); break;
+        case 8: launch_k(k_csr_chunk<8, T, XF, EPI>, dim3(g), dim3(CWARPS * 32), s, n, rp, ci, v, xf, epi); break;
+        case 16: launch_k(k_csr_chunk<16, T, XF, EPI>, dim3(g), dim3(CWARPS * 32), s, n, rp, ci, v, xf, epi); break;
+        default: launch_k(k_csr_chunk<32, T, XF, EPI>, dim3(g), dim3(CWARPS * 32), s, n, rp, ci, v, xf, epi); break;
     }
 }
 
 // ---------------------------------------------------------- SELL-C-sigma
-// One warp per slice of C = 32/G rows, G lanes per row.  Each step of the
-// slice is 32 contiguous entries (coalesced value and column loads); a lane
-// runs one FMA chain over its entries t*G + g and the row's G partial sums
-// meet in a fixed shuffle tree.  The slice width L is warp-uniform, so each
-// round issues U independent value/column loads, then U gathers, then U
-// FMAs without divergence: the longest slice costs ceil(L/U) dependent
-// load-gather rounds.  Padding entries carry zero values and a column of
-// the same row.
-//
-// Per precision (fitted to GB300 timings of every AMG level's products):
-// FP64 issues U = 4 loads per round and loads the epilogue's row values
-// after the products, so registers go to more resident warps; FP32 issues
-// U = 8 and (PF) starts the epilogue's row loads and the next slice's
-// offsets before the products, so they overlap them.  Both stay within 48
-// registers (5 blocks, 40 warps per SM).
-template <class T>
-struct SellCfg { static constexpr int U = 4, PF = 0; };
-template <>
-struct SellCfg<float> { static constexpr int U = 8, PF = 1; };
-constexpr int SELL_BLOCKS = 5;
-
+// k_sell: one warp per slice (layout and row sums in sell.cuh), grid-stride
+// over slices; FP32 (PF) starts a slice's epilogue loads and the next
+// slice's offsets before the slice's products.
 template <int G, class T, class XF, class EPI>
 __global__ void __launch_bounds__(256, SELL_BLOCKS)
     k_sell(int nsl, const long long *__restrict__ sptr, const int *__restrict__ slen,
            const int *__restrict__ perm, const int *__restrict__ sci, const T *__restrict__ sv, XF xf,
            EPI epi) {
-    constexpr int U = SellCfg<T>::U, PF = SellCfg<T>::PF;
+    constexpr int PF = SellCfg<T>::PF;
     constexpr int C = 32 / G;
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -161,6 +148,8 @@ __global__ void __launch_bounds__(256, SELL_BLOCKS)
     int L = __ldg(slen + sl);
     long long base = __ldg(sptr + sl) + lane;
     int row = __ldg(perm + (long long)sl * C + lane / G);
+    pdl_wait();  // slice offsets and rows above are read-only
+    pdl_launch_dependents();
     for (;;) {
         const bool own = (lane % G == 0) && row >= 0;
         typename EPI::Pre pre{};
@@ -173,26 +162,7 @@ __global__ void __launch_bounds__(256, SELL_BLOCKS)
             base2 = __ldg(sptr + nx) + lane;
             row2 = __ldg(perm + (long long)nx * C + lane / G);
         }
-        T acc = (T)0;
-        for (int t = 0; t < L; t += U) {
-            T vv[U], xx[U];
-            int cc[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                if (t + u < L) {
-                    const long long o = base + (long long)(t + u) * 32;
-                    vv[u] = __ldg(sv + o);
-                    cc[u] = __ldg(sci + o);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; u++)
-                if (t + u < L) xx[u] = xf(cc[u]);
-#pragma unroll
-            for (int u = 0; u < U; u++)
-                if (t + u < L) acc = fma(vv[u], xx[u], acc);
-        }
-        if (G > 1) acc = group_sum<G, T>(acc);
+        const T acc = sell_rows<G, T>(L, base, sci, sv, xf);
         if (own) epi.put(row, acc, PF ? pre : epi.pre(row));
         if (nx >= nsl) break;
         sl = nx;
@@ -206,20 +176,13 @@ __global__ void __launch_bounds__(256, SELL_BLOCKS)
     }
 }
 
-template <class T>
-__host__ __device__ inline const T *sell_vals(const DCSR &M);
-template <>
-inline const double *sell_vals<double>(const DCSR &M) { return M.sv; }
-template <>
-inline const float *sell_vals<float>(const DCSR &M) { return M.sv32; }
-
 template <int G, class T, class XF, class EPI>
 static void sell_launch(const DCSR &M, const T *vals, XF xf, EPI epi, cudaStream_t s) {
     long long blocks = ((long long)M.nsl * 32 + 255) / 256;
     const long long cap = (long long)NUM_SMS * SELL_BLOCKS * 2;
     if (blocks > cap) blocks = cap;
-    k_sell<G, T, XF, EPI><<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(M.nsl, M.sptr, M.slen, M.perm,
-                                                                            M.sci, vals, xf, epi);
+    launch_k(k_sell<G, T, XF, EPI>, dim3((unsigned)(blocks < 1 ? 1 : blocks)), dim3(256), s, M.nsl, M.sptr,
+             M.slen, M.perm, M.sci, vals, xf, epi);
 }
 
 // Row products over a matrix: SELL-C-sigma when built, else the chunk engine.
@@ -352,7 +315,7 @@ struct EPost {  // xout = x + d (r - A x)
     struct Pre { T r, d, x; };
     __device__ __forceinline__ Pre pre(int row) const { return {(T)r[row], d[row], x[row]}; }
     __device__ __forceinline__ void put(int row, T s, const Pre &p) const {
-        xout[row] = (TV)(p.x + p.d * (p.r - s));
+        xout[row] = (TV)fma(p.d, p.r - s, p.x);
     }
     EPI_CALL
 };
@@ -402,6 +365,8 @@ template <int B>
 __global__ void k_bsrB(int nb, const int *__restrict__ rp, const int *__restrict__ ci,
                        const double *__restrict__ val, const double *__restrict__ x,
                        const double *bvec, double *y, double alpha, double beta, int mode) {
+    pdl_wait();
+    pdl_launch_dependents();
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)nb * B) return;
     int I = (int)(t / B), r = (int)(t % B);
@@ -430,9 +395,9 @@ static void bsr_dispatch(int nb, int b, long long nnzb, const int *rp, const int
     long long n = (long long)nb * b;
     unsigned grid = GRIDN(n, 256);
     switch (b) {
-        case 2: k_bsrB<2><<<grid, 256, 0, s>>>(nb, rp, ci, val, x, bvec, y, alpha, beta, mode); break;
-        case 3: k_bsrB<3><<<grid, 256, 0, s>>>(nb, rp, ci, val, x, bvec, y, alpha, beta, mode); break;
-        default: k_bsrB<4><<<grid, 256, 0, s>>>(nb, rp, ci, val, x, bvec, y, alpha, beta, mode); break;
+        case 2: launch_k(k_bsrB<2>, dim3(grid), dim3(256), s, nb, rp, ci, val, x, bvec, y, alpha, beta, mode); break;
+        case 3: launch_k(k_bsrB<3>, dim3(grid), dim3(256), s, nb, rp, ci, val, x, bvec, y, alpha, beta, mode); break;
+        default: launch_k(k_bsrB<4>, dim3(grid), dim3(256), s, nb, rp, ci, val, x, bvec, y, alpha, beta, mode); break;
     }
 }
 
@@ -453,6 +418,8 @@ void launch_bsr_residual(int nb, int b, const int *rp, const int *ci, const doub
 template <class T, class TV>
 __global__ void k_frelax_first(int nF, const int *fidx, const int *gstart, const int *gsize,
                                const T *dinv, T omega, const TV *v, T *zF) {
+    pdl_wait();
+    pdl_launch_dependents();
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nF) return;
     int g = gstart[f], k = gsize[f];
@@ -465,7 +432,7 @@ template <class T, class TV>
 void launch_frelax_first(int nF, const int *fidx, const int *gstart, const int *gsize,
                          const T *dinv, T omega, const TV *v, T *zF, cudaStream_t s) {
     if (nF == 0) return;
-    k_frelax_first<T, TV><<<GRIDN(nF, 256), 256, 0, s>>>(nF, fidx, gstart, gsize, dinv, omega, v, zF);
+    launch_k(k_frelax_first<T, TV>, dim3(GRIDN(nF, 256)), dim3(256), s, nF, fidx, gstart, gsize, dinv, omega, v, zF);
 }
 
 // r_F = v_F - A_FF z_F
@@ -479,6 +446,8 @@ void launch_frelax_residual(const DCSR &AFF, const T *vals, const int *fidx, con
 template <class T>
 __global__ void k_frelax_update(int nF, const int *gstart, const int *gsize, const T *dinv, T omega,
                                 const T *rF, T *zF, int transpose) {
+    pdl_wait();
+    pdl_launch_dependents();
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nF) return;
     int g = gstart[f], k = gsize[f], r = f - g;
@@ -494,7 +463,7 @@ template <class T>
 void launch_frelax_update(int nF, const int *gstart, const int *gsize, const T *dinv, T omega,
                           const T *rF, T *zF, int transpose, cudaStream_t s) {
     if (nF == 0) return;
-    k_frelax_update<T><<<GRIDN(nF, 256), 256, 0, s>>>(nF, gstart, gsize, dinv, omega, rF, zF, transpose);
+    launch_k(k_frelax_update<T>, dim3(GRIDN(nF, 256)), dim3(256), s, nF, gstart, gsize, dinv, omega, rF, zF, transpose);
 }
 
 // injection restriction of the residual: v_C = v[C] - A_CF z_F
@@ -506,6 +475,8 @@ void launch_mgr_restrict(const DCSR &ACF, const T *vals, const int *cidx, const 
 
 template <class T, class TV>
 __global__ void k_scatter_c(int nC, const int *cidx, const T *eC, TV *z) {
+    pdl_wait();
+    pdl_launch_dependents();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nC) z[cidx[i]] = (TV)eC[i];
 }
@@ -515,12 +486,14 @@ template <class T, class TV>
 void launch_mgr_interp(const DCSR &W, const T *wvals, int nC, const int *fidx, const int *cidx,
                        const T *zF, const T *eC, TV *z, cudaStream_t s) {
     spmv_rows<T>(W, wvals, XPlain<T, T>{eC}, EInterp<T, TV>{fidx, zF, z}, s);
-    if (nC > 0) k_scatter_c<T, TV><<<GRIDN(nC, 256), 256, 0, s>>>(nC, cidx, eC, z);
+    if (nC > 0) launch_k(k_scatter_c<T, TV>, dim3(GRIDN(nC, 256)), dim3(256), s, nC, cidx, eC, z);
 }
 
 // transposed-cycle pieces
 template <class T, class TV>
 __global__ void k_gather(const int *idx, int n, const TV *v, T *out) {
+    pdl_wait();
+    pdl_launch_dependents();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (T)v[idx[i]];
 }
@@ -528,7 +501,7 @@ __global__ void k_gather(const int *idx, int n, const TV *v, T *out) {
 template <class T, class TV>
 void launch_gather(const int *idx, int n, const TV *v, T *out, cudaStream_t s) {
     if (n == 0) return;
-    k_gather<T, TV><<<GRIDN(n, 256), 256, 0, s>>>(idx, n, v, out);
+    launch_k(k_gather<T, TV>, dim3(GRIDN(n, 256)), dim3(256), s, idx, n, v, out);
 }
 
 // y[i] = bsrc[idx_b[i]] + sign * (M x)_i
@@ -541,6 +514,8 @@ void launch_csr_axpy_gather(const DCSR &M, const T *vals, const T *x, const int 
 template <class T, class TV>
 __global__ void k_scatter2(int nF, int nC, const int *fidx, const int *cidx, const T *zF,
                            const T *eC, TV *z) {
+    pdl_wait();
+    pdl_launch_dependents();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nF) z[fidx[i]] = (TV)zF[i];
     else if (i < nF + nC) z[cidx[i - nF]] = (TV)eC[i - nF];
@@ -549,7 +524,7 @@ __global__ void k_scatter2(int nF, int nC, const int *fidx, const int *cidx, con
 template <class T, class TV>
 void launch_scatter2(int nF, int nC, const int *fidx, const int *cidx, const T *zF, const T *eC,
                      TV *z, cudaStream_t s) {
-    k_scatter2<T, TV><<<GRIDN(nF + nC, 256), 256, 0, s>>>(nF, nC, fidx, cidx, zF, eC, z);
+    launch_k(k_scatter2<T, TV>, dim3(GRIDN(nF + nC, 256)), dim3(256), s, nF, nC, fidx, cidx, zF, eC, z);
 }
 
 // ---------------------------------------------------------------- AMG level
@@ -585,13 +560,15 @@ void launch_mgr_restrict_scaled(const DCSR &ACF, const T *vals, const int *cidx,
 
 template <class T, class TV>
 __global__ void k_scale(int n, const T *d, const TV *r, T *x) {
+    pdl_wait();
+    pdl_launch_dependents();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = d[i] * (T)r[i];
 }
 
 template <class T, class TV>
 void launch_scale(int n, const T *d, const TV *r, T *x, cudaStream_t s) {
-    if (n > 0) k_scale<T, TV><<<GRIDN(n, 256), 256, 0, s>>>(n, d, r, x);
+    if (n > 0) launch_k(k_scale<T, TV>, dim3(GRIDN(n, 256)), dim3(256), s, n, d, r, x);
 }
 
 // post-smoothing: xout_i = x_i + dinv_i (r_i - sum_j a_ij x_j)
@@ -604,11 +581,13 @@ void launch_amg_post_smooth(const DCSR &A, const T *vals, const T *dinv, const T
 // coarsest grid: x = A^{-1} r with the explicit FP64 inverse; one warp per row
 template <class TV>
 __global__ void k_dense_matvec(int n, const double *inv, const TV *r, TV *x) {
+    pdl_wait();
+    pdl_launch_dependents();
     int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (row >= n) return;
     double s = 0.0;
-    for (int c = lane; c < n; c += 32) s += inv[(long long)row * n + c] * (double)r[c];
+    for (int c = lane; c < n; c += 32) s = fma(inv[(long long)row * n + c], (double)r[c], s);
     s = group_sum<32, double>(s);
     if (lane == 0) x[row] = (TV)s;
 }
@@ -616,11 +595,13 @@ __global__ void k_dense_matvec(int n, const double *inv, const TV *r, TV *x) {
 template <class TV>
 void launch_dense_matvec(int n, const double *inv, const TV *r, TV *x, cudaStream_t s) {
     if (n == 0) return;
-    k_dense_matvec<TV><<<GRIDN((long long)n * 32, 256), 256, 0, s>>>(n, inv, r, x);
+    launch_k(k_dense_matvec<TV>, dim3(GRIDN((long long)n * 32, 256)), dim3(256), s, n, inv, r, x);
 }
 
 template <class TV>
 __global__ void k_copy_cast(const TV *in, double *out, int n) {
+    pdl_wait();
+    pdl_launch_dependents();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (double)in[i];
 }
@@ -628,7 +609,7 @@ __global__ void k_copy_cast(const TV *in, double *out, int n) {
 template <class TV>
 void launch_copy_cast(const TV *in, double *out, int n, cudaStream_t s) {
     if (n == 0) return;
-    k_copy_cast<TV><<<GRIDN(n, 256), 256, 0, s>>>(in, out, n);
+    launch_k(k_copy_cast<TV>, dim3(GRIDN(n, 256)), dim3(256), s, in, out, n);
 }
 
 // ------------------------------------------------------------- Krylov (FP64)
@@ -731,6 +712,8 @@ __global__ void __launch_bounds__(RED_THREADS, 2) k_dots(const double *__restric
                                                          const double *__restrict__ w, int n,
                                                          double *partial, double *h, unsigned *ticket,
                                                          const int *flag) {
+    pdl_wait();
+    pdl_launch_dependents();
     if (flag && *flag == 0) return;
     constexpr int KB = K < 8 ? K : 8;
     double acc[K];
@@ -782,6 +765,8 @@ __global__ void __launch_bounds__(RED_THREADS, 2) k_update_norm(const double *__
                                                                 const double *__restrict__ h, double *w,
                                                                 int n, double *partial, double *nrm2,
                                                                 unsigned *ticket, int *flag, int mode) {
+    pdl_wait();
+    pdl_launch_dependents();
     if (mode == 2 && *flag == 0) return;
     constexpr int KB = K < 16 ? K : 16;
     __shared__ double hs[K];
@@ -838,7 +823,7 @@ __global__ void __launch_bounds__(RED_THREADS, 2) k_update_norm(const double *__
 void launch_dots(const double *V, long long ldv, int k, const double *w, int n, double *partial,
                  double *h, unsigned *ticket, const int *flag, int nblk, cudaStream_t s) {
     switch (k) {
-#define X(K) case K: k_dots<K><<<nblk, RED_THREADS, 0, s>>>(V, ldv, w, n, partial, h, ticket, flag); break;
+#define X(K) case K: launch_k(k_dots<K>, dim3(nblk), dim3(RED_THREADS), s, V, ldv, w, n, partial, h, ticket, flag); break;
         K_CASES(X)
 #undef X
         default: break;
@@ -849,7 +834,7 @@ void launch_update_norm(const double *V, long long ldv, int k, const double *h, 
                         double *partial, double *nrm2, unsigned *ticket, int *flag, int mode,
                         int nblk, cudaStream_t s) {
     switch (k) {
-#define X(K) case K: k_update_norm<K><<<nblk, RED_THREADS, 0, s>>>(V, ldv, h, w, n, partial, nrm2, ticket, flag, mode); break;
+#define X(K) case K: launch_k(k_update_norm<K>, dim3(nblk), dim3(RED_THREADS), s, V, ldv, h, w, n, partial, nrm2, ticket, flag, mode); break;
         K_CASES(X)
 #undef X
         default: break;
@@ -860,6 +845,8 @@ void launch_update_norm(const double *V, long long ldv, int k, const double *h, 
 __global__ void __launch_bounds__(RED_THREADS) k_dot2(const double *x, const double *y, int n,
                                                       double *partial, double *out, unsigned *ticket,
                                                       int sqrt_out) {
+    pdl_wait();
+    pdl_launch_dependents();
     double acc[1] = {0.0};
     const long long stride = (long long)gridDim.x * RED_THREADS;
     for (long long e = (long long)blockIdx.x * RED_THREADS + threadIdx.x; e < n; e += stride)
@@ -877,11 +864,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot2(const double *x, const dou
 
 void launch_dot(const double *x, const double *y, int n, double *partial, double *out,
                 unsigned *ticket, int sqrt_out, int nblk, cudaStream_t s) {
-    k_dot2<<<nblk, RED_THREADS, 0, s>>>(x, y, n, partial, out, ticket, sqrt_out);
+    launch_k(k_dot2, dim3(nblk), dim3(RED_THREADS), s, x, y, n, partial, out, ticket, sqrt_out);
 }
 
 // y = x * s  or  y = x / s  (s a device scalar)
 __global__ void k_vec_scale(const double *x, double *y, const double *sc, int invert, int n) {
+    pdl_wait();
+    pdl_launch_dependents();
     const double f = invert ? 1.0 / *sc : *sc;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x)
@@ -891,12 +880,14 @@ __global__ void k_vec_scale(const double *x, double *y, const double *sc, int in
 void launch_vec_scale(const double *x, double *y, const double *scale_num, const double *,
                       int invert, int n, cudaStream_t s) {
     unsigned g = GRIDN(n, 256);
-    k_vec_scale<<<g > NUM_SMS * 8 ? NUM_SMS * 8 : g, 256, 0, s>>>(x, y, scale_num, invert, n);
+    launch_k(k_vec_scale, dim3(g > NUM_SMS * 8 ? NUM_SMS * 8 : g), dim3(256), s, x, y, scale_num, invert, n);
 }
 
 // x += sum_i y_i Z_i
 __global__ void k_multi_axpy(const double *__restrict__ Z, long long ldz, int k,
                              const double *__restrict__ y, double *x, int n) {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ double ys[32];
     if (threadIdx.x < k) ys[threadIdx.x] = y[threadIdx.x];
     __syncthreads();
@@ -911,12 +902,14 @@ __global__ void k_multi_axpy(const double *__restrict__ Z, long long ldz, int k,
 void launch_multi_axpy(const double *Z, long long ldz, int k, const double *y, double *x, int n,
                        cudaStream_t s) {
     unsigned g = GRIDN(n, 256);
-    k_multi_axpy<<<g > NUM_SMS * 8 ? NUM_SMS * 8 : g, 256, 0, s>>>(Z, ldz, k, y, x, n);
+    launch_k(k_multi_axpy, dim3(g > NUM_SMS * 8 ? NUM_SMS * 8 : g), dim3(256), s, Z, ldz, k, y, x, n);
 }
 
 // dA[p, r, c] = -lam[I*b + r] * x[J*b + c]
 __global__ void k_grad_values(int nb, int b, const int *rp, const int *ci, const double *lam,
                               const double *x, double *dA) {
+    pdl_wait();
+    pdl_launch_dependents();
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)nb * b) return;
     int I = (int)(t / b), r = (int)(t % b);
@@ -929,7 +922,7 @@ __global__ void k_grad_values(int nb, int b, const int *rp, const int *ci, const
 
 void launch_grad_values(int nb, int b, const int *rp, const int *ci, const double *lam,
                         const double *x, double *dA, cudaStream_t s) {
-    k_grad_values<<<GRIDN((long long)nb * b, 256), 256, 0, s>>>(nb, b, rp, ci, lam, x, dA);
+    launch_k(k_grad_values, dim3(GRIDN((long long)nb * b, 256)), dim3(256), s, nb, b, rp, ci, lam, x, dA);
 }
 
 // ------------------------------------------------------------- misc
@@ -937,6 +930,8 @@ void launch_grad_values(int nb, int b, const int *rp, const int *ci, const doubl
 // non-finite value, bit 16 a missing diagonal block
 __global__ void k_validate_bsr(int nb, int b, const int *rp, const int *ci, const double *val,
                                int *err) {
+    pdl_wait();
+    pdl_launch_dependents();
     int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nb) return;
     int p0 = rp[I], p1 = rp[I + 1];
@@ -955,10 +950,12 @@ __global__ void k_validate_bsr(int nb, int b, const int *rp, const int *ci, cons
 
 void launch_validate_bsr(int nb, int b, const int *rp, const int *ci, const double *val, int *err,
                          cudaStream_t s) {
-    k_validate_bsr<<<GRIDN(nb, 256), 256, 0, s>>>(nb, b, rp, ci, val, err);
+    launch_k(k_validate_bsr, dim3(GRIDN(nb, 256)), dim3(256), s, nb, b, rp, ci, val, err);
 }
 
 __global__ void k_transpose_dense(int n, const double *in, double *out) {
+    pdl_wait();
+    pdl_launch_dependents();
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= (long long)n * n) return;
     int r = (int)(e / n), c = (int)(e % n);
@@ -967,7 +964,7 @@ __global__ void k_transpose_dense(int n, const double *in, double *out) {
 
 void launch_transpose_dense(int n, const double *in, double *out, cudaStream_t s) {
     if (n == 0) return;
-    k_transpose_dense<<<GRIDN((long long)n * n, 256), 256, 0, s>>>(n, in, out);
+    launch_k(k_transpose_dense, dim3(GRIDN((long long)n * n, 256)), dim3(256), s, n, in, out);
 }
 
 // H is (m+1) x m row-major.  h1[0..j] first-pass projections and h1[j+1] =
@@ -979,6 +976,8 @@ __global__ void k_arnoldi_finish(int j, int m, const double *h1, const double *h
                                  const double *nrmA, const double *nrmB, const int *flag,
                                  double *H, double *cs, double *sn, double *g, double *hn_out,
                                  double *stat, const double *tol) {
+    pdl_wait();
+    pdl_launch_dependents();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double tol_abs = *tol;
     const int re = *flag;
@@ -1010,19 +1009,23 @@ __global__ void k_arnoldi_finish(int j, int m, const double *h1, const double *h
 void launch_arnoldi_finish(int j, int m, const double *h1, const double *h2, const double *nrmA,
                            const double *nrmB, const int *flag, double *H, double *cs, double *sn,
                            double *g, double *hn, double *stat, const double *tol, cudaStream_t s) {
-    k_arnoldi_finish<<<1, 32, 0, s>>>(j, m, h1, h2, nrmA, nrmB, flag, H, cs, sn, g, hn, stat, tol);
+    launch_k(k_arnoldi_finish, dim3(1), dim3(32), s, j, m, h1, h2, nrmA, nrmB, flag, H, cs, sn, g, hn, stat, tol);
 }
 
 __global__ void k_init_g(double *g, int m, const double *beta) {
+    pdl_wait();
+    pdl_launch_dependents();
     int i = threadIdx.x;
     if (i <= m) g[i] = i == 0 ? *beta : 0.0;
 }
 
 void launch_init_g(double *g, int m, const double *beta, cudaStream_t s) {
-    k_init_g<<<1, 64, 0, s>>>(g, m, beta);
+    launch_k(k_init_g, dim3(1), dim3(64), s, g, m, beta);
 }
 
 __global__ void k_solve_upper(int k, int m, const double *H, const double *g, double *y) {
+    pdl_wait();
+    pdl_launch_dependents();
     if (threadIdx.x != 0) return;
     for (int i = k - 1; i >= 0; i--) {
         double s = g[i];
@@ -1032,25 +1035,29 @@ __global__ void k_solve_upper(int k, int m, const double *H, const double *g, do
 }
 
 void launch_solve_upper(int k, int m, const double *H, const double *g, double *y, cudaStream_t s) {
-    k_solve_upper<<<1, 32, 0, s>>>(k, m, H, g, y);
+    launch_k(k_solve_upper, dim3(1), dim3(32), s, k, m, H, g, y);
 }
 
 __global__ void k_iota(int *a, int n) {
+    pdl_wait();
+    pdl_launch_dependents();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = i;
 }
 
 void launch_iota(int *a, int n, cudaStream_t s) {
-    if (n > 0) k_iota<<<GRIDN(n, 256), 256, 0, s>>>(a, n);
+    if (n > 0) launch_k(k_iota, dim3(GRIDN(n, 256)), dim3(256), s, a, n);
 }
 
 __global__ void k_gather_int(const int *idx, int n, const int *v, int *out) {
+    pdl_wait();
+    pdl_launch_dependents();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = v[idx[i]];
 }
 
 void launch_gather_int(const int *idx, int n, const int *v, int *out, cudaStream_t s) {
-    if (n > 0) k_gather_int<<<GRIDN(n, 256), 256, 0, s>>>(idx, n, v, out);
+    if (n > 0) launch_k(k_gather_int, dim3(GRIDN(n, 256)), dim3(256), s, idx, n, v, out);
 }
 
 
@@ -1139,6 +1146,8 @@ template <int R, class T, class TV, int OP>
 __global__ void __launch_bounds__(CWARPS * 32) k_bchunk(const BJob *__restrict__ jobs,
                                                         const long long *__restrict__ prefix,
                                                         int njobs, int js) {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ T sv[CWARPS][CCAP];
     __shared__ int sc[CWARPS][CCAP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1178,12 +1187,12 @@ static void bchunk_dispatch(const BJob *jobs, const long long *prefix, int njobs
     if (blocks > NUM_SMS * 8) blocks = NUM_SMS * 8;
     unsigned g = (unsigned)(blocks < 1 ? 1 : blocks);
     switch (R) {
-        case 1: k_bchunk<1, T, TV, OP><<<g, CWARPS * 32, 0, s>>>(jobs, prefix, njobs, js); break;
-        case 2: k_bchunk<2, T, TV, OP><<<g, CWARPS * 32, 0, s>>>(jobs, prefix, njobs, js); break;
-        case 4: k_bchunk<4, T, TV, OP><<<g, CWARPS * 32, 0, s>>>(jobs, prefix, njobs, js); break;
-        case 8: k_bchunk<8, T, TV, OP><<<g, CWARPS * 32, 0, s>>>(jobs, prefix, njobs, js); break;
-        case 16: k_bchunk<16, T, TV, OP><<<g, CWARPS * 32, 0, s>>>(jobs, prefix, njobs, js); break;
-        default: k_bchunk<32, T, TV, OP><<<g, CWARPS * 32, 0, s>>>(jobs, prefix, njobs, js); break;
+        case 1: launch_k(k_bchunk<1, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
+        case 2: launch_k(k_bchunk<2, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
+        case 4: launch_k(k_bchunk<4, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
+        case 8: launch_k(k_bchunk<8, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
+        case 16: launch_k(k_bchunk<16, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
+        default: launch_k(k_bchunk<32, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
     }
 }
 
@@ -1225,6 +1234,8 @@ static inline unsigned elem_grid(long long total) {
 // z_F = omega D^{-1} v_F (first F-relaxation sweep), per system
 template <class T, class TV>
 __global__ void k_bfrelax_first(const BJob *jobs, const long long *prefix, int njobs, T omega, int js) {
+    pdl_wait();
+    pdl_launch_dependents();
     const long long total = prefix[njobs];
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
          g += (long long)gridDim.x * blockDim.x) {
@@ -1244,12 +1255,14 @@ __global__ void k_bfrelax_first(const BJob *jobs, const long long *prefix, int n
 template <class T, class TV>
 void launch_bfrelax_first(const BJob *jobs, const long long *prefix, int njobs, long long total,
                           T omega, int js, cudaStream_t s) {
-    if (total > 0) k_bfrelax_first<T, TV><<<elem_grid(total), 256, 0, s>>>(jobs, prefix, njobs, omega, js);
+    if (total > 0) launch_k(k_bfrelax_first<T, TV>, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs, omega, js);
 }
 
 // z[cidx[i]] = e_C[i], per system
 template <class T, class TV>
 __global__ void k_bscatter(const BJob *jobs, const long long *prefix, int njobs, int js) {
+    pdl_wait();
+    pdl_launch_dependents();
     const long long total = prefix[njobs];
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
          g += (long long)gridDim.x * blockDim.x) {
@@ -1264,12 +1277,14 @@ __global__ void k_bscatter(const BJob *jobs, const long long *prefix, int njobs,
 template <class T, class TV>
 void launch_bscatter(const BJob *jobs, const long long *prefix, int njobs, long long total, int js,
                      cudaStream_t s) {
-    if (total > 0) k_bscatter<T, TV><<<elem_grid(total), 256, 0, s>>>(jobs, prefix, njobs, js);
+    if (total > 0) launch_k(k_bscatter<T, TV>, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs, js);
 }
 
 // coarsest dense solves: one warp per row over every system's coarsest grid
 template <class TV>
 __global__ void k_bdense(const BJob *jobs, const long long *prefix, int njobs, int js) {
+    pdl_wait();
+    pdl_launch_dependents();
     const long long total = prefix[njobs];
     const int lane = threadIdx.x & 31;
     for (long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; g < total;
@@ -1281,7 +1296,7 @@ __global__ void k_bdense(const BJob *jobs, const long long *prefix, int njobs, i
         const double *inv = (const double *)J.v;
         const TV *r = (const TV *)J.r;
         double s = 0.0;
-        for (int c = lane; c < n; c += 32) s += inv[(long long)row * n + c] * (double)r[c];
+        for (int c = lane; c < n; c += 32) s = fma(inv[(long long)row * n + c], (double)r[c], s);
         s = group_sum<32, double>(s);
         if (lane == 0) ((TV *)J.o1)[row] = (TV)s;
     }
@@ -1293,12 +1308,14 @@ void launch_bdense(const BJob *jobs, const long long *prefix, int njobs, long lo
     if (total <= 0) return;
     long long g = (total * 32 + 255) / 256;
     if (g > NUM_SMS * 8) g = NUM_SMS * 8;
-    k_bdense<TV><<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(jobs, prefix, njobs, js);
+    launch_k(k_bdense<TV>, dim3((unsigned)(g < 1 ? 1 : g)), dim3(256), s, jobs, prefix, njobs, js);
 }
 
 // outer block-CSR product (b > 1), one thread per scalar row; r != null: residual
 template <int B>
 __global__ void k_bbsr(const BJob *jobs, const long long *prefix, int njobs, int js) {
+    pdl_wait();
+    pdl_launch_dependents();
     const long long total = prefix[njobs];
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
          g += (long long)gridDim.x * blockDim.x) {
@@ -1327,14 +1344,16 @@ void launch_bbsr(int b, const BJob *jobs, const long long *prefix, int njobs, lo
     if (total <= 0) return;
     unsigned g = elem_grid(total);
     switch (b) {
-        case 2: k_bbsr<2><<<g, 256, 0, s>>>(jobs, prefix, njobs, js); break;
-        case 3: k_bbsr<3><<<g, 256, 0, s>>>(jobs, prefix, njobs, js); break;
-        default: k_bbsr<4><<<g, 256, 0, s>>>(jobs, prefix, njobs, js); break;
+        case 2: launch_k(k_bbsr<2>, dim3(g), dim3(256), s, jobs, prefix, njobs, js); break;
+        case 3: launch_k(k_bbsr<3>, dim3(g), dim3(256), s, jobs, prefix, njobs, js); break;
+        default: launch_k(k_bbsr<4>, dim3(g), dim3(256), s, jobs, prefix, njobs, js); break;
     }
 }
 
 // y = x / scale or x * scale, per system (scale a device scalar in J.d)
 __global__ void k_bscale(const BJob *jobs, const long long *prefix, int njobs, int js, int invert) {
+    pdl_wait();
+    pdl_launch_dependents();
     const long long total = prefix[njobs];
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
          g += (long long)gridDim.x * blockDim.x) {
@@ -1350,11 +1369,13 @@ __global__ void k_bscale(const BJob *jobs, const long long *prefix, int njobs, i
 
 void launch_bscale(const BJob *jobs, const long long *prefix, int njobs, long long total, int js,
                    int invert, cudaStream_t s) {
-    if (total > 0) k_bscale<<<elem_grid(total), 256, 0, s>>>(jobs, prefix, njobs, js, invert);
+    if (total > 0) launch_k(k_bscale, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs, js, invert);
 }
 
 // x += sum_{i < k} y_i Z_i per system (k in *J.gz, y in J.r, Z in J.v, x in J.o1)
 __global__ void k_bmulti_axpy(const BJob *jobs, const long long *prefix, int njobs) {
+    pdl_wait();
+    pdl_launch_dependents();
     const long long total = prefix[njobs];
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
          g += (long long)gridDim.x * blockDim.x) {
@@ -1371,7 +1392,7 @@ __global__ void k_bmulti_axpy(const BJob *jobs, const long long *prefix, int njo
 
 void launch_bmulti_axpy(const BJob *jobs, const long long *prefix, int njobs, long long total,
                         cudaStream_t s) {
-    if (total > 0) k_bmulti_axpy<<<elem_grid(total), 256, 0, s>>>(jobs, prefix, njobs);
+    if (total > 0) launch_k(k_bmulti_axpy, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs);
 }
 
 // Segmented Arnoldi projections: the blocks of system j are blocks
@@ -1381,6 +1402,8 @@ template <int K>
 __global__ void __launch_bounds__(RED_THREADS) k_bdots(const BJob *jobs, const long long *bprefix,
                                                        int njobs, int js, int conditional,
                                                        int sqrt_out) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int j = find_job(bprefix, njobs, blockIdx.x);
     const BJob &J = jobs[j];
     if (job_off(J)) return;
@@ -1444,6 +1467,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_bdots(const BJob *jobs, const l
 template <int K>
 __global__ void __launch_bounds__(RED_THREADS) k_bupdate_norm(const BJob *jobs, const long long *bprefix,
                                                               int njobs, int js, int mode) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int j = find_job(bprefix, njobs, blockIdx.x);
     const BJob &J = jobs[j];
     if (job_off(J)) return;
@@ -1509,7 +1534,7 @@ void launch_bdots(int k, const BJob *jobs, const long long *bprefix, int njobs, 
     if (nblocks <= 0) return;
     unsigned g = (unsigned)nblocks;
     switch (k) {
-#define X(K) case K: k_bdots<K><<<g, RED_THREADS, 0, s>>>(jobs, bprefix, njobs, js, conditional, sqrt_out); break;
+#define X(K) case K: launch_k(k_bdots<K>, dim3(g), dim3(RED_THREADS), s, jobs, bprefix, njobs, js, conditional, sqrt_out); break;
         K_CASES(X)
 #undef X
         default: break;
@@ -1521,7 +1546,7 @@ void launch_bupdate_norm(int k, const BJob *jobs, const long long *bprefix, int 
     if (nblocks <= 0) return;
     unsigned g = (unsigned)nblocks;
     switch (k) {
-#define X(K) case K: k_bupdate_norm<K><<<g, RED_THREADS, 0, s>>>(jobs, bprefix, njobs, js, mode); break;
+#define X(K) case K: launch_k(k_bupdate_norm<K>, dim3(g), dim3(RED_THREADS), s, jobs, bprefix, njobs, js, mode); break;
         K_CASES(X)
 #undef X
         default: break;

@@ -43,7 +43,8 @@ class mgr_options(C.Structure):
                 ("relax_weight", C.c_double * MAX_LEVELS), ("amg_theta", C.c_double),
                 ("amg_max_levels", C.c_int32), ("amg_max_coarse", C.c_int32),
                 ("amg_pmax", C.c_int32), ("amg_num_functions", C.c_int32),
-                ("precision", C.c_int32), ("restart", C.c_int32), ("use_graphs", C.c_int32)]
+                ("precision", C.c_int32), ("restart", C.c_int32), ("use_graphs", C.c_int32),
+                ("amg_tail_nnz", C.c_int32)]
 
 
 class mgr_solve_info(C.Structure):
@@ -126,7 +127,8 @@ def _ptr(t):
 
 
 def options(relax=("jacobi",), sweeps=(), weights=(), theta=0.25, max_levels=25, max_coarse=256,
-            pmax=4, num_functions=1, precision="fp64", restart=30, use_graphs=True) -> mgr_options:
+            pmax=4, num_functions=1, precision="fp64", restart=30, use_graphs=True,
+            tail_nnz=None) -> mgr_options:
     o = mgr_options()
     lib().mgr_options_default(C.byref(o))
     for l, r in enumerate(relax):
@@ -143,6 +145,8 @@ def options(relax=("jacobi",), sweeps=(), weights=(), theta=0.25, max_levels=25,
     o.precision = {"fp64": 0, "fp32": 1}[precision] if isinstance(precision, str) else int(precision)
     o.restart = restart
     o.use_graphs = int(bool(use_graphs))
+    if tail_nnz is not None:
+        o.amg_tail_nnz = int(tail_nnz)
     return o
 
 

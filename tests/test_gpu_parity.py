@@ -115,6 +115,64 @@ def test_sell_products_over_row_shapes(n, K, keep):
         assert np.linalg.norm(z32 - zo) <= 1e-4 * np.linalg.norm(zo)
 
 
+# ------------------------------------------------------- fused AMG tail
+TAIL_SYSTEMS = {
+    "mimetic24": lambda: make_mimetic(24, 24, 24),
+    "two_phase32x32x16": lambda: make_two_phase(32, 32, 16),
+}
+
+
+@pytest.mark.parametrize("name", list(TAIL_SYSTEMS))
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fused_tail_is_bitwise_the_per_level_cycle(name, precision):
+    """The coarse AMG levels as one cluster launch give the same bits as one
+    launch per step (same row sums and epilogues), forward and transposed."""
+    s = TAIL_SYSTEMS[name]()
+    fused = solver(s, precision=precision, tail_nnz=400000)
+    plain = solver(s, precision=precision, tail_nnz=0)
+    assert fused.info()["amg_levels"] >= 3
+    v = t(np.random.default_rng(11).standard_normal(s.n))
+    fused.profile(True)
+    for trans in (False, True):
+        a = fused.apply(v, transpose=trans)
+        b = plain.apply(v, transpose=trans)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), (trans, float((a - b).abs().max()))
+    names = [r["name"] for r in fused.profile_table()]
+    fused.profile(False)
+    assert any(n.startswith("amg_tail") for n in names), names
+    assert not any(n.startswith("amg_tail") for n in [r["name"] for r in plain.profile_table()])
+    xf, inf_f = fused.solve(t(s.rhs), rtol=1e-8)
+    xp, inf_p = plain.solve(t(s.rhs), rtol=1e-8)
+    assert inf_f["iterations"] == inf_p["iterations"] and torch.equal(xf, xp)
+
+
+def test_programmatic_launch_changes_no_bits(tmp_path):
+    """Kernels may be scheduled while their predecessor drains (programmatic
+    dependent launch) but wait for its results: the same solves in a fresh
+    process with MGR_PDL=0 (plain stream order) give the same bits."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2101_11649_gb300 import mgr as M\n"
+        "from paper_2101_11649_gb300.synth import make_mimetic\n"
+        "s = make_mimetic(24, 24, 24)\n"
+        "b = torch.as_tensor(s.rhs, device='cuda')\n"
+        "for p in ('fp64', 'fp32'):\n"
+        "    x, info = M.MGRSolver.from_system(s, precision=p).solve(b, rtol=1e-10)\n"
+        f"    np.save(r'{tmp_path}' + '/x_' + p + '.npy', x.cpu().numpy())\n")
+    env = dict(os.environ, MGR_PDL="0")
+    subprocess.run([sys.executable, "-c", code], env=env, check=True, cwd=root, timeout=600)
+    s = make_mimetic(24, 24, 24)
+    for p in ("fp64", "fp32"):
+        x, _ = solver(s, precision=p).solve(t(s.rhs), rtol=1e-10)
+        x0 = np.load(tmp_path / f"x_{p}.npy")
+        assert np.array_equal(x0.view(np.int64), x.cpu().numpy().view(np.int64)), p
+
+
 # ------------------------------------------------------ setup, bit-exact
 def _same_csr(a, b, what):
     assert a is not None and b is not None, what
