@@ -337,27 +337,44 @@ def test_repeat_solves_bitwise_identical():
     assert torch.equal(x1, x2)
 
 
-# ------------------------------------------------ full-size bench workload
+# ------------------------------------------------ full-size configurations
+FULL = ["mimetic_64", "compositional_128x128x32", "poromech_64"]
+
+
 @pytest.mark.slow
-def test_mimetic_64_full_size():
-    """The 64^3 hybrid mimetic system (1,060,864 unknowns) as the benchmark
-    runs it: bit-exact hierarchy on every level, sampled V-cycle entries,
-    iteration parity and the true residual of both precisions."""
-    s = make_mimetic(64, 64, 64)
+@pytest.mark.parametrize("name", FULL)
+def test_full_size(name):
+    """The large configurations at their full sizes (mimetic 64^3: 1,060,864
+    unknowns; compositional 128x128x32 with wells: 2,097,216; poromechanics
+    64^3 with a fracture plane: 826,179): bit-exact hierarchy on every MGR and
+    AMG level, the outer SpMV entry by entry, one V-cycle, iteration parity
+    and the true residual of both precisions."""
+    from paper_2101_11649_gb300.synth import CONFIGS
+    s = CONFIGS[name]()
     g = solver(s)
     o = O.Oracle(s)
-    for l in range(2):
+    assert g.info()["mgr_levels"] == o.mgr_nlevels and g.info()["amg_levels"] == o.amg_nlevels
+    for l in range(s.num_levels + 1):
         _same_csr(g.matrix(0, l, 0), o.mgr_matrix(l, "A"), f"MGR A_{l}")
     for k in range(o.amg_nlevels):
         _same_csr(g.matrix(1, k, 0), o.amg_matrix(k, "A"), f"AMG A_{k}")
-    v = np.random.default_rng(1).standard_normal(s.n)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(s.n)
+    y = g.spmv(t(x)).cpu().numpy()
+    ref = O.spmv_bsr(s.nb, s.b, s.row_ptr, s.col_idx, s.val, x)
+    absref = O.spmv_bsr(s.nb, s.b, s.row_ptr, s.col_idx, np.abs(s.val), np.abs(x)) + 1e-300
+    assert (np.abs(y - ref) / absref).max() <= 1e-13
+    v = rng.standard_normal(s.n)
     zg = g.apply(t(v)).cpu().numpy()
     zo = o.apply(v)
     assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo)
     ro = o.solve(s.rhs, rtol=1e-8)
+    bn = np.linalg.norm(s.rhs)
     for prec in ("fp64", "fp32"):
-        gp = g if prec == "fp64" else solver(s, precision="fp32")
-        x, info = gp.solve(t(s.rhs), rtol=1e-8)
+        gp = g if prec == "fp64" else solver(s, precision=prec)
+        xg, info = gp.solve(t(s.rhs), rtol=1e-8)
         assert info["status"] == 0 and info["rel_residual"] <= 1e-8
+        r = s.rhs - O.spmv_bsr(s.nb, s.b, s.row_ptr, s.col_idx, s.val, xg.cpu().numpy())
+        assert np.linalg.norm(r) <= 1.01e-8 * bn
         if prec == "fp64":
-            assert abs(info["iterations"] - ro["iters"]) <= 1
+            assert abs(info["iterations"] - ro["iters"]) <= 1, (info["iterations"], ro["iters"])
