@@ -84,10 +84,11 @@ enum { MGR_PREC_FP64 = 0, MGR_PREC_FP32 = 1 };
  * FP64).  restart = FGMRES m.  use_graphs != 0 replays the per-iteration
  * kernel sequence from captured CUDA graphs.  amg_tail_nnz: the AMG levels
  * from the first level k >= 1 whose operator has at most this many nonzeros
- * down to the coarsest run as one launch of one thread-block cluster (same
- * arithmetic, bitwise the same result as one launch per step); 0 (the
- * default) runs every step as its own launch, which measured faster on
- * GB300 for the workloads here.  Devices without cluster launches ignore it.
+ * down to the coarsest run as one cooperative launch over the GPU, the steps
+ * separated by grid-wide barriers (same arithmetic, bitwise the same result
+ * as one launch per step); 0 (the default) runs every step as its own
+ * launch.  Devices without cooperative launches ignore it.  A barrier wait
+ * that runs out (it should not) makes mgr_solve return MGR_ERR_TIMEOUT.
  */
 typedef struct {
     int32_t relax_type[MGR_MAX_LEVELS];

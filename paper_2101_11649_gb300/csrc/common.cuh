@@ -91,9 +91,9 @@ struct SellView {
 
 // Fused AMG tail: levels k_t .. k_c - 1 of an AMG V(1,1) cycle (residual,
 // restriction, then after the coarsest solve prolongation and post-smoothing)
-// plus the coarsest dense solve, in one launch of one thread-block cluster.
+// plus the coarsest dense solve, in one cooperative launch over the GPU.
 // The launch walks a list of phases built at setup; consecutive phases meet
-// at a cluster barrier.  Vectors are of the kernel's precision T (void here).
+// at a grid-wide barrier.  Vectors are of the kernel's precision T (void here).
 enum { TAIL_RESID = 0, TAIL_RESTRICT_SCALED = 1, TAIL_RESTRICT = 2, TAIL_DENSE = 3, TAIL_PROLONG = 4,
        TAIL_POST = 5 };
 constexpr int TAIL_MAX_PHASES = 64;
@@ -112,11 +112,13 @@ struct TailPlan {
     int nphase = 0;
     TailPhase ph[TAIL_MAX_PHASES];
 };
+// sync: 3 device words (arrivals, generation, error), zero before the first
+// launch; the error word is nonzero after a barrier wait ran out.
 template <class T>
-int launch_amg_tail(const TailPlan *plan_device, int cluster, cudaStream_t s);
-// Cluster size (16, else 8) the device can run the fused tail with; 0 when
-// it cannot (the cycle then launches the levels one kernel at a time).
-int amg_tail_cluster(void);
+int launch_amg_tail(const TailPlan *plan_device, int grid, unsigned *sync, cudaStream_t s);
+// CTAs of a cooperative tail launch (SMs x resident CTAs per SM); 0 when the
+// device cannot run it (the cycle then launches the levels one at a time).
+int amg_tail_grid(void);
 
 // SELL-C-sigma build from the CSR arrays (values of both precisions when present)
 int build_sell(DCSR &M, cudaStream_t s, Arena &ar);

@@ -106,8 +106,9 @@ struct mgr_ctx {
     AmgLevel amg[32];
     int nco = 0;
     double *coinv = nullptr, *coinvT = nullptr;
-    // fused AMG tail (levels tail_k .. namg-1 in one cluster launch), -1: off
-    int tail_k = -1, tail_cl = 0;
+    // fused AMG tail (levels tail_k .. namg-1 in one cooperative launch), -1: off
+    int tail_k = -1, tail_grid = 0;
+    unsigned *tail_sync = nullptr;  // grid barrier words (arrivals, generation, error)
     TailPlan *tail_plan[2] = {nullptr, nullptr};  // device phase lists [trans]
     int *errw = nullptr;
     Krylov kr;
@@ -622,8 +623,8 @@ static int setup_tail(mgr_handle h, int tail_nnz, cudaStream_t s, Arena &ar) {
         }
     if (kt < 0) return ST_OK;
     if (h->namg - 1 - kt > TAIL_MAX_PHASES / 4 - 1) kt = h->namg - 1 - (TAIL_MAX_PHASES / 4 - 1);
-    const int cl = amg_tail_cluster();
-    if (cl <= 0) return ST_OK;
+    const int grid = amg_tail_grid();
+    if (grid <= 0) return ST_OK;
     h->tail_k = kt;
     for (int trans = 0; trans < 2; trans++) {
         TailPlan plan;
@@ -639,7 +640,11 @@ static int setup_tail(mgr_handle h, int tail_nnz, cudaStream_t s, Arena &ar) {
             cudaStreamSynchronize(s) != cudaSuccess)
             return ST_CUDA;
     }
-    h->tail_cl = cl;
+    h->tail_sync = ar.alloc<unsigned>(4);
+    if (!h->tail_sync) return ST_NOMEM;
+    if (cudaMemsetAsync(h->tail_sync, 0, 4 * sizeof(unsigned), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return ST_CUDA;
+    h->tail_grid = grid;
     return ST_OK;
 }
 
@@ -673,19 +678,19 @@ static void amg_cycle(mgr_handle h, int k, const TV *r, TV *x, int trans) {
     cudaStream_t s = h->s;
     AmgLevel &L = h->amg[k];
     if constexpr (std::is_same<T, TV>::value) {
-        if (k == h->tail_k && h->tail_cl > 0 && (const void *)r == (const void *)Sel<T>::r(L) &&
+        if (k == h->tail_k && h->tail_grid > 0 && (const void *)r == (const void *)Sel<T>::r(L) &&
             (void *)x == (void *)Sel<T>::x(L)) {
             double by, fm;
             tail_cost(h, sizeof(T), by, fm);
             int rc;
             {
                 KScope ks(h, "amg_tail", k, by, fm);
-                rc = launch_amg_tail<T>(h->tail_plan[trans ? 1 : 0], h->tail_cl, s);
+                rc = launch_amg_tail<T>(h->tail_plan[trans ? 1 : 0], h->tail_grid, h->tail_sync, s);
             }
             if (rc == cudaSuccess) return;
-            // a refused cluster launch: clear it, keep to one launch per step
+            // a refused cooperative launch: clear it, keep to one launch per step
             cudaGetLastError();
-            h->tail_cl = 0;
+            h->tail_grid = 0;
         }
     }
     if (k == h->namg - 1) {
@@ -998,6 +1003,17 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
         }
     }
     cudaStreamSynchronize(s);
+    if (h->tail_sync) {
+        unsigned terr = 0;
+        cudaMemcpyAsync(&terr, h->tail_sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        if (terr) {
+            cudaMemsetAsync(h->tail_sync, 0, 4 * sizeof(unsigned), s);
+            cudaStreamSynchronize(s);
+            st = MGR_ERR_TIMEOUT;
+            h->err = "a grid barrier of the fused AMG tail ran out of time";
+        }
+    }
     double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) {
         memset(info, 0, sizeof(*info));

@@ -1,16 +1,17 @@
 // Fused AMG tail: the small coarse levels of the AMG V(1,1) cycle and the
-// coarsest dense solve in one launch of a single thread-block cluster.
+// coarsest dense solve in one cooperative launch over the whole GPU.
 //
 // On the small levels every separate kernel costs a launch, a ramp and a
-// drain for a few microseconds of work.  Here the cluster's warps stride over
-// each phase's SELL slices and the phases meet at hardware cluster barriers
-// (release/acquire, no spin waits).  The phase list lives in device memory
-// (built at setup).  Vectors written inside the launch are
-// read through L2 (ld.global.cg), so no SM sees a stale L1 line of another
-// SM's result; matrices and diagonals are read-only.  Each row sum and each
-// epilogue is the same operation sequence as in the per-level kernels
-// (sell.cuh and the epilogues of solve.cu), so the result is bitwise the
-// one the per-level kernels give.
+// drain for a few microseconds of work.  Here the grid's warps stride over
+// each phase's SELL slices and the phases meet at grid-wide barriers (all
+// CTAs are co-resident by the cooperative launch; a barrier's wait is bounded
+// and a wait that runs out sets an error word and ends the launch).  The
+// phase list lives in device memory (built at setup).  Vectors written inside
+// the launch are read through L2 (ld.global.cg), so no SM sees a stale L1
+// line of another SM's result; matrices and diagonals are read-only.  Each
+// row sum and each epilogue is the same operation sequence as in the
+// per-level kernels (sell.cuh and the epilogues of solve.cu), so the result
+// is bitwise the one the per-level kernels give.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -19,6 +20,7 @@
 namespace mgr {
 
 static constexpr int TAIL_THREADS = 512;
+static constexpr long long TAIL_SPIN = 1LL << 23;  // ~0.5 s of 32 ns sleeps
 
 template <class T>
 struct XCg {
@@ -26,21 +28,44 @@ struct XCg {
     __device__ __forceinline__ T operator()(int j) const { return __ldcg(x + j); }
 };
 
-__device__ __forceinline__ void cluster_barrier() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ int cluster_rank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return (int)r;
-}
-__device__ __forceinline__ int cluster_ctas() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-    return (int)r;
+// Grid-wide barrier.  sync[0]: arrivals, sync[1]: generation, sync[2]: error.
+// Each CTA reads the generation before it arrives (it cannot move before
+// this CTA's arrival); the last arrival resets the count and advances the
+// generation; the others poll it.  false: this CTA must stop (a wait ran out
+// here or elsewhere).
+__device__ __forceinline__ bool grid_barrier(unsigned *sync) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = sync + 1;
+        volatile unsigned *err = sync + 2;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(sync, 1u) + 1u;
+        int ok = 1;
+        if (arrived == gridDim.x) {
+            atomicExch(sync, 0u);
+            __threadfence();
+            atomicAdd(sync + 1, 1u);
+        } else {
+            long long i = 0;
+            while (*gen == g) {
+                if (++i > TAIL_SPIN || *err) {
+                    ok = 0;
+                    atomicOr(sync + 2, 1u);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        ok_s = ok && *err == 0;
+    }
+    __syncthreads();
+    return ok_s != 0;
 }
 
-// one phase: every slice of M, the cluster's warps striding over them.  G is
+// one phase: every slice of M, the grid's warps striding over them.  G is
 // a run-time value here (one loop per phase kind instead of one per lane
 // count); the chain and the tree are those of sell_rows.
 template <class T, class F>
@@ -96,12 +121,10 @@ struct FPost {  // x = xw + d (r - s)
 };
 
 template <class T>
-__global__ void __launch_bounds__(TAIL_THREADS, 1) k_amg_tail(const TailPlan *__restrict__ plan) {
-    pdl_wait();
-    pdl_launch_dependents();
+__global__ void __launch_bounds__(TAIL_THREADS, 1) k_amg_tail(const TailPlan *__restrict__ plan, unsigned *sync) {
     const int lane = threadIdx.x & 31;
-    const int gw = cluster_rank() * (TAIL_THREADS / 32) + (int)(threadIdx.x >> 5);
-    const int W = cluster_ctas() * (TAIL_THREADS / 32);
+    const int gw = (int)blockIdx.x * (TAIL_THREADS / 32) + (int)(threadIdx.x >> 5);
+    const int W = (int)gridDim.x * (TAIL_THREADS / 32);
     const int np = plan->nphase;
     for (int p = 0; p < np; p++) {
         const TailPhase &P = plan->ph[p];
@@ -133,69 +156,45 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_amg_tail(const TailPlan *__
                     break;
             }
         }
-        if (p + 1 < np) cluster_barrier();
+        if (p + 1 < np && !grid_barrier(sync)) return;
     }
 }
 
 template <class T>
-int launch_amg_tail(const TailPlan *plan, int cluster, cudaStream_t s) {
+int launch_amg_tail(const TailPlan *plan, int grid, unsigned *sync, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)cluster);
+    cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(TAIL_THREADS);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
-    cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[1].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = pdl_on() ? 2 : 1;
-    return (int)cudaLaunchKernelEx(&cfg, k_amg_tail<T>, plan);
-}
-
-template <class T>
-static bool tail_fits(int cl) {
-    if (cl > 8 && cudaFuncSetAttribute(k_amg_tail<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                      cudaSuccess)
-        return false;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)cl);
-    cfg.blockDim = dim3(TAIL_THREADS);
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)cl;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, k_amg_tail<T>, &cfg) != cudaSuccess) return false;
-    return nc >= 1;
+    return (int)cudaLaunchKernelEx(&cfg, k_amg_tail<T>, plan, sync);
 }
 
-int amg_tail_cluster(void) {
+int amg_tail_grid(void) {
     static int cached[64];
     static bool known[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     if (!known[dev]) {
-        int cl = 0;
-        for (int c : {16, 8})
-            if (tail_fits<double>(c) && tail_fits<float>(c)) {
-                cl = c;
-                break;
-            }
-        cudaGetLastError();  // a refused size leaves no error behind
-        cached[dev] = cl;
+        int coop = 0, sms = 0, b64 = 0, b32 = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_amg_tail<double>, TAIL_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_amg_tail<float>, TAIL_THREADS, 0);
+        cudaGetLastError();
+        const int b = b64 < b32 ? b64 : b32;
+        cached[dev] = (coop && b >= 1) ? sms * b : 0;
         known[dev] = true;
     }
     return cached[dev];
 }
 
-template int launch_amg_tail<double>(const TailPlan *, int, cudaStream_t);
-template int launch_amg_tail<float>(const TailPlan *, int, cudaStream_t);
+template int launch_amg_tail<double>(const TailPlan *, int, unsigned *, cudaStream_t);
+template int launch_amg_tail<float>(const TailPlan *, int, unsigned *, cudaStream_t);
 
 }  // namespace mgr
