@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-profile", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-configs", action="store_true")
     return p.parse_args()
 
 
@@ -437,6 +438,50 @@ def run_gb300(args, world, rank, local):
                 batched["speedup_vs_sequential_fp64"] = round(seq / ms, 3)
             bt.close()
 
+    # ---- the other configurations: solve times and the outer SpMV (b = 2, 4, 3)
+    configs = None
+    if not args.no_configs:
+        from paper_2101_11649_gb300.synth import CONFIGS
+        configs = {}
+        st = torch.cuda.current_stream()
+
+        def ev_ms(fn, reps):
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st); out = fn(); e1.record(st); e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return statistics.median(ts), out
+
+        for name in ("two_phase_16x16x8", "compositional_128x128x32", "poromech_64"):
+            cs = CONFIGS[name]()
+            bq = torch.as_tensor(cs.rhs, device=dev)
+            ent = {"n": cs.n, "b": cs.b, "nnzb": int(cs.col_idx.size), "mgr_levels": cs.num_levels}
+            for prec in ("fp64", "fp32"):
+                t0 = time.perf_counter()
+                sv = M.MGRSolver.from_system(cs, precision=prec)
+                torch.cuda.synchronize()
+                ent[f"setup_{prec}_ms"] = round((time.perf_counter() - t0) * 1e3, 1)
+                for _ in range(2):
+                    sv.solve(bq, rtol=args.rtol)
+                ms, (_, inf) = ev_ms(lambda: sv.solve(bq, rtol=args.rtol), 5)
+                ent[f"{prec}_ms"] = round(ms, 3)
+                ent[f"{prec}_iterations"] = inf["iterations"]
+                ent[f"{prec}_rel_residual"] = inf["rel_residual"]
+                if prec == "fp64":
+                    xq = torch.randn(cs.n, dtype=torch.float64, device=dev)
+                    yq = torch.empty_like(xq)
+                    for _ in range(3):
+                        sv.spmv(xq, yq)
+                    us, _ = ev_ms(lambda: sv.spmv(xq, yq), 20)
+                    by = cs.col_idx.size * (cs.b * cs.b * 8 + 4) + 4 * (cs.nb + 1) + 16 * cs.n
+                    ent["spmv_us"] = round(us * 1e3, 2)
+                    ent["spmv_gbs"] = round(by / (us / 1e3) / 1e9, 1)
+                    ent["spmv_frac"] = round(by / (us / 1e3) / 1e9 / peak_gbs, 4)
+                sv.close()
+            configs[name] = ent
+
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -462,7 +507,7 @@ def run_gb300(args, world, rank, local):
                 "levels": {"mgr": info64["mgr_levels"], "amg": info64["amg_levels"],
                            "rows": info64["level_rows"], "nnz": info64["level_nnz"],
                            "operator_complexity": round(info64["operator_complexity"], 3)},
-                "vcycle": vcycle, "roofline": roofline, "batched": batched,
+                "vcycle": vcycle, "roofline": roofline, "batched": batched, "configs": configs,
                 "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
                             for r in kernels[:12]],
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
