@@ -784,84 +784,175 @@ __global__ void k_extpi_bound(int n, const int *rp, const int *ci, const uint8_t
 }
 
 // Pass 1: Chat_i (sorted, unique) and the untruncated weights into scratch;
-// final row length into len[i].
+// final row length into len[i].  One warp per row.  Lanes gather candidates,
+// compute terms and update the num slots (within one neighbour row k every
+// entry names a different column, so every slot gets at most one term per k);
+// every scalar the definition accumulates in order (the diagonal, each den)
+// is summed in that order by all lanes alike, from shuffled terms, so the
+// result equals the row-by-row definition bit for bit.
+__device__ __forceinline__ int find_sorted(const int *a, int len, int j) {
+    int lo = 0, hi = len - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int x = a[mid];
+        if (x == j) return mid;
+        if (x < j) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+// acc += the terms t of the lanes in mask, in ascending lane order (all lanes)
+__device__ __forceinline__ double ordered_add(double acc, unsigned mask, double t) {
+    for (unsigned m = mask; m; m &= m - 1) acc = acc + __shfl_sync(0xffffffffu, t, __ffs(m) - 1);
+    return acc;
+}
+
 __global__ void k_extpi_weights(int n, const int *rp, const int *ci, const double *v,
                                 const uint8_t *sflag, const int *cf, const int *func,
                                 const long long *boff, int *cand, double *wts, int *chat_len,
                                 int *len, int pmax) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (cf[i] == 1) { len[i] = 1; chat_len[i] = 0; return; }
+    const unsigned FULL = 0xffffffffu;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= n) return;  // whole warps
+    const int i = (int)wid;
+    if (cf[i] == 1) {
+        if (lane == 0) { len[i] = 1; chat_len[i] = 0; }
+        return;
+    }
     int *L = cand + boff[i];
     double *num = wts + boff[i];
+    const int r0 = rp[i], r1 = rp[i + 1];
+    const unsigned below = (1u << lane) - 1u;
+    // candidates: strong C neighbours, and strong C neighbours of strong F neighbours
     int cnt = 0;
-    for (int p = rp[i]; p < rp[i + 1]; p++) {
-        if (!sflag[p]) continue;
-        int j = ci[p];
-        if (cf[j] == 1) L[cnt++] = j;
-        else
-            for (int q = rp[j]; q < rp[j + 1]; q++)
-                if (sflag[q] && cf[ci[q]] == 1) L[cnt++] = ci[q];
+    for (int p0 = r0; p0 < r1; p0 += 32) {
+        const int p = p0 + lane;
+        bool take = false;
+        int j = 0;
+        if (p < r1 && sflag[p]) { j = ci[p]; take = cf[j] == 1; }
+        const unsigned m = __ballot_sync(FULL, take);
+        if (take) L[cnt + __popc(m & below)] = j;
+        cnt += __popc(m);
     }
-    // sort + unique
-    const int gaps[8] = {701, 301, 132, 57, 23, 10, 4, 1};
-    for (int gi = 0; gi < 8; gi++) {
-        int g = gaps[gi];
-        for (int a = g; a < cnt; a++) {
-            int kc = L[a], b = a;
-            while (b >= g && L[b - g] > kc) { L[b] = L[b - g]; b -= g; }
-            L[b] = kc;
+    for (int p = r0; p < r1; p++) {
+        if (!sflag[p]) continue;
+        const int j = ci[p];
+        if (cf[j] == 1) continue;
+        const int q1 = rp[j + 1];
+        for (int q0 = rp[j]; q0 < q1; q0 += 32) {
+            const int q = q0 + lane;
+            bool take = false;
+            int c = 0;
+            if (q < q1 && sflag[q]) { c = ci[q]; take = cf[c] == 1; }
+            const unsigned m = __ballot_sync(FULL, take);
+            if (take) L[cnt + __popc(m & below)] = c;
+            cnt += __popc(m);
         }
     }
-    int u = 0;
-    for (int a = 0; a < cnt; a++)
-        if (u == 0 || L[a] != L[u - 1]) L[u++] = L[a];
-    cnt = u;
-    chat_len[i] = cnt;
-    if (cnt == 0) { len[i] = 0; return; }
-    for (int t = 0; t < cnt; t++) num[t] = 0.0;
-    double diag = 0.0;
-    for (int p = rp[i]; p < rp[i + 1]; p++)
-        if (ci[p] == i) diag = v[p];
-    int fi = func[i];
-    // phase 1
-    for (int p = rp[i]; p < rp[i + 1]; p++) {
-        int j = ci[p];
-        if (j == i || func[j] != fi) continue;
-        int lo = 0, hi = cnt - 1, at = -1;
-        while (lo <= hi) { int mid = (lo + hi) >> 1; if (L[mid] == j) { at = mid; break; } if (L[mid] < j) lo = mid + 1; else hi = mid - 1; }
-        if (at >= 0) num[at] = num[at] + v[p];
-        else if (!sflag[p]) diag = diag + v[p];
+    __syncwarp();
+    // sort + unique (one lane)
+    if (lane == 0) {
+        const int gaps[8] = {701, 301, 132, 57, 23, 10, 4, 1};
+        for (int gi = 0; gi < 8; gi++) {
+            const int g = gaps[gi];
+            for (int a = g; a < cnt; a++) {
+                int kc = L[a], b = a;
+                while (b >= g && L[b - g] > kc) { L[b] = L[b - g]; b -= g; }
+                L[b] = kc;
+            }
+        }
+        int u = 0;
+        for (int a = 0; a < cnt; a++)
+            if (u == 0 || L[a] != L[u - 1]) L[u++] = L[a];
+        cnt = u;
+        chat_len[i] = cnt;
     }
-    // phase 2
-    for (int p = rp[i]; p < rp[i + 1]; p++) {
-        int k = ci[p];
+    cnt = __shfl_sync(FULL, cnt, 0);
+    __syncwarp();
+    if (cnt == 0) {
+        if (lane == 0) len[i] = 0;
+        return;
+    }
+    for (int t = lane; t < cnt; t += 32) num[t] = 0.0;
+    double diag = 0.0;
+    for (int p0 = r0; p0 < r1; p0 += 32) {
+        const int p = p0 + lane;
+        const bool d = p < r1 && ci[p] == i;
+        const unsigned m = __ballot_sync(FULL, d);
+        if (m) diag = __shfl_sync(FULL, d ? v[p] : 0.0, 31 - __clz(m));
+    }
+    const int fi = func[i];
+    __syncwarp();
+    // phase 1
+    for (int p0 = r0; p0 < r1; p0 += 32) {
+        const int p = p0 + lane;
+        bool dt = false;
+        double t = 0.0;
+        if (p < r1) {
+            const int j = ci[p];
+            if (j != i && func[j] == fi) {
+                const int at = find_sorted(L, cnt, j);
+                if (at >= 0) num[at] = num[at] + v[p];
+                else if (!sflag[p]) { dt = true; t = v[p]; }
+            }
+        }
+        diag = ordered_add(diag, __ballot_sync(FULL, dt), t);
+    }
+    __syncwarp();
+    // phase 2: strong F neighbours k in row order
+    for (int p = r0; p < r1; p++) {
+        const int k = ci[p];
         if (k == i || !sflag[p] || cf[k] == 1) continue;
-        double aik = v[p];
+        const double aik = v[p];
+        const int k0 = rp[k], k1 = rp[k + 1];
         double akk = 0.0;
-        for (int q = rp[k]; q < rp[k + 1]; q++)
-            if (ci[q] == k) akk = v[q];
-        int fk = func[k];
+        for (int q0 = k0; q0 < k1; q0 += 32) {
+            const int q = q0 + lane;
+            const bool d = q < k1 && ci[q] == k;
+            const unsigned m = __ballot_sync(FULL, d);
+            if (m) akk = __shfl_sync(FULL, d ? v[q] : 0.0, 31 - __clz(m));
+        }
+        const int fk = func[k];
         double den = 0.0;
-        for (int q = rp[k]; q < rp[k + 1]; q++) {
-            int l = ci[q];
-            if (l == k || func[l] != fk) continue;
-            if (l == i || in_sorted(L, cnt, l)) den = den + abar(akk, v[q]);
+        for (int q0 = k0; q0 < k1; q0 += 32) {
+            const int q = q0 + lane;
+            bool sel = false;
+            double t = 0.0;
+            if (q < k1) {
+                const int l = ci[q];
+                if (l != k && func[l] == fk && (l == i || find_sorted(L, cnt, l) >= 0)) {
+                    sel = true;
+                    t = abar(akk, v[q]);
+                }
+            }
+            den = ordered_add(den, __ballot_sync(FULL, sel), t);
         }
         if (den == 0.0) { diag = diag + aik; continue; }
-        double f = aik / den;
-        for (int q = rp[k]; q < rp[k + 1]; q++) {
-            int l = ci[q];
-            if (l == k || func[l] != fk) continue;
-            int lo = 0, hi = cnt - 1, at = -1;
-            while (lo <= hi) { int mid = (lo + hi) >> 1; if (L[mid] == l) { at = mid; break; } if (L[mid] < l) lo = mid + 1; else hi = mid - 1; }
-            if (at >= 0) num[at] = num[at] + f * abar(akk, v[q]);
-            else if (l == i) diag = diag + f * abar(akk, v[q]);
+        const double f = aik / den;
+        for (int q0 = k0; q0 < k1; q0 += 32) {
+            const int q = q0 + lane;
+            bool dt = false;
+            double t = 0.0;
+            if (q < k1) {
+                const int l = ci[q];
+                if (l != k && func[l] == fk) {
+                    const int at = find_sorted(L, cnt, l);
+                    if (at >= 0) num[at] = num[at] + f * abar(akk, v[q]);
+                    else if (l == i) { dt = true; t = f * abar(akk, v[q]); }
+                }
+            }
+            diag = ordered_add(diag, __ballot_sync(FULL, dt), t);
         }
+        __syncwarp();
     }
-    if (diag == 0.0) { len[i] = 0; return; }
-    for (int t = 0; t < cnt; t++) num[t] = -(num[t] / diag);
-    len[i] = (pmax > 0 && cnt > pmax) ? pmax : cnt;
+    if (diag == 0.0) {
+        if (lane == 0) len[i] = 0;
+        return;
+    }
+    for (int t = lane; t < cnt; t += 32) num[t] = -(num[t] / diag);
+    if (lane == 0) len[i] = (pmax > 0 && cnt > pmax) ? pmax : cnt;
 }
 
 // Pass 2: truncation (pmax largest |w|, ties to the lower column; rescale by
@@ -951,8 +1042,8 @@ int amg_extpi(const DCSR &A, const uint8_t *sflag, const int *cf, const int *fun
     int *cand = ar.alloc<int>(totb + 1);
     double *wts = ar.alloc<double>(totb + 1);
     if (!cand || !wts) return ST_NOMEM;
-    k_extpi_weights<<<GRID(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, sflag, cf, func, boff, cand,
-                                                 wts, chat, len, pmax);
+    k_extpi_weights<<<GRID((long long)n * 32, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, sflag, cf, func, boff,
+                                                                 cand, wts, chat, len, pmax);
     P.n = n; P.m = *nc;
     P.rp = ar.alloc<int>(n + 1);
     if (!P.rp) return ST_NOMEM;
