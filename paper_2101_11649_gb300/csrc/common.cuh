@@ -47,6 +47,19 @@ __device__ __forceinline__ void pdl_launch_dependents() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 bool pdl_on();  // false when the environment sets MGR_PDL=0
+// The batched form's kernels are launched in plain stream order: with many
+// systems per launch, early scheduling of the successor measured slower.
+template <class... KArgs, class... Args>
+inline void launch_plain(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 template <class... KArgs, class... Args>
 inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args &&...args) {
     cudaLaunchConfig_t cfg = {};

@@ -432,59 +432,118 @@ __global__ void k_spgemm_bound(int n, const int *arp, const int *aci, const int 
 
 __device__ __forceinline__ unsigned hash_col(int j) { return (unsigned)j * 2654435761u; }
 
+// One warp per row of C = A B (+ E).  The entries p of A's row are taken in
+// order; for each, the lanes insert the distinct columns of B's row k = a_p
+// into the row's hash table at once (slots claimed with atomicCAS), and the
+// warp synchronises before the next p, so every entry of C receives its
+// contributions in ascending p order and E's entry last, as the row-by-row
+// definition sums them.  NUMERIC = false counts the distinct columns; the
+// numeric pass gathers the table and sorts the row by column.
+__device__ __forceinline__ void spgemm_insert(int *key, double *val, unsigned cap, int j, double prod,
+                                              bool numeric, int &claimed, int *errw) {
+    unsigned h = hash_col(j) & (cap - 1);
+    for (unsigned probe = 0; probe < cap; probe++) {
+        int kk = ((volatile int *)key)[h];
+        if (kk < 0) {
+            kk = atomicCAS(key + h, -1, j);
+            if (kk < 0) {
+                if (numeric) { val[h] = 0.0; val[h] = val[h] + prod; }
+                claimed++;
+                return;
+            }
+        }
+        if (kk == j) {
+            if (numeric) val[h] = val[h] + prod;
+            return;
+        }
+        h = (h + 1) & (cap - 1);
+    }
+    atomicOr(errw, ERRW_OVERFLOW);  // table full: cannot happen when cap >= 2 * distinct
+}
+
 template <bool NUMERIC>
 __global__ void k_spgemm_row(int r0, int r1, const int *arp, const int *aci, const double *av,
                              const int *brp, const int *bci, const double *bv, const int *erp,
                              const int *eci, const double *ev, const long long *capoff,
                              long long base, int *hkey, double *hval, int *cnt, const int *crp,
                              int *cci, double *cv, int *errw) {
-    int i = r0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= r1) return;
-    long long off = capoff[i] - base;
-    unsigned cap = (unsigned)(capoff[i + 1] - capoff[i]);
+    const unsigned FULL = 0xffffffffu;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= r1 - r0) return;  // whole warps
+    const int i = r0 + (int)wid;
+    const long long off = capoff[i] - base;
+    const unsigned cap = (unsigned)(capoff[i + 1] - capoff[i]);
     int *key = hkey + off;
     double *val = hval + off;
-    for (unsigned t = 0; t < cap; t++) key[t] = -1;
-    int distinct = 0;
-    auto insert = [&](int j, double prod) {
-        unsigned h = hash_col(j) & (cap - 1);
-        for (unsigned probe = 0; probe < cap; probe++) {
-            int kk = key[h];
-            if (kk == j) { if (NUMERIC) val[h] = val[h] + prod; return; }
-            if (kk < 0) {
-                key[h] = j;
-                if (NUMERIC) { val[h] = 0.0; val[h] = val[h] + prod; }
-                distinct++;
-                return;
-            }
-            h = (h + 1) & (cap - 1);
-        }
-        atomicOr(errw, ERRW_OVERFLOW);  // table full: cannot happen when cap >= 2 * distinct
-    };
+    for (unsigned t = lane; t < cap; t += 32) key[t] = -1;
+    __syncwarp();
+    int claimed = 0;
     for (int p = arp[i]; p < arp[i + 1]; p++) {
-        int k = aci[p];
-        double a = NUMERIC ? av[p] : 0.0;
-        for (int q = brp[k]; q < brp[k + 1]; q++) insert(bci[q], NUMERIC ? a * bv[q] : 0.0);
+        const int k = aci[p];
+        const double a = NUMERIC ? av[p] : 0.0;
+        const int q1 = brp[k + 1];
+        for (int q = brp[k] + lane; q < q1; q += 32)
+            spgemm_insert(key, val, cap, bci[q], NUMERIC ? a * bv[q] : 0.0, NUMERIC, claimed, errw);
+        __syncwarp();
     }
-    if (erp)
-        for (int q = erp[i]; q < erp[i + 1]; q++) insert(eci[q], NUMERIC ? ev[q] : 0.0);
-    if (!NUMERIC) { cnt[i] = distinct; return; }
-    // gather and sort by column (shell sort, Ciura gaps)
-    int o = crp[i], len = 0;
-    for (unsigned t = 0; t < cap; t++)
-        if (key[t] >= 0) { cci[o + len] = key[t]; cv[o + len] = val[t]; len++; }
-    const int gaps[8] = {701, 301, 132, 57, 23, 10, 4, 1};
-    for (int gi = 0; gi < 8; gi++) {
-        int g = gaps[gi];
-        for (int a = g; a < len; a++) {
-            int kc = cci[o + a];
-            double kv = cv[o + a];
-            int b = a;
-            while (b >= g && cci[o + b - g] > kc) {
-                cci[o + b] = cci[o + b - g]; cv[o + b] = cv[o + b - g];
-                b -= g;
+    if (erp) {
+        for (int q = erp[i] + lane; q < erp[i + 1]; q += 32)
+            spgemm_insert(key, val, cap, eci[q], NUMERIC ? ev[q] : 0.0, NUMERIC, claimed, errw);
+        __syncwarp();
+    }
+    if (!NUMERIC) {
+        for (int o = 16; o > 0; o >>= 1) claimed += __shfl_xor_sync(FULL, claimed, o);
+        if (lane == 0) cnt[i] = claimed;
+        return;
+    }
+    // gather the table into the row (unsorted), then sort by column
+    const int o = crp[i];
+    int len = 0;
+    const unsigned below = (1u << lane) - 1u;
+    for (unsigned t0 = 0; t0 < cap; t0 += 32) {
+        const unsigned t = t0 + lane;
+        const bool has = t < cap && key[t] >= 0;
+        const unsigned m = __ballot_sync(FULL, has);
+        if (has) {
+            cci[o + len + __popc(m & below)] = key[t];
+            cv[o + len + __popc(m & below)] = val[t];
+        }
+        len += __popc(m);
+    }
+    __syncwarp();
+    if (len <= 2048) {
+        // rank sort (columns are distinct): entry e goes to the number of smaller columns,
+        // through the table's storage, then back
+        for (int e = lane; e < len; e += 32) {
+            const int ce = cci[o + e];
+            int r = 0;
+            for (int f = 0; f < len; f++) r += cci[o + f] < ce;
+            key[r] = ce;
+            val[r] = cv[o + e];
+        }
+        __syncwarp();
+        for (int e = lane; e < len; e += 32) {
+            cci[o + e] = key[e];
+            cv[o + e] = val[e];
+        }
+    } else if (lane == 0) {
+        // shell sort (Ciura gaps) for long rows
+        const int gaps[8] = {701, 301, 132, 57, 23, 10, 4, 1};
+        for (int gi = 0; gi < 8; gi++) {
+            const int g = gaps[gi];
+            for (int a2 = g; a2 < len; a2++) {
+                const int kc = cci[o + a2];
+                const double kv = cv[o + a2];
+                int b2 = a2;
+                while (b2 >= g && cci[o + b2 - g] > kc) {
+                    cci[o + b2] = cci[o + b2 - g];
+                    cv[o + b2] = cv[o + b2 - g];
+                    b2 -= g;
+                }
+                cci[o + b2] = kc;
+                cv[o + b2] = kv;
             }
-            cci[o + b] = kc; cv[o + b] = kv;
         }
     }
 }
@@ -523,7 +582,7 @@ int spgemm(const DCSR &A, const DCSR &B, const DCSR *E, DCSR &C, cudaStream_t s,
     const double *ev = E ? E->v : nullptr;
     for (size_t c = 0; c + 1 < cuts.size(); c++) {
         int r0 = cuts[c], r1 = cuts[c + 1];
-        k_spgemm_row<false><<<GRID(r1 - r0, 128), 128, 0, s>>>(
+        k_spgemm_row<false><<<GRID((long long)(r1 - r0) * 32, 256), 256, 0, s>>>(
             r0, r1, A.rp, A.ci, A.v, B.rp, B.ci, B.v, erp, eci, ev, capoff, hoff[r0], hkey, hval,
             cnt, nullptr, nullptr, nullptr, errw);
     }
@@ -536,7 +595,7 @@ int spgemm(const DCSR &A, const DCSR &B, const DCSR *E, DCSR &C, cudaStream_t s,
     if (!C.ci || !C.v) return ST_NOMEM;
     for (size_t c = 0; c + 1 < cuts.size(); c++) {
         int r0 = cuts[c], r1 = cuts[c + 1];
-        k_spgemm_row<true><<<GRID(r1 - r0, 128), 128, 0, s>>>(
+        k_spgemm_row<true><<<GRID((long long)(r1 - r0) * 32, 256), 256, 0, s>>>(
             r0, r1, A.rp, A.ci, A.v, B.rp, B.ci, B.v, erp, eci, ev, capoff, hoff[r0], hkey, hval,
             cnt, C.rp, C.ci, C.v, errw);
     }

@@ -1187,12 +1187,12 @@ static void bchunk_dispatch(const BJob *jobs, const long long *prefix, int njobs
     if (blocks > NUM_SMS * 8) blocks = NUM_SMS * 8;
     unsigned g = (unsigned)(blocks < 1 ? 1 : blocks);
     switch (R) {
-        case 1: launch_k(k_bchunk<1, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
-        case 2: launch_k(k_bchunk<2, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
-        case 4: launch_k(k_bchunk<4, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
-        case 8: launch_k(k_bchunk<8, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
-        case 16: launch_k(k_bchunk<16, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
-        default: launch_k(k_bchunk<32, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
+        case 1: launch_plain(k_bchunk<1, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
+        case 2: launch_plain(k_bchunk<2, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
+        case 4: launch_plain(k_bchunk<4, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
+        case 8: launch_plain(k_bchunk<8, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
+        case 16: launch_plain(k_bchunk<16, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
+        default: launch_plain(k_bchunk<32, T, TV, OP>, dim3(g), dim3(CWARPS * 32), s, jobs, prefix, njobs, js); break;
     }
 }
 
@@ -1255,7 +1255,7 @@ __global__ void k_bfrelax_first(const BJob *jobs, const long long *prefix, int n
 template <class T, class TV>
 void launch_bfrelax_first(const BJob *jobs, const long long *prefix, int njobs, long long total,
                           T omega, int js, cudaStream_t s) {
-    if (total > 0) launch_k(k_bfrelax_first<T, TV>, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs, omega, js);
+    if (total > 0) launch_plain(k_bfrelax_first<T, TV>, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs, omega, js);
 }
 
 // z[cidx[i]] = e_C[i], per system
@@ -1277,7 +1277,7 @@ __global__ void k_bscatter(const BJob *jobs, const long long *prefix, int njobs,
 template <class T, class TV>
 void launch_bscatter(const BJob *jobs, const long long *prefix, int njobs, long long total, int js,
                      cudaStream_t s) {
-    if (total > 0) launch_k(k_bscatter<T, TV>, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs, js);
+    if (total > 0) launch_plain(k_bscatter<T, TV>, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs, js);
 }
 
 // coarsest dense solves: one warp per row over every system's coarsest grid
@@ -1308,7 +1308,7 @@ void launch_bdense(const BJob *jobs, const long long *prefix, int njobs, long lo
     if (total <= 0) return;
     long long g = (total * 32 + 255) / 256;
     if (g > NUM_SMS * 8) g = NUM_SMS * 8;
-    launch_k(k_bdense<TV>, dim3((unsigned)(g < 1 ? 1 : g)), dim3(256), s, jobs, prefix, njobs, js);
+    launch_plain(k_bdense<TV>, dim3((unsigned)(g < 1 ? 1 : g)), dim3(256), s, jobs, prefix, njobs, js);
 }
 
 // outer block-CSR product (b > 1), one thread per scalar row; r != null: residual
@@ -1344,9 +1344,9 @@ void launch_bbsr(int b, const BJob *jobs, const long long *prefix, int njobs, lo
     if (total <= 0) return;
     unsigned g = elem_grid(total);
     switch (b) {
-        case 2: launch_k(k_bbsr<2>, dim3(g), dim3(256), s, jobs, prefix, njobs, js); break;
-        case 3: launch_k(k_bbsr<3>, dim3(g), dim3(256), s, jobs, prefix, njobs, js); break;
-        default: launch_k(k_bbsr<4>, dim3(g), dim3(256), s, jobs, prefix, njobs, js); break;
+        case 2: launch_plain(k_bbsr<2>, dim3(g), dim3(256), s, jobs, prefix, njobs, js); break;
+        case 3: launch_plain(k_bbsr<3>, dim3(g), dim3(256), s, jobs, prefix, njobs, js); break;
+        default: launch_plain(k_bbsr<4>, dim3(g), dim3(256), s, jobs, prefix, njobs, js); break;
     }
 }
 
@@ -1369,7 +1369,7 @@ __global__ void k_bscale(const BJob *jobs, const long long *prefix, int njobs, i
 
 void launch_bscale(const BJob *jobs, const long long *prefix, int njobs, long long total, int js,
                    int invert, cudaStream_t s) {
-    if (total > 0) launch_k(k_bscale, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs, js, invert);
+    if (total > 0) launch_plain(k_bscale, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs, js, invert);
 }
 
 // x += sum_{i < k} y_i Z_i per system (k in *J.gz, y in J.r, Z in J.v, x in J.o1)
@@ -1392,7 +1392,7 @@ __global__ void k_bmulti_axpy(const BJob *jobs, const long long *prefix, int njo
 
 void launch_bmulti_axpy(const BJob *jobs, const long long *prefix, int njobs, long long total,
                         cudaStream_t s) {
-    if (total > 0) launch_k(k_bmulti_axpy, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs);
+    if (total > 0) launch_plain(k_bmulti_axpy, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs);
 }
 
 // Segmented Arnoldi projections: the blocks of system j are blocks
@@ -1534,7 +1534,7 @@ void launch_bdots(int k, const BJob *jobs, const long long *bprefix, int njobs, 
     if (nblocks <= 0) return;
     unsigned g = (unsigned)nblocks;
     switch (k) {
-#define X(K) case K: launch_k(k_bdots<K>, dim3(g), dim3(RED_THREADS), s, jobs, bprefix, njobs, js, conditional, sqrt_out); break;
+#define X(K) case K: launch_plain(k_bdots<K>, dim3(g), dim3(RED_THREADS), s, jobs, bprefix, njobs, js, conditional, sqrt_out); break;
         K_CASES(X)
 #undef X
         default: break;
@@ -1546,7 +1546,7 @@ void launch_bupdate_norm(int k, const BJob *jobs, const long long *bprefix, int 
     if (nblocks <= 0) return;
     unsigned g = (unsigned)nblocks;
     switch (k) {
-#define X(K) case K: launch_k(k_bupdate_norm<K>, dim3(g), dim3(RED_THREADS), s, jobs, bprefix, njobs, js, mode); break;
+#define X(K) case K: launch_plain(k_bupdate_norm<K>, dim3(g), dim3(RED_THREADS), s, jobs, bprefix, njobs, js, mode); break;
         K_CASES(X)
 #undef X
         default: break;
