@@ -173,18 +173,28 @@ def max_over_ranks(world, v, dev):
     return float(t.item())
 
 
+KERNEL_SOURCES = ("sell.cuh", "spmv.cuh", "reduce.cuh", "solve.cu", "krylov.cu")
+
+
+def kernel_sources_sha1():
+    """SHA-1 over the solve-phase kernel sources, in a fixed order."""
+    import hashlib
+    h = hashlib.sha1()
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2101_11649_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def ncu_traffic(kernel_class):
     """DRAM bytes per launch of a kernel class from the committed ncu capture
-    (profiles/traffic.json), or None when the kernel source changed since."""
-    import hashlib
+    (profiles/traffic.json), or None when the kernel sources changed since."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2101_11649_gb300", "csrc", "solve.cu")
     try:
         d = json.load(open(path))
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        sha = kernel_sources_sha1()
     except Exception:
         return None
-    if d.get("solve_cu_sha1") != sha:
+    if d.get("kernel_sources_sha1") != sha:
         return None
     k = d.get("kernels", {}).get(kernel_class)
     if not k or "note" in k:

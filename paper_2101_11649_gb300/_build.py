@@ -21,6 +21,8 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
 UNITS = {
     "setup.cu": ["--fmad=false"],
     "solve.cu": [],
+    "krylov.cu": [],
+    "batched.cu": [],
     "mgr_api.cu": [],
     "noalloc.cu": [],
     "tail.cu": [],
