@@ -1,4 +1,4 @@
-// SELL-C-sigma row products shared by the solve-phase kernels (solve.cu)
+// SELL-C-sigma row products shared by the solve-phase kernels (spmv.cuh)
 // and the fused coarse-level kernel (tail.cu): one routine, so a row's sum
 // has the same operation order, and the same bits, wherever it is formed.
 #pragma once

@@ -39,7 +39,7 @@ void launch_csr_residual(const DCSR &A, const double *x, const double *bvec, dou
 }
 
 // -------------------------------------------------------------- BSR (FP64)
-// b == 1 is CSR (chunk engine).  b > 1: one thread per scalar row (I, r);
+// b == 1 without a handle is CSR (chunk engine).  b > 1: one thread per scalar row (I, r);
 // the b values of row r of each block are contiguous.
 template <int B>
 __global__ void k_bsrB(int nb, const int *__restrict__ rp, const int *__restrict__ ci,

@@ -10,7 +10,7 @@
 // the launch are read through L2 (ld.global.cg), so no SM sees a stale L1
 // line of another SM's result; matrices and diagonals are read-only.  Each
 // row sum and each epilogue is the same operation sequence as in the
-// per-level kernels (sell.cuh and the epilogues of solve.cu), so the result
+// per-level kernels (sell.cuh and the epilogues of spmv.cuh), so the result
 // is bitwise the one the per-level kernels give.
 #include <cuda_runtime.h>
 
@@ -85,7 +85,7 @@ __device__ __forceinline__ void tail_phase(const SellView &M, const T *x, const 
 }
 
 // phase epilogues: the operation sequences of EResid, EStoreScaled, EStore,
-// EAdd and EPost in solve.cu
+// EAdd and EPost in spmv.cuh
 template <class T>
 struct FResid {  // res = r - s
     const T *r;
