@@ -114,7 +114,7 @@ typedef struct {
 } mgr_solve_info;
 
 /* Defaults: Jacobi, 1 sweep, omega 1 on every level; theta 0.25, 25 AMG
- * levels, coarsest <= 256 rows, P_max 4, 1 function; FP64; m = 30; graphs on;
+ * levels, coarsest <= 1024 rows, P_max 4, 1 function; FP64; m = 30; graphs on;
  * no fused AMG tail. */
 void mgr_options_default(mgr_options *opt);
 

@@ -108,7 +108,7 @@ class Options:
     weights: list = field(default_factory=list)
     theta: float = 0.25
     max_levels: int = 25
-    max_coarse: int = 256
+    max_coarse: int = 1024
     pmax: int = 4
     num_functions: int = 1
     restart: int = 30

@@ -194,7 +194,7 @@ extern "C" void mgr_options_default(mgr_options *o) {
     }
     o->amg_theta = 0.25;
     o->amg_max_levels = 25;
-    o->amg_max_coarse = 256;
+    o->amg_max_coarse = 1024;
     o->amg_pmax = 4;
     o->amg_num_functions = 1;
     o->precision = MGR_PREC_FP64;
@@ -272,7 +272,7 @@ static mgr_status setup_amg(mgr_handle h, DCSR A0) {
     }
     AmgLevel &Lc = h->amg[h->namg - 1];
     h->nco = Lc.A.n;
-    if (h->nco > 1024) return fail(h, MGR_ERR_UNSUPPORTED, "AMG coarsening stalled above 1024 rows");
+    if (h->nco > 4096) return fail(h, MGR_ERR_UNSUPPORTED, "AMG coarsening stalled above 4096 rows");
     h->coinv = ar.alloc<double>((size_t)h->nco * h->nco + 1);
     h->coinvT = ar.alloc<double>((size_t)h->nco * h->nco + 1);
     if (!h->coinv || !h->coinvT) return fail(h, MGR_ERR_NOMEM, "coarsest inverse");

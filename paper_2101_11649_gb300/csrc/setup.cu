@@ -1174,66 +1174,100 @@ __global__ void k_dense_fill(int n, const int *rp, const int *ci, const double *
         for (int p = rp[i]; p < rp[i + 1]; p++) M[(long long)i * 2 * n + ci[p]] = v[p];
 }
 
-__global__ void k_gauss_jordan(int n, double *M, double *inv, int *errw) {
-    __shared__ double red_v[1024];
-    __shared__ int red_i[1024];
-    __shared__ int piv_row;
-    __shared__ double piv_val;
-    int tid = threadIdx.x, nt = blockDim.x;
-    long long ld = 2LL * n;
-    for (int c = 0; c < n; c++) {
-        double best = -1.0;
-        int bi = c;
-        for (int r = c + tid; r < n; r += nt) {
-            double x = fabs(M[r * ld + c]);
-            if (x > best || (x == best && r < bi)) { best = x; bi = r; }
+// Gauss-Jordan inverse with partial pivoting (the largest |entry| of the
+// column, ties to the lower row), one launch per pivot column over the whole
+// grid.  Step c reads the augmented matrix [A | I] from Min and writes Mout
+// (the two alternate, so no CTA reads a row another CTA is writing): every
+// CTA finds the same pivot p, stages the pivot row scaled by 1/a_pc in
+// shared memory, and updates its share of the entries; row c takes the
+// scaled pivot row, row p the eliminated old row c, and column c becomes
+// e_c.  The operations per entry are those of the one-CTA sweep (a division
+// for the pivot row, a separately rounded multiply and subtract elsewhere).
+static constexpr int GJ_THREADS = 256;
+
+__global__ void __launch_bounds__(GJ_THREADS) k_gj_step(int n, int c, const double *__restrict__ Min,
+                                                        double *__restrict__ Mout, int *errw) {
+    extern __shared__ double prow[];  // [2n] scaled pivot row
+    __shared__ double red_v[GJ_THREADS];
+    __shared__ int red_i[GJ_THREADS];
+    const int tid = threadIdx.x;
+    const long long ld = 2LL * n;
+    double best = -1.0;
+    int bi = c;
+    for (int r = c + tid; r < n; r += GJ_THREADS) {
+        const double x = fabs(Min[r * ld + c]);
+        if (x > best || (x == best && r < bi)) { best = x; bi = r; }
+    }
+    red_v[tid] = best;
+    red_i[tid] = bi;
+    __syncthreads();
+    for (int o = GJ_THREADS / 2; o > 0; o >>= 1) {
+        if (tid < o) {
+            const double a = red_v[tid], b = red_v[tid + o];
+            const int ia = red_i[tid], ib = red_i[tid + o];
+            if (b > a || (b == a && ib < ia)) { red_v[tid] = b; red_i[tid] = ib; }
         }
-        red_v[tid] = best; red_i[tid] = bi;
-        __syncthreads();
-        for (int o = nt / 2; o > 0; o >>= 1) {
-            if (tid < o) {
-                double a = red_v[tid], b = red_v[tid + o];
-                int ia = red_i[tid], ib = red_i[tid + o];
-                if (b > a || (b == a && ib < ia)) { red_v[tid] = b; red_i[tid] = ib; }
-            }
-            __syncthreads();
-        }
-        if (tid == 0) { piv_row = red_i[0]; piv_val = M[red_i[0] * ld + c]; }
-        __syncthreads();
-        if (piv_val == 0.0) { if (tid == 0) atomicOr(errw, ERRW_SINGULAR); return; }
-        int p = piv_row;
-        if (p != c)
-            for (int t = tid; t < 2 * n; t += nt) {
-                double a = M[c * ld + t]; M[c * ld + t] = M[p * ld + t]; M[p * ld + t] = a;
-            }
-        __syncthreads();
-        double pv = piv_val;
-        for (int t = tid; t < 2 * n; t += nt) M[c * ld + t] = M[c * ld + t] / pv;
-        __syncthreads();
-        for (long long e = tid; e < (long long)n * 2 * n; e += nt) {
-            int r = (int)(e / (2 * n)), t = (int)(e % (2 * n));
-            if (r == c || t == c) continue;
-            M[r * ld + t] = M[r * ld + t] - M[r * ld + c] * M[c * ld + t];
-        }
-        __syncthreads();
-        for (int r = tid; r < n; r += nt)
-            if (r != c) M[r * ld + c] = 0.0;
         __syncthreads();
     }
-    for (long long e = tid; e < (long long)n * n; e += nt) {
-        int r = (int)(e / n), t = (int)(e % n);
+    const int p = red_i[0];
+    const double pv = Min[p * ld + c];
+    if (pv == 0.0) {
+        if (blockIdx.x == 0 && tid == 0) atomicOr(errw, ERRW_SINGULAR);
+        return;
+    }
+    for (int t = tid; t < 2 * n; t += GJ_THREADS) prow[t] = Min[p * ld + t] / pv;
+    __syncthreads();
+    const long long tot = (long long)n * ld;
+    for (long long e = (long long)blockIdx.x * GJ_THREADS + tid; e < tot; e += (long long)gridDim.x * GJ_THREADS) {
+        const int r = (int)(e / ld), t = (int)(e % ld);
+        double out;
+        if (r == c) {
+            out = prow[t];
+        } else if (t == c) {
+            out = 0.0;
+        } else {
+            const int src = (r == p) ? c : r;  // after the swap row p holds the old row c
+            out = Min[src * ld + t] - Min[src * ld + c] * prow[t];
+        }
+        Mout[e] = out;
+    }
+}
+
+__global__ void k_gj_extract(int n, const double *M, double *inv) {
+    const long long ld = 2LL * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), t = (int)(e % n);
         inv[e] = M[r * ld + n + t];
     }
 }
 
 int dense_inverse(const DCSR &A, double *inv, int *errw, cudaStream_t s, Arena &ar) {
-    int n = A.n;
+    const int n = A.n;
+    if (n <= 0) return ST_OK;
     double *M = ar.alloc<double>((size_t)n * 2 * n + 1);
-    if (!M) return ST_NOMEM;
+    double *M2 = ar.alloc<double>((size_t)n * 2 * n + 1);
+    if (!M || !M2) return ST_NOMEM;
     k_dense_fill<<<n, 256, 0, s>>>(n, A.rp, A.ci, A.v, M);
-    k_gauss_jordan<<<1, 1024, 0, s>>>(n, M, inv, errw);
+    const long long tot = 2LL * n * n;
+    long long blocks = (tot + GJ_THREADS * 8 - 1) / (GJ_THREADS * 8);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    const size_t sh = (size_t)2 * n * sizeof(double);
+    if (sh > 48 * 1024 &&
+        cudaFuncSetAttribute(k_gj_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh) != cudaSuccess)
+        return ST_CUDA;
+    double *a = M, *b = M2;
+    for (int c = 0; c < n; c++) {
+        k_gj_step<<<(unsigned)blocks, GJ_THREADS, sh, s>>>(n, c, a, b, errw);
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    k_gj_extract<<<GRID((long long)n * n, 256) > 8192 ? 8192 : GRID((long long)n * n, 256), 256, 0, s>>>(n, a, inv);
     cudaStreamSynchronize(s);
     ar.release(M);
+    ar.release(M2);
     return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
 }
 

@@ -126,7 +126,7 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def options(relax=("jacobi",), sweeps=(), weights=(), theta=0.25, max_levels=25, max_coarse=256,
+def options(relax=("jacobi",), sweeps=(), weights=(), theta=0.25, max_levels=25, max_coarse=1024,
             pmax=4, num_functions=1, precision="fp64", restart=30, use_graphs=True,
             tail_nnz=None) -> mgr_options:
     o = mgr_options()

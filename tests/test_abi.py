@@ -38,7 +38,7 @@ def test_options_default_and_null_handling():
     from paper_2101_11649_gb300 import mgr as M
     o = M.mgr_options()
     lib.mgr_options_default(ctypes.byref(o))
-    assert o.amg_theta == 0.25 and o.amg_max_coarse == 256 and o.amg_pmax == 4 and o.restart == 30
+    assert o.amg_theta == 0.25 and o.amg_max_coarse == 1024 and o.amg_pmax == 4 and o.restart == 30
     assert list(o.relax_sweeps)[:2] == [1, 1] and o.relax_weight[0] == 1.0
     lib.mgr_free(None)  # no-op
     lib.mgr_setup.restype = ctypes.c_int

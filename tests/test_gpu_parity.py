@@ -39,6 +39,15 @@ def solver(sysm, precision="fp64", **kw):
     return M.MGRSolver.from_system(sysm, precision=precision, **kw)
 
 
+# the small systems stop coarsening at 32 rows (both sides), so their AMG
+# hierarchies keep several levels under the default coarsest size of 1024
+SMALL_COARSE = 32
+
+
+def oracle_of(sysm, **kw):
+    return O.Oracle(sysm, O.Options(relax=list(sysm.relax), num_functions=sysm.num_functions, **kw))
+
+
 # ------------------------------------------------------------------ SpMV
 @pytest.mark.parametrize("b", [1, 2, 3, 4])
 @pytest.mark.parametrize("nb", [1, 7, 33, 1000])
@@ -186,8 +195,8 @@ def _same_csr(a, b, what):
 @pytest.mark.parametrize("name", list(SMALL))
 def test_hierarchy_bit_exact(name):
     s = SMALL[name]()
-    g = solver(s)
-    o = O.Oracle(s)
+    g = solver(s, max_coarse=SMALL_COARSE)
+    o = oracle_of(s, max_coarse=SMALL_COARSE)
     info = g.info()
     assert info["mgr_levels"] == o.mgr_nlevels
     assert info["amg_levels"] == o.amg_nlevels
@@ -211,8 +220,8 @@ def test_hierarchy_bit_exact(name):
 @pytest.mark.parametrize("name", list(SMALL))
 def test_vcycle_parity(name):
     s = SMALL[name]()
-    g = solver(s)
-    o = O.Oracle(s)
+    g = solver(s, max_coarse=SMALL_COARSE)
+    o = oracle_of(s, max_coarse=SMALL_COARSE)
     rng = np.random.default_rng(5)
     for trans in (False, True):
         v = rng.standard_normal(s.n)
@@ -224,8 +233,8 @@ def test_vcycle_parity(name):
 @pytest.mark.parametrize("name", list(SMALL))
 def test_solve_parity(name):
     s = SMALL[name]()
-    g = solver(s)
-    o = O.Oracle(s)
+    g = solver(s, max_coarse=SMALL_COARSE)
+    o = oracle_of(s, max_coarse=SMALL_COARSE)
     ro = o.solve(s.rhs, rtol=1e-8)
     xg, ig = g.solve(t(s.rhs), rtol=1e-8)
     assert ig["status"] == 0 and ro["status"] == 0
@@ -241,8 +250,8 @@ def test_solve_parity(name):
 @pytest.mark.parametrize("name", list(SMALL))
 def test_fp32_preconditioner_reaches_fp64_tolerance(name):
     s = SMALL[name]()
-    g = solver(s, precision="fp32")
-    o = O.Oracle(s)
+    g = solver(s, precision="fp32", max_coarse=SMALL_COARSE)
+    o = oracle_of(s, max_coarse=SMALL_COARSE)
     xg, ig = g.solve(t(s.rhs), rtol=1e-8)
     assert ig["status"] == 0 and ig["rel_residual"] <= 1e-8
     ro = o.solve(s.rhs, rtol=1e-8)
@@ -255,8 +264,8 @@ def test_fp32_preconditioner_reaches_fp64_tolerance(name):
 
 def test_transpose_solve_and_gradient():
     s = make_two_phase(6, 5, 4)
-    g = solver(s)
-    o = O.Oracle(s)
+    g = solver(s, max_coarse=SMALL_COARSE)
+    o = oracle_of(s, max_coarse=SMALL_COARSE)
     gvec = np.random.default_rng(9).standard_normal(s.n)
     lam, info = g.solve(t(gvec), rtol=1e-12, transpose=True)
     ro = o.solve(gvec, rtol=1e-12, trans=True)
