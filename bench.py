@@ -207,10 +207,14 @@ def make_system(grid):
     return make_mimetic(grid, grid, grid)
 
 
-def oracle_solve_ms(sysm, rtol, steps, warmup):
-    """CPU oracle: setup once (untimed), then `warmup` + `steps` full solves."""
+def oracle_solve_ms(sysm, rtol, steps, warmup, setup_out=None):
+    """CPU oracle: setup once (timed apart, into setup_out[0] when given),
+    then `warmup` + `steps` full solves."""
     from oracle import oracle as O
+    t0 = time.perf_counter()
     o = O.Oracle(sysm)
+    if setup_out is not None:
+        setup_out.append((time.perf_counter() - t0) * 1e3)
     for _ in range(warmup):
         o.solve(sysm.rhs, rtol=rtol)
     ts, its = [], []
@@ -497,8 +501,13 @@ def run_gb300(args, world, rank, local):
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
+    setup = {"gpu_fp64_ms": round(setup64_ms, 1), "gpu_fp32_ms": round(setup32_ms, 1)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ms, its = oracle_solve_ms(sysm, args.rtol, 1, 0)
+        osetup = []
+        ms, its = oracle_solve_ms(sysm, args.rtol, 1, 0, osetup)
+        setup["oracle_ms"] = round(osetup[0], 1)
+        setup["oracle_cores"] = 1
+        setup["speedup_fp64"] = round(osetup[0] / setup64_ms, 1)
         cpu = {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
                "sample": f"one full solve of the same system to {args.rtol:g} (setup untimed), "
                          f"single thread, {its[0]} iterations"}
@@ -517,6 +526,7 @@ def run_gb300(args, world, rank, local):
                              "rel_residual": info32["rel_residual"],
                              "speedup_vs_fp64": round(ms64 / ms32, 3)},
                 "setup_ms": {"fp64": round(setup64_ms, 1), "fp32": round(setup32_ms, 1)},
+                "setup": setup,
                 "levels": {"mgr": info64["mgr_levels"], "amg": info64["amg_levels"],
                            "rows": info64["level_rows"], "nnz": info64["level_nnz"],
                            "operator_complexity": round(info64["operator_complexity"], 3)},

@@ -210,9 +210,6 @@ void launch_scatter2(int nF, int nC, const int *fidx, const int *cidx, const T *
                      TV *z, cudaStream_t s);
 
 // AMG level kernels
-template <class T, class TV>
-void launch_amg_smooth0_residual(const DCSR &A, const T *vals, const T *dinv, const TV *r, T *x,
-                                 T *res, cudaStream_t s);
 template <class T>
 void launch_csr_spmv(const DCSR &A, const T *vals, const T *x, T *y, cudaStream_t s);
 template <class T>
@@ -233,8 +230,6 @@ template <class T, class TV>
 void launch_scale(int n, const T *d, const TV *r, T *x, cudaStream_t s);
 template <class TV>
 void launch_dense_matvec(int n, const double *inv, const TV *r, TV *x, cudaStream_t s);
-template <class TV>
-void launch_copy_cast(const TV *in, double *out, int n, cudaStream_t s);
 
 // Krylov pieces (FP64); reductions finish in their last block (ticket)
 void launch_vec_scale(const double *x, double *y, const double *scale_num, const double *scale_den,

@@ -210,11 +210,6 @@ void launch_scatter2(int nF, int nC, const int *fidx, const int *cidx, const T *
 // ---------------------------------------------------------------- AMG level
 // pre-smoothing from x = 0 fused with the residual:
 //   x_i = dinv_i r_i ;  res_i = r_i - sum_j a_ij dinv_j r_j
-template <class T, class TV>
-void launch_amg_smooth0_residual(const DCSR &A, const T *vals, const T *dinv, const TV *r, T *x,
-                                 T *res, cudaStream_t s) {
-    spmv_rows<T>(A, vals, XScaled<T, TV>{dinv, r}, ESmooth0<T, TV>{r, dinv, x, res}, s);
-}
 
 // residual of the pre-smoothed iterate x = D r computed by the producer of r:
 //   res_i = r_i - sum_j a_ij x_j
@@ -278,19 +273,6 @@ void launch_dense_matvec(int n, const double *inv, const TV *r, TV *x, cudaStrea
     launch_k(k_dense_matvec<TV>, dim3(GRIDN((long long)n * 32, 256)), dim3(256), s, n, inv, r, x);
 }
 
-template <class TV>
-__global__ void k_copy_cast(const TV *in, double *out, int n) {
-    pdl_wait();
-    pdl_launch_dependents();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (double)in[i];
-}
-
-template <class TV>
-void launch_copy_cast(const TV *in, double *out, int n, cudaStream_t s) {
-    if (n == 0) return;
-    launch_k(k_copy_cast<TV>, dim3(GRIDN(n, 256)), dim3(256), s, in, out, n);
-}
 
 // ------------------------------------------------------- instantiations
 #define INST_T_TV(T, TV)                                                                          \
@@ -307,8 +289,6 @@ void launch_copy_cast(const TV *in, double *out, int n, cudaStream_t s) {
                                                 const TV *, T, T *, cudaStream_t);                \
     template void launch_scatter2<T, TV>(int, int, const int *, const int *, const T *, const T *,\
                                          TV *, cudaStream_t);                                     \
-    template void launch_amg_smooth0_residual<T, TV>(const DCSR &, const T *, const T *,          \
-                                                     const TV *, T *, T *, cudaStream_t);         \
     template void launch_amg_post_smooth<T, TV>(const DCSR &, const T *, const T *, const TV *,   \
                                                 const T *, TV *, cudaStream_t);                   \
     template void launch_amg_residual<T, TV>(const DCSR &, const T *, const T *, const TV *, T *, \
@@ -341,7 +321,5 @@ template void launch_csr_spmv_add<float>(const DCSR &, const float *, const floa
 template void launch_dense_matvec<double>(int, const double *, const double *, double *,
                                           cudaStream_t);
 template void launch_dense_matvec<float>(int, const double *, const float *, float *, cudaStream_t);
-template void launch_copy_cast<double>(const double *, double *, int, cudaStream_t);
-template void launch_copy_cast<float>(const float *, double *, int, cudaStream_t);
 
 }  // namespace mgr

@@ -197,12 +197,6 @@ struct XPlain {
     const XT *x;
     __device__ __forceinline__ T operator()(int j) const { return (T)__ldg(x + j); }
 };
-template <class T, class TV>
-struct XScaled {  // x_j = d_j r_j (pre-smoothing from zero)
-    const T *d;
-    const TV *r;
-    __device__ __forceinline__ T operator()(int j) const { return __ldg(d + j) * (T)__ldg(r + j); }
-};
 
 // epilogues.  pre(row) issues the loads an epilogue needs from its row
 // alone (so the SELL kernel can start them before the row's products);
@@ -278,19 +272,6 @@ struct EResid {  // res = r - s
     struct Pre { T r; };
     __device__ __forceinline__ Pre pre(int row) const { return {(T)r[row]}; }
     __device__ __forceinline__ void put(int row, T s, const Pre &p) const { res[row] = p.r - s; }
-    EPI_CALL
-};
-template <class T, class TV>
-struct ESmooth0 {  // x = d r ; res = r - A (d r)
-    const TV *r;
-    const T *d;
-    T *x, *res;
-    struct Pre { T r, d; };
-    __device__ __forceinline__ Pre pre(int row) const { return {(T)r[row], d[row]}; }
-    __device__ __forceinline__ void put(int row, T s, const Pre &p) const {
-        x[row] = p.d * p.r;
-        res[row] = p.r - s;
-    }
     EPI_CALL
 };
 template <class T, class TV>
