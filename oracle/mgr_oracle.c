@@ -23,7 +23,7 @@
 #include <string.h>
 
 enum { OR_OK = 0, OR_INVALID = 1, OR_NOMEM = 2, OR_SINGULAR = 4, OR_NOT_CONVERGED = 5 };
-enum { OR_JACOBI = 0, OR_L1_JACOBI = 1, OR_BLOCK_JACOBI = 2 };
+enum { OR_JACOBI = 0, OR_L1_JACOBI = 1, OR_BLOCK_JACOBI = 2, OR_AMG_RELAX = 3 };
 
 /* ------------------------------------------------------------------ CSR */
 typedef struct {
@@ -675,6 +675,8 @@ typedef struct {
     int *gstart, *gsize;       /* D block of every F point: first F position and size */
     double *dinv;              /* per F point: row of its block inverse (gsize entries) */
     double *zF, *rF, *tF, *vC, *eC;
+    int nfunc;                 /* OR_AMG_RELAX: functions of the unknown approach on A_FF */
+    amg_h famg;                /* OR_AMG_RELAX: AMG hierarchy of A_FF (M_FF^{-1} = one V-cycle) */
 } mgr_level;
 
 typedef struct or_ctx {
@@ -720,7 +722,8 @@ static double csr_get(const csr *a, int i, int j) {
 }
 
 /*
- * D_FF^{-1} of Eq. 4 and of the F-relaxation M_FF.  Jacobi: 1/a_ii;
+ * D_FF^{-1} of Eq. 4 and of the F-relaxation M_FF.  Jacobi (and the AMG
+ * F-relaxation, whose interpolation uses D_FF = diag(A_FF), Sec. 4.3): 1/a_ii;
  * l1-Jacobi: 1/(a_ii + sign(a_ii) sum_{j in F, j != i} |a_ij|);
  * block-Jacobi: the inverse of the F-by-F block of each original BSR block
  * row (Gauss-Jordan with partial pivoting).  The same D is used for W.
@@ -819,6 +822,7 @@ static void mgr_level_free(mgr_level *L) {
     csr_free(&L->AFFT); csr_free(&L->ACFT); csr_free(&L->WT);
     free(L->gstart); free(L->gsize); free(L->dinv);
     free(L->zF); free(L->rF); free(L->tF); free(L->vC); free(L->eC);
+    amg_free(&L->famg);
 }
 
 void or_free(or_ctx *c) {
@@ -838,7 +842,8 @@ void or_free(or_ctx *c) {
  */
 or_ctx *or_setup(int nb, int b, const int *rp, const int *ci, const double *val,
                  const signed char *dof_level, int num_levels, const int *relax_type,
-                 const int *relax_sweeps, const double *relax_weight, double theta,
+                 const int *relax_sweeps, const double *relax_weight,
+                 const int *relax_functions, double theta,
                  int max_levels, int max_coarse, int pmax, int num_functions, int *status) {
     *status = OR_INVALID;
     if (b < 1 || b > 4 || nb < 1 || num_levels < 0 || num_levels > 8) return NULL;
@@ -863,6 +868,10 @@ or_ctx *or_setup(int nb, int b, const int *rp, const int *ci, const double *val,
         L->A = cur; L->gdof = gdof; L->n = cur.n;
         L->relax = relax_type[l]; L->sweeps = relax_sweeps[l] < 1 ? 1 : relax_sweeps[l];
         L->omega = relax_weight[l];
+        L->nfunc = relax_functions ? relax_functions[l] : 1;
+        if (L->relax < OR_JACOBI || L->relax > OR_AMG_RELAX) {
+            c->nlev = l; csr_free(&cur); free(gdof); *status = OR_INVALID; or_free(c); return NULL;
+        }
         int n = L->n;
         int *fpos = (int *)malloc(((size_t)n + 1) * sizeof(int));
         int *cpos = (int *)malloc(((size_t)n + 1) * sizeof(int));
@@ -890,6 +899,18 @@ or_ctx *or_setup(int nb, int b, const int *rp, const int *ci, const double *val,
         if (!rc) rc = csr_transpose(&L->AFF, &L->AFFT);
         if (!rc) rc = csr_transpose(&L->ACF, &L->ACFT);
         if (!rc) rc = csr_transpose(&L->W, &L->WT);
+        if (!rc && L->relax == OR_AMG_RELAX) {
+            /* the F-relaxation's own AMG hierarchy, built on a copy of A_FF
+             * with the same AMG parameters as the final coarse block */
+            csr cp;
+            rc = csr_alloc(&cp, L->AFF.n, L->AFF.m, L->AFF.nnz);
+            if (!rc) {
+                memcpy(cp.rp, L->AFF.rp, ((size_t)L->AFF.n + 1) * sizeof(int));
+                memcpy(cp.ci, L->AFF.ci, (size_t)L->AFF.nnz * sizeof(int));
+                memcpy(cp.v, L->AFF.v, (size_t)L->AFF.nnz * sizeof(double));
+                rc = amg_setup(&cp, L->nfunc, theta, max_levels, max_coarse, pmax, &L->famg);
+            }
+        }
         if (rc) { c->nlev = l + 1; csr_free(&next); or_free(c); *status = rc; return NULL; }
         L->zF = (double *)calloc((size_t)nF + 1, sizeof(double));
         L->rF = (double *)calloc((size_t)nF + 1, sizeof(double));
@@ -908,8 +929,10 @@ or_ctx *or_setup(int nb, int b, const int *rp, const int *ci, const double *val,
     return c;
 }
 
-/* z_F <- sweeps of z_F += omega D^{-1} (y - A z_F) from z_F = 0 (Alg. 1,
- * F-relaxation with M_FF = D); trans uses A_FF^T and D^{-T}. */
+/* z_F <- sweeps of z_F += omega M_FF^{-1} (y - A z_F) from z_F = 0 (Alg. 1,
+ * F-relaxation).  M_FF = D (Jacobi, l1-Jacobi, block-Jacobi), or, for
+ * OR_AMG_RELAX, M_FF^{-1} = one AMG V(1,1) cycle on A_FF (Sec. 4.3, MGR_U).
+ * trans uses A_FF^T and D^{-T}, or the transposed V-cycle. */
 static void mgr_frelax(mgr_level *L, const double *y, int trans) {
     const csr *AFF = trans ? &L->AFFT : &L->AFF;
     int nF = L->nF;
@@ -917,6 +940,12 @@ static void mgr_frelax(mgr_level *L, const double *y, int trans) {
     for (int s = 0; s < L->sweeps; s++) {
         csr_matvec(AFF, L->zF, L->tF);
         for (int f = 0; f < nF; f++) L->rF[f] = y[f] - L->tF[f];
+        if (L->relax == OR_AMG_RELAX) {
+            amg_vcycle(&L->famg, 0, L->rF, L->tF, trans);
+            for (int f = 0; f < nF; f++) L->tF[f] = L->omega * L->tF[f];
+            for (int f = 0; f < nF; f++) L->zF[f] = L->zF[f] + L->tF[f];
+            continue;
+        }
         for (int f = 0; f < nF; f++) {
             int g = L->gstart[f], k = L->gsize[f], r = f - g;
             double s2 = 0.0;
@@ -1098,9 +1127,19 @@ static const csr *mgr_mat(or_ctx *c, int l, int which) {
     }
 }
 
-static const csr *amg_mat(or_ctx *c, int k, int which) {
-    if (k < 0 || k >= c->amg.nlev) return NULL;
-    amg_level *L = &c->amg.lev[k];
+/* amg = 1: the final coarse block's hierarchy; amg = 2 + l: the hierarchy
+ * of MGR level l's AMG F-relaxation (NULL when that level has none) */
+static amg_h *amg_of(or_ctx *c, int amg) {
+    if (amg == 1) return &c->amg;
+    int l = amg - 2;
+    if (l < 0 || l >= c->nlev || c->lev[l].relax != OR_AMG_RELAX) return NULL;
+    return &c->lev[l].famg;
+}
+
+static const csr *amg_mat(or_ctx *c, int amg, int k, int which) {
+    amg_h *H = amg_of(c, amg);
+    if (!H || k < 0 || k >= H->nlev) return NULL;
+    amg_level *L = &H->lev[k];
     switch (which) {
         case 0: return &L->A;
         case 1: return L->P.rp ? &L->P : NULL;
@@ -1110,14 +1149,14 @@ static const csr *amg_mat(or_ctx *c, int k, int which) {
 
 /* dims[0..2] = rows, cols, nnz of the selected matrix; -1 when absent */
 int or_mat_dims(or_ctx *c, int amg, int lvl, int which, int *dims) {
-    const csr *a = amg ? amg_mat(c, lvl, which) : mgr_mat(c, lvl, which);
+    const csr *a = amg ? amg_mat(c, amg, lvl, which) : mgr_mat(c, lvl, which);
     if (!a) { dims[0] = dims[1] = dims[2] = -1; return OR_INVALID; }
     dims[0] = a->n; dims[1] = a->m; dims[2] = a->nnz;
     return OR_OK;
 }
 
 int or_mat_copy(or_ctx *c, int amg, int lvl, int which, int *rp, int *ci, double *v) {
-    const csr *a = amg ? amg_mat(c, lvl, which) : mgr_mat(c, lvl, which);
+    const csr *a = amg ? amg_mat(c, amg, lvl, which) : mgr_mat(c, lvl, which);
     if (!a) return OR_INVALID;
     memcpy(rp, a->rp, ((size_t)a->n + 1) * sizeof(int));
     memcpy(ci, a->ci, (size_t)a->nnz * sizeof(int));
@@ -1134,10 +1173,17 @@ int or_mgr_dinv(or_ctx *c, int l, double *dinv, int *gsize) {
     return OR_OK;
 }
 
-int or_amg_cf(or_ctx *c, int k, int *cf) {
-    if (k < 0 || k >= c->amg.nlev - 1) return OR_INVALID;
-    memcpy(cf, c->amg.lev[k].cf, (size_t)c->amg.lev[k].A.n * sizeof(int));
+int or_amg_cf(or_ctx *c, int amg, int k, int *cf) {
+    amg_h *H = amg_of(c, amg);
+    if (!H || k < 0 || k >= H->nlev - 1) return OR_INVALID;
+    memcpy(cf, H->lev[k].cf, (size_t)H->lev[k].A.n * sizeof(int));
     return OR_OK;
+}
+
+/* AMG levels of hierarchy amg (as above); 0 when there is none */
+int or_amg_nlevels_of(or_ctx *c, int amg) {
+    amg_h *H = amg_of(c, amg);
+    return H ? H->nlev : 0;
 }
 
 int or_amg_coarse_n(or_ctx *c) { return c->amg.nco; }

@@ -21,7 +21,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libmgr_oracle.so")
 
 OK, INVALID, NOMEM, SINGULAR, NOT_CONVERGED = 0, 1, 2, 4, 5
-RELAX = {"jacobi": 0, "l1_jacobi": 1, "block_jacobi": 2}
+RELAX = {"jacobi": 0, "l1_jacobi": 1, "block_jacobi": 2, "amg": 3}
 
 
 def build(force: bool = False) -> str:
@@ -45,7 +45,7 @@ def lib():
         L = C.CDLL(LIB)
         vp, ip, dp = C.c_void_p, C.c_int, C.c_double
         L.or_setup.restype = vp
-        L.or_setup.argtypes = [ip, ip, vp, vp, vp, vp, ip, vp, vp, vp, dp, ip, ip, ip, ip, vp]
+        L.or_setup.argtypes = [ip, ip, vp, vp, vp, vp, ip, vp, vp, vp, vp, dp, ip, ip, ip, ip, vp]
         L.or_free.argtypes = [vp]
         L.or_apply.argtypes = [vp, vp, vp]
         L.or_apply_transpose.argtypes = [vp, vp, vp]
@@ -59,7 +59,8 @@ def lib():
         L.or_mat_dims.argtypes = [vp, ip, ip, ip, vp]
         L.or_mat_copy.argtypes = [vp, ip, ip, ip, vp, vp, vp]
         L.or_mgr_dinv.argtypes = [vp, ip, vp, vp]
-        L.or_amg_cf.argtypes = [vp, ip, vp]
+        L.or_amg_cf.argtypes = [vp, ip, ip, vp]
+        L.or_amg_nlevels_of.argtypes = [vp, ip]
         L.or_amg_split_interp.argtypes = [ip, vp, vp, vp, vp, dp, ip, ip, vp, vp, vp, vp, ip, vp]
         L.or_amg_strength.argtypes = [ip, vp, vp, vp, vp, dp, vp, vp, ip]
         _lib = L
@@ -111,6 +112,7 @@ class Options:
     max_coarse: int = 1024
     pmax: int = 4
     num_functions: int = 1
+    relax_functions: list = field(default_factory=list)
     restart: int = 30
 
 
@@ -119,7 +121,8 @@ class Oracle:
 
     def __init__(self, sysm, opts: Options | None = None):
         if opts is None:
-            opts = Options(relax=list(sysm.relax), num_functions=sysm.num_functions)
+            opts = Options(relax=list(sysm.relax), num_functions=sysm.num_functions,
+                           relax_functions=list(getattr(sysm, "relax_functions", ())))
         L = lib()
         nl = sysm.num_levels
         self.opts = opts
@@ -129,11 +132,12 @@ class Oracle:
         rt = np.array([RELAX[r] for r in (opts.relax + ["jacobi"] * nl)[:nl]] + [0], np.int32)
         sw = np.array(((opts.sweeps or []) + [1] * nl)[:nl] + [1], np.int32)
         wt = np.array(((opts.weights or []) + [1.0] * nl)[:nl] + [1.0], np.float64)
-        self._keep += [rt, sw, wt]
+        fn = np.array(((opts.relax_functions or []) + [1] * nl)[:nl] + [1], np.int32)
+        self._keep += [rt, sw, wt, fn]
         st = np.zeros(1, np.int32)
         rp, ci, v, lv = self._keep[:4]
         self.h = L.or_setup(sysm.nb, sysm.b, _p(rp), _p(ci), _p(v), _p(lv), nl, _p(rt), _p(sw),
-                            _p(wt), opts.theta, opts.max_levels, opts.max_coarse, opts.pmax,
+                            _p(wt), _p(fn), opts.theta, opts.max_levels, opts.max_coarse, opts.pmax,
                             opts.num_functions, _p(st))
         self.status = int(st[0])
         if not self.h:
@@ -197,15 +201,23 @@ class Oracle:
         the final coarse block handed to AMG."""
         return self._mat(0, lvl, self.MGR_WHICH[which])
 
-    def amg_matrix(self, k, which="A"):
-        return self._mat(1, k, {"A": 0, "P": 1}[which])
+    def amg_matrix(self, k, which="A", frelax_level=None):
+        """AMG level k of the final coarse block, or of MGR level
+        ``frelax_level``'s AMG F-relaxation."""
+        amg = 1 if frelax_level is None else 2 + frelax_level
+        return self._mat(amg, k, {"A": 0, "P": 1}[which])
 
-    def amg_cf(self, k):
-        n = self.amg_matrix(k, "A")[3][0]
+    def amg_cf(self, k, frelax_level=None):
+        amg = 1 if frelax_level is None else 2 + frelax_level
+        n = self.amg_matrix(k, "A", frelax_level)[3][0]
         cf = np.zeros(n, np.int32)
-        if lib().or_amg_cf(self.h, k, _p(cf)):
+        if lib().or_amg_cf(self.h, amg, k, _p(cf)):
             return None
         return cf
+
+    def frelax_amg_nlevels(self, lvl):
+        """AMG levels of MGR level ``lvl``'s F-relaxation (0: not AMG)."""
+        return lib().or_amg_nlevels_of(self.h, 2 + lvl)
 
     def mgr_dinv(self, lvl):
         rp = self.mgr_matrix(lvl, "AFF")[0]

@@ -34,10 +34,13 @@ class BlockSystem:
     dof_level: np.ndarray
     num_levels: int
     rhs: np.ndarray
-    # per-level relaxation type names ("jacobi", "l1_jacobi", "block_jacobi")
+    # per-level relaxation type names ("jacobi", "l1_jacobi", "block_jacobi",
+    # "amg": one AMG V-cycle on A_FF)
     relax: list = field(default_factory=list)
     # AMG "unknown approach" function count on the final coarse block
     num_functions: int = 1
+    # per-level function count of an "amg" F-relaxation's hierarchy
+    relax_functions: list = field(default_factory=list)
     # dofs that are identity padding (excluded from algorithmic byte counts)
     n_pad: int = 0
     meta: dict = field(default_factory=dict)

@@ -16,8 +16,14 @@ Recipe (a synthetic stand-in for the paper's GEOSX fracture model, App. C):
   * A symmetric per-field diagonal scaling (one factor for u, one for p)
     brings both block diagonals to O(1); both sides see the scaled matrix.
   * Fracture pressures are packed three per 3x3 block row after the nodes.
-  * Labels: p -> level 0 (F, l1-Jacobi), u -> level 1 (C, AMG with the
-    unknown approach, 3 functions).  This is MGR_P of Sec. 4.3.
+  * Labels, strategy "mgr_p" (default): p -> level 0 (F, l1-Jacobi),
+    u -> level 1 (C, AMG with the unknown approach, 3 functions).  This is
+    MGR_P of Sec. 4.3.
+  * Strategy "mgr_u" (MGR_U of Sec. 4.3): u -> level 0 (F), relaxed by one
+    AMG V-cycle on A_uu with the unknown approach (3 functions), and
+    D_uu = diag(A_uu) in the interpolation; p -> level 1, the final coarse
+    block S = A_pp - A_pu D_uu^-1 A_up, one AMG V-cycle (1 function).  The
+    padding dofs keep label 0.
   * rhs ~ N(0,1).
 """
 from __future__ import annotations
@@ -60,7 +66,7 @@ def q1_unit_stiffness(nu=0.25):
     return K
 
 
-def make_poromech(ne=64, nf=48, seed=0, name="poromech") -> BlockSystem:
+def make_poromech(ne=64, nf=48, seed=0, name="poromech", strategy="mgr_p") -> BlockSystem:
     nn1 = ne + 1
     NN = nn1 ** 3
     h, nu, eta, Kf, dt = 4.0, 0.25, 0.01, 2e9, 1.0
@@ -155,10 +161,20 @@ def make_poromech(ne=64, nf=48, seed=0, name="poromech") -> BlockSystem:
         rows.append(np.array([nb - 1])); cols.append(np.array([nb - 1])); vals.append(pb)
     rp, ci, val = assemble_bsr(nb, 3, np.concatenate(rows), np.concatenate(cols),
                                np.concatenate(vals, 0))
-    lvl = np.concatenate([np.ones(NN * 3, np.int8), np.zeros(nbp * 3, np.int8)])
     rhs = rs["rhs"].standard_normal(nb * 3)
     if npad:
         rhs[-npad:] = 0.0
+    meta = dict(ne=ne, nf=nf, seed=seed, su=su, sp=sp, strategy=strategy)
+    if strategy == "mgr_u":
+        lvl = np.concatenate([np.zeros(NN * 3, np.int8), np.ones(nbp * 3, np.int8)])
+        if npad:
+            lvl[-npad:] = 0
+        return BlockSystem(name=name, b=3, row_ptr=rp, col_idx=ci, val=val, dof_level=lvl,
+                           num_levels=1, rhs=rhs, relax=["amg"], num_functions=1,
+                           relax_functions=[3], n_pad=npad, meta=meta)
+    if strategy != "mgr_p":
+        raise ValueError(f"unknown poromechanics strategy {strategy!r}")
+    lvl = np.concatenate([np.ones(NN * 3, np.int8), np.zeros(nbp * 3, np.int8)])
     return BlockSystem(name=name, b=3, row_ptr=rp, col_idx=ci, val=val, dof_level=lvl,
                        num_levels=1, rhs=rhs, relax=["l1_jacobi"], num_functions=3,
-                       n_pad=npad, meta=dict(ne=ne, nf=nf, seed=seed, su=su, sp=sp))
+                       n_pad=npad, meta=meta)

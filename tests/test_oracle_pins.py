@@ -340,6 +340,13 @@ def test_amg_vcycle_convergence_factor_poisson():
     (lambda: make_compositional(8, 8, 2, nwell_side=2),
      O.Options(relax=["block_jacobi", "block_jacobi"], sweeps=[2, 1])),
     (lambda: make_poromech(6, 4), None),
+    (lambda: make_poromech(6, 4, strategy="mgr_u"),
+     O.Options(relax=["amg"], relax_functions=[3], max_coarse=32)),
+    # a nonsymmetric A_FF (upwinded saturation block): the transposed
+    # V-cycle differs from the forward one
+    (lambda: make_two_phase(8, 6, 3), O.Options(relax=["amg"], max_coarse=16)),
+    (lambda: make_poromech(6, 4, strategy="mgr_u"),
+     O.Options(relax=["amg"], relax_functions=[3], sweeps=[2], weights=[0.8], max_coarse=32)),
 ])
 def test_transpose_cycle_is_adjoint(make, opts):
     s = make()
@@ -375,3 +382,100 @@ def test_compositional_and_poromech_small_converge():
     for s in (make_compositional(16, 16, 4), make_poromech(8, 4)):
         r = O.Oracle(s).solve(s.rhs, rtol=1e-8)
         assert r["status"] == 0 and r["relres"] <= 1e-8
+
+
+# ------------------------------------- AMG F-relaxation (MGR_U, Sec. 4.3)
+def _mgr_cycle_dense(A, F, Cc, K):
+    """Algorithm 1 with F-relaxation operator K, W = -diag(A_FF)^-1 A_FC
+    (Jacobi interpolation, D_uu = diag(A_uu)) and an exact coarse solve, as
+    one dense matrix M^-1 = [K 0; 0 0] + [W; I] S^-1 [-A_CF K, I]."""
+    AFF, AFC = A[np.ix_(F, F)], A[np.ix_(F, Cc)]
+    ACF, ACC = A[np.ix_(Cc, F)], A[np.ix_(Cc, Cc)]
+    W = -AFC / np.diag(AFF)[:, None]
+    S = ACC + ACF @ W
+    nF, nC = F.size, Cc.size
+    Mf = np.zeros((A.shape[0], A.shape[0]))
+    blk = np.zeros((nF + nC, nF + nC))
+    blk[:nF, :nF] = K
+    Pc = np.vstack([W, np.eye(nC)])
+    Rc = np.hstack([-ACF @ K, np.eye(nC)])
+    blk += Pc @ np.linalg.solve(S, Rc)
+    order = np.concatenate([F, Cc])
+    Mf[np.ix_(order, order)] = blk
+    return Mf
+
+
+@pytest.mark.parametrize("sweeps,omega", [(1, 1.0), (2, 0.8), (3, 0.6)])
+def test_amg_frelax_exact_grids_match_dense_cycle(sweeps, omega):
+    """MGR_U with both AMG hierarchies a single dense level (max_coarse above
+    both block sizes): one V-cycle on A_uu is an exact solve, so s weighted
+    sweeps from zero give K = (1 - (1 - omega)^s) A_uu^-1, and the MGR cycle
+    and its transpose equal the dense operator of Algorithm 1 with that K."""
+    s = make_poromech(6, 4, strategy="mgr_u")
+    o = O.Oracle(s, O.Options(relax=["amg"], relax_functions=[3], sweeps=[sweeps],
+                              weights=[omega], max_coarse=4096))
+    assert o.frelax_amg_nlevels(0) == 1 and o.amg_nlevels == 1
+    A = dense_of(s)
+    F = np.flatnonzero(s.dof_level == 0); Cc = np.flatnonzero(s.dof_level == 1)
+    K = (1 - (1 - omega) ** sweeps) * np.linalg.inv(A[np.ix_(F, F)])
+    Mi = _mgr_cycle_dense(A, F, Cc, K)
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(s.n)
+    ref = Mi @ v
+    assert np.linalg.norm(o.apply(v) - ref) <= 1e-10 * np.linalg.norm(ref)
+    reft = Mi.T @ v
+    assert np.linalg.norm(o.apply_transpose(v) - reft) <= 1e-10 * np.linalg.norm(reft)
+
+
+def test_amg_frelax_on_diagonal_F_block_is_direct():
+    """An AMG F-relaxation of a diagonal A_FF (MGR_P on the mimetic system)
+    finds no strong couplings, keeps one level and solves A_FF exactly; with
+    an exact coarse solve the cycle is A^-1 and FGMRES takes one iteration."""
+    s = make_mimetic(4, 4, 4)
+    o = O.Oracle(s, O.Options(relax=["amg"], relax_functions=[1]))
+    assert o.frelax_amg_nlevels(0) == 1 and o.amg_nlevels == 1
+    A = dense_of(s)
+    v = np.random.default_rng(3).standard_normal(s.n)
+    ref = np.linalg.solve(A, v)
+    assert np.linalg.norm(o.apply(v) - ref) <= 1e-10 * np.linalg.norm(ref)
+    r = o.solve(s.rhs, rtol=1e-12)
+    assert r["status"] == 0 and r["iters"] == 1
+
+
+def test_amg_frelax_hierarchy_is_galerkin_on_A_uu():
+    """The F-relaxation hierarchy starts from A_FF itself (not A or the
+    coarse block) and every coarser operator is P^T A P, densely; the
+    unknown approach keeps P from mixing displacement components."""
+    s = make_poromech(6, 4, strategy="mgr_u")
+    o = O.Oracle(s, O.Options(relax=["amg"], relax_functions=[3], max_coarse=32))
+    nl = o.frelax_amg_nlevels(0)
+    assert nl >= 3
+    A0 = csr_dense(o.amg_matrix(0, "A", frelax_level=0))
+    assert np.array_equal(A0, csr_dense(o.mgr_matrix(0, "AFF")))
+    func = np.arange(A0.shape[0]) % 3
+    for k in range(nl - 1):
+        Ak = csr_dense(o.amg_matrix(k, "A", frelax_level=0))
+        P = csr_dense(o.amg_matrix(k, "P", frelax_level=0))
+        Ac = csr_dense(o.amg_matrix(k + 1, "A", frelax_level=0))
+        ref = P.T @ Ak @ P
+        assert np.max(np.abs(Ac - ref)) <= 1e-12 * np.max(np.abs(ref))
+        cf = o.amg_cf(k, frelax_level=0)
+        assert set(np.unique(cf)) <= {-1, 1}
+        # each coarse column takes the function of the C point it comes from
+        cfunc = func[cf == 1]
+        rows, cols = np.nonzero(P)
+        assert np.all(func[rows] == cfunc[cols])
+        func = cfunc
+
+
+def test_mgr_u_fewer_iterations_than_mgr_p():
+    """Sec. 4.3 / Table 7: eliminating the displacement first (MGR_U, AMG
+    F-relaxation) needs fewer FGMRES iterations than eliminating the
+    fracture pressure first (MGR_P) on the same system."""
+    its = {}
+    for strat in ("mgr_p", "mgr_u"):
+        s = make_poromech(16, 8, strategy=strat)
+        r = O.Oracle(s).solve(s.rhs, rtol=1e-8, maxit=500)
+        assert r["status"] == 0
+        its[strat] = r["iters"]
+    assert its["mgr_u"] < its["mgr_p"], its
