@@ -68,7 +68,7 @@ typedef struct {
     const int8_t *dof_level;
 } mgr_labels;
 
-enum { MGR_RELAX_JACOBI = 0, MGR_RELAX_L1_JACOBI = 1, MGR_RELAX_BLOCK_JACOBI = 2 };
+enum { MGR_RELAX_JACOBI = 0, MGR_RELAX_L1_JACOBI = 1, MGR_RELAX_BLOCK_JACOBI = 2, MGR_RELAX_AMG = 3 };
 enum { MGR_PREC_FP64 = 0, MGR_PREC_FP32 = 1 };
 #define MGR_MAX_LEVELS 8
 
@@ -76,6 +76,13 @@ enum { MGR_PREC_FP64 = 0, MGR_PREC_FP32 = 1 };
  * Options.  Per MGR level l: F-relaxation type (D_FF of Eq. 4 is the same
  * matrix: its diagonal, its l1-row-scaled diagonal, or its per-block-row
  * F-by-F blocks), number of sweeps (from z = 0) and weight omega.
+ * MGR_RELAX_AMG (MGR_U of Sec. 4.3): each sweep applies one AMG V(1,1)
+ * cycle on A_FF, from an AMG hierarchy of A_FF built at setup with the AMG
+ * parameters below and relax_functions[l] functions of the unknown approach
+ * (function of an F dof = its F index mod relax_functions[l]); the
+ * interpolation uses D_FF = diag(A_FF).  A sweep computes
+ * z_F += omega * B (v_F - A_FF z_F) with B the V-cycle.  Batched solves do
+ * not take it (MGR_ERR_UNSUPPORTED).
  * AMG: strength threshold theta, level and coarse-size limits, max
  * interpolation entries per row (0 = no truncation), number of functions
  * of the unknown approach (function of a coarse-block dof = its index mod
@@ -100,6 +107,7 @@ typedef struct {
     int32_t restart;
     int32_t use_graphs;
     int32_t amg_tail_nnz;
+    int32_t relax_functions[MGR_MAX_LEVELS];
 } mgr_options;
 
 /* Solve report.  level_rows/level_nnz list the MGR levels, then the AMG levels. */
@@ -115,7 +123,7 @@ typedef struct {
 
 /* Defaults: Jacobi, 1 sweep, omega 1 on every level; theta 0.25, 25 AMG
  * levels, coarsest <= 1024 rows, P_max 4, 1 function; FP64; m = 30; graphs on;
- * no fused AMG tail. */
+ * no fused AMG tail; 1 function in every F-relaxation AMG hierarchy. */
 void mgr_options_default(mgr_options *opt);
 
 /*
@@ -231,15 +239,25 @@ const char *mgr_last_error(mgr_handle h);
  * For parity tests and tooling.  which: 0 = the level matrix; for MGR
  * levels 1 = A_FF, 2 = A_FC, 3 = A_CF, 4 = W; for AMG levels 1 = P.
  * amg = 0 selects MGR level `level` (level == mgr levels is the final coarse
- * block), amg = 1 AMG level `level`.  dims (host int32[3]) receives rows,
+ * block), amg = 1 AMG level `level` of the final coarse block's hierarchy,
+ * amg = 2 + l AMG level `level` of MGR level l's AMG F-relaxation.  dims (host int32[3]) receives rows,
  * cols, nnz; when rp/ci/v (host) are non-NULL they receive the CSR arrays
  * (rp: rows+1, ci and v: nnz).  INVALID if the matrix does not exist.
  */
 mgr_status mgr_get_matrix(mgr_handle h, int32_t amg, int32_t level, int32_t which, int32_t *dims,
                           int32_t *rp, int32_t *ci, double *v);
 
-/* AMG level C/F marks (host int32[rows]: +1 C, -1 F). */
+/* AMG level C/F marks (host int32[rows]: +1 C, -1 F) of the final coarse
+ * block's hierarchy. */
 mgr_status mgr_get_cf(mgr_handle h, int32_t level, int32_t *cf);
+
+/* The same for hierarchy amg: 1 = the final coarse block's, 2 + l = the AMG
+ * F-relaxation hierarchy of MGR level l.  INVALID if there is none or the
+ * level has no C/F split (the coarsest). */
+mgr_status mgr_get_amg_cf(mgr_handle h, int32_t amg, int32_t level, int32_t *cf);
+
+/* AMG levels of hierarchy amg (numbered as above); 0 if it does not exist. */
+int32_t mgr_get_amg_levels(mgr_handle h, int32_t amg);
 
 /* MGR level D_FF^{-1}: per F point 4 slots (its row of the block inverse)
  * and its block size (host double[nF*4], int32[nF]). */

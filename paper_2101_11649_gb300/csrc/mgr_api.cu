@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <new>
 #include <type_traits>
 #include <chrono>
 #include <string>
@@ -29,6 +30,8 @@ void launch_init_g(double *g, int m, const double *beta, cudaStream_t s);
 void launch_solve_upper(int k, int m, const double *H, const double *g, double *y, cudaStream_t s);
 void launch_iota(int *a, int n, cudaStream_t s);
 void launch_gather_int(const int *idx, int n, const int *v, int *out, cudaStream_t s);
+template <class T>
+void launch_frelax_scale(int nF, T omega, const T *t, T *zF, int accumulate, cudaStream_t s);
 
 struct MgrLevel {
     int n = 0, nF = 0, nC = 0;
@@ -42,6 +45,11 @@ struct MgrLevel {
     // work vectors (FP64 and FP32 variants)
     double *zF = nullptr, *rF = nullptr, *vC = nullptr, *eC = nullptr;
     float *zF32 = nullptr, *rF32 = nullptr, *vC32 = nullptr, *eC32 = nullptr;
+    // AMG F-relaxation (MGR_RELAX_AMG): the hierarchy of A_FF and the
+    // V-cycle output of a weighted or repeated sweep
+    struct AmgH *famg = nullptr;
+    double *tF = nullptr;
+    float *tF32 = nullptr;
 };
 
 struct AmgLevel {
@@ -52,6 +60,20 @@ struct AmgLevel {
     int nc = 0;
     double *r = nullptr, *x = nullptr, *xw = nullptr, *res = nullptr;
     float *r32 = nullptr, *x32 = nullptr, *xw32 = nullptr, *res32 = nullptr;
+};
+
+// One AMG hierarchy: the final coarse block's, or the one an AMG
+// F-relaxation (MGR_U, Sec. 4.3) builds on A_FF of its MGR level.
+struct AmgH {
+    int namg = 0;
+    AmgLevel amg[32];
+    int nco = 0;
+    double *coinv = nullptr, *coinvT = nullptr;
+    // fused AMG tail (levels tail_k .. namg-1 in one cooperative launch), -1: off
+    int tail_k = -1, tail_grid = 0;
+    unsigned *tail_sync = nullptr;  // grid barrier words (arrivals, generation, error)
+    TailPlan *tail_plan[2] = {nullptr, nullptr};  // device phase lists [trans]
+    int frelax = 0;                 // 1: an F-relaxation hierarchy (profile names)
 };
 
 struct Krylov {
@@ -102,14 +124,7 @@ struct mgr_ctx {
     int8_t *dlevel = nullptr;
     int nlev = 0;
     MgrLevel lev[MGR_MAX_LEVELS];
-    int namg = 0;
-    AmgLevel amg[32];
-    int nco = 0;
-    double *coinv = nullptr, *coinvT = nullptr;
-    // fused AMG tail (levels tail_k .. namg-1 in one cooperative launch), -1: off
-    int tail_k = -1, tail_grid = 0;
-    unsigned *tail_sync = nullptr;  // grid barrier words (arrivals, generation, error)
-    TailPlan *tail_plan[2] = {nullptr, nullptr};  // device phase lists [trans]
+    AmgH H;  // the final coarse block's AMG hierarchy
     int *errw = nullptr;
     Krylov kr;
     Prof prof;
@@ -119,7 +134,7 @@ struct mgr_ctx {
 
 static thread_local std::string g_last_error;
 
-static int setup_tail(mgr_handle h, int tail_nnz, cudaStream_t s, Arena &ar);
+static int setup_tail(mgr_handle h, AmgH &G, int tail_nnz, cudaStream_t s, Arena &ar);
 
 static mgr_status fail(mgr_handle h, mgr_status st, const std::string &msg) {
     if (h) h->err = msg;
@@ -201,6 +216,7 @@ extern "C" void mgr_options_default(mgr_options *o) {
     o->restart = 30;
     o->use_graphs = 1;
     o->amg_tail_nnz = 0;
+    for (int l = 0; l < MGR_MAX_LEVELS; l++) o->relax_functions[l] = 1;
 }
 
 // ---------------------------------------------------------------- helpers
@@ -220,20 +236,23 @@ static int to_f32(mgr_handle h, DCSR &M) {
     return 0;
 }
 
-static mgr_status setup_amg(mgr_handle h, DCSR A0) {
+// AMG setup of hierarchy G on A0 (strength, PMIS, extended+i, Galerkin
+// products, l1 smoother scaling, dense inverse of the coarsest grid) with
+// nfunc functions of the unknown approach.
+static mgr_status setup_amg(mgr_handle h, AmgH &G, DCSR A0, int nfunc) {
     Arena &ar = h->ar;
     cudaStream_t s = h->s;
     const mgr_options &o = h->opt;
     int maxl = o.amg_max_levels < 1 ? 1 : (o.amg_max_levels > 32 ? 32 : o.amg_max_levels);
-    h->amg[0].A = A0;
-    h->amg[0].func = ar.alloc<int>(A0.n + 1);
-    if (!h->amg[0].func) return fail(h, MGR_ERR_NOMEM, "amg func");
-    launch_iota_mod(h->amg[0].func, A0.n, o.amg_num_functions, s);
+    G.amg[0].A = A0;
+    G.amg[0].func = ar.alloc<int>(A0.n + 1);
+    if (!G.amg[0].func) return fail(h, MGR_ERR_NOMEM, "amg func");
+    launch_iota_mod(G.amg[0].func, A0.n, nfunc < 1 ? 1 : nfunc, s);
     int k = 0;
     for (;;) {
-        AmgLevel &L = h->amg[k];
+        AmgLevel &L = G.amg[k];
         int n = L.A.n;
-        h->namg = k + 1;
+        G.namg = k + 1;
         if (transpose(L.A, L.AT, s, ar)) return fail(h, MGR_ERR_NOMEM, "amg transpose");
         if (n <= o.amg_max_coarse || k + 1 >= maxl) break;
         uint8_t *sflag = ar.alloc<uint8_t>(L.A.nnz + 1);
@@ -258,7 +277,7 @@ static mgr_status setup_amg(mgr_handle h, DCSR A0) {
         if (transpose(L.P, L.R, s, ar)) return fail(h, MGR_ERR_NOMEM, "P^T");
         DCSR AP;
         if (spgemm(L.A, L.P, nullptr, AP, s, ar)) return fail(h, MGR_ERR_NOMEM, "A P");
-        AmgLevel &C = h->amg[k + 1];
+        AmgLevel &C = G.amg[k + 1];
         if (spgemm(L.R, AP, nullptr, C.A, s, ar)) return fail(h, MGR_ERR_NOMEM, "P^T A P");
         ar.release(AP.rp); ar.release(AP.ci); ar.release(AP.v);
         C.func = ar.alloc<int>(nc + 1);
@@ -270,23 +289,23 @@ static mgr_status setup_amg(mgr_handle h, DCSR A0) {
         if (read_errw(h) & ERRW_SINGULAR) return fail(h, MGR_ERR_SINGULAR, "zero l1 row scaling in AMG smoother");
         k++;
     }
-    AmgLevel &Lc = h->amg[h->namg - 1];
-    h->nco = Lc.A.n;
-    if (h->nco > 4096) return fail(h, MGR_ERR_UNSUPPORTED, "AMG coarsening stalled above 4096 rows");
-    h->coinv = ar.alloc<double>((size_t)h->nco * h->nco + 1);
-    h->coinvT = ar.alloc<double>((size_t)h->nco * h->nco + 1);
-    if (!h->coinv || !h->coinvT) return fail(h, MGR_ERR_NOMEM, "coarsest inverse");
-    if (h->nco > 0) {
-        if (dense_inverse(Lc.A, h->coinv, h->errw, s, ar)) return fail(h, MGR_ERR_NOMEM, "coarsest");
+    AmgLevel &Lc = G.amg[G.namg - 1];
+    G.nco = Lc.A.n;
+    if (G.nco > 4096) return fail(h, MGR_ERR_UNSUPPORTED, "AMG coarsening stalled above 4096 rows");
+    G.coinv = ar.alloc<double>((size_t)G.nco * G.nco + 1);
+    G.coinvT = ar.alloc<double>((size_t)G.nco * G.nco + 1);
+    if (!G.coinv || !G.coinvT) return fail(h, MGR_ERR_NOMEM, "coarsest inverse");
+    if (G.nco > 0) {
+        if (dense_inverse(Lc.A, G.coinv, h->errw, s, ar)) return fail(h, MGR_ERR_NOMEM, "coarsest");
         if (read_errw(h) & ERRW_SINGULAR) return fail(h, MGR_ERR_SINGULAR, "singular coarsest AMG grid");
-        launch_transpose_dense(h->nco, h->coinv, h->coinvT, s);
+        launch_transpose_dense(G.nco, G.coinv, G.coinvT, s);
     }
     // FP32 copies and work vectors
-    for (int q = 0; q < h->namg; q++) {
-        AmgLevel &L = h->amg[q];
+    for (int q = 0; q < G.namg; q++) {
+        AmgLevel &L = G.amg[q];
         int n = L.A.n;
         if (to_f32(h, L.A) || to_f32(h, L.AT)) return fail(h, MGR_ERR_NOMEM, "fp32 copies");
-        if (q < h->namg - 1 && (to_f32(h, L.P) || to_f32(h, L.R))) return fail(h, MGR_ERR_NOMEM, "fp32 copies");
+        if (q < G.namg - 1 && (to_f32(h, L.P) || to_f32(h, L.R))) return fail(h, MGR_ERR_NOMEM, "fp32 copies");
         L.r = ar.alloc<double>(n + 1); L.x = ar.alloc<double>(n + 1);
         L.xw = ar.alloc<double>(n + 1); L.res = ar.alloc<double>(n + 1);
         L.r32 = ar.alloc<float>(n + 1); L.x32 = ar.alloc<float>(n + 1);
@@ -388,7 +407,7 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
         L.relax = h->opt.relax_type[l];
         L.sweeps = h->opt.relax_sweeps[l] < 1 ? 1 : h->opt.relax_sweeps[l];
         L.omega = h->opt.relax_weight[l];
-        if (L.relax < 0 || L.relax > 2) { mgr_free(h); return fail(nullptr, MGR_ERR_INVALID, "relax type"); }
+        if (L.relax < MGR_RELAX_JACOBI || L.relax > MGR_RELAX_AMG) { mgr_free(h); return fail(nullptr, MGR_ERR_INVALID, "relax type"); }
         int nl = L.n;
         int *isF = ar.alloc<int>(nl + 1), *isC = ar.alloc<int>(nl + 1);
         int *fpos = ar.alloc<int>(nl + 1), *cpos = ar.alloc<int>(nl + 1);
@@ -428,16 +447,37 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
         DCSR next;
         if (spgemm(L.ACF, L.W, &ACC, next, s, ar)) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "coarse operator"); }
         ar.release(ACC.rp); ar.release(ACC.ci); ar.release(ACC.v);
-        if (transpose(L.AFF, L.AFFT, s, ar) || transpose(L.ACF, L.ACFT, s, ar) || transpose(L.W, L.WT, s, ar)) {
+        if (L.relax == MGR_RELAX_AMG) {
+            // the F-relaxation's AMG hierarchy on A_FF (same AMG parameters as
+            // the final coarse block); its level 0 holds A_FF, A_FF^T and their
+            // FP32 copies, which the level shares
+            L.famg = new (std::nothrow) AmgH();
+            if (!L.famg) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "F-relaxation AMG"); }
+            L.famg->frelax = 1;
+            mgr_status fst = setup_amg(h, *L.famg, L.AFF, h->opt.relax_functions[l]);
+            if (fst != MGR_OK) {
+                std::string m = "F-relaxation AMG at MGR level " + std::to_string(l) + ": " + h->err;
+                mgr_free(h); return fail(nullptr, fst, m);
+            }
+            L.AFF = L.famg->amg[0].A;
+            L.AFFT = L.famg->amg[0].AT;
+        } else if (transpose(L.AFF, L.AFFT, s, ar)) {
             mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level transposes");
         }
-        if (to_f32(h, L.AFF) || to_f32(h, L.ACF) || to_f32(h, L.W) || to_f32(h, L.AFFT) ||
+        if (transpose(L.ACF, L.ACFT, s, ar) || transpose(L.W, L.WT, s, ar)) {
+            mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level transposes");
+        }
+        if ((!L.famg && (to_f32(h, L.AFF) || to_f32(h, L.AFFT))) || to_f32(h, L.ACF) || to_f32(h, L.W) ||
             to_f32(h, L.ACFT) || to_f32(h, L.WT)) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "fp32"); }
         L.fiota = ar.alloc<int>(nF + 1);
         L.zF = ar.alloc<double>(nF + 1); L.rF = ar.alloc<double>(nF + 1);
         L.vC = ar.alloc<double>(nC + 1); L.eC = ar.alloc<double>(nC + 1);
         L.zF32 = ar.alloc<float>(nF + 1); L.rF32 = ar.alloc<float>(nF + 1);
         L.vC32 = ar.alloc<float>(nC + 1); L.eC32 = ar.alloc<float>(nC + 1);
+        if (L.famg) {
+            L.tF = ar.alloc<double>(nF + 1); L.tF32 = ar.alloc<float>(nF + 1);
+            if (!L.tF || !L.tF32) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level vectors"); }
+        }
         int *g2 = ar.alloc<int>(nC + 1);
         if (!L.fiota || !L.zF || !L.rF || !L.vC || !L.eC || !L.zF32 || !L.rF32 || !L.vC32 || !L.eC32 || !g2) {
             mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level vectors");
@@ -450,7 +490,7 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
         gdof = g2;
         cur = next;
     }
-    mgr_status st = setup_amg(h, cur);
+    mgr_status st = setup_amg(h, h->H, cur, h->opt.amg_num_functions);
     if (st != MGR_OK) { std::string m = h->err; mgr_free(h); return fail(nullptr, st, m); }
     // Krylov workspace
     Krylov &K = h->kr;
@@ -479,16 +519,28 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
     // SELL-C-sigma copies of every matrix the solve phase multiplies with
     {
         int rc2 = 0;
+        auto sell_amg = [&](AmgH &G) {
+            for (int k = 0; k + 1 < G.namg && !rc2; k++) {
+                AmgLevel &A = G.amg[k];
+                DCSR *ms[] = {&A.A, &A.AT, &A.P, &A.R};
+                for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
+            }
+        };
         for (int l = 0; l < h->nlev && !rc2; l++) {
             MgrLevel &L = h->lev[l];
-            DCSR *ms[] = {&L.AFF, &L.ACF, &L.W, &L.AFFT, &L.ACFT, &L.WT};
-            for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
+            if (L.famg && L.famg->namg > 1) {
+                // A_FF and A_FF^T are the F hierarchy's level 0: one SELL copy
+                sell_amg(*L.famg);
+                L.AFF = L.famg->amg[0].A;
+                L.AFFT = L.famg->amg[0].AT;
+                DCSR *ms[] = {&L.ACF, &L.W, &L.ACFT, &L.WT};
+                for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
+            } else {
+                DCSR *ms[] = {&L.AFF, &L.ACF, &L.W, &L.AFFT, &L.ACFT, &L.WT};
+                for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
+            }
         }
-        for (int k = 0; k + 1 < h->namg && !rc2; k++) {
-            AmgLevel &A = h->amg[k];
-            DCSR *ms[] = {&A.A, &A.AT, &A.P, &A.R};
-            for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
-        }
+        sell_amg(h->H);
         if (b == 1) {
             h->Aout.n = h->Aout.m = n;
             h->Aout.nnz = (int)nnzb;
@@ -499,7 +551,7 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
         if (rc2) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "SELL copies"); }
     }
     {
-        const int rc3 = setup_tail(h, h->opt.amg_tail_nnz, s, ar);
+        const int rc3 = setup_tail(h, h->H, h->opt.amg_tail_nnz, s, ar);
         if (rc3) {
             mgr_free(h);
             return fail(nullptr, rc3 == ST_NOMEM ? MGR_ERR_NOMEM : MGR_ERR_CUDA, "fused AMG tail");
@@ -520,6 +572,7 @@ template <> struct Sel<double> {
     static double *rF(MgrLevel &L) { return L.rF; }
     static double *vC(MgrLevel &L) { return L.vC; }
     static double *eC(MgrLevel &L) { return L.eC; }
+    static double *tF(MgrLevel &L) { return L.tF; }
     static const double *dinv(MgrLevel &L) { return L.dinv; }
     static const double *dinv(AmgLevel &L) { return L.dinv; }
     static double *r(AmgLevel &L) { return L.r; }
@@ -533,6 +586,7 @@ template <> struct Sel<float> {
     static float *rF(MgrLevel &L) { return L.rF32; }
     static float *vC(MgrLevel &L) { return L.vC32; }
     static float *eC(MgrLevel &L) { return L.eC32; }
+    static float *tF(MgrLevel &L) { return L.tF32; }
     static const float *dinv(MgrLevel &L) { return L.dinv32; }
     static const float *dinv(AmgLevel &L) { return L.dinv32; }
     static float *r(AmgLevel &L) { return L.r32; }
@@ -558,8 +612,8 @@ static SellView sell_view(const DCSR &M) {
 // The phase list of levels tail_k .. namg-1 (the order of amg_cycle below).
 // false when a matrix of the tail has no SELL copy of this precision.
 template <class T>
-static bool build_tail_plan(mgr_handle h, int trans, TailPlan &P) {
-    const int kt = h->tail_k, kc = h->namg - 1;
+static bool build_tail_plan(AmgH &G, int trans, TailPlan &P) {
+    const int kt = G.tail_k, kc = G.namg - 1;
     P.nphase = 0;
     auto add = [&](int kind) -> TailPhase & {
         TailPhase &q = P.ph[P.nphase++];
@@ -568,7 +622,7 @@ static bool build_tail_plan(mgr_handle h, int trans, TailPlan &P) {
         return q;
     };
     for (int k = kt; k < kc; k++) {
-        AmgLevel &L = h->amg[k];
+        AmgLevel &L = G.amg[k];
         const DCSR &A = trans ? L.AT : L.A;
         if (!A.sptr || !sell_vals<T>(A) || !L.R.sptr || !sell_vals<T>(L.R) || !L.P.sptr || !sell_vals<T>(L.P))
             return false;
@@ -577,7 +631,7 @@ static bool build_tail_plan(mgr_handle h, int trans, TailPlan &P) {
         q.x = Sel<T>::xw(L);
         q.r = Sel<T>::r(L);
         q.y = Sel<T>::res(L);
-        AmgLevel &C = h->amg[k + 1];
+        AmgLevel &C = G.amg[k + 1];
         TailPhase &q2 = add(k + 1 < kc ? TAIL_RESTRICT_SCALED : TAIL_RESTRICT);
         q2.M = sell_view<T>(L.R);
         q2.x = Sel<T>::res(L);
@@ -588,16 +642,16 @@ static bool build_tail_plan(mgr_handle h, int trans, TailPlan &P) {
         }
     }
     TailPhase &qd = add(TAIL_DENSE);
-    qd.n = h->nco;
-    qd.inv = trans ? h->coinvT : h->coinv;
-    qd.x = Sel<T>::r(h->amg[kc]);
-    qd.y = Sel<T>::x(h->amg[kc]);
+    qd.n = G.nco;
+    qd.inv = trans ? G.coinvT : G.coinv;
+    qd.x = Sel<T>::r(G.amg[kc]);
+    qd.y = Sel<T>::x(G.amg[kc]);
     for (int k = kc - 1; k >= kt; k--) {
-        AmgLevel &L = h->amg[k];
+        AmgLevel &L = G.amg[k];
         const DCSR &A = trans ? L.AT : L.A;
         TailPhase &q = add(TAIL_PROLONG);
         q.M = sell_view<T>(L.P);
-        q.x = Sel<T>::x(h->amg[k + 1]);
+        q.x = Sel<T>::x(G.amg[k + 1]);
         q.y = Sel<T>::xw(L);
         TailPhase &q2 = add(TAIL_POST);
         q2.M = sell_view<T>(A);
@@ -612,52 +666,52 @@ static bool build_tail_plan(mgr_handle h, int trans, TailPlan &P) {
 // Choose the tail's first level and upload its phase lists (both
 // orientations).  Leaves the tail off when the option, the hierarchy or the
 // device does not allow it.
-static int setup_tail(mgr_handle h, int tail_nnz, cudaStream_t s, Arena &ar) {
-    h->tail_k = -1;
-    if (tail_nnz <= 0 || h->namg < 3) return ST_OK;
+static int setup_tail(mgr_handle h, AmgH &G, int tail_nnz, cudaStream_t s, Arena &ar) {
+    G.tail_k = -1;
+    if (tail_nnz <= 0 || G.namg < 3) return ST_OK;
     int kt = -1;
-    for (int k = 1; k < h->namg - 1; k++)
-        if (h->amg[k].A.nnz <= tail_nnz) {
+    for (int k = 1; k < G.namg - 1; k++)
+        if (G.amg[k].A.nnz <= tail_nnz) {
             kt = k;
             break;
         }
     if (kt < 0) return ST_OK;
-    if (h->namg - 1 - kt > TAIL_MAX_PHASES / 4 - 1) kt = h->namg - 1 - (TAIL_MAX_PHASES / 4 - 1);
+    if (G.namg - 1 - kt > TAIL_MAX_PHASES / 4 - 1) kt = G.namg - 1 - (TAIL_MAX_PHASES / 4 - 1);
     const int grid = amg_tail_grid();
     if (grid <= 0) return ST_OK;
-    h->tail_k = kt;
+    G.tail_k = kt;
     for (int trans = 0; trans < 2; trans++) {
         TailPlan plan;
-        const bool ok = h->opt.precision == MGR_PREC_FP32 ? build_tail_plan<float>(h, trans, plan)
-                                                          : build_tail_plan<double>(h, trans, plan);
+        const bool ok = h->opt.precision == MGR_PREC_FP32 ? build_tail_plan<float>(G, trans, plan)
+                                                          : build_tail_plan<double>(G, trans, plan);
         if (!ok) {
-            h->tail_k = -1;
+            G.tail_k = -1;
             return ST_OK;
         }
-        h->tail_plan[trans] = ar.alloc<TailPlan>(1);
-        if (!h->tail_plan[trans]) return ST_NOMEM;
-        if (cudaMemcpyAsync(h->tail_plan[trans], &plan, sizeof(TailPlan), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        G.tail_plan[trans] = ar.alloc<TailPlan>(1);
+        if (!G.tail_plan[trans]) return ST_NOMEM;
+        if (cudaMemcpyAsync(G.tail_plan[trans], &plan, sizeof(TailPlan), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return ST_CUDA;
     }
-    h->tail_sync = ar.alloc<unsigned>(4);
-    if (!h->tail_sync) return ST_NOMEM;
-    if (cudaMemsetAsync(h->tail_sync, 0, 4 * sizeof(unsigned), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    G.tail_sync = ar.alloc<unsigned>(4);
+    if (!G.tail_sync) return ST_NOMEM;
+    if (cudaMemsetAsync(G.tail_sync, 0, 4 * sizeof(unsigned), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
         return ST_CUDA;
-    h->tail_grid = grid;
+    G.tail_grid = grid;
     return ST_OK;
 }
 
 // Algorithmic bytes and FP64 FMAs of one tail launch: the sums of the
 // per-step kernel classes it replaces.
-static void tail_cost(mgr_handle h, double ts, double &bytes, double &fma) {
-    const int kt = h->tail_k, kc = h->namg - 1;
+static void tail_cost(const AmgH &G, double ts, double &bytes, double &fma) {
+    const int kt = G.tail_k, kc = G.namg - 1;
     const double f64 = ts == 8 ? 1.0 : 0.0;
     bytes = 0;
     fma = 0;
     for (int k = kt; k < kc; k++) {
-        AmgLevel &L = h->amg[k];
-        const double an = L.A.n, annz = L.A.nnz, nc = h->amg[k + 1].A.n;
+        const AmgLevel &L = G.amg[k];
+        const double an = L.A.n, annz = L.A.nnz, nc = G.amg[k + 1].A.n;
         const bool cc = (k + 1 == kc);
         bytes += annz * (ts + 4) + (an + 1) * 4 + an * (3 * ts);
         bytes += (double)L.R.nnz * (ts + 4) + (nc + 1) * 4 + an * ts + nc * ts * (cc ? 1 : 3);
@@ -665,77 +719,124 @@ static void tail_cost(mgr_handle h, double ts, double &bytes, double &fma) {
         bytes += annz * (ts + 4) + (an + 1) * 4 + an * (4 * ts);
         fma += f64 * (2 * annz + L.R.nnz + L.P.nnz + an);
     }
-    bytes += (double)h->nco * h->nco * 8 + 2.0 * h->nco * ts;
-    fma += (double)h->nco * h->nco;
+    bytes += (double)G.nco * G.nco * 8 + 2.0 * G.nco * ts;
+    fma += (double)G.nco * G.nco;
 }
+
+// Profile names of the AMG steps: [0] the final coarse block's hierarchy,
+// [1] an F-relaxation hierarchy.
+enum { NM_COARSE, NM_RESID, NM_RESTRICT, NM_PROLONG, NM_POST, NM_SCALE };
+static const char *const AMG_NAMES[2][6] = {
+    {"coarsest_dense_solve", "amg_residual", "amg_restrict", "amg_prolong", "amg_post_smooth", "amg_scale"},
+    {"frelax_coarsest_dense_solve", "frelax_amg_residual", "frelax_amg_restrict", "frelax_amg_prolong",
+     "frelax_amg_post_smooth", "frelax_amg_scale"}};
 
 // AMG V(1,1) on level k: r (TV) -> x (TV).  On entry L.xw already holds the
 // pre-smoothed iterate D_k r (l1-Jacobi from zero), written by whoever
 // produced r.  trans uses A_k^T and the transposed coarsest inverse (the
 // exact transpose of the cycle).
 template <class T, class TV>
-static void amg_cycle(mgr_handle h, int k, const TV *r, TV *x, int trans) {
+static void amg_cycle(mgr_handle h, AmgH &G, int k, const TV *r, TV *x, int trans) {
     cudaStream_t s = h->s;
-    AmgLevel &L = h->amg[k];
+    AmgLevel &L = G.amg[k];
     if constexpr (std::is_same<T, TV>::value) {
-        if (k == h->tail_k && h->tail_grid > 0 && (const void *)r == (const void *)Sel<T>::r(L) &&
+        if (k == G.tail_k && G.tail_grid > 0 && (const void *)r == (const void *)Sel<T>::r(L) &&
             (void *)x == (void *)Sel<T>::x(L)) {
             double by, fm;
-            tail_cost(h, sizeof(T), by, fm);
+            tail_cost(G, sizeof(T), by, fm);
             int rc;
             {
                 KScope ks(h, "amg_tail", k, by, fm);
-                rc = launch_amg_tail<T>(h->tail_plan[trans ? 1 : 0], h->tail_grid, h->tail_sync, s);
+                rc = launch_amg_tail<T>(G.tail_plan[trans ? 1 : 0], G.tail_grid, G.tail_sync, s);
             }
             if (rc == cudaSuccess) return;
             // a refused cooperative launch: clear it, keep to one launch per step
             cudaGetLastError();
-            h->tail_grid = 0;
+            G.tail_grid = 0;
         }
     }
-    if (k == h->namg - 1) {
-        KScope ks(h, "coarsest_dense_solve", k, (double)h->nco * h->nco * 8 + 2.0 * h->nco * sizeof(TV),
-                  (double)h->nco * h->nco);
-        launch_dense_matvec<TV>(h->nco, trans ? h->coinvT : h->coinv, r, x, s);
+    if (k == G.namg - 1) {
+        KScope ks(h, AMG_NAMES[G.frelax][NM_COARSE], k, (double)G.nco * G.nco * 8 + 2.0 * G.nco * sizeof(TV),
+                  (double)G.nco * G.nco);
+        launch_dense_matvec<TV>(G.nco, trans ? G.coinvT : G.coinv, r, x, s);
         return;
     }
     const DCSR &A = trans ? L.AT : L.A;
     const T *av = Sel<T>::v(A);
     const T *d = Sel<T>::dinv(L);
     T *xw = Sel<T>::xw(L), *res = Sel<T>::res(L);
-    AmgLevel &C = h->amg[k + 1];
-    const bool c_coarsest = (k + 1 == h->namg - 1);
+    AmgLevel &C = G.amg[k + 1];
+    const bool c_coarsest = (k + 1 == G.namg - 1);
     const double ts = sizeof(T), tv = sizeof(TV);
     const double f64 = sizeof(T) == 8 ? 1.0 : 0.0;  // FP64 FMAs only in the FP64 form
     double an = A.n, annz = A.nnz, nc = C.A.n;
     {
-        KScope ks(h, "amg_residual", k, annz * (ts + 4) + (an + 1) * 4 + an * (2 * ts + tv), f64 * annz);
+        KScope ks(h, AMG_NAMES[G.frelax][NM_RESID], k, annz * (ts + 4) + (an + 1) * 4 + an * (2 * ts + tv), f64 * annz);
         launch_amg_residual<T, TV>(A, av, xw, r, res, s);
     }
     {
-        KScope ks(h, "amg_restrict", k, (double)L.R.nnz * (ts + 4) + (nc + 1) * 4 + an * ts + nc * ts * (c_coarsest ? 1 : 3),
+        KScope ks(h, AMG_NAMES[G.frelax][NM_RESTRICT], k, (double)L.R.nnz * (ts + 4) + (nc + 1) * 4 + an * ts + nc * ts * (c_coarsest ? 1 : 3),
                   f64 * L.R.nnz);
         if (c_coarsest) launch_csr_spmv<T>(L.R, Sel<T>::v(L.R), res, Sel<T>::r(C), s);
         else launch_restrict_scaled<T>(L.R, Sel<T>::v(L.R), res, Sel<T>::r(C), Sel<T>::dinv(C), Sel<T>::xw(C), s);
     }
-    amg_cycle<T, T>(h, k + 1, Sel<T>::r(C), Sel<T>::x(C), trans);
+    amg_cycle<T, T>(h, G, k + 1, Sel<T>::r(C), Sel<T>::x(C), trans);
     {
-        KScope ks(h, "amg_prolong", k, (double)L.P.nnz * (ts + 4) + (an + 1) * 4 + nc * ts + 2 * an * ts, f64 * L.P.nnz);
+        KScope ks(h, AMG_NAMES[G.frelax][NM_PROLONG], k, (double)L.P.nnz * (ts + 4) + (an + 1) * 4 + nc * ts + 2 * an * ts, f64 * L.P.nnz);
         launch_csr_spmv_add<T>(L.P, Sel<T>::v(L.P), Sel<T>::x(C), xw, s);
     }
     {
-        KScope ks(h, "amg_post_smooth", k, annz * (ts + 4) + (an + 1) * 4 + an * (2 * ts + 2 * tv), f64 * (annz + an));
+        KScope ks(h, AMG_NAMES[G.frelax][NM_POST], k, annz * (ts + 4) + (an + 1) * 4 + an * (2 * ts + 2 * tv), f64 * (annz + an));
         launch_amg_post_smooth<T, TV>(A, av, d, r, xw, x, s);
     }
 }
 
 // x_0 = D_0 r for the AMG entry when r is not produced by a fused epilogue
 template <class T, class TV>
-static void amg_prepare(mgr_handle h, const TV *r) {
-    if (h->namg < 2) return;
-    AmgLevel &L = h->amg[0];
-    KScope ks(h, "amg_scale", 0, (double)L.A.n * (2 * sizeof(T) + sizeof(TV)));
+static void amg_prepare(mgr_handle h, AmgH &G, const TV *r) {
+    if (G.namg < 2) return;
+    AmgLevel &L = G.amg[0];
+    KScope ks(h, AMG_NAMES[G.frelax][NM_SCALE], 0, (double)L.A.n * (2 * sizeof(T) + sizeof(TV)));
     launch_scale<T, TV>(L.A.n, Sel<T>::dinv(L), r, Sel<T>::xw(L), h->s);
+}
+
+// AMG F-relaxation of MGR level l (MGR_U, Sec. 4.3): s sweeps of
+// z_F += omega B (y_F - A_FF z_F) from z_F = 0, B one AMG V(1,1) cycle on A_FF
+// (trans: the transposed cycle on A_FF^T).  Forward: y_F = v_F, gathered
+// here; transposed: y_F is already in r_F and is rebuilt for later sweeps.
+template <class T, class TV>
+static void frelax_amg(mgr_handle h, int l, const TV *v, int trans) {
+    cudaStream_t s = h->s;
+    MgrLevel &L = h->lev[l];
+    AmgH &G = *L.famg;
+    T *zF = Sel<T>::zF(L), *rF = Sel<T>::rF(L), *tF = Sel<T>::tF(L), *eC = Sel<T>::eC(L);
+    const T om = (T)L.omega;
+    const double ts = sizeof(T), tv = sizeof(TV), nF = L.nF, nC = L.nC;
+    if (!trans) {
+        KScope ks(h, "mgr_frelax_gather", l, nF * (4 + tv + ts));
+        launch_gather<T, TV>(L.fidx, L.nF, v, rF, s);
+    }
+    for (int sw = 0; sw < L.sweeps; sw++) {
+        if (sw > 0) {
+            if (!trans) {
+                KScope ks(h, "mgr_frelax_residual", l, (double)L.AFF.nnz * (ts + 4) + (nF + 1) * 4 + nF * (4 + tv + 2 * ts));
+                launch_frelax_residual<T, TV>(L.AFF, Sel<T>::v(L.AFF), L.fidx, v, zF, rF, s);
+            } else {
+                { KScope ks(h, "mgrT_interp", l, (double)L.ACFT.nnz * (ts + 4) + (nF + 1) * 4 + nC * ts + nF * (4 + tv + ts));
+                  launch_csr_axpy_gather<T, TV>(L.ACFT, Sel<T>::v(L.ACFT), eC, L.fidx, v, (T)-1, rF, s); }
+                { KScope ks(h, "mgrT_frelax_residual", l, (double)L.AFFT.nnz * (ts + 4) + (nF + 1) * 4 + nF * (4 + 3 * ts));
+                  launch_csr_axpy_gather<T, T>(L.AFFT, Sel<T>::v(L.AFFT), zF, L.fiota, rF, (T)-1, rF, s); }
+            }
+        }
+        amg_prepare<T, T>(h, G, rF);
+        if (sw == 0 && L.omega == 1.0) {
+            amg_cycle<T, T>(h, G, 0, rF, zF, trans);  // z_F = 1 * B y_F
+            continue;
+        }
+        amg_cycle<T, T>(h, G, 0, rF, tF, trans);
+        KScope ks(h, "mgr_frelax_scale", l, nF * (sw > 0 ? 3 : 2) * ts);
+        launch_frelax_scale<T>(L.nF, om, tF, zF, sw > 0, s);
+    }
 }
 
 // MGR level l forward cycle (Algorithm 1): v (TV) -> z (TV)
@@ -743,8 +844,8 @@ template <class T, class TV>
 static void mgr_cycle(mgr_handle h, int l, const TV *v, TV *z) {
     cudaStream_t s = h->s;
     if (l == h->nlev) {
-        if (l == 0) amg_prepare<T, TV>(h, v);
-        amg_cycle<T, TV>(h, 0, v, z, 0);
+        if (l == 0) amg_prepare<T, TV>(h, h->H, v);
+        amg_cycle<T, TV>(h, h->H, 0, v, z, 0);
         return;
     }
     MgrLevel &L = h->lev[l];
@@ -754,11 +855,13 @@ static void mgr_cycle(mgr_handle h, int l, const TV *v, TV *z) {
     const double ts = sizeof(T), tv = sizeof(TV);
     const double f64 = sizeof(T) == 8 ? 1.0 : 0.0;
     double nF = L.nF, nC = L.nC, gs = L.relax == 2 ? 4.0 : 1.0;
-    {
+    if (L.famg) {
+        frelax_amg<T, TV>(h, l, v, 0);
+    } else {
         KScope ks(h, "mgr_frelax_first", l, nF * (gs * ts + 4 + tv + ts + (L.relax == 2 ? 8 : 0)));
         launch_frelax_first<T, TV>(L.nF, L.fidx, L.gstart, L.gsize, dinv, om, v, zF, s);
     }
-    for (int sw = 1; sw < L.sweeps; sw++) {
+    for (int sw = 1; sw < L.sweeps && !L.famg; sw++) {
         {
             KScope ks(h, "mgr_frelax_residual", l, (double)L.AFF.nnz * (ts + 4) + (nF + 1) * 4 + nF * (4 + tv + 2 * ts));
             launch_frelax_residual<T, TV>(L.AFF, Sel<T>::v(L.AFF), L.fidx, v, zF, rF, s);
@@ -767,11 +870,11 @@ static void mgr_cycle(mgr_handle h, int l, const TV *v, TV *z) {
         launch_frelax_update<T>(L.nF, L.gstart, L.gsize, dinv, om, rF, zF, 0, s);
     }
     {
-        const bool fuse = (l + 1 == h->nlev) && h->namg > 1;
+        const bool fuse = (l + 1 == h->nlev) && h->H.namg > 1;
         KScope ks(h, "mgr_restrict", l, (double)L.ACF.nnz * (ts + 4) + (nC + 1) * 4 + nF * ts + nC * (4 + tv + ts + (fuse ? 2 * ts : 0)),
                   f64 * L.ACF.nnz);
         if (fuse) launch_mgr_restrict_scaled<T, TV>(L.ACF, Sel<T>::v(L.ACF), L.cidx, v, zF, vC,
-                                                    Sel<T>::dinv(h->amg[0]), Sel<T>::xw(h->amg[0]), s);
+                                                    Sel<T>::dinv(h->H.amg[0]), Sel<T>::xw(h->H.amg[0]), s);
         else launch_mgr_restrict<T, TV>(L.ACF, Sel<T>::v(L.ACF), L.cidx, v, zF, vC, s);
     }
     mgr_cycle<T, T>(h, l + 1, vC, eC);
@@ -788,8 +891,8 @@ template <class T, class TV>
 static void mgr_cycle_t(mgr_handle h, int l, const TV *v, TV *z) {
     cudaStream_t s = h->s;
     if (l == h->nlev) {
-        amg_prepare<T, TV>(h, v);
-        amg_cycle<T, TV>(h, 0, v, z, 1);
+        amg_prepare<T, TV>(h, h->H, v);
+        amg_cycle<T, TV>(h, h->H, 0, v, z, 1);
         return;
     }
     MgrLevel &L = h->lev[l];
@@ -805,6 +908,12 @@ static void mgr_cycle_t(mgr_handle h, int l, const TV *v, TV *z) {
     mgr_cycle_t<T, T>(h, l + 1, vC, eC);
     { KScope ks(h, "mgrT_interp", l, (double)L.ACFT.nnz * (ts + 4) + (nF + 1) * 4 + nC * ts + nF * (4 + tv + ts));
       launch_csr_axpy_gather<T, TV>(L.ACFT, Sel<T>::v(L.ACFT), eC, L.fidx, v, (T)-1, rF, s); }  // y_F
+    if (L.famg) {
+        frelax_amg<T, TV>(h, l, v, 1);
+        { KScope ks(h, "mgrT_scatter", l, (nF + nC) * (4 + ts + tv));
+          launch_scatter2<T, TV>(L.nF, L.nC, L.fidx, L.cidx, zF, eC, z, s); }
+        return;
+    }
     // K^T y_F: sweeps of z += omega D^{-T} (y - A_FF^T z) from z = 0
     cudaMemsetAsync(zF, 0, sizeof(T) * L.nF, s);
     { KScope ks(h, "mgrT_frelax_update", l, nF * (gs * ts + 3 * ts + 8));
@@ -1003,12 +1112,12 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
         }
     }
     cudaStreamSynchronize(s);
-    if (h->tail_sync) {
+    if (h->H.tail_sync) {
         unsigned terr = 0;
-        cudaMemcpyAsync(&terr, h->tail_sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&terr, h->H.tail_sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
         if (terr) {
-            cudaMemsetAsync(h->tail_sync, 0, 4 * sizeof(unsigned), s);
+            cudaMemsetAsync(h->H.tail_sync, 0, 4 * sizeof(unsigned), s);
             cudaStreamSynchronize(s);
             st = MGR_ERR_TIMEOUT;
             h->err = "a grid barrier of the fused AMG tail ran out of time";
@@ -1022,14 +1131,14 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
         info->setup_ms = h->setup_ms;
         info->solve_ms = ms;
         info->mgr_levels = h->nlev;
-        info->amg_levels = h->namg;
+        info->amg_levels = h->H.namg;
         int q = 0;
         double tot = 0, base = 0;
         for (int l = 0; l < h->nlev && q < 40; l++, q++) { info->level_rows[q] = h->lev[l].n; info->level_nnz[q] = h->lev[l].A.nnz; }
-        for (int k = 0; k < h->namg && q < 40; k++, q++) {
-            info->level_rows[q] = h->amg[k].A.n; info->level_nnz[q] = h->amg[k].A.nnz;
-            tot += h->amg[k].A.nnz;
-            if (k == 0) base = h->amg[k].A.nnz;
+        for (int k = 0; k < h->H.namg && q < 40; k++, q++) {
+            info->level_rows[q] = h->H.amg[k].A.n; info->level_nnz[q] = h->H.amg[k].A.nnz;
+            tot += h->H.amg[k].A.nnz;
+            if (k == 0) base = h->H.amg[k].A.nnz;
         }
         info->operator_complexity = base > 0 ? tot / base : 0.0;
         info->reorth_steps = reorth;
@@ -1098,6 +1207,10 @@ extern "C" mgr_status mgr_bsr_spmv(int32_t nb, int32_t b, const int32_t *row_ptr
 extern "C" void mgr_free(mgr_handle h) {
     if (!h) return;
     cudaStreamSynchronize(h->s);
+    for (int l = 0; l < MGR_MAX_LEVELS; l++) {
+        delete h->lev[l].famg;
+        h->lev[l].famg = nullptr;
+    }
     for (int d = 0; d < 2; d++)
         for (auto g : h->kr.graphs[d]) if (g) cudaGraphExecDestroy(g);
     if (h->kr.hstat) cudaFreeHost(h->kr.hstat);
@@ -1112,10 +1225,19 @@ extern "C" const char *mgr_last_error(mgr_handle h) {
 }
 
 // -------------------------------------------------------------- inspection
+// amg = 1: the final coarse block's hierarchy; 2 + l: MGR level l's AMG
+// F-relaxation hierarchy (nullptr when that level has none)
+static const AmgH *amg_of(mgr_handle h, int amg) {
+    if (amg == 1) return &h->H;
+    const int l = amg - 2;
+    if (l < 0 || l >= h->nlev) return nullptr;
+    return h->lev[l].famg;
+}
+
 static const DCSR *pick(mgr_handle h, int amg, int level, int which) {
     if (!amg) {
         if (level < 0 || level > h->nlev) return nullptr;
-        if (level == h->nlev) return which == 0 ? &h->amg[0].A : nullptr;
+        if (level == h->nlev) return which == 0 ? &h->H.amg[0].A : nullptr;
         MgrLevel &L = h->lev[level];
         switch (which) {
             case 0: return &L.A;
@@ -1126,9 +1248,10 @@ static const DCSR *pick(mgr_handle h, int amg, int level, int which) {
         }
         return nullptr;
     }
-    if (level < 0 || level >= h->namg) return nullptr;
-    if (which == 0) return &h->amg[level].A;
-    if (which == 1) return h->amg[level].P.rp ? &h->amg[level].P : nullptr;
+    const AmgH *G = amg_of(h, amg);
+    if (!G || level < 0 || level >= G->namg) return nullptr;
+    if (which == 0) return &G->amg[level].A;
+    if (which == 1) return G->amg[level].P.rp ? &G->amg[level].P : nullptr;
     return nullptr;
 }
 
@@ -1147,11 +1270,22 @@ extern "C" mgr_status mgr_get_matrix(mgr_handle h, int32_t amg, int32_t level, i
 }
 
 extern "C" mgr_status mgr_get_cf(mgr_handle h, int32_t level, int32_t *cf) {
+    return mgr_get_amg_cf(h, 1, level, cf);
+}
+
+extern "C" mgr_status mgr_get_amg_cf(mgr_handle h, int32_t amg, int32_t level, int32_t *cf) {
     if (!h || !cf) return fail(h, MGR_ERR_INVALID, "NULL argument");
-    if (level < 0 || level >= h->namg - 1 || !h->amg[level].cf) return fail(h, MGR_ERR_INVALID, "no C/F split on that level");
+    const AmgH *G = amg_of(h, amg);
+    if (!G || level < 0 || level >= G->namg - 1 || !G->amg[level].cf) return fail(h, MGR_ERR_INVALID, "no C/F split on that level");
     cudaStreamSynchronize(h->s);
-    cudaMemcpy(cf, h->amg[level].cf, sizeof(int) * h->amg[level].A.n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(cf, G->amg[level].cf, sizeof(int) * G->amg[level].A.n, cudaMemcpyDeviceToHost);
     return MGR_OK;
+}
+
+extern "C" int32_t mgr_get_amg_levels(mgr_handle h, int32_t amg) {
+    if (!h) return 0;
+    const AmgH *G = amg_of(h, amg);
+    return G ? G->namg : 0;
 }
 
 extern "C" mgr_status mgr_get_dinv(mgr_handle h, int32_t level, double *dinv, int32_t *gsize) {
@@ -1166,7 +1300,7 @@ extern "C" mgr_status mgr_get_dinv(mgr_handle h, int32_t level, double *dinv, in
 
 extern "C" mgr_status mgr_get_info(mgr_handle h, int32_t *out) {
     if (!h || !out) return fail(h, MGR_ERR_INVALID, "NULL argument");
-    out[0] = h->nlev; out[1] = h->namg; out[2] = h->n;
+    out[0] = h->nlev; out[1] = h->H.namg; out[2] = h->n;
     return MGR_OK;
 }
 
@@ -1345,7 +1479,7 @@ static void amg_io(mgr_handle h, int k, void **r, void **x) {
         *r = sel<T>(L.vC, L.vC32);
         *x = sel<T>(L.eC, L.eC32);
     } else {
-        AmgLevel &A = h->amg[k];
+        AmgLevel &A = h->H.amg[k];
         *r = sel<T>(A.r, A.r32);
         *x = sel<T>(A.x, A.x32);
     }
@@ -1374,9 +1508,9 @@ static int build_tables(mgr_batch bh) {
             BJob r; r.n = M.nC; r.rp = M.ACF.rp; r.ci = M.ACF.ci; r.v = vals_of<T>(M.ACF);
             r.x = sel<T>(M.zF, M.zF32); r.idx = M.cidx; r.r = vin; r.sr = st;
             r.o1 = sel<T>(M.vC, M.vC32); r.active = act;
-            if (l + 1 == L && h->namg > 1) {
-                r.d = sel<T>(h->amg[0].dinv, h->amg[0].dinv32);
-                r.o2 = sel<T>(h->amg[0].xw, h->amg[0].xw32);
+            if (l + 1 == L && h->H.namg > 1) {
+                r.d = sel<T>(h->H.amg[0].dinv, h->H.amg[0].dinv32);
+                r.o2 = sel<T>(h->H.amg[0].xw, h->H.amg[0].xw32);
             }
             bh->mgr_restrict[l].host.push_back(r);
             BJob w; w.n = M.nF; w.rp = M.W.rp; w.ci = M.W.ci; w.v = vals_of<T>(M.W);
@@ -1387,10 +1521,10 @@ static int build_tables(mgr_batch bh) {
             c.active = act;
             bh->mgr_scatter[l].host.push_back(c);
         }
-        const int cl = h->namg - 1;  // this system's coarsest AMG level
+        const int cl = h->H.namg - 1;  // this system's coarsest AMG level
         for (int k = 0; k < cl; k++) {
-            AmgLevel &A = h->amg[k];
-            AmgLevel &C = h->amg[k + 1];
+            AmgLevel &A = h->H.amg[k];
+            AmgLevel &C = h->H.amg[k + 1];
             void *rk, *xk;
             amg_io<T>(h, k, &rk, &xk);
             void *rc, *xc;
@@ -1413,7 +1547,7 @@ static int build_tables(mgr_batch bh) {
         {
             void *rc, *xc;
             amg_io<T>(h, cl, &rc, &xc);
-            BJob c; c.n = h->nco; c.v = h->coinv; c.r = rc; c.o1 = xc; c.active = act;
+            BJob c; c.n = h->H.nco; c.v = h->H.coinv; c.r = rc; c.o1 = xc; c.active = act;
             bh->coarse.host.push_back(c);
         }
         // outer product w = A z_j -> V_{j+1}
@@ -1654,8 +1788,10 @@ extern "C" mgr_status mgr_setup_batched(int32_t nsys, const mgr_bsr *A, const mg
     bh->nlev = cf[0].num_levels;
     bh->b = A[0].b;
     if (bh->nlev < 1) { mgr_free_batched(bh); return bfail(nullptr, MGR_ERR_UNSUPPORTED, "batched solves need at least one MGR level"); }
-    for (int l = 0; l < bh->nlev; l++)
+    for (int l = 0; l < bh->nlev; l++) {
         if (o.relax_sweeps[l] > 1) { mgr_free_batched(bh); return bfail(nullptr, MGR_ERR_UNSUPPORTED, "batched solves use one F-relaxation sweep"); }
+        if (o.relax_type[l] == MGR_RELAX_AMG) { mgr_free_batched(bh); return bfail(nullptr, MGR_ERR_UNSUPPORTED, "batched solves take diagonal or block F-relaxations"); }
+    }
     for (int s = 0; s < nsys; s++) {
         if (A[s].b != bh->b || cf[s].num_levels != bh->nlev) {
             mgr_free_batched(bh);
@@ -1671,7 +1807,7 @@ extern "C" mgr_status mgr_setup_batched(int32_t nsys, const mgr_bsr *A, const mg
             return bfail(nullptr, st, buf + m);
         }
         bh->hs.push_back(h);
-        bh->kmax = std::max(bh->kmax, h->namg - 1);
+        bh->kmax = std::max(bh->kmax, h->H.namg - 1);
     }
     bh->m = bh->hs[0]->kr.m;
     Arena &ar = bh->ar;
@@ -1828,7 +1964,7 @@ extern "C" mgr_status mgr_solve_batched(mgr_batch bh, const double *const *bvec,
             info[i].setup_ms = bh->hs[i]->setup_ms;
             info[i].solve_ms = ms;
             info[i].mgr_levels = bh->hs[i]->nlev;
-            info[i].amg_levels = bh->hs[i]->namg;
+            info[i].amg_levels = bh->hs[i]->H.namg;
         }
     }
     if (bad) return bfail(bh, MGR_ERR_INVALID, "a residual became non-finite");

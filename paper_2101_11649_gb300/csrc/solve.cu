@@ -146,6 +146,28 @@ void launch_frelax_update(int nF, const int *gstart, const int *gsize, const T *
     launch_k(k_frelax_update<T>, dim3(GRIDN(nF, 256)), dim3(256), s, nF, gstart, gsize, dinv, omega, rF, zF, transpose);
 }
 
+// AMG F-relaxation step: t = omega * (V-cycle output), rounded, then
+// z_F = t (first sweep) or z_F = z_F + t (no fused multiply-add, so the
+// two roundings match a plain multiply and add)
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+template <class T>
+__global__ void k_frelax_scale(int nF, T omega, const T *t, T *zF, int accumulate) {
+    pdl_wait();
+    pdl_launch_dependents();
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nF) return;
+    const T w = mul_rn(omega, t[f]);
+    zF[f] = accumulate ? zF[f] + w : w;
+}
+
+template <class T>
+void launch_frelax_scale(int nF, T omega, const T *t, T *zF, int accumulate, cudaStream_t s) {
+    if (nF == 0) return;
+    launch_k(k_frelax_scale<T>, dim3(GRIDN(nF, 256)), dim3(256), s, nF, omega, t, zF, accumulate);
+}
+
 // injection restriction of the residual: v_C = v[C] - A_CF z_F
 template <class T, class TV>
 void launch_mgr_restrict(const DCSR &ACF, const T *vals, const int *cidx, const TV *v,
@@ -306,6 +328,8 @@ template void launch_frelax_update<double>(int, const int *, const int *, const 
                                            const double *, double *, int, cudaStream_t);
 template void launch_frelax_update<float>(int, const int *, const int *, const float *, float,
                                           const float *, float *, int, cudaStream_t);
+template void launch_frelax_scale<double>(int, double, const double *, double *, int, cudaStream_t);
+template void launch_frelax_scale<float>(int, float, const float *, float *, int, cudaStream_t);
 template void launch_csr_spmv<double>(const DCSR &, const double *, const double *, double *,
                                       cudaStream_t);
 template void launch_csr_spmv<float>(const DCSR &, const float *, const float *, float *,

@@ -18,7 +18,7 @@ MGR_OK, MGR_ERR_INVALID, MGR_ERR_NOMEM, MGR_ERR_CUDA, MGR_ERR_SINGULAR = 0, 1, 2
 MGR_ERR_NOT_CONVERGED, MGR_ERR_TIMEOUT, MGR_ERR_UNSUPPORTED = 5, 6, 7
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "SINGULAR", 5: "NOT_CONVERGED",
                 6: "TIMEOUT", 7: "UNSUPPORTED"}
-RELAX = {"jacobi": 0, "l1_jacobi": 1, "block_jacobi": 2}
+RELAX = {"jacobi": 0, "l1_jacobi": 1, "block_jacobi": 2, "amg": 3}
 MAX_LEVELS = 8
 
 
@@ -44,7 +44,7 @@ class mgr_options(C.Structure):
                 ("amg_max_levels", C.c_int32), ("amg_max_coarse", C.c_int32),
                 ("amg_pmax", C.c_int32), ("amg_num_functions", C.c_int32),
                 ("precision", C.c_int32), ("restart", C.c_int32), ("use_graphs", C.c_int32),
-                ("amg_tail_nnz", C.c_int32)]
+                ("amg_tail_nnz", C.c_int32), ("relax_functions", C.c_int32 * MAX_LEVELS)]
 
 
 class mgr_solve_info(C.Structure):
@@ -95,6 +95,9 @@ def lib(build_if_missing: bool = True):
     L.mgr_last_error.restype = C.c_char_p
     L.mgr_get_matrix.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp]
     L.mgr_get_cf.argtypes = [vp, i32, vp]
+    L.mgr_get_amg_cf.argtypes = [vp, i32, i32, vp]
+    L.mgr_get_amg_levels.argtypes = [vp, i32]
+    L.mgr_get_amg_levels.restype = i32
     L.mgr_get_dinv.argtypes = [vp, i32, vp, vp]
     L.mgr_get_info.argtypes = [vp, vp]
     L.mgr_residual_norm_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -128,7 +131,7 @@ def _ptr(t):
 
 def options(relax=("jacobi",), sweeps=(), weights=(), theta=0.25, max_levels=25, max_coarse=1024,
             pmax=4, num_functions=1, precision="fp64", restart=30, use_graphs=True,
-            tail_nnz=None) -> mgr_options:
+            tail_nnz=None, relax_functions=()) -> mgr_options:
     o = mgr_options()
     lib().mgr_options_default(C.byref(o))
     for l, r in enumerate(relax):
@@ -147,6 +150,8 @@ def options(relax=("jacobi",), sweeps=(), weights=(), theta=0.25, max_levels=25,
     o.use_graphs = int(bool(use_graphs))
     if tail_nnz is not None:
         o.amg_tail_nnz = int(tail_nnz)
+    for l, f in enumerate(relax_functions):
+        o.relax_functions[l] = int(f)
     return o
 
 
@@ -195,6 +200,7 @@ class MGRSolver:
 
     @classmethod
     def from_system(cls, sysm, precision="fp64", **kw):
+        kw.setdefault("relax_functions", tuple(getattr(sysm, "relax_functions", ())))
         o = options(relax=tuple(sysm.relax), num_functions=sysm.num_functions, precision=precision,
                     **kw)
         return cls(sysm.row_ptr, sysm.col_idx, sysm.val, sysm.b, sysm.dof_level, sysm.num_levels,
@@ -297,11 +303,18 @@ class MGRSolver:
                                     rp.ctypes.data, ci.ctypes.data, v.ctypes.data), self.h)
         return rp, ci[:nnz], v[:nnz], (n, m)
 
-    def amg_cf(self, level):
-        n = self.matrix(1, level)[3][0]
+    def amg_cf(self, level, frelax_level=None):
+        """C/F marks of AMG level ``level`` of the final coarse block's
+        hierarchy, or of MGR level ``frelax_level``'s AMG F-relaxation."""
+        amg = 1 if frelax_level is None else 2 + int(frelax_level)
+        n = self.matrix(amg, level)[3][0]
         cf = np.zeros(n, np.int32)
-        st = lib().mgr_get_cf(self.h, int(level), cf.ctypes.data)
+        st = lib().mgr_get_amg_cf(self.h, amg, int(level), cf.ctypes.data)
         return cf if st == MGR_OK else None
+
+    def frelax_amg_levels(self, level):
+        """AMG levels of MGR level ``level``'s F-relaxation (0: not AMG)."""
+        return int(lib().mgr_get_amg_levels(self.h, 2 + int(level)))
 
     def mgr_dinv(self, level):
         rp = self.matrix(0, level, 1)[0]

@@ -11,12 +11,14 @@ from .compositional import make_compositional
 from .poromech import make_poromech
 from .batched import make_batch, batch_grids
 
-# The five named workloads at full size (small variants for fast tests).
+# The named workloads at full size (small variants for fast tests); the
+# fracture system comes with both of its strategies (MGR_P, MGR_U).
 CONFIGS = {
     "two_phase_16x16x8": lambda: make_two_phase(16, 16, 8),
     "mimetic_64": lambda: make_mimetic(64, 64, 64),
     "compositional_128x128x32": lambda: make_compositional(128, 128, 32),
     "poromech_64": lambda: make_poromech(64, 48),
+    "poromech_64_mgr_u": lambda: make_poromech(64, 48, name="poromech_mgr_u", strategy="mgr_u"),
 }
 
 __all__ = ["BlockSystem", "assemble_bsr", "make_two_phase", "make_mimetic",

@@ -6,6 +6,8 @@ the FP64 arithmetic: SpMV per entry relative to sum_j |a_ij x_j| (1e-13),
 V-cycle 1e-11 relative, FGMRES iterations +-1 and solutions 1e-8 relative
 when both are converged to 1e-12.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -28,6 +30,12 @@ SMALL = {
     "mimetic": lambda: make_mimetic(7, 6, 5),
     "compositional": lambda: make_compositional(16, 12, 4),
     "poromech": lambda: make_poromech(8, 4),
+    # MGR_U (Sec. 4.3): displacement first, one AMG V-cycle as F-relaxation
+    "poromech_mgr_u": lambda: make_poromech(8, 4, strategy="mgr_u"),
+    # an AMG F-relaxation of a nonsymmetric (upwinded) A_FF, so that the
+    # transposed V-cycle differs from the forward one
+    "two_phase_amg_relax": lambda: dataclasses.replace(make_two_phase(8, 7, 5), relax=["amg"],
+                                                       relax_functions=[1]),
 }
 
 
@@ -45,7 +53,8 @@ SMALL_COARSE = 32
 
 
 def oracle_of(sysm, **kw):
-    return O.Oracle(sysm, O.Options(relax=list(sysm.relax), num_functions=sysm.num_functions, **kw))
+    return O.Oracle(sysm, O.Options(relax=list(sysm.relax), num_functions=sysm.num_functions,
+                                    relax_functions=list(sysm.relax_functions), **kw))
 
 
 # ------------------------------------------------------------------ SpMV
@@ -214,6 +223,20 @@ def test_hierarchy_bit_exact(name):
         if k < o.amg_nlevels - 1:
             _same_csr(g.matrix(1, k, 1), o.amg_matrix(k, "P"), f"AMG P_{k}")
             assert np.array_equal(g.amg_cf(k), o.amg_cf(k)), f"C/F split level {k}"
+    _same_frelax_hierarchies(g, o, s)
+
+
+def _same_frelax_hierarchies(g, o, s):
+    """The AMG hierarchies of AMG F-relaxations (MGR_U), level by level."""
+    for l in range(s.num_levels):
+        nl = o.frelax_amg_nlevels(l)
+        assert g.frelax_amg_levels(l) == nl, (l, g.frelax_amg_levels(l), nl)
+        for k in range(nl):
+            _same_csr(g.matrix(2 + l, k, 0), o.amg_matrix(k, "A", frelax_level=l), f"F-AMG[{l}] A_{k}")
+            if k < nl - 1:
+                _same_csr(g.matrix(2 + l, k, 1), o.amg_matrix(k, "P", frelax_level=l),
+                          f"F-AMG[{l}] P_{k}")
+                assert np.array_equal(g.amg_cf(k, frelax_level=l), o.amg_cf(k, frelax_level=l))
 
 
 # -------------------------------------------------------- V-cycle, solve
@@ -228,6 +251,43 @@ def test_vcycle_parity(name):
         zg = g.apply(t(v), transpose=trans).cpu().numpy()
         zo = o.apply_transpose(v) if trans else o.apply(v)
         assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo), (trans, np.linalg.norm(zg - zo) / np.linalg.norm(zo))
+
+
+@pytest.mark.parametrize("name", ["poromech_mgr_u", "two_phase_amg_relax"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("sweeps,omega", [(2, 0.8), (3, 1.0)])
+def test_amg_frelax_sweeps_and_weight(name, precision, sweeps, omega):
+    """Repeated and weighted AMG F-relaxation sweeps, forward and transposed
+    cycle.  FP32 hierarchies against the FP64 oracle within 1e-4."""
+    s = SMALL[name]()
+    g = solver(s, precision=precision, max_coarse=SMALL_COARSE, sweeps=[sweeps], weights=[omega])
+    o = oracle_of(s, max_coarse=SMALL_COARSE, sweeps=[sweeps], weights=[omega])
+    tol = 1e-11 if precision == "fp64" else 1e-4
+    rng = np.random.default_rng(9)
+    for trans in (False, True):
+        v = rng.standard_normal(s.n)
+        zg = g.apply(t(v), transpose=trans).cpu().numpy()
+        zo = o.apply_transpose(v) if trans else o.apply(v)
+        assert np.linalg.norm(zg - zo) <= tol * np.linalg.norm(zo), (trans, np.linalg.norm(zg - zo) / np.linalg.norm(zo))
+
+
+def test_mgr_u_fewer_iterations_than_mgr_p_on_gpu():
+    """The MGR_U strategy (AMG F-relaxation of the displacement) converges in
+    fewer FGMRES iterations than MGR_P on the same fracture system."""
+    its = {}
+    for strat in ("mgr_p", "mgr_u"):
+        s = make_poromech(16, 8, strategy=strat)
+        _, info = solver(s).solve(t(s.rhs), rtol=1e-8)
+        assert info["status"] == 0
+        its[strat] = info["iterations"]
+    assert its["mgr_u"] < its["mgr_p"], its
+
+
+def test_batched_rejects_amg_frelax():
+    s = SMALL["poromech_mgr_u"]()
+    with pytest.raises(M.MGRError) as e:
+        M.MGRBatch([s, s])
+    assert e.value.status == M.MGR_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("name", list(SMALL))
@@ -347,7 +407,7 @@ def test_repeat_solves_bitwise_identical():
 
 
 # ------------------------------------------------ full-size configurations
-FULL = ["mimetic_64", "compositional_128x128x32", "poromech_64"]
+FULL = ["mimetic_64", "compositional_128x128x32", "poromech_64", "poromech_64_mgr_u"]
 
 
 @pytest.mark.slow
@@ -367,6 +427,10 @@ def test_full_size(name):
         _same_csr(g.matrix(0, l, 0), o.mgr_matrix(l, "A"), f"MGR A_{l}")
     for k in range(o.amg_nlevels):
         _same_csr(g.matrix(1, k, 0), o.amg_matrix(k, "A"), f"AMG A_{k}")
+    for l in range(s.num_levels):
+        assert g.frelax_amg_levels(l) == o.frelax_amg_nlevels(l)
+        for k in range(o.frelax_amg_nlevels(l)):
+            _same_csr(g.matrix(2 + l, k, 0), o.amg_matrix(k, "A", frelax_level=l), f"F-AMG[{l}] A_{k}")
     rng = np.random.default_rng(1)
     x = rng.standard_normal(s.n)
     y = g.spmv(t(x)).cpu().numpy()
