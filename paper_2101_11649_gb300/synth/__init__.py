@@ -12,11 +12,14 @@ from .poromech import make_poromech
 from .batched import make_batch, batch_grids
 
 # The named workloads at full size (small variants for fast tests); the
-# fracture system comes with both of its strategies (MGR_P, MGR_U).
+# compositional and fracture systems come with two reduction orders each
+# (3- and 4-level; MGR_P and MGR_U).
 CONFIGS = {
     "two_phase_16x16x8": lambda: make_two_phase(16, 16, 8),
     "mimetic_64": lambda: make_mimetic(64, 64, 64),
     "compositional_128x128x32": lambda: make_compositional(128, 128, 32),
+    "compositional_128x128x32_4level": lambda: make_compositional(
+        128, 128, 32, name="compositional_4level", strategy="mgr4"),
     "poromech_64": lambda: make_poromech(64, 48),
     "poromech_64_mgr_u": lambda: make_poromech(64, 48, name="poromech_mgr_u", strategy="mgr_u"),
 }

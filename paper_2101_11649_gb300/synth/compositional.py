@@ -22,8 +22,18 @@ Recipe (a synthetic stand-in; the paper's EOS-based model is App. B):
     hole-pressure control, even wells: zero diagonal, Sec. 4.2) or q (rate
     control, odd wells).  Perforation sources WI_k lambda_c (p_k - p_w) enter
     the cell mass balances; WI_k = K_k.
-  * Labels: cell masses and pads -> level 0 (F, 3x3 / 2x2 block-Jacobi),
-    well dofs -> level 1 (F, exact 2x2), cell pressure -> level 2 (C, AMG).
+  * Labels, strategy "mgr3" (default): cell masses and pads -> level 0
+    (F, 3x3 / 2x2 block-Jacobi), well dofs -> level 1 (F, exact 2x2), cell
+    pressure -> level 2 (C, AMG).
+  * Strategy "mgr4" (the 4-level order of Sec. 4.2, wells kept to the
+    coarsest grid): the first two rows of every cell block are swapped, so
+    that the volume constraint row is aligned with m1 (a density whose row
+    is diagonal in every unknown, like the paper's rho_2) and the first mass
+    balance with p.  Levels: m1 and pads -> 0 (Jacobi, exact), m2, m3 -> 1
+    (Jacobi), cell pressure -> 2 (F-relaxation by one AMG V-cycle on the
+    reduced pressure block, the CPR-like pressure system), well dofs -> 3
+    (the final coarse block, 2 dofs per well: one dense direct solve, its
+    BHP-controlled rows with zero diagonals included).
   * rhs ~ N(0,1) on real dofs, 0 on pads.
 """
 from __future__ import annotations
@@ -35,7 +45,9 @@ from .two_phase import _neighbor_pairs
 
 
 def make_compositional(nx=128, ny=128, nz=32, nwell_side=4, seed=0,
-                       name="compositional") -> BlockSystem:
+                       name="compositional", strategy="mgr3") -> BlockSystem:
+    if strategy not in ("mgr3", "mgr4"):
+        raise ValueError(f"unknown compositional strategy {strategy!r}")
     nc = nx * ny * nz
     rs = streams(seed, ["perm", "mass", "pres", "coup", "rhs"])
     K = np.exp(1.5 * rs["perm"].standard_normal(nc))
@@ -105,11 +117,20 @@ def make_compositional(nx=128, ny=128, nz=32, nwell_side=4, seed=0,
     nb = nc + nw
     rp, ci, val = assemble_bsr(nb, b, np.concatenate(rows), np.concatenate(cols),
                                np.concatenate(blks, 0))
-    lvl = np.concatenate([np.tile(np.array([2, 0, 0, 0], np.int8), nc),
-                          np.tile(np.array([1, 1, 0, 0], np.int8), nw)])
     rhs = rs["rhs"].standard_normal(nb * b)
     rhs[nc * b:].reshape(nw, b)[:, 2:] = 0.0
+    meta = dict(grid=(nx, ny, nz), n_wells=nw, acc=acc, seed=seed, strategy=strategy)
+    if strategy == "mgr4":
+        cell_rows = np.repeat(np.arange(nb) < nc, np.diff(rp))
+        val[cell_rows] = val[cell_rows][:, [1, 0, 2, 3], :]
+        rhs[:nc * b].reshape(nc, b)[:, [0, 1]] = rhs[:nc * b].reshape(nc, b)[:, [1, 0]]
+        lvl = np.concatenate([np.tile(np.array([2, 0, 1, 1], np.int8), nc),
+                              np.tile(np.array([3, 3, 0, 0], np.int8), nw)])
+        return BlockSystem(name=name, b=b, row_ptr=rp, col_idx=ci, val=val, dof_level=lvl,
+                           num_levels=3, rhs=rhs, relax=["jacobi", "jacobi", "amg"],
+                           num_functions=1, relax_functions=[1, 1, 1], n_pad=2 * nw, meta=meta)
+    lvl = np.concatenate([np.tile(np.array([2, 0, 0, 0], np.int8), nc),
+                          np.tile(np.array([1, 1, 0, 0], np.int8), nw)])
     return BlockSystem(name=name, b=b, row_ptr=rp, col_idx=ci, val=val, dof_level=lvl,
                        num_levels=2, rhs=rhs, relax=["block_jacobi", "block_jacobi"],
-                       num_functions=1, n_pad=2 * nw,
-                       meta=dict(grid=(nx, ny, nz), n_wells=nw, acc=acc, seed=seed))
+                       num_functions=1, n_pad=2 * nw, meta=meta)

@@ -29,6 +29,9 @@ SMALL = {
     "two_phase": lambda: make_two_phase(8, 7, 5),
     "mimetic": lambda: make_mimetic(7, 6, 5),
     "compositional": lambda: make_compositional(16, 12, 4),
+    # the 4-level order of Sec. 4.2: Jacobi, Jacobi, AMG F-relaxation of the
+    # reservoir pressure, wells solved directly on the coarsest grid
+    "compositional_4level": lambda: make_compositional(16, 12, 4, strategy="mgr4"),
     "poromech": lambda: make_poromech(8, 4),
     # MGR_U (Sec. 4.3): displacement first, one AMG V-cycle as F-relaxation
     "poromech_mgr_u": lambda: make_poromech(8, 4, strategy="mgr_u"),
@@ -407,7 +410,8 @@ def test_repeat_solves_bitwise_identical():
 
 
 # ------------------------------------------------ full-size configurations
-FULL = ["mimetic_64", "compositional_128x128x32", "poromech_64", "poromech_64_mgr_u"]
+FULL = ["mimetic_64", "compositional_128x128x32", "compositional_128x128x32_4level", "poromech_64",
+        "poromech_64_mgr_u"]
 
 
 @pytest.mark.slow

@@ -479,3 +479,49 @@ def test_mgr_u_fewer_iterations_than_mgr_p():
         assert r["status"] == 0
         its[strat] = r["iters"]
     assert its["mgr_u"] < its["mgr_p"], its
+
+
+# --------------------------- 4-level compositional order (Sec. 4.2, mgr4)
+def test_compositional_4level_first_reduction_is_exact():
+    """The volume-constraint rows, aligned with a density, are diagonal in
+    every unknown: level 0's A_FF is diagonal, so the first reduction is the
+    exact Schur complement and one Jacobi sweep is an exact F solve."""
+    s = make_compositional(8, 6, 3, nwell_side=2, strategy="mgr4")
+    o = O.Oracle(s)
+    A = dense_of(s)
+    F = np.flatnonzero(s.dof_level == 0); Cc = np.flatnonzero(s.dof_level > 0)
+    AFF = A[np.ix_(F, F)]
+    assert np.count_nonzero(AFF - np.diag(np.diag(AFF))) == 0
+    S = A[np.ix_(Cc, Cc)] - A[np.ix_(Cc, F)] @ np.linalg.solve(AFF, A[np.ix_(F, Cc)])
+    got = csr_dense(o.mgr_matrix(1, "A"))
+    assert np.max(np.abs(got - S)) <= 1e-13 * np.max(np.abs(S))
+
+
+def test_compositional_4level_keeps_wells_to_a_direct_coarsest_solve():
+    """Wells survive to the final coarse block (2 dofs per well), which is
+    solved directly (one dense level) although its BHP-control rows have zero
+    diagonals; those rows pass every reduction unchanged.  The reservoir
+    pressure level is relaxed by an AMG V-cycle."""
+    s = make_compositional(16, 12, 4, nwell_side=2, strategy="mgr4")
+    o = O.Oracle(s, O.Options(relax=list(s.relax), relax_functions=list(s.relax_functions),
+                              max_coarse=32))
+    nw = s.meta["n_wells"]
+    Af = csr_dense(o.mgr_matrix(3, "A"))
+    assert Af.shape == (2 * nw, 2 * nw) and o.amg_nlevels == 1
+    assert o.frelax_amg_nlevels(2) >= 2
+    for w in range(0, nw, 2):          # BHP control: row q = p_w
+        row = np.zeros(2 * nw); row[2 * w] = 1.0
+        assert np.array_equal(Af[2 * w + 1], row)
+    r = o.solve(s.rhs, rtol=1e-10, maxit=300)
+    assert r["status"] == 0 and r["relres"] <= 1e-10
+
+
+def test_compositional_4level_is_a_row_permutation_of_the_3level_system():
+    a3 = make_compositional(6, 5, 3, nwell_side=2)
+    a4 = make_compositional(6, 5, 3, nwell_side=2, strategy="mgr4")
+    D3, D4 = dense_of(a3), dense_of(a4)
+    nc = 6 * 5 * 3
+    perm = np.arange(a3.n)
+    perm[:4 * nc].reshape(nc, 4)[:, [0, 1]] = perm[:4 * nc].reshape(nc, 4)[:, [1, 0]]
+    assert np.array_equal(D4, D3[perm])
+    assert np.array_equal(a4.rhs, a3.rhs[perm])
