@@ -471,7 +471,8 @@ def run_gb300(args, world, rank, local):
                 ts.append(e0.elapsed_time(e1))
             return statistics.median(ts), out
 
-        for name in ("two_phase_16x16x8", "compositional_128x128x32", "compositional_128x128x32_4level",
+        for name in ("two_phase_16x16x8", "mimetic_64_tpfa_mgr_pi", "compositional_128x128x32",
+                     "compositional_128x128x32_4level",
                      "poromech_64", "poromech_64_mgr_u"):
             cs = CONFIGS[name]()
             bq = torch.as_tensor(cs.rhs, device=dev)

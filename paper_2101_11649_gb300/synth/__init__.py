@@ -12,11 +12,13 @@ from .poromech import make_poromech
 from .batched import make_batch, batch_grids
 
 # The named workloads at full size (small variants for fast tests); the
-# compositional and fracture systems come with two reduction orders each
-# (3- and 4-level; MGR_P and MGR_U).
+# mimetic (consistent MGR_P, TPFA MGR_Pi), compositional (3- and 4-level)
+# and fracture (MGR_P, MGR_U) systems come with two variants each.
 CONFIGS = {
     "two_phase_16x16x8": lambda: make_two_phase(16, 16, 8),
     "mimetic_64": lambda: make_mimetic(64, 64, 64),
+    "mimetic_64_tpfa_mgr_pi": lambda: make_mimetic(64, 64, 64, name="mimetic_tpfa",
+                                                   scheme="tpfa", strategy="mgr_pi"),
     "compositional_128x128x32": lambda: make_compositional(128, 128, 32),
     "compositional_128x128x32_4level": lambda: make_compositional(
         128, 128, 32, name="compositional_4level", strategy="mgr4"),

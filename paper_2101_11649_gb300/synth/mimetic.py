@@ -18,9 +18,16 @@ Recipe:
       Abar_pp = A_pp + D^T M^{-1} D            (diagonal)
       Abar_ppi = D^T M^{-1} C,  Abar_pip = C^T M^{-1} D,
       Abar_pipi = C^T M^{-1} C.
+  * scheme="tpfa" (the TPFA approach of Sec. 4.1): every block of A_ww is
+    diagonal, M_c = diag(1 / T_cf) with the half-transmissibilities
+    T_cf = (N_f . K N_f) / (X_f . N_f), so Abar_pipi is diagonal too.
   * Unknown order: cell pressures, then x-, y-, z-face multipliers.
-  * Labels: cells -> level 0 (F, Jacobi; Abar_pp diagonal, inverted
-    exactly), faces -> level 1 (C, AMG).  This is MGR_P, Eq. 9.
+  * Labels, strategy "mgr_p" (default): cells -> level 0 (F, Jacobi;
+    Abar_pp diagonal, inverted exactly), faces -> level 1 (C, AMG).  This
+    is MGR_P, Eq. 9.  Strategy "mgr_pi" (for TPFA): faces -> level 0 (F,
+    Jacobi on the diagonal Abar_pipi: exact relaxation and ideal
+    interpolation), cells -> level 1 (C, AMG on the exact Schur complement
+    of Eq. 8, the cell-centred TPFA operator).
   * rhs ~ N(0,1).
 """
 from __future__ import annotations
@@ -80,7 +87,10 @@ def _geometry(nx, ny, nz, distort, rng):
     return N, X, vol
 
 
-def make_mimetic(nx=64, ny=64, nz=64, seed=0, distort=0.1, name="mimetic") -> BlockSystem:
+def make_mimetic(nx=64, ny=64, nz=64, seed=0, distort=0.1, name="mimetic", scheme="consistent",
+                 strategy="mgr_p") -> BlockSystem:
+    if scheme not in ("consistent", "tpfa") or strategy not in ("mgr_p", "mgr_pi"):
+        raise ValueError(f"unknown mimetic scheme/strategy {scheme!r}/{strategy!r}")
     nc = nx * ny * nz
     rs = streams(seed, ["perm", "geom", "rhs"])
     kappa = np.exp(2.0 * rs["perm"].standard_normal(nc))
@@ -93,6 +103,12 @@ def make_mimetic(nx=64, ny=64, nz=64, seed=0, distort=0.1, name="mimetic") -> Bl
     M = XKX / vol[:, None, None] + t[:, None, None] * stab
     Minv = np.linalg.inv(M)
     Minv = 0.5 * (Minv + np.transpose(Minv, (0, 2, 1)))
+    if scheme == "tpfa":
+        # half-transmissibility of each one-sided face: (N.K N) / (X.N)
+        NKN = np.einsum("cfa,ca,cfa->cf", N, 1.0 / kinv, N)
+        Thalf = NKN / np.einsum("cfa,cfa->cf", X, N)
+        Minv = np.zeros((nc, 6, 6))
+        Minv[:, np.arange(6), np.arange(6)] = Thalf
     fid, nf = _face_ids(nx, ny, nz)
     app = 1e-3 * kappa.mean()
 
@@ -110,9 +126,12 @@ def make_mimetic(nx=64, ny=64, nz=64, seed=0, distort=0.1, name="mimetic") -> Bl
     vals = np.concatenate([v_pp, v_pf, v_fp, v_ff])
     n = nc + nf
     rp, ci, val = scalar_coo_to_bsr1(n, rows, cols, vals)
-    lvl = np.concatenate([np.zeros(nc, np.int8), np.ones(nf, np.int8)])
+    if strategy == "mgr_p":
+        lvl = np.concatenate([np.zeros(nc, np.int8), np.ones(nf, np.int8)])
+    else:
+        lvl = np.concatenate([np.ones(nc, np.int8), np.zeros(nf, np.int8)])
     rhs = rs["rhs"].standard_normal(n)
     return BlockSystem(name=name, b=1, row_ptr=rp, col_idx=ci, val=val, dof_level=lvl,
                        num_levels=1, rhs=rhs, relax=["jacobi"], num_functions=1,
                        meta=dict(grid=(nx, ny, nz), n_cells=nc, n_faces=nf, seed=seed,
-                                 distort=distort))
+                                 distort=distort, scheme=scheme, strategy=strategy))

@@ -28,6 +28,8 @@ DEV = torch.device("cuda:0")
 SMALL = {
     "two_phase": lambda: make_two_phase(8, 7, 5),
     "mimetic": lambda: make_mimetic(7, 6, 5),
+    # TPFA with the face multipliers as F-points (MGR_Pi, Sec. 4.1)
+    "mimetic_tpfa_mgr_pi": lambda: make_mimetic(7, 6, 5, scheme="tpfa", strategy="mgr_pi"),
     "compositional": lambda: make_compositional(16, 12, 4),
     # the 4-level order of Sec. 4.2: Jacobi, Jacobi, AMG F-relaxation of the
     # reservoir pressure, wells solved directly on the coarsest grid
@@ -410,7 +412,7 @@ def test_repeat_solves_bitwise_identical():
 
 
 # ------------------------------------------------ full-size configurations
-FULL = ["mimetic_64", "compositional_128x128x32", "compositional_128x128x32_4level", "poromech_64",
+FULL = ["mimetic_64", "mimetic_64_tpfa_mgr_pi", "compositional_128x128x32", "compositional_128x128x32_4level", "poromech_64",
         "poromech_64_mgr_u"]
 
 

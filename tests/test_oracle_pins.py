@@ -525,3 +525,48 @@ def test_compositional_4level_is_a_row_permutation_of_the_3level_system():
     perm[:4 * nc].reshape(nc, 4)[:, [0, 1]] = perm[:4 * nc].reshape(nc, 4)[:, [1, 0]]
     assert np.array_equal(D4, D3[perm])
     assert np.array_equal(a4.rhs, a3.rhs[perm])
+
+
+# ------------------------------------- MGR_Pi on the TPFA scheme (Sec. 4.1)
+def test_mgr_pi_tpfa_coarse_operator_is_the_harmonic_tpfa_stencil():
+    """TPFA makes Abar_pipi diagonal, so with faces as F-points one Jacobi
+    sweep and the Jacobi interpolation are exact, and the coarse operator is
+    the exact Schur complement of Eq. 8.  Eliminating the face multipliers
+    reproduces the cell-centred TPFA scheme: neighbours couple through the
+    harmonic combination T1 T2 / (T1 + T2) of their half-transmissibilities
+    (read from the matrix: Abar_ppi = -T), boundary faces carry no flux."""
+    s = make_mimetic(5, 4, 3, scheme="tpfa", strategy="mgr_pi")
+    o = O.Oracle(s)
+    A = dense_of(s)
+    nc = s.meta["n_cells"]
+    cells, faces = np.arange(nc), np.arange(nc, s.n)
+    assert np.array_equal(np.flatnonzero(s.dof_level == 1), cells)
+    Aff = A[np.ix_(faces, faces)]
+    assert np.count_nonzero(Aff - np.diag(np.diag(Aff))) == 0
+    T = -A[np.ix_(cells, faces)]                     # half-transmissibilities, [cell, face]
+    S = np.diag(np.diag(A)[:nc])
+    for f in range(faces.size):
+        on = np.flatnonzero(T[:, f])
+        tot = T[on, f].sum()
+        assert np.isclose(tot, Aff[f, f], rtol=1e-14)
+        if on.size == 2:
+            c1, c2 = on
+            h = T[c1, f] * T[c2, f] / tot
+            S[c1, c2] -= h; S[c2, c1] -= h
+            S[c1, c1] -= T[c1, f] ** 2 / tot; S[c2, c2] -= T[c2, f] ** 2 / tot
+        else:                                        # boundary face: no flux
+            S[on[0], on[0]] -= T[on[0], f]
+    got = csr_dense(o.mgr_matrix(1, "A"))
+    assert np.max(np.abs(got - S)) <= 1e-12 * np.max(np.abs(S))
+    assert max(np.count_nonzero(np.abs(S[i]) > 1e-12 * np.abs(S).max()) for i in range(nc)) <= 7
+
+
+def test_mgr_pi_tpfa_two_level_is_direct():
+    """With the coarse grid solved exactly, MGR_Pi on TPFA is a direct solver."""
+    s = make_mimetic(6, 5, 4, scheme="tpfa", strategy="mgr_pi")
+    o = O.Oracle(s)
+    assert o.amg_nlevels == 1
+    v = np.random.default_rng(8).standard_normal(s.n)
+    ref = np.linalg.solve(dense_of(s), v)
+    assert np.linalg.norm(o.apply(v) - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert o.solve(s.rhs, rtol=1e-12)["iters"] == 1
