@@ -24,6 +24,7 @@
 
 enum { OR_OK = 0, OR_INVALID = 1, OR_NOMEM = 2, OR_SINGULAR = 4, OR_NOT_CONVERGED = 5 };
 enum { OR_JACOBI = 0, OR_L1_JACOBI = 1, OR_BLOCK_JACOBI = 2, OR_AMG_RELAX = 3 };
+enum { OR_RESTRICT_INJECTION = 0, OR_RESTRICT_JACOBI = 1 };
 
 /* ------------------------------------------------------------------ CSR */
 typedef struct {
@@ -677,6 +678,9 @@ typedef struct {
     double *zF, *rF, *tF, *vC, *eC;
     int nfunc;                 /* OR_AMG_RELAX: functions of the unknown approach on A_FF */
     amg_h famg;                /* OR_AMG_RELAX: AMG hierarchy of A_FF (M_FF^{-1} = one V-cycle) */
+    int rtype;                 /* restriction: injection (Eq. 4 approx.) or [Z, I] (Eq. 5) */
+    csr Z, ZT;                 /* OR_RESTRICT_JACOBI: Z = -A_CF D^{-1} and its transpose */
+    double *qF;                /* OR_RESTRICT_JACOBI: Z^T e_C in the transposed cycle */
 } mgr_level;
 
 typedef struct or_ctx {
@@ -823,6 +827,7 @@ static void mgr_level_free(mgr_level *L) {
     free(L->gstart); free(L->gsize); free(L->dinv);
     free(L->zF); free(L->rF); free(L->tF); free(L->vC); free(L->eC);
     amg_free(&L->famg);
+    csr_free(&L->Z); csr_free(&L->ZT); free(L->qF);
 }
 
 void or_free(or_ctx *c) {
@@ -835,15 +840,40 @@ void or_free(or_ctx *c) {
 }
 
 /*
+ * Z^T = -D^{-1} A_CF^T for a diagonal D (the restriction block of Eq. 5,
+ * Z = -A_CF D^{-1}), from the transpose ACFT: row f of Z^T is row f of
+ * ACFT times -d_f, each entry formed as acc = 0 + d_f a, value -acc.
+ */
+static int build_zt(mgr_level *L) {
+    const csr *B = &L->ACFT;
+    int rc = csr_alloc(&L->ZT, B->n, B->m, B->nnz);
+    if (rc) return rc;
+    for (int f = 0; f <= B->n; f++) L->ZT.rp[f] = B->rp[f];
+    for (int f = 0; f < B->n; f++) {
+        double d = L->dinv[(size_t)f * 4];
+        for (int p = B->rp[f]; p < B->rp[f + 1]; p++) {
+            double acc = 0.0;
+            acc = acc + d * B->v[p];
+            L->ZT.ci[p] = B->ci[p];
+            L->ZT.v[p] = -acc;
+        }
+    }
+    return csr_transpose(&L->ZT, &L->Z);
+}
+
+/*
  * MGR setup (Sec. 3): for each level l < num_levels, F = {dof_level == l},
  * C = {dof_level > l}; D_FF^{-1}; W = -D^{-1} A_FC; the coarse operator
- * A_{l+1} = R~ A P~ = A_CC + A_CF W (Eq. 4 operators; the product order of
- * csr_matmat_add with A_CC added last).  The final coarse block gets AMG.
+ * A_{l+1} = R~ A P~.  With injection (Eq. 4 approx.) that is
+ * A_CC + A_CF W (the product order of csr_matmat_add with A_CC added last).
+ * With R~ = [Z, I] (Eq. 5) it is Z (A_FF W + A_FC) + (A_CF W + A_CC), each
+ * bracket one csr_matmat_add and the outer product added last.  The final
+ * coarse block gets AMG.
  */
 or_ctx *or_setup(int nb, int b, const int *rp, const int *ci, const double *val,
                  const signed char *dof_level, int num_levels, const int *relax_type,
                  const int *relax_sweeps, const double *relax_weight,
-                 const int *relax_functions, double theta,
+                 const int *relax_functions, const int *restrict_type, double theta,
                  int max_levels, int max_coarse, int pmax, int num_functions, int *status) {
     *status = OR_INVALID;
     if (b < 1 || b > 4 || nb < 1 || num_levels < 0 || num_levels > 8) return NULL;
@@ -869,7 +899,10 @@ or_ctx *or_setup(int nb, int b, const int *rp, const int *ci, const double *val,
         L->relax = relax_type[l]; L->sweeps = relax_sweeps[l] < 1 ? 1 : relax_sweeps[l];
         L->omega = relax_weight[l];
         L->nfunc = relax_functions ? relax_functions[l] : 1;
-        if (L->relax < OR_JACOBI || L->relax > OR_AMG_RELAX) {
+        L->rtype = restrict_type ? restrict_type[l] : OR_RESTRICT_INJECTION;
+        if (L->relax < OR_JACOBI || L->relax > OR_AMG_RELAX ||
+            L->rtype < OR_RESTRICT_INJECTION || L->rtype > OR_RESTRICT_JACOBI ||
+            (L->rtype == OR_RESTRICT_JACOBI && L->relax == OR_BLOCK_JACOBI)) {
             c->nlev = l; csr_free(&cur); free(gdof); *status = OR_INVALID; or_free(c); return NULL;
         }
         int n = L->n;
@@ -894,10 +927,20 @@ or_ctx *or_setup(int nb, int b, const int *rp, const int *ci, const double *val,
         if (!rc) rc = mgr_build_w(L);
         csr next;
         memset(&next, 0, sizeof(next));
-        if (!rc) rc = csr_matmat_add(&L->ACF, &L->W, &ACC, &next);
+        if (!rc) rc = csr_transpose(&L->ACF, &L->ACFT);
+        if (L->rtype == OR_RESTRICT_JACOBI) {
+            csr T1, U;
+            memset(&T1, 0, sizeof(T1)); memset(&U, 0, sizeof(U));
+            if (!rc) rc = build_zt(L);
+            if (!rc) rc = csr_matmat_add(&L->AFF, &L->W, &L->AFC, &T1);
+            if (!rc) rc = csr_matmat_add(&L->ACF, &L->W, &ACC, &U);
+            if (!rc) rc = csr_matmat_add(&L->Z, &T1, &U, &next);
+            csr_free(&T1); csr_free(&U);
+        } else if (!rc) {
+            rc = csr_matmat_add(&L->ACF, &L->W, &ACC, &next);
+        }
         csr_free(&ACC);
         if (!rc) rc = csr_transpose(&L->AFF, &L->AFFT);
-        if (!rc) rc = csr_transpose(&L->ACF, &L->ACFT);
         if (!rc) rc = csr_transpose(&L->W, &L->WT);
         if (!rc && L->relax == OR_AMG_RELAX) {
             /* the F-relaxation's own AMG hierarchy, built on a copy of A_FF
@@ -917,6 +960,7 @@ or_ctx *or_setup(int nb, int b, const int *rp, const int *ci, const double *val,
         L->tF = (double *)calloc((size_t)nF + 1, sizeof(double));
         L->vC = (double *)calloc((size_t)nC + 1, sizeof(double));
         L->eC = (double *)calloc((size_t)nC + 1, sizeof(double));
+        L->qF = (double *)calloc((size_t)nF + 1, sizeof(double));
         int *g2 = (int *)malloc(((size_t)nC + 1) * sizeof(int));
         for (int t = 0; t < nC; t++) g2[t] = gdof[L->cidx[t]];
         gdof = g2;
@@ -973,6 +1017,15 @@ static void mgr_vcycle(or_ctx *c, int l, const double *v, double *z) {
     mgr_frelax(L, yF, 0);
     csr_matvec(&L->ACF, L->zF, L->vC);
     for (int t = 0; t < L->nC; t++) L->vC[t] = v[L->cidx[t]] - L->vC[t];
+    if (L->rtype == OR_RESTRICT_JACOBI) {
+        /* r_C += Z r_F with r_F = v_F - A_FF z_F (Alg. 1 line 5, R~ of Eq. 5) */
+        double *sC = (double *)malloc(((size_t)L->nC + 1) * sizeof(double));
+        csr_matvec(&L->AFF, L->zF, L->tF);
+        for (int f = 0; f < L->nF; f++) L->rF[f] = yF[f] - L->tF[f];
+        csr_matvec(&L->Z, L->rF, sC);
+        for (int t = 0; t < L->nC; t++) L->vC[t] = L->vC[t] + sC[t];
+        free(sC);
+    }
     double *vC = (double *)malloc(((size_t)L->nC + 1) * sizeof(double));
     double *eC = (double *)malloc(((size_t)L->nC + 1) * sizeof(double));
     memcpy(vC, L->vC, (size_t)L->nC * sizeof(double));
@@ -987,10 +1040,12 @@ static void mgr_vcycle(or_ctx *c, int l, const double *v, double *z) {
 }
 
 /*
- * Exact transpose of mgr_vcycle.  With M^{-1} = [K 0; 0 0] + [W; I] B [-A_CF K, I]
- * (K = the F-relaxation operator, B = the coarse cycle):
- *   r_C = v_C + W^T v_F;  e_C = B^T r_C;  z_C = e_C;
- *   z_F = K^T (v_F - A_CF^T e_C), K^T = the same sweeps on A_FF^T with D^{-T}.
+ * Exact transpose of mgr_vcycle.  With K_e = [K 0; 0 0] (K = the
+ * F-relaxation operator), B = the coarse cycle, P~ = [W; I] and
+ * R~ = [Z, I] (Z = 0 for injection): M^{-1} = K_e + P~ B R~ (I - A K_e), so
+ *   r_C = v_C + W^T v_F;  e_C = B^T r_C;  z_C = e_C;  q_F = Z^T e_C;
+ *   z_F = K^T (v_F - A_CF^T e_C - A_FF^T q_F) + q_F,
+ * K^T = the same sweeps on A_FF^T with D^{-T} (or the transposed V-cycle).
  */
 static void mgr_vcycle_t(or_ctx *c, int l, const double *v, double *z) {
     if (l == c->nlev) { amg_vcycle(&c->amg, 0, v, z, 1); return; }
@@ -1005,7 +1060,16 @@ static void mgr_vcycle_t(or_ctx *c, int l, const double *v, double *z) {
     mgr_vcycle_t(c, l + 1, rC, eC);
     csr_matvec(&L->ACFT, eC, tF);
     for (int f = 0; f < L->nF; f++) tF[f] = vF[f] - tF[f];
+    if (L->rtype == OR_RESTRICT_JACOBI) {
+        double *sF = (double *)malloc(((size_t)L->nF + 1) * sizeof(double));
+        csr_matvec(&L->ZT, eC, L->qF);
+        csr_matvec(&L->AFFT, L->qF, sF);
+        for (int f = 0; f < L->nF; f++) tF[f] = tF[f] - sF[f];
+        free(sF);
+    }
     mgr_frelax(L, tF, 1);
+    if (L->rtype == OR_RESTRICT_JACOBI)
+        for (int f = 0; f < L->nF; f++) L->zF[f] = L->zF[f] + L->qF[f];
     for (int t = 0; t < L->nC; t++) z[L->cidx[t]] = eC[t];
     for (int f = 0; f < L->nF; f++) z[L->fidx[f]] = L->zF[f];
     free(vF); free(rC); free(eC); free(tF);
@@ -1123,6 +1187,7 @@ static const csr *mgr_mat(or_ctx *c, int l, int which) {
         case 2: return &L->AFC;
         case 3: return &L->ACF;
         case 4: return &L->W;
+        case 5: return L->Z.rp ? &L->Z : NULL;
         default: return NULL;
     }
 }

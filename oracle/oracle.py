@@ -22,6 +22,7 @@ LIB = os.path.join(LIBDIR, "libmgr_oracle.so")
 
 OK, INVALID, NOMEM, SINGULAR, NOT_CONVERGED = 0, 1, 2, 4, 5
 RELAX = {"jacobi": 0, "l1_jacobi": 1, "block_jacobi": 2, "amg": 3}
+RESTRICT = {"injection": 0, "jacobi": 1}
 
 
 def build(force: bool = False) -> str:
@@ -45,7 +46,7 @@ def lib():
         L = C.CDLL(LIB)
         vp, ip, dp = C.c_void_p, C.c_int, C.c_double
         L.or_setup.restype = vp
-        L.or_setup.argtypes = [ip, ip, vp, vp, vp, vp, ip, vp, vp, vp, vp, dp, ip, ip, ip, ip, vp]
+        L.or_setup.argtypes = [ip, ip, vp, vp, vp, vp, ip, vp, vp, vp, vp, vp, dp, ip, ip, ip, ip, vp]
         L.or_free.argtypes = [vp]
         L.or_apply.argtypes = [vp, vp, vp]
         L.or_apply_transpose.argtypes = [vp, vp, vp]
@@ -113,6 +114,8 @@ class Options:
     pmax: int = 4
     num_functions: int = 1
     relax_functions: list = field(default_factory=list)
+    # per-level restriction: "injection" (R = [0, I]) or "jacobi" (R = [-A_CF D^-1, I], Eq. 5)
+    restrict: list = field(default_factory=list)
     restart: int = 30
 
 
@@ -133,11 +136,13 @@ class Oracle:
         sw = np.array(((opts.sweeps or []) + [1] * nl)[:nl] + [1], np.int32)
         wt = np.array(((opts.weights or []) + [1.0] * nl)[:nl] + [1.0], np.float64)
         fn = np.array(((opts.relax_functions or []) + [1] * nl)[:nl] + [1], np.int32)
-        self._keep += [rt, sw, wt, fn]
+        rs = np.array([RESTRICT[r] if isinstance(r, str) else int(r)
+                       for r in ((opts.restrict or []) + ["injection"] * nl)[:nl]] + [0], np.int32)
+        self._keep += [rt, sw, wt, fn, rs]
         st = np.zeros(1, np.int32)
         rp, ci, v, lv = self._keep[:4]
         self.h = L.or_setup(sysm.nb, sysm.b, _p(rp), _p(ci), _p(v), _p(lv), nl, _p(rt), _p(sw),
-                            _p(wt), _p(fn), opts.theta, opts.max_levels, opts.max_coarse, opts.pmax,
+                            _p(wt), _p(fn), _p(rs), opts.theta, opts.max_levels, opts.max_coarse, opts.pmax,
                             opts.num_functions, _p(st))
         self.status = int(st[0])
         if not self.h:
@@ -194,7 +199,7 @@ class Oracle:
         lib().or_mat_copy(self.h, amg, lvl, which, _p(rp), _p(ci), _p(v))
         return rp, ci[:nnz], v[:nnz], (n, m)
 
-    MGR_WHICH = {"A": 0, "AFF": 1, "AFC": 2, "ACF": 3, "W": 4}
+    MGR_WHICH = {"A": 0, "AFF": 1, "AFC": 2, "ACF": 3, "W": 4, "Z": 5}
 
     def mgr_matrix(self, lvl, which="A"):
         """CSR (rp, ci, v, shape) of MGR level ``lvl``; lvl == num_levels is

@@ -345,6 +345,12 @@ def test_amg_vcycle_convergence_factor_poisson():
     # a nonsymmetric A_FF (upwinded saturation block): the transposed
     # V-cycle differs from the forward one
     (lambda: make_two_phase(8, 6, 3), O.Options(relax=["amg"], max_coarse=16)),
+    # the restriction of Eq. 5 (R = [-A_CF D^-1, I]) on a nonsymmetric system,
+    # with repeated weighted sweeps, and on every level of the 4-level order
+    (lambda: make_two_phase(8, 6, 3),
+     O.Options(relax=["jacobi"], sweeps=[2], weights=[0.8], restrict=["jacobi"], max_coarse=16)),
+    (lambda: make_compositional(16, 12, 4, nwell_side=2, strategy="mgr4"),
+     O.Options(relax=["jacobi", "jacobi", "amg"], restrict=["jacobi"] * 3, max_coarse=32)),
     (lambda: make_poromech(6, 4, strategy="mgr_u"),
      O.Options(relax=["amg"], relax_functions=[3], sweeps=[2], weights=[0.8], max_coarse=32)),
 ])
@@ -570,3 +576,95 @@ def test_mgr_pi_tpfa_two_level_is_direct():
     ref = np.linalg.solve(dense_of(s), v)
     assert np.linalg.norm(o.apply(v) - ref) <= 1e-10 * np.linalg.norm(ref)
     assert o.solve(s.rhs, rtol=1e-12)["iters"] == 1
+
+
+# ------------------------------------------ the SPD restriction of Eq. 5
+def _two_level_blocks(A, lvl):
+    F = np.flatnonzero(lvl == 0); Cc = np.flatnonzero(lvl > 0)
+    return F, Cc, A[np.ix_(F, F)], A[np.ix_(F, Cc)], A[np.ix_(Cc, F)], A[np.ix_(Cc, Cc)]
+
+
+@pytest.mark.parametrize("make,relax", [
+    (lambda: make_two_phase(6, 5, 3), "jacobi"),
+    (lambda: make_poromech(6, 4), "l1_jacobi"),
+])
+def test_jacobi_restriction_coarse_operator_is_petrov_galerkin(make, relax):
+    """With R~ = [-A_CF D^-1, I] and P~ = [-D^-1 A_FC; I] (Eq. 5) the coarse
+    operator is the triple product R~ A P~, densely."""
+    s = make()
+    o = O.Oracle(s, O.Options(relax=[relax], restrict=["jacobi"], num_functions=s.num_functions))
+    A = dense_of(s)
+    F, Cc, AFF, AFC, ACF, ACC = _two_level_blocks(A, s.dof_level)
+    d = np.diag(AFF).copy()
+    if relax == "l1_jacobi":
+        off = np.abs(AFF).sum(1) - np.abs(d)
+        d = np.where(d < 0, d - off, d + off)
+    R = np.hstack([-ACF / d[None, :], np.eye(Cc.size)])
+    P = np.vstack([-AFC / d[:, None], np.eye(Cc.size)])
+    Ap = np.block([[AFF, AFC], [ACF, ACC]])
+    S = R @ Ap @ P
+    got = csr_dense(o.mgr_matrix(1, "A"))
+    assert np.max(np.abs(got - S)) <= 1e-12 * np.max(np.abs(S))
+    Z = csr_dense(o.mgr_matrix(0, "Z"))
+    assert np.max(np.abs(Z - R[:, :F.size])) <= 1e-15 * np.abs(Z).max()
+
+
+def test_jacobi_restriction_keeps_spd_coarse_grids():
+    """Sec. 3: for an SPD matrix, R~ = P~^T (Eq. 5) makes each coarse
+    operator the Galerkin product P~^T A P~, again SPD, and the coarse-grid
+    correction I - P~ S^-1 P~^T A an A-orthogonal projection (it never
+    increases the energy norm of the error)."""
+    from paper_2101_11649_gb300.synth.bsr import BlockSystem
+    rp, ci, v = poisson(12, 10)
+    n = 120
+    k = np.arange(n)
+    lvl = np.where(k % 3 == 0, 1, 0).astype(np.int8)      # coupled F points
+    lvl[(lvl == 1) & (k % 2 == 0)] = 2
+    sysm = BlockSystem(name="poisson2d", b=1, row_ptr=rp, col_idx=ci, val=v.reshape(-1, 1, 1),
+                       dof_level=lvl, num_levels=2, rhs=np.ones(n), relax=["jacobi", "jacobi"])
+    o = O.Oracle(sysm, O.Options(relax=["jacobi", "jacobi"], restrict=["jacobi"] * 2, max_coarse=4))
+    Al = csr_dense(o.mgr_matrix(0, "A"))
+    rng = np.random.default_rng(13)
+    for lv in (0, 1):
+        assert np.count_nonzero(csr_dense(o.mgr_matrix(lv, "AFF")) - np.diag(np.diag(
+            csr_dense(o.mgr_matrix(lv, "AFF"))))) > 0
+        S = csr_dense(o.mgr_matrix(lv + 1, "A"))
+        assert np.max(np.abs(S - S.T)) <= 1e-14 * np.max(np.abs(S))
+        assert np.linalg.eigvalsh(S).min() > 0
+        # P~ in the level's own ordering: identity on C rows, W on F rows
+        sub = lvl[lvl >= lv] if lv == 0 else lvl[lvl >= 1]
+        F = np.flatnonzero(sub == lv); Cc = np.flatnonzero(sub > lv)
+        P = np.zeros((sub.size, Cc.size))
+        P[F] = csr_dense(o.mgr_matrix(lv, "W")); P[Cc, np.arange(Cc.size)] = 1.0
+        assert np.max(np.abs(P.T @ Al @ P - S)) <= 1e-13 * np.max(np.abs(S))
+        for _ in range(5):
+            e = rng.standard_normal(sub.size)
+            e2 = e - P @ np.linalg.solve(S, P.T @ (Al @ e))
+            assert e2 @ Al @ e2 <= e @ Al @ e * (1 + 1e-12)
+        Al = S
+
+
+@pytest.mark.parametrize("sweeps,omega", [(1, 1.0), (2, 0.7)])
+def test_jacobi_restriction_cycle_matches_dense_algorithm_1(sweeps, omega):
+    """Algorithm 1 with R~ of Eq. 5, s weighted Jacobi sweeps from zero and an
+    exact coarse solve: M^-1 = K_e + P~ S^-1 R~ (I - A K_e), K_e = [K 0; 0 0],
+    K = (I - (I - omega D^-1 A_FF)^s) A_FF^-1; and its transpose."""
+    s = make_two_phase(6, 5, 3)
+    o = O.Oracle(s, O.Options(relax=["jacobi"], sweeps=[sweeps], weights=[omega],
+                              restrict=["jacobi"], max_coarse=4096))
+    assert o.amg_nlevels == 1
+    A = dense_of(s)
+    F, Cc, AFF, AFC, ACF, ACC = _two_level_blocks(A, s.dof_level)
+    d = np.diag(AFF)
+    E = np.eye(F.size) - omega * AFF / d[:, None]
+    K = (np.eye(F.size) - np.linalg.matrix_power(E, sweeps)) @ np.linalg.inv(AFF)
+    R = np.hstack([-ACF / d[None, :], np.eye(Cc.size)])
+    P = np.vstack([-AFC / d[:, None], np.eye(Cc.size)])
+    Ap = np.block([[AFF, AFC], [ACF, ACC]])
+    Ke = np.zeros_like(Ap); Ke[:F.size, :F.size] = K
+    Mp = Ke + P @ np.linalg.solve(R @ Ap @ P, R @ (np.eye(s.n) - Ap @ Ke))
+    order = np.concatenate([F, Cc])
+    Mi = np.zeros_like(Mp); Mi[np.ix_(order, order)] = Mp
+    v = np.random.default_rng(12).standard_normal(s.n)
+    for got, ref in ((o.apply(v), Mi @ v), (o.apply_transpose(v), Mi.T @ v)):
+        assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
