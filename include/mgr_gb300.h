@@ -69,6 +69,7 @@ typedef struct {
 } mgr_labels;
 
 enum { MGR_RELAX_JACOBI = 0, MGR_RELAX_L1_JACOBI = 1, MGR_RELAX_BLOCK_JACOBI = 2, MGR_RELAX_AMG = 3 };
+enum { MGR_RESTRICT_INJECTION = 0, MGR_RESTRICT_JACOBI = 1 };
 enum { MGR_PREC_FP64 = 0, MGR_PREC_FP32 = 1 };
 #define MGR_MAX_LEVELS 8
 
@@ -83,6 +84,12 @@ enum { MGR_PREC_FP64 = 0, MGR_PREC_FP32 = 1 };
  * interpolation uses D_FF = diag(A_FF).  A sweep computes
  * z_F += omega * B (v_F - A_FF z_F) with B the V-cycle.  Batched solves do
  * not take it (MGR_ERR_UNSUPPORTED).
+ * restrict_type[l]: MGR_RESTRICT_INJECTION (R~ = [0, I], the default) or
+ * MGR_RESTRICT_JACOBI (R~ = [-A_CF D^{-1}, I] of Eq. 5, the transpose of
+ * P~ for symmetric A): the coarse operator becomes the triple product
+ * R~ A P~ and the cycle restricts v_C - A_CF z_F + Z (v_F - A_FF z_F),
+ * Z = -A_CF D^{-1}.  It needs a diagonal D (not block-Jacobi:
+ * MGR_ERR_UNSUPPORTED); batched solves restrict by injection only.
  * AMG: strength threshold theta, level and coarse-size limits, max
  * interpolation entries per row (0 = no truncation), number of functions
  * of the unknown approach (function of a coarse-block dof = its index mod
@@ -108,6 +115,7 @@ typedef struct {
     int32_t use_graphs;
     int32_t amg_tail_nnz;
     int32_t relax_functions[MGR_MAX_LEVELS];
+    int32_t restrict_type[MGR_MAX_LEVELS];
 } mgr_options;
 
 /* Solve report.  level_rows/level_nnz list the MGR levels, then the AMG levels. */
@@ -123,7 +131,8 @@ typedef struct {
 
 /* Defaults: Jacobi, 1 sweep, omega 1 on every level; theta 0.25, 25 AMG
  * levels, coarsest <= 1024 rows, P_max 4, 1 function; FP64; m = 30; graphs on;
- * no fused AMG tail; 1 function in every F-relaxation AMG hierarchy. */
+ * no fused AMG tail; 1 function in every F-relaxation AMG hierarchy;
+ * injection restriction on every level. */
 void mgr_options_default(mgr_options *opt);
 
 /*
@@ -237,7 +246,8 @@ const char *mgr_last_error(mgr_handle h);
 
 /* -------------------------------------------------- hierarchy inspection
  * For parity tests and tooling.  which: 0 = the level matrix; for MGR
- * levels 1 = A_FF, 2 = A_FC, 3 = A_CF, 4 = W; for AMG levels 1 = P.
+ * levels 1 = A_FF, 2 = A_FC, 3 = A_CF, 4 = W, 5 = Z (restriction of Eq. 5
+ * only); for AMG levels 1 = P.
  * amg = 0 selects MGR level `level` (level == mgr levels is the final coarse
  * block), amg = 1 AMG level `level` of the final coarse block's hierarchy,
  * amg = 2 + l AMG level `level` of MGR level l's AMG F-relaxation.  dims (host int32[3]) receives rows,

@@ -50,6 +50,12 @@ struct MgrLevel {
     struct AmgH *famg = nullptr;
     double *tF = nullptr;
     float *tF32 = nullptr;
+    // restriction of Eq. 5 (MGR_RESTRICT_JACOBI): Z = -A_CF D^{-1} and Z^T;
+    // q_F = Z^T e_C and y_F of the transposed cycle
+    int rtype = MGR_RESTRICT_INJECTION;
+    DCSR Z, ZT;
+    double *qF = nullptr, *yF = nullptr;
+    float *qF32 = nullptr, *yF32 = nullptr;
 };
 
 struct AmgLevel {
@@ -216,7 +222,10 @@ extern "C" void mgr_options_default(mgr_options *o) {
     o->restart = 30;
     o->use_graphs = 1;
     o->amg_tail_nnz = 0;
-    for (int l = 0; l < MGR_MAX_LEVELS; l++) o->relax_functions[l] = 1;
+    for (int l = 0; l < MGR_MAX_LEVELS; l++) {
+        o->relax_functions[l] = 1;
+        o->restrict_type[l] = MGR_RESTRICT_INJECTION;
+    }
 }
 
 // ---------------------------------------------------------------- helpers
@@ -408,6 +417,13 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
         L.sweeps = h->opt.relax_sweeps[l] < 1 ? 1 : h->opt.relax_sweeps[l];
         L.omega = h->opt.relax_weight[l];
         if (L.relax < MGR_RELAX_JACOBI || L.relax > MGR_RELAX_AMG) { mgr_free(h); return fail(nullptr, MGR_ERR_INVALID, "relax type"); }
+        L.rtype = h->opt.restrict_type[l];
+        if (L.rtype < MGR_RESTRICT_INJECTION || L.rtype > MGR_RESTRICT_JACOBI) {
+            mgr_free(h); return fail(nullptr, MGR_ERR_INVALID, "restriction type");
+        }
+        if (L.rtype == MGR_RESTRICT_JACOBI && L.relax == MGR_RELAX_BLOCK_JACOBI) {
+            mgr_free(h); return fail(nullptr, MGR_ERR_UNSUPPORTED, "the restriction of Eq. 5 takes a diagonal D_FF");
+        }
         int nl = L.n;
         int *isF = ar.alloc<int>(nl + 1), *isC = ar.alloc<int>(nl + 1);
         int *fpos = ar.alloc<int>(nl + 1), *cpos = ar.alloc<int>(nl + 1);
@@ -445,7 +461,20 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
         launch_cast_f32(L.dinv, L.dinv32, (long long)nF * 4, s);
         if (mgr_build_w(L.AFC, L.gstart, L.gsize, L.dinv, L.W, s, ar)) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "W"); }
         DCSR next;
-        if (spgemm(L.ACF, L.W, &ACC, next, s, ar)) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "coarse operator"); }
+        if (transpose(L.ACF, L.ACFT, s, ar)) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level transposes"); }
+        if (L.rtype == MGR_RESTRICT_JACOBI) {
+            // R~ A P~ = Z (A_FF W + A_FC) + (A_CF W + A_CC), Z^T = -D^{-1} A_CF^T
+            DCSR T1, U;
+            if (mgr_build_w(L.ACFT, L.gstart, L.gsize, L.dinv, L.ZT, s, ar) || transpose(L.ZT, L.Z, s, ar) ||
+                spgemm(L.AFF, L.W, &L.AFC, T1, s, ar) || spgemm(L.ACF, L.W, &ACC, U, s, ar) ||
+                spgemm(L.Z, T1, &U, next, s, ar)) {
+                mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "coarse operator");
+            }
+            ar.release(T1.rp); ar.release(T1.ci); ar.release(T1.v);
+            ar.release(U.rp); ar.release(U.ci); ar.release(U.v);
+        } else if (spgemm(L.ACF, L.W, &ACC, next, s, ar)) {
+            mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "coarse operator");
+        }
         ar.release(ACC.rp); ar.release(ACC.ci); ar.release(ACC.v);
         if (L.relax == MGR_RELAX_AMG) {
             // the F-relaxation's AMG hierarchy on A_FF (same AMG parameters as
@@ -464,11 +493,14 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
         } else if (transpose(L.AFF, L.AFFT, s, ar)) {
             mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level transposes");
         }
-        if (transpose(L.ACF, L.ACFT, s, ar) || transpose(L.W, L.WT, s, ar)) {
+        if (transpose(L.W, L.WT, s, ar)) {
             mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level transposes");
         }
         if ((!L.famg && (to_f32(h, L.AFF) || to_f32(h, L.AFFT))) || to_f32(h, L.ACF) || to_f32(h, L.W) ||
-            to_f32(h, L.ACFT) || to_f32(h, L.WT)) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "fp32"); }
+            to_f32(h, L.ACFT) || to_f32(h, L.WT) ||
+            (L.rtype == MGR_RESTRICT_JACOBI && (to_f32(h, L.Z) || to_f32(h, L.ZT)))) {
+            mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "fp32");
+        }
         L.fiota = ar.alloc<int>(nF + 1);
         L.zF = ar.alloc<double>(nF + 1); L.rF = ar.alloc<double>(nF + 1);
         L.vC = ar.alloc<double>(nC + 1); L.eC = ar.alloc<double>(nC + 1);
@@ -477,6 +509,11 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
         if (L.famg) {
             L.tF = ar.alloc<double>(nF + 1); L.tF32 = ar.alloc<float>(nF + 1);
             if (!L.tF || !L.tF32) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level vectors"); }
+        }
+        if (L.rtype == MGR_RESTRICT_JACOBI) {
+            L.qF = ar.alloc<double>(nF + 1); L.qF32 = ar.alloc<float>(nF + 1);
+            L.yF = ar.alloc<double>(nF + 1); L.yF32 = ar.alloc<float>(nF + 1);
+            if (!L.qF || !L.qF32 || !L.yF || !L.yF32) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level vectors"); }
         }
         int *g2 = ar.alloc<int>(nC + 1);
         if (!L.fiota || !L.zF || !L.rF || !L.vC || !L.eC || !L.zF32 || !L.rF32 || !L.vC32 || !L.eC32 || !g2) {
@@ -539,6 +576,7 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
                 DCSR *ms[] = {&L.AFF, &L.ACF, &L.W, &L.AFFT, &L.ACFT, &L.WT};
                 for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
             }
+            if (L.rtype == MGR_RESTRICT_JACOBI) rc2 |= build_sell(L.Z, s, ar) | build_sell(L.ZT, s, ar);
         }
         sell_amg(h->H);
         if (b == 1) {
@@ -573,6 +611,8 @@ template <> struct Sel<double> {
     static double *vC(MgrLevel &L) { return L.vC; }
     static double *eC(MgrLevel &L) { return L.eC; }
     static double *tF(MgrLevel &L) { return L.tF; }
+    static double *qF(MgrLevel &L) { return L.qF; }
+    static double *yF(MgrLevel &L) { return L.yF; }
     static const double *dinv(MgrLevel &L) { return L.dinv; }
     static const double *dinv(AmgLevel &L) { return L.dinv; }
     static double *r(AmgLevel &L) { return L.r; }
@@ -587,6 +627,8 @@ template <> struct Sel<float> {
     static float *vC(MgrLevel &L) { return L.vC32; }
     static float *eC(MgrLevel &L) { return L.eC32; }
     static float *tF(MgrLevel &L) { return L.tF32; }
+    static float *qF(MgrLevel &L) { return L.qF32; }
+    static float *yF(MgrLevel &L) { return L.yF32; }
     static const float *dinv(MgrLevel &L) { return L.dinv32; }
     static const float *dinv(AmgLevel &L) { return L.dinv32; }
     static float *r(AmgLevel &L) { return L.r32; }
@@ -800,6 +842,26 @@ static void amg_prepare(mgr_handle h, AmgH &G, const TV *r) {
     launch_scale<T, TV>(L.A.n, Sel<T>::dinv(L), r, Sel<T>::xw(L), h->s);
 }
 
+// Transposed cycle, sweeps after the first: r_F = y_F - A_FF^T z_F.  y_F is
+// v_F - A_CF^T e_C, rebuilt from v for injection, or kept in y_F (it also
+// holds - A_FF^T Z^T e_C) for the restriction of Eq. 5.
+template <class T, class TV>
+static void t_sweep_residual(mgr_handle h, int l, const TV *v) {
+    cudaStream_t s = h->s;
+    MgrLevel &L = h->lev[l];
+    T *zF = Sel<T>::zF(L), *rF = Sel<T>::rF(L), *eC = Sel<T>::eC(L);
+    const double ts = sizeof(T), tv = sizeof(TV), nF = L.nF, nC = L.nC;
+    if (L.rtype == MGR_RESTRICT_JACOBI) {
+        KScope ks(h, "mgrT_frelax_residual", l, (double)L.AFFT.nnz * (ts + 4) + (nF + 1) * 4 + nF * (4 + 3 * ts));
+        launch_csr_axpy_gather<T, T>(L.AFFT, Sel<T>::v(L.AFFT), zF, L.fiota, Sel<T>::yF(L), (T)-1, rF, s);
+        return;
+    }
+    { KScope ks(h, "mgrT_interp", l, (double)L.ACFT.nnz * (ts + 4) + (nF + 1) * 4 + nC * ts + nF * (4 + tv + ts));
+      launch_csr_axpy_gather<T, TV>(L.ACFT, Sel<T>::v(L.ACFT), eC, L.fidx, v, (T)-1, rF, s); }
+    { KScope ks(h, "mgrT_frelax_residual", l, (double)L.AFFT.nnz * (ts + 4) + (nF + 1) * 4 + nF * (4 + 3 * ts));
+      launch_csr_axpy_gather<T, T>(L.AFFT, Sel<T>::v(L.AFFT), zF, L.fiota, rF, (T)-1, rF, s); }
+}
+
 // AMG F-relaxation of MGR level l (MGR_U, Sec. 4.3): s sweeps of
 // z_F += omega B (y_F - A_FF z_F) from z_F = 0, B one AMG V(1,1) cycle on A_FF
 // (trans: the transposed cycle on A_FF^T).  Forward: y_F = v_F, gathered
@@ -809,9 +871,9 @@ static void frelax_amg(mgr_handle h, int l, const TV *v, int trans) {
     cudaStream_t s = h->s;
     MgrLevel &L = h->lev[l];
     AmgH &G = *L.famg;
-    T *zF = Sel<T>::zF(L), *rF = Sel<T>::rF(L), *tF = Sel<T>::tF(L), *eC = Sel<T>::eC(L);
+    T *zF = Sel<T>::zF(L), *rF = Sel<T>::rF(L), *tF = Sel<T>::tF(L);
     const T om = (T)L.omega;
-    const double ts = sizeof(T), tv = sizeof(TV), nF = L.nF, nC = L.nC;
+    const double ts = sizeof(T), tv = sizeof(TV), nF = L.nF;
     if (!trans) {
         KScope ks(h, "mgr_frelax_gather", l, nF * (4 + tv + ts));
         launch_gather<T, TV>(L.fidx, L.nF, v, rF, s);
@@ -822,10 +884,7 @@ static void frelax_amg(mgr_handle h, int l, const TV *v, int trans) {
                 KScope ks(h, "mgr_frelax_residual", l, (double)L.AFF.nnz * (ts + 4) + (nF + 1) * 4 + nF * (4 + tv + 2 * ts));
                 launch_frelax_residual<T, TV>(L.AFF, Sel<T>::v(L.AFF), L.fidx, v, zF, rF, s);
             } else {
-                { KScope ks(h, "mgrT_interp", l, (double)L.ACFT.nnz * (ts + 4) + (nF + 1) * 4 + nC * ts + nF * (4 + tv + ts));
-                  launch_csr_axpy_gather<T, TV>(L.ACFT, Sel<T>::v(L.ACFT), eC, L.fidx, v, (T)-1, rF, s); }
-                { KScope ks(h, "mgrT_frelax_residual", l, (double)L.AFFT.nnz * (ts + 4) + (nF + 1) * 4 + nF * (4 + 3 * ts));
-                  launch_csr_axpy_gather<T, T>(L.AFFT, Sel<T>::v(L.AFFT), zF, L.fiota, rF, (T)-1, rF, s); }
+                t_sweep_residual<T, TV>(h, l, v);
             }
         }
         amg_prepare<T, T>(h, G, rF);
@@ -869,13 +928,26 @@ static void mgr_cycle(mgr_handle h, int l, const TV *v, TV *z) {
         KScope ks(h, "mgr_frelax_update", l, nF * (gs * ts + 3 * ts + 8));
         launch_frelax_update<T>(L.nF, L.gstart, L.gsize, dinv, om, rF, zF, 0, s);
     }
+    if (L.rtype == MGR_RESTRICT_JACOBI) {
+        // r_F = v_F - A_FF z_F for the restricted residual of Eq. 5
+        KScope ks(h, "mgr_frelax_residual", l, (double)L.AFF.nnz * (ts + 4) + (nF + 1) * 4 + nF * (4 + tv + 2 * ts));
+        launch_frelax_residual<T, TV>(L.AFF, Sel<T>::v(L.AFF), L.fidx, v, zF, rF, s);
+    }
     {
-        const bool fuse = (l + 1 == h->nlev) && h->H.namg > 1;
+        const bool fuse = (l + 1 == h->nlev) && h->H.namg > 1 && L.rtype == MGR_RESTRICT_INJECTION;
         KScope ks(h, "mgr_restrict", l, (double)L.ACF.nnz * (ts + 4) + (nC + 1) * 4 + nF * ts + nC * (4 + tv + ts + (fuse ? 2 * ts : 0)),
                   f64 * L.ACF.nnz);
         if (fuse) launch_mgr_restrict_scaled<T, TV>(L.ACF, Sel<T>::v(L.ACF), L.cidx, v, zF, vC,
                                                     Sel<T>::dinv(h->H.amg[0]), Sel<T>::xw(h->H.amg[0]), s);
         else launch_mgr_restrict<T, TV>(L.ACF, Sel<T>::v(L.ACF), L.cidx, v, zF, vC, s);
+    }
+    if (L.rtype == MGR_RESTRICT_JACOBI) {
+        {
+            KScope ks(h, "mgr_restrict_z", l, (double)L.Z.nnz * (ts + 4) + (nC + 1) * 4 + nF * ts + 2 * nC * ts,
+                      f64 * L.Z.nnz);
+            launch_csr_spmv_add<T>(L.Z, Sel<T>::v(L.Z), rF, vC, s);  // r_C += Z r_F
+        }
+        if (l + 1 == h->nlev) amg_prepare<T, T>(h, h->H, vC);
     }
     mgr_cycle<T, T>(h, l + 1, vC, eC);
     {
@@ -908,31 +980,39 @@ static void mgr_cycle_t(mgr_handle h, int l, const TV *v, TV *z) {
     mgr_cycle_t<T, T>(h, l + 1, vC, eC);
     { KScope ks(h, "mgrT_interp", l, (double)L.ACFT.nnz * (ts + 4) + (nF + 1) * 4 + nC * ts + nF * (4 + tv + ts));
       launch_csr_axpy_gather<T, TV>(L.ACFT, Sel<T>::v(L.ACFT), eC, L.fidx, v, (T)-1, rF, s); }  // y_F
+    T *qF = Sel<T>::qF(L);
+    if (L.rtype == MGR_RESTRICT_JACOBI) {
+        // q_F = Z^T e_C;  y_F -= A_FF^T q_F (kept in y_F for later sweeps)
+        { KScope ks(h, "mgrT_restrict_z", l, (double)L.ZT.nnz * (ts + 4) + (nF + 1) * 4 + nC * ts + nF * ts,
+                    (sizeof(T) == 8 ? 1.0 : 0.0) * L.ZT.nnz);
+          launch_csr_spmv<T>(L.ZT, Sel<T>::v(L.ZT), eC, qF, s); }
+        { KScope ks(h, "mgrT_frelax_residual", l, (double)L.AFFT.nnz * (ts + 4) + (nF + 1) * 4 + nF * (4 + 3 * ts));
+          launch_csr_axpy_gather<T, T>(L.AFFT, Sel<T>::v(L.AFFT), qF, L.fiota, rF, (T)-1, rF, s); }
+        if (L.sweeps > 1) cudaMemcpyAsync(Sel<T>::yF(L), rF, sizeof(T) * L.nF, cudaMemcpyDeviceToDevice, s);
+    }
+    auto finish = [&]() {
+        if (L.rtype == MGR_RESTRICT_JACOBI) {
+            KScope ks(h, "mgr_frelax_scale", l, nF * 3 * ts);
+            launch_frelax_scale<T>(L.nF, (T)1, qF, zF, 1, s);  // z_F = K^T y_F + q_F
+        }
+        KScope ks(h, "mgrT_scatter", l, (nF + nC) * (4 + ts + tv));
+        launch_scatter2<T, TV>(L.nF, L.nC, L.fidx, L.cidx, zF, eC, z, s);
+    };
     if (L.famg) {
         frelax_amg<T, TV>(h, l, v, 1);
-        { KScope ks(h, "mgrT_scatter", l, (nF + nC) * (4 + ts + tv));
-          launch_scatter2<T, TV>(L.nF, L.nC, L.fidx, L.cidx, zF, eC, z, s); }
+        finish();
         return;
     }
     // K^T y_F: sweeps of z += omega D^{-T} (y - A_FF^T z) from z = 0
     cudaMemsetAsync(zF, 0, sizeof(T) * L.nF, s);
     { KScope ks(h, "mgrT_frelax_update", l, nF * (gs * ts + 3 * ts + 8));
       launch_frelax_update<T>(L.nF, L.gstart, L.gsize, dinv, om, rF, zF, 1, s); }
-    if (L.sweeps > 1) {
-        // keep y_F in vC's tail is unsafe; y_F must survive: copy to eC-sized scratch is not
-        // possible (sizes differ), so rebuild it from v each sweep.
-        for (int sw = 1; sw < L.sweeps; sw++) {
-            // rF <- y_F - A_FF^T z  with y_F = v_F - A_CF^T e_C
-            { KScope ks(h, "mgrT_interp", l, (double)L.ACFT.nnz * (ts + 4) + (nF + 1) * 4 + nC * ts + nF * (4 + tv + ts));
-              launch_csr_axpy_gather<T, TV>(L.ACFT, Sel<T>::v(L.ACFT), eC, L.fidx, v, (T)-1, rF, s); }
-            { KScope ks(h, "mgrT_frelax_residual", l, (double)L.AFFT.nnz * (ts + 4) + (nF + 1) * 4 + nF * (4 + 3 * ts));
-              launch_csr_axpy_gather<T, T>(L.AFFT, Sel<T>::v(L.AFFT), zF, L.fiota, rF, (T)-1, rF, s); }
-            { KScope ks(h, "mgrT_frelax_update", l, nF * (gs * ts + 3 * ts + 8));
-              launch_frelax_update<T>(L.nF, L.gstart, L.gsize, dinv, om, rF, zF, 1, s); }
-        }
+    for (int sw = 1; sw < L.sweeps; sw++) {
+        t_sweep_residual<T, TV>(h, l, v);  // r_F = y_F - A_FF^T z_F
+        KScope ks(h, "mgrT_frelax_update", l, nF * (gs * ts + 3 * ts + 8));
+        launch_frelax_update<T>(L.nF, L.gstart, L.gsize, dinv, om, rF, zF, 1, s);
     }
-    { KScope ks(h, "mgrT_scatter", l, (nF + nC) * (4 + ts + tv));
-      launch_scatter2<T, TV>(L.nF, L.nC, L.fidx, L.cidx, zF, eC, z, s); }
+    finish();
 }
 
 static void vcycle(mgr_handle h, const double *v, double *z, int trans) {
@@ -1245,6 +1325,7 @@ static const DCSR *pick(mgr_handle h, int amg, int level, int which) {
             case 2: return &L.AFC;
             case 3: return &L.ACF;
             case 4: return &L.W;
+            case 5: return L.rtype == MGR_RESTRICT_JACOBI ? &L.Z : nullptr;
         }
         return nullptr;
     }
@@ -1791,6 +1872,7 @@ extern "C" mgr_status mgr_setup_batched(int32_t nsys, const mgr_bsr *A, const mg
     for (int l = 0; l < bh->nlev; l++) {
         if (o.relax_sweeps[l] > 1) { mgr_free_batched(bh); return bfail(nullptr, MGR_ERR_UNSUPPORTED, "batched solves use one F-relaxation sweep"); }
         if (o.relax_type[l] == MGR_RELAX_AMG) { mgr_free_batched(bh); return bfail(nullptr, MGR_ERR_UNSUPPORTED, "batched solves take diagonal or block F-relaxations"); }
+        if (o.restrict_type[l] != MGR_RESTRICT_INJECTION) { mgr_free_batched(bh); return bfail(nullptr, MGR_ERR_UNSUPPORTED, "batched solves restrict by injection"); }
     }
     for (int s = 0; s < nsys; s++) {
         if (A[s].b != bh->b || cf[s].num_levels != bh->nlev) {

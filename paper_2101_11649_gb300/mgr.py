@@ -19,6 +19,7 @@ MGR_ERR_NOT_CONVERGED, MGR_ERR_TIMEOUT, MGR_ERR_UNSUPPORTED = 5, 6, 7
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "SINGULAR", 5: "NOT_CONVERGED",
                 6: "TIMEOUT", 7: "UNSUPPORTED"}
 RELAX = {"jacobi": 0, "l1_jacobi": 1, "block_jacobi": 2, "amg": 3}
+RESTRICT = {"injection": 0, "jacobi": 1}
 MAX_LEVELS = 8
 
 
@@ -44,7 +45,8 @@ class mgr_options(C.Structure):
                 ("amg_max_levels", C.c_int32), ("amg_max_coarse", C.c_int32),
                 ("amg_pmax", C.c_int32), ("amg_num_functions", C.c_int32),
                 ("precision", C.c_int32), ("restart", C.c_int32), ("use_graphs", C.c_int32),
-                ("amg_tail_nnz", C.c_int32), ("relax_functions", C.c_int32 * MAX_LEVELS)]
+                ("amg_tail_nnz", C.c_int32), ("relax_functions", C.c_int32 * MAX_LEVELS),
+                ("restrict_type", C.c_int32 * MAX_LEVELS)]
 
 
 class mgr_solve_info(C.Structure):
@@ -131,7 +133,7 @@ def _ptr(t):
 
 def options(relax=("jacobi",), sweeps=(), weights=(), theta=0.25, max_levels=25, max_coarse=1024,
             pmax=4, num_functions=1, precision="fp64", restart=30, use_graphs=True,
-            tail_nnz=None, relax_functions=()) -> mgr_options:
+            tail_nnz=None, relax_functions=(), restrict=()) -> mgr_options:
     o = mgr_options()
     lib().mgr_options_default(C.byref(o))
     for l, r in enumerate(relax):
@@ -152,6 +154,8 @@ def options(relax=("jacobi",), sweeps=(), weights=(), theta=0.25, max_levels=25,
         o.amg_tail_nnz = int(tail_nnz)
     for l, f in enumerate(relax_functions):
         o.relax_functions[l] = int(f)
+    for l, r in enumerate(restrict):
+        o.restrict_type[l] = RESTRICT[r] if isinstance(r, str) else int(r)
     return o
 
 

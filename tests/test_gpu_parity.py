@@ -295,6 +295,71 @@ def test_batched_rejects_amg_frelax():
     assert e.value.status == M.MGR_ERR_UNSUPPORTED
 
 
+# the restriction of Eq. 5 (R = [-A_CF D^-1, I]) on every level
+RESTRICT_CASES = ["two_phase", "mimetic", "poromech", "poromech_mgr_u", "compositional_4level"]
+
+
+@pytest.mark.parametrize("name", RESTRICT_CASES)
+def test_jacobi_restriction_hierarchy_bit_exact(name):
+    s = SMALL[name]()
+    rs = ["jacobi"] * s.num_levels
+    g = solver(s, max_coarse=SMALL_COARSE, restrict=rs)
+    o = oracle_of(s, max_coarse=SMALL_COARSE, restrict=rs)
+    assert g.info()["amg_levels"] == o.amg_nlevels
+    for l in range(s.num_levels + 1):
+        _same_csr(g.matrix(0, l, 0), o.mgr_matrix(l, "A"), f"MGR A_{l}")
+    for l in range(s.num_levels):
+        _same_csr(g.matrix(0, l, 5), o.mgr_matrix(l, "Z"), f"MGR Z_{l}")
+    for k in range(o.amg_nlevels):
+        _same_csr(g.matrix(1, k, 0), o.amg_matrix(k, "A"), f"AMG A_{k}")
+    _same_frelax_hierarchies(g, o, s)
+
+
+@pytest.mark.parametrize("name", RESTRICT_CASES)
+@pytest.mark.parametrize("sweeps,omega", [(1, 1.0), (2, 0.8)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_jacobi_restriction_vcycle_parity(name, sweeps, omega, precision):
+    s = SMALL[name]()
+    nl = s.num_levels
+    kw = dict(max_coarse=SMALL_COARSE, restrict=["jacobi"] * nl, sweeps=[sweeps] * nl,
+              weights=[omega] * nl)
+    g = solver(s, precision=precision, **kw)
+    o = oracle_of(s, **kw)
+    tol = 1e-11 if precision == "fp64" else 1e-4
+    rng = np.random.default_rng(21)
+    for trans in (False, True):
+        v = rng.standard_normal(s.n)
+        zg = g.apply(t(v), transpose=trans).cpu().numpy()
+        zo = o.apply_transpose(v) if trans else o.apply(v)
+        assert np.linalg.norm(zg - zo) <= tol * np.linalg.norm(zo), (trans, np.linalg.norm(zg - zo) / np.linalg.norm(zo))
+
+
+@pytest.mark.parametrize("name", RESTRICT_CASES)
+def test_jacobi_restriction_solve_parity(name):
+    s = SMALL[name]()
+    rs = ["jacobi"] * s.num_levels
+    g = solver(s, max_coarse=SMALL_COARSE, restrict=rs)
+    o = oracle_of(s, max_coarse=SMALL_COARSE, restrict=rs)
+    ro = o.solve(s.rhs, rtol=1e-8, maxit=500)
+    xg, ig = g.solve(t(s.rhs), rtol=1e-8, maxit=500)
+    assert ig["status"] == 0 and ro["status"] == 0
+    assert abs(ig["iterations"] - ro["iters"]) <= 1, (ig["iterations"], ro["iters"])
+    xl, il = g.solve(t(s.rhs), rtol=1e-8, maxit=500, transpose=True)
+    rl = o.solve(s.rhs, rtol=1e-8, maxit=500, trans=True)
+    assert il["status"] == 0 and abs(il["iterations"] - rl["iters"]) <= 1
+
+
+def test_jacobi_restriction_rejected_with_block_jacobi_and_in_batches():
+    s = SMALL["compositional"]()
+    with pytest.raises(M.MGRError) as e:
+        solver(s, restrict=["jacobi", "injection"])
+    assert e.value.status == M.MGR_ERR_UNSUPPORTED
+    s2 = SMALL["two_phase"]()
+    with pytest.raises(M.MGRError) as e:
+        M.MGRBatch([s2, s2], restrict=["jacobi"])
+    assert e.value.status == M.MGR_ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("name", list(SMALL))
 def test_solve_parity(name):
     s = SMALL[name]()
