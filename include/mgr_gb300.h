@@ -175,8 +175,21 @@ mgr_status mgr_solve_transpose(mgr_handle h, const double *g, double *lam, doubl
  * device) in the operator that mgr_spmv, mgr_solve and mgr_solve_transpose
  * apply, keeping the MGR/AMG hierarchy built by mgr_setup as the
  * preconditioner: the reuse of a hierarchy across Newton steps (Sec. 5.3).
- * Synchronises the stream.  INVALID on a non-finite value. */
+ * Synchronises the stream.  INVALID on a non-finite value (the handle is
+ * left unchanged). */
 mgr_status mgr_update_values(mgr_handle h, const double *val, int32_t on_device);
+
+/* Replace the values of A (same pattern, as mgr_update_values) and rebuild
+ * the hierarchy numerically from them: every MGR level (D_FF, W, Z, coarse
+ * operators) and the final coarse block's AMG hierarchy, while every AMG
+ * F-relaxation hierarchy built before is kept as it is (the setup reuse of
+ * Sec. 4.3: the mechanics block of MGR_U is fixed across Newton steps, so its
+ * AMG hierarchy is reused; when A_FF did change, the kept hierarchy is the
+ * one built from the old A_FF, and the level's own residuals use the new
+ * A_FF).  Labels and options are those of mgr_setup.  Synchronises the
+ * stream.  INVALID on a non-finite value; UNSUPPORTED for a handle of a
+ * batch; on any other failure the handle reports INVALID from then on. */
+mgr_status mgr_refresh(mgr_handle h, const double *val, int32_t on_device);
 
 /* dA_val[p*b*b + r*b + c] = -lam[I*b + r] * x[J*b + c] for block p = (I, J):
  * the gradient of a scalar loss with respect to the stored values of A when

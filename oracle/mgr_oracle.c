@@ -869,12 +869,17 @@ static int build_zt(mgr_level *L) {
  * With R~ = [Z, I] (Eq. 5) it is Z (A_FF W + A_FC) + (A_CF W + A_CC), each
  * bracket one csr_matmat_add and the outer product added last.  The final
  * coarse block gets AMG.
+ * reuse (may be NULL): a context built before on the same pattern and
+ * labels; the AMG hierarchy of each AMG F-relaxation is taken over from it
+ * instead of being rebuilt (the setup reuse of Sec. 4.3), and reuse is left
+ * without those hierarchies (free it next).
  */
 or_ctx *or_setup(int nb, int b, const int *rp, const int *ci, const double *val,
                  const signed char *dof_level, int num_levels, const int *relax_type,
                  const int *relax_sweeps, const double *relax_weight,
                  const int *relax_functions, const int *restrict_type, double theta,
-                 int max_levels, int max_coarse, int pmax, int num_functions, int *status) {
+                 int max_levels, int max_coarse, int pmax, int num_functions, or_ctx *reuse,
+                 int *status) {
     *status = OR_INVALID;
     if (b < 1 || b > 4 || nb < 1 || num_levels < 0 || num_levels > 8) return NULL;
     or_ctx *c = (or_ctx *)calloc(1, sizeof(or_ctx));
@@ -942,7 +947,13 @@ or_ctx *or_setup(int nb, int b, const int *rp, const int *ci, const double *val,
         csr_free(&ACC);
         if (!rc) rc = csr_transpose(&L->AFF, &L->AFFT);
         if (!rc) rc = csr_transpose(&L->W, &L->WT);
-        if (!rc && L->relax == OR_AMG_RELAX) {
+        if (!rc && L->relax == OR_AMG_RELAX && reuse && l < reuse->nlev &&
+            reuse->lev[l].relax == OR_AMG_RELAX && reuse->lev[l].famg.nlev > 0 &&
+            reuse->lev[l].famg.lev[0].A.n == L->AFF.n && reuse->lev[l].famg.lev[0].A.nnz == L->AFF.nnz) {
+            /* kept: the hierarchy built from the earlier A_FF */
+            L->famg = reuse->lev[l].famg;
+            memset(&reuse->lev[l].famg, 0, sizeof(amg_h));
+        } else if (!rc && L->relax == OR_AMG_RELAX) {
             /* the F-relaxation's own AMG hierarchy, built on a copy of A_FF
              * with the same AMG parameters as the final coarse block */
             csr cp;

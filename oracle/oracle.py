@@ -46,7 +46,7 @@ def lib():
         L = C.CDLL(LIB)
         vp, ip, dp = C.c_void_p, C.c_int, C.c_double
         L.or_setup.restype = vp
-        L.or_setup.argtypes = [ip, ip, vp, vp, vp, vp, ip, vp, vp, vp, vp, vp, dp, ip, ip, ip, ip, vp]
+        L.or_setup.argtypes = [ip, ip, vp, vp, vp, vp, ip, vp, vp, vp, vp, vp, dp, ip, ip, ip, ip, vp, vp]
         L.or_free.argtypes = [vp]
         L.or_apply.argtypes = [vp, vp, vp]
         L.or_apply_transpose.argtypes = [vp, vp, vp]
@@ -122,7 +122,10 @@ class Options:
 class Oracle:
     """An MGR hierarchy built by the oracle for one :class:`BlockSystem`."""
 
-    def __init__(self, sysm, opts: Options | None = None):
+    def __init__(self, sysm, opts: Options | None = None, reuse: "Oracle | None" = None):
+        """reuse: an oracle built before on the same pattern and labels whose
+        AMG F-relaxation hierarchies are taken over (the setup reuse of
+        Sec. 4.3); it is closed afterwards."""
         if opts is None:
             opts = Options(relax=list(sysm.relax), num_functions=sysm.num_functions,
                            relax_functions=list(getattr(sysm, "relax_functions", ())))
@@ -143,7 +146,9 @@ class Oracle:
         rp, ci, v, lv = self._keep[:4]
         self.h = L.or_setup(sysm.nb, sysm.b, _p(rp), _p(ci), _p(v), _p(lv), nl, _p(rt), _p(sw),
                             _p(wt), _p(fn), _p(rs), opts.theta, opts.max_levels, opts.max_coarse, opts.pmax,
-                            opts.num_functions, _p(st))
+                            opts.num_functions, reuse.h if reuse is not None else None, _p(st))
+        if reuse is not None:
+            reuse.close()
         self.status = int(st[0])
         if not self.h:
             raise RuntimeError(f"oracle setup failed with status {self.status}")

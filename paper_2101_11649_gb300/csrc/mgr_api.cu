@@ -48,6 +48,7 @@ struct MgrLevel {
     // AMG F-relaxation (MGR_RELAX_AMG): the hierarchy of A_FF and the
     // V-cycle output of a weighted or repeated sweep
     struct AmgH *famg = nullptr;
+    bool fshared = false;  // A_FF, A_FF^T are famg's level 0 (not after a refresh)
     double *tF = nullptr;
     float *tF32 = nullptr;
     // restriction of Eq. 5 (MGR_RESTRICT_JACOBI): Z = -A_CF D^{-1} and Z^T;
@@ -80,6 +81,8 @@ struct AmgH {
     unsigned *tail_sync = nullptr;  // grid barrier words (arrivals, generation, error)
     TailPlan *tail_plan[2] = {nullptr, nullptr};  // device phase lists [trans]
     int frelax = 0;                 // 1: an F-relaxation hierarchy (profile names)
+    Arena ar;                       // F-relaxation hierarchies own their memory
+    bool sell = false;              // SELL copies built
 };
 
 struct Krylov {
@@ -131,6 +134,11 @@ struct mgr_ctx {
     int nlev = 0;
     MgrLevel lev[MGR_MAX_LEVELS];
     AmgH H;  // the final coarse block's AMG hierarchy
+    // the hierarchy below (MGR levels, H, their SELL copies and the fused
+    // tail) lives in its own arena so that mgr_refresh can rebuild it
+    Arena lar;
+    DCSR A0;  // level-0 scalar CSR (in lar)
+    bool ready = false, in_batch = false;
     int *errw = nullptr;
     Krylov kr;
     Prof prof;
@@ -237,23 +245,44 @@ static int read_errw(mgr_handle h) {
     return e;
 }
 
-static int to_f32(mgr_handle h, DCSR &M) {
-    if (M.nnz == 0) { M.v32 = h->ar.alloc<float>(1); return M.v32 ? 0 : ST_NOMEM; }
-    M.v32 = h->ar.alloc<float>(M.nnz);
+static int to_f32(Arena &ar, DCSR &M, cudaStream_t s) {
+    if (M.nnz == 0) { M.v32 = ar.alloc<float>(1); return M.v32 ? 0 : ST_NOMEM; }
+    M.v32 = ar.alloc<float>(M.nnz);
     if (!M.v32) return ST_NOMEM;
-    launch_cast_f32(M.v, M.v32, M.nnz, h->s);
+    launch_cast_f32(M.v, M.v32, M.nnz, s);
     return 0;
+}
+
+// Deep copy of a CSR matrix (pattern and FP64 values) into ar.
+static int copy_csr(const DCSR &A, DCSR &out, Arena &ar, cudaStream_t s) {
+    out = DCSR();
+    out.n = A.n; out.m = A.m; out.nnz = A.nnz;
+    out.rp = ar.alloc<int>(A.n + 1);
+    out.ci = ar.alloc<int>(A.nnz + 1);
+    out.v = ar.alloc<double>(A.nnz + 1);
+    if (!out.rp || !out.ci || !out.v) return ST_NOMEM;
+    cudaMemcpyAsync(out.rp, A.rp, sizeof(int) * (A.n + 1), cudaMemcpyDeviceToDevice, s);
+    if (A.nnz) {
+        cudaMemcpyAsync(out.ci, A.ci, sizeof(int) * A.nnz, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(out.v, A.v, sizeof(double) * A.nnz, cudaMemcpyDeviceToDevice, s);
+    }
+    return ST_OK;
 }
 
 // AMG setup of hierarchy G on A0 (strength, PMIS, extended+i, Galerkin
 // products, l1 smoother scaling, dense inverse of the coarsest grid) with
-// nfunc functions of the unknown approach.
-static mgr_status setup_amg(mgr_handle h, AmgH &G, DCSR A0, int nfunc) {
-    Arena &ar = h->ar;
+// nfunc functions of the unknown approach, allocated from ar.  own_copy:
+// level 0 holds a copy of A0 (a hierarchy that outlives A0's arena).
+static mgr_status setup_amg(mgr_handle h, AmgH &G, DCSR A0, int nfunc, Arena &ar, bool own_copy) {
     cudaStream_t s = h->s;
     const mgr_options &o = h->opt;
     int maxl = o.amg_max_levels < 1 ? 1 : (o.amg_max_levels > 32 ? 32 : o.amg_max_levels);
-    G.amg[0].A = A0;
+    if (own_copy) {
+        if (copy_csr(A0, G.amg[0].A, ar, s)) return fail(h, MGR_ERR_NOMEM, "amg level 0");
+    } else {
+        G.amg[0].A = A0;
+    }
+    A0 = G.amg[0].A;
     G.amg[0].func = ar.alloc<int>(A0.n + 1);
     if (!G.amg[0].func) return fail(h, MGR_ERR_NOMEM, "amg func");
     launch_iota_mod(G.amg[0].func, A0.n, nfunc < 1 ? 1 : nfunc, s);
@@ -313,14 +342,206 @@ static mgr_status setup_amg(mgr_handle h, AmgH &G, DCSR A0, int nfunc) {
     for (int q = 0; q < G.namg; q++) {
         AmgLevel &L = G.amg[q];
         int n = L.A.n;
-        if (to_f32(h, L.A) || to_f32(h, L.AT)) return fail(h, MGR_ERR_NOMEM, "fp32 copies");
-        if (q < G.namg - 1 && (to_f32(h, L.P) || to_f32(h, L.R))) return fail(h, MGR_ERR_NOMEM, "fp32 copies");
+        if (to_f32(ar, L.A, s) || to_f32(ar, L.AT, s)) return fail(h, MGR_ERR_NOMEM, "fp32 copies");
+        if (q < G.namg - 1 && (to_f32(ar, L.P, s) || to_f32(ar, L.R, s))) return fail(h, MGR_ERR_NOMEM, "fp32 copies");
         L.r = ar.alloc<double>(n + 1); L.x = ar.alloc<double>(n + 1);
         L.xw = ar.alloc<double>(n + 1); L.res = ar.alloc<double>(n + 1);
         L.r32 = ar.alloc<float>(n + 1); L.x32 = ar.alloc<float>(n + 1);
         L.xw32 = ar.alloc<float>(n + 1); L.res32 = ar.alloc<float>(n + 1);
         if (!L.r || !L.x || !L.xw || !L.res || !L.r32 || !L.x32 || !L.xw32 || !L.res32)
             return fail(h, MGR_ERR_NOMEM, "amg vectors");
+    }
+    return MGR_OK;
+}
+
+// The MGR hierarchy below the outer operator (Sec. 3): the level-0 scalar
+// CSR, every MGR level (split, D_FF, W, Z, coarse operator, F-relaxation
+// AMG), the final coarse block's AMG hierarchy, their SELL copies and the
+// fused AMG tail, all in h->lar (F-relaxation hierarchies in their own
+// arenas).  reuse: keep the AMG F-relaxation hierarchies a previous build
+// left (mgr_refresh).  On failure the handle is not usable (ready stays
+// false).
+static mgr_status build_levels(mgr_handle h, bool reuse) {
+    Arena &ar = h->lar;
+    cudaStream_t s = h->s;
+    const int nb = h->nb, b = h->b, n = h->n;
+    const long long nnzb = h->nnzb;
+    // level-0 scalar CSR
+    DCSR A0;
+    A0.n = A0.m = n;
+    A0.nnz = (int)(nnzb * b * b);
+    A0.rp = ar.alloc<int>(n + 1);
+    A0.ci = ar.alloc<int>(A0.nnz);
+    A0.v = ar.alloc<double>(A0.nnz);
+    if (!A0.rp || !A0.ci || !A0.v) return fail(h, MGR_ERR_NOMEM, "scalar copy");
+    launch_bsr_to_csr(nb, b, h->brp, h->bci, h->bval, A0, s);
+    h->A0 = A0;
+    DCSR cur = A0;
+    int *gdof = nullptr;
+    for (int l = 0; l < h->nlev; l++) {
+        MgrLevel &L = h->lev[l];
+        L.A = cur; L.gdof = gdof; L.n = cur.n;
+        L.relax = h->opt.relax_type[l];
+        L.sweeps = h->opt.relax_sweeps[l] < 1 ? 1 : h->opt.relax_sweeps[l];
+        L.omega = h->opt.relax_weight[l];
+        if (L.relax < MGR_RELAX_JACOBI || L.relax > MGR_RELAX_AMG) { return fail(h, MGR_ERR_INVALID, "relax type"); }
+        L.rtype = h->opt.restrict_type[l];
+        if (L.rtype < MGR_RESTRICT_INJECTION || L.rtype > MGR_RESTRICT_JACOBI) {
+            return fail(h, MGR_ERR_INVALID, "restriction type");
+        }
+        if (L.rtype == MGR_RESTRICT_JACOBI && L.relax == MGR_RELAX_BLOCK_JACOBI) {
+            return fail(h, MGR_ERR_UNSUPPORTED, "the restriction of Eq. 5 takes a diagonal D_FF");
+        }
+        int nl = L.n;
+        int *isF = ar.alloc<int>(nl + 1), *isC = ar.alloc<int>(nl + 1);
+        int *fpos = ar.alloc<int>(nl + 1), *cpos = ar.alloc<int>(nl + 1);
+        int *fmap = ar.alloc<int>(nl + 1), *cmap = ar.alloc<int>(nl + 1);
+        L.fidx = ar.alloc<int>(nl + 1); L.cidx = ar.alloc<int>(nl + 1);
+        if (!isF || !isC || !fpos || !cpos || !fmap || !cmap || !L.fidx || !L.cidx) {
+            return fail(h, MGR_ERR_NOMEM, "level maps");
+        }
+        launch_level_flags(h->dlevel, gdof, nl, l, isF, isC, h->errw, s);
+        int nF = 0, nC = 0;
+        scan_exclusive(isF, fpos, nl, s, ar, &nF);
+        scan_exclusive(isC, cpos, nl, s, ar, &nC);
+        if (read_errw(h)) { return fail(h, MGR_ERR_INVALID, "labels: a dof eliminated twice"); }
+        if (nF == 0 || nC == 0) {
+            char buf[128];
+            snprintf(buf, sizeof buf, "MGR level %d has an empty %s set", l, nF == 0 ? "F" : "C");
+            return fail(h, MGR_ERR_INVALID, buf);
+        }
+        L.nF = nF; L.nC = nC;
+        launch_index_maps(isF, isC, fpos, cpos, nl, L.fidx, L.cidx, fmap, cmap, s);
+        DCSR ACC;
+        int rc = extract_submatrix(cur, L.fidx, nF, fmap, nF, L.AFF, s, ar);
+        if (!rc) rc = extract_submatrix(cur, L.fidx, nF, cmap, nC, L.AFC, s, ar);
+        if (!rc) rc = extract_submatrix(cur, L.cidx, nC, fmap, nF, L.ACF, s, ar);
+        if (!rc) rc = extract_submatrix(cur, L.cidx, nC, cmap, nC, ACC, s, ar);
+        L.gstart = ar.alloc<int>(nF + 1); L.gsize = ar.alloc<int>(nF + 1);
+        L.dinv = ar.alloc<double>((size_t)nF * 4 + 4); L.dinv32 = ar.alloc<float>((size_t)nF * 4 + 4);
+        if (rc || !L.gstart || !L.gsize || !L.dinv || !L.dinv32) { return fail(h, MGR_ERR_NOMEM, "level blocks"); }
+        mgr_dinv(L.AFF, L.fidx, gdof, b, L.relax, L.gstart, L.gsize, L.dinv, h->errw, s);
+        if (read_errw(h) & ERRW_SINGULAR) {
+            char buf[128];
+            snprintf(buf, sizeof buf, "singular D_FF (zero diagonal or singular block) at MGR level %d", l);
+            return fail(h, MGR_ERR_SINGULAR, buf);
+        }
+        launch_cast_f32(L.dinv, L.dinv32, (long long)nF * 4, s);
+        if (mgr_build_w(L.AFC, L.gstart, L.gsize, L.dinv, L.W, s, ar)) { return fail(h, MGR_ERR_NOMEM, "W"); }
+        DCSR next;
+        if (transpose(L.ACF, L.ACFT, s, ar)) { return fail(h, MGR_ERR_NOMEM, "level transposes"); }
+        if (L.rtype == MGR_RESTRICT_JACOBI) {
+            // R~ A P~ = Z (A_FF W + A_FC) + (A_CF W + A_CC), Z^T = -D^{-1} A_CF^T
+            DCSR T1, U;
+            if (mgr_build_w(L.ACFT, L.gstart, L.gsize, L.dinv, L.ZT, s, ar) || transpose(L.ZT, L.Z, s, ar) ||
+                spgemm(L.AFF, L.W, &L.AFC, T1, s, ar) || spgemm(L.ACF, L.W, &ACC, U, s, ar) ||
+                spgemm(L.Z, T1, &U, next, s, ar)) {
+                return fail(h, MGR_ERR_NOMEM, "coarse operator");
+            }
+            ar.release(T1.rp); ar.release(T1.ci); ar.release(T1.v);
+            ar.release(U.rp); ar.release(U.ci); ar.release(U.v);
+        } else if (spgemm(L.ACF, L.W, &ACC, next, s, ar)) {
+            return fail(h, MGR_ERR_NOMEM, "coarse operator");
+        }
+        ar.release(ACC.rp); ar.release(ACC.ci); ar.release(ACC.v);
+        const bool keep = reuse && L.relax == MGR_RELAX_AMG && L.famg && L.famg->namg > 0 &&
+                          L.famg->amg[0].A.n == nF && L.famg->amg[0].A.nnz == L.AFF.nnz;
+        if (!keep && L.famg) {
+            L.famg->ar.free_all();
+            delete L.famg;
+            L.famg = nullptr;
+        }
+        L.fshared = false;
+        if (L.relax == MGR_RELAX_AMG && !keep) {
+            // the F-relaxation's AMG hierarchy on A_FF (same AMG parameters as
+            // the final coarse block), in an arena of its own so that a
+            // refresh can keep it; its level 0 holds a copy of A_FF, A_FF^T
+            // and their FP32 copies, which the level shares
+            L.famg = new (std::nothrow) AmgH();
+            if (!L.famg) return fail(h, MGR_ERR_NOMEM, "F-relaxation AMG");
+            L.famg->frelax = 1;
+            mgr_status fst = setup_amg(h, *L.famg, L.AFF, h->opt.relax_functions[l], L.famg->ar, true);
+            if (fst != MGR_OK) {
+                std::string m = "F-relaxation AMG at MGR level " + std::to_string(l) + ": " + h->err;
+                return fail(h, fst, m);
+            }
+            L.AFF = L.famg->amg[0].A;
+            L.AFFT = L.famg->amg[0].AT;
+            L.fshared = true;
+        } else if (transpose(L.AFF, L.AFFT, s, ar)) {
+            // (a kept hierarchy relaxes with the A_FF it was built from; the
+            // level's own residuals use the new A_FF)
+            return fail(h, MGR_ERR_NOMEM, "level transposes");
+        }
+        if (transpose(L.W, L.WT, s, ar)) {
+            return fail(h, MGR_ERR_NOMEM, "level transposes");
+        }
+        if ((!L.fshared && (to_f32(ar, L.AFF, s) || to_f32(ar, L.AFFT, s))) || to_f32(ar, L.ACF, s) ||
+            to_f32(ar, L.W, s) || to_f32(ar, L.ACFT, s) || to_f32(ar, L.WT, s) ||
+            (L.rtype == MGR_RESTRICT_JACOBI && (to_f32(ar, L.Z, s) || to_f32(ar, L.ZT, s)))) {
+            return fail(h, MGR_ERR_NOMEM, "fp32");
+        }
+        L.fiota = ar.alloc<int>(nF + 1);
+        L.zF = ar.alloc<double>(nF + 1); L.rF = ar.alloc<double>(nF + 1);
+        L.vC = ar.alloc<double>(nC + 1); L.eC = ar.alloc<double>(nC + 1);
+        L.zF32 = ar.alloc<float>(nF + 1); L.rF32 = ar.alloc<float>(nF + 1);
+        L.vC32 = ar.alloc<float>(nC + 1); L.eC32 = ar.alloc<float>(nC + 1);
+        if (L.famg) {
+            L.tF = ar.alloc<double>(nF + 1); L.tF32 = ar.alloc<float>(nF + 1);
+            if (!L.tF || !L.tF32) { return fail(h, MGR_ERR_NOMEM, "level vectors"); }
+        }
+        if (L.rtype == MGR_RESTRICT_JACOBI) {
+            L.qF = ar.alloc<double>(nF + 1); L.qF32 = ar.alloc<float>(nF + 1);
+            L.yF = ar.alloc<double>(nF + 1); L.yF32 = ar.alloc<float>(nF + 1);
+            if (!L.qF || !L.qF32 || !L.yF || !L.yF32) { return fail(h, MGR_ERR_NOMEM, "level vectors"); }
+        }
+        int *g2 = ar.alloc<int>(nC + 1);
+        if (!L.fiota || !L.zF || !L.rF || !L.vC || !L.eC || !L.zF32 || !L.rF32 || !L.vC32 || !L.eC32 || !g2) {
+            return fail(h, MGR_ERR_NOMEM, "level vectors");
+        }
+        launch_iota(L.fiota, nF, s);
+        // original dof of each C point (the next level's rows)
+        if (gdof) launch_gather_int(L.cidx, nC, gdof, g2, s);
+        else cudaMemcpyAsync(g2, L.cidx, sizeof(int) * nC, cudaMemcpyDeviceToDevice, s);
+        ar.release(isF); ar.release(isC); ar.release(fpos); ar.release(cpos); ar.release(fmap); ar.release(cmap);
+        gdof = g2;
+        cur = next;
+    }
+    mgr_status st = setup_amg(h, h->H, cur, h->opt.amg_num_functions, ar, false);
+    if (st != MGR_OK) return st;
+    // SELL-C-sigma copies of every matrix the solve phase multiplies with
+    {
+        int rc2 = 0;
+        auto sell_amg = [&](AmgH &G, Arena &gar) {
+            if (G.sell) return;
+            for (int k = 0; k + 1 < G.namg && !rc2; k++) {
+                AmgLevel &A = G.amg[k];
+                DCSR *ms[] = {&A.A, &A.AT, &A.P, &A.R};
+                for (DCSR *m : ms) rc2 |= build_sell(*m, s, gar);
+            }
+            G.sell = !rc2;
+        };
+        for (int l = 0; l < h->nlev && !rc2; l++) {
+            MgrLevel &L = h->lev[l];
+            if (L.famg) sell_amg(*L.famg, L.famg->ar);
+            if (L.fshared && L.famg->namg > 1) {
+                // A_FF and A_FF^T are the F hierarchy's level 0: one SELL copy
+                L.AFF = L.famg->amg[0].A;
+                L.AFFT = L.famg->amg[0].AT;
+                DCSR *ms[] = {&L.ACF, &L.W, &L.ACFT, &L.WT};
+                for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
+            } else {
+                DCSR *ms[] = {&L.AFF, &L.ACF, &L.W, &L.AFFT, &L.ACFT, &L.WT};
+                for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
+            }
+            if (L.rtype == MGR_RESTRICT_JACOBI) rc2 |= build_sell(L.Z, s, ar) | build_sell(L.ZT, s, ar);
+        }
+        sell_amg(h->H, ar);
+        if (rc2) return fail(h, MGR_ERR_NOMEM, "SELL copies");
+    }
+    {
+        const int rc3 = setup_tail(h, h->H, h->opt.amg_tail_nnz, s, ar);
+        if (rc3) return fail(h, rc3 == ST_NOMEM ? MGR_ERR_NOMEM : MGR_ERR_CUDA, "fused AMG tail");
     }
     return MGR_OK;
 }
@@ -397,138 +618,12 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
                     : (ew & 16) ? "missing diagonal block"
                     : "row_ptr/col_idx malformed (unsorted, duplicate or out-of-range column)");
     }
-    // level-0 scalar CSR
-    DCSR A0;
-    A0.n = A0.m = n;
-    A0.nnz = (int)(nnzb * b * b);
-    A0.rp = ar.alloc<int>(n + 1);
-    A0.ci = ar.alloc<int>(A0.nnz);
-    A0.v = ar.alloc<double>(A0.nnz);
-    if (!A0.rp || !A0.ci || !A0.v) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "scalar copy"); }
-    launch_bsr_to_csr(nb, b, h->brp, h->bci, h->bval, A0, s);
-    if (transpose(A0, h->A0T, s, ar)) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "A^T"); }
     h->nlev = cf->num_levels;
-    DCSR cur = A0;
-    int *gdof = nullptr;
-    for (int l = 0; l < h->nlev; l++) {
-        MgrLevel &L = h->lev[l];
-        L.A = cur; L.gdof = gdof; L.n = cur.n;
-        L.relax = h->opt.relax_type[l];
-        L.sweeps = h->opt.relax_sweeps[l] < 1 ? 1 : h->opt.relax_sweeps[l];
-        L.omega = h->opt.relax_weight[l];
-        if (L.relax < MGR_RELAX_JACOBI || L.relax > MGR_RELAX_AMG) { mgr_free(h); return fail(nullptr, MGR_ERR_INVALID, "relax type"); }
-        L.rtype = h->opt.restrict_type[l];
-        if (L.rtype < MGR_RESTRICT_INJECTION || L.rtype > MGR_RESTRICT_JACOBI) {
-            mgr_free(h); return fail(nullptr, MGR_ERR_INVALID, "restriction type");
-        }
-        if (L.rtype == MGR_RESTRICT_JACOBI && L.relax == MGR_RELAX_BLOCK_JACOBI) {
-            mgr_free(h); return fail(nullptr, MGR_ERR_UNSUPPORTED, "the restriction of Eq. 5 takes a diagonal D_FF");
-        }
-        int nl = L.n;
-        int *isF = ar.alloc<int>(nl + 1), *isC = ar.alloc<int>(nl + 1);
-        int *fpos = ar.alloc<int>(nl + 1), *cpos = ar.alloc<int>(nl + 1);
-        int *fmap = ar.alloc<int>(nl + 1), *cmap = ar.alloc<int>(nl + 1);
-        L.fidx = ar.alloc<int>(nl + 1); L.cidx = ar.alloc<int>(nl + 1);
-        if (!isF || !isC || !fpos || !cpos || !fmap || !cmap || !L.fidx || !L.cidx) {
-            mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level maps");
-        }
-        launch_level_flags(h->dlevel, gdof, nl, l, isF, isC, h->errw, s);
-        int nF = 0, nC = 0;
-        scan_exclusive(isF, fpos, nl, s, ar, &nF);
-        scan_exclusive(isC, cpos, nl, s, ar, &nC);
-        if (read_errw(h)) { mgr_free(h); return fail(nullptr, MGR_ERR_INVALID, "labels: a dof eliminated twice"); }
-        if (nF == 0 || nC == 0) {
-            char buf[128];
-            snprintf(buf, sizeof buf, "MGR level %d has an empty %s set", l, nF == 0 ? "F" : "C");
-            mgr_free(h); return fail(nullptr, MGR_ERR_INVALID, buf);
-        }
-        L.nF = nF; L.nC = nC;
-        launch_index_maps(isF, isC, fpos, cpos, nl, L.fidx, L.cidx, fmap, cmap, s);
-        DCSR ACC;
-        int rc = extract_submatrix(cur, L.fidx, nF, fmap, nF, L.AFF, s, ar);
-        if (!rc) rc = extract_submatrix(cur, L.fidx, nF, cmap, nC, L.AFC, s, ar);
-        if (!rc) rc = extract_submatrix(cur, L.cidx, nC, fmap, nF, L.ACF, s, ar);
-        if (!rc) rc = extract_submatrix(cur, L.cidx, nC, cmap, nC, ACC, s, ar);
-        L.gstart = ar.alloc<int>(nF + 1); L.gsize = ar.alloc<int>(nF + 1);
-        L.dinv = ar.alloc<double>((size_t)nF * 4 + 4); L.dinv32 = ar.alloc<float>((size_t)nF * 4 + 4);
-        if (rc || !L.gstart || !L.gsize || !L.dinv || !L.dinv32) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level blocks"); }
-        mgr_dinv(L.AFF, L.fidx, gdof, b, L.relax, L.gstart, L.gsize, L.dinv, h->errw, s);
-        if (read_errw(h) & ERRW_SINGULAR) {
-            char buf[128];
-            snprintf(buf, sizeof buf, "singular D_FF (zero diagonal or singular block) at MGR level %d", l);
-            mgr_free(h); return fail(nullptr, MGR_ERR_SINGULAR, buf);
-        }
-        launch_cast_f32(L.dinv, L.dinv32, (long long)nF * 4, s);
-        if (mgr_build_w(L.AFC, L.gstart, L.gsize, L.dinv, L.W, s, ar)) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "W"); }
-        DCSR next;
-        if (transpose(L.ACF, L.ACFT, s, ar)) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level transposes"); }
-        if (L.rtype == MGR_RESTRICT_JACOBI) {
-            // R~ A P~ = Z (A_FF W + A_FC) + (A_CF W + A_CC), Z^T = -D^{-1} A_CF^T
-            DCSR T1, U;
-            if (mgr_build_w(L.ACFT, L.gstart, L.gsize, L.dinv, L.ZT, s, ar) || transpose(L.ZT, L.Z, s, ar) ||
-                spgemm(L.AFF, L.W, &L.AFC, T1, s, ar) || spgemm(L.ACF, L.W, &ACC, U, s, ar) ||
-                spgemm(L.Z, T1, &U, next, s, ar)) {
-                mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "coarse operator");
-            }
-            ar.release(T1.rp); ar.release(T1.ci); ar.release(T1.v);
-            ar.release(U.rp); ar.release(U.ci); ar.release(U.v);
-        } else if (spgemm(L.ACF, L.W, &ACC, next, s, ar)) {
-            mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "coarse operator");
-        }
-        ar.release(ACC.rp); ar.release(ACC.ci); ar.release(ACC.v);
-        if (L.relax == MGR_RELAX_AMG) {
-            // the F-relaxation's AMG hierarchy on A_FF (same AMG parameters as
-            // the final coarse block); its level 0 holds A_FF, A_FF^T and their
-            // FP32 copies, which the level shares
-            L.famg = new (std::nothrow) AmgH();
-            if (!L.famg) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "F-relaxation AMG"); }
-            L.famg->frelax = 1;
-            mgr_status fst = setup_amg(h, *L.famg, L.AFF, h->opt.relax_functions[l]);
-            if (fst != MGR_OK) {
-                std::string m = "F-relaxation AMG at MGR level " + std::to_string(l) + ": " + h->err;
-                mgr_free(h); return fail(nullptr, fst, m);
-            }
-            L.AFF = L.famg->amg[0].A;
-            L.AFFT = L.famg->amg[0].AT;
-        } else if (transpose(L.AFF, L.AFFT, s, ar)) {
-            mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level transposes");
-        }
-        if (transpose(L.W, L.WT, s, ar)) {
-            mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level transposes");
-        }
-        if ((!L.famg && (to_f32(h, L.AFF) || to_f32(h, L.AFFT))) || to_f32(h, L.ACF) || to_f32(h, L.W) ||
-            to_f32(h, L.ACFT) || to_f32(h, L.WT) ||
-            (L.rtype == MGR_RESTRICT_JACOBI && (to_f32(h, L.Z) || to_f32(h, L.ZT)))) {
-            mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "fp32");
-        }
-        L.fiota = ar.alloc<int>(nF + 1);
-        L.zF = ar.alloc<double>(nF + 1); L.rF = ar.alloc<double>(nF + 1);
-        L.vC = ar.alloc<double>(nC + 1); L.eC = ar.alloc<double>(nC + 1);
-        L.zF32 = ar.alloc<float>(nF + 1); L.rF32 = ar.alloc<float>(nF + 1);
-        L.vC32 = ar.alloc<float>(nC + 1); L.eC32 = ar.alloc<float>(nC + 1);
-        if (L.famg) {
-            L.tF = ar.alloc<double>(nF + 1); L.tF32 = ar.alloc<float>(nF + 1);
-            if (!L.tF || !L.tF32) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level vectors"); }
-        }
-        if (L.rtype == MGR_RESTRICT_JACOBI) {
-            L.qF = ar.alloc<double>(nF + 1); L.qF32 = ar.alloc<float>(nF + 1);
-            L.yF = ar.alloc<double>(nF + 1); L.yF32 = ar.alloc<float>(nF + 1);
-            if (!L.qF || !L.qF32 || !L.yF || !L.yF32) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level vectors"); }
-        }
-        int *g2 = ar.alloc<int>(nC + 1);
-        if (!L.fiota || !L.zF || !L.rF || !L.vC || !L.eC || !L.zF32 || !L.rF32 || !L.vC32 || !L.eC32 || !g2) {
-            mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "level vectors");
-        }
-        launch_iota(L.fiota, nF, s);
-        // original dof of each C point (the next level's rows)
-        if (gdof) launch_gather_int(L.cidx, nC, gdof, g2, s);
-        else cudaMemcpyAsync(g2, L.cidx, sizeof(int) * nC, cudaMemcpyDeviceToDevice, s);
-        ar.release(isF); ar.release(isC); ar.release(fpos); ar.release(cpos); ar.release(fmap); ar.release(cmap);
-        gdof = g2;
-        cur = next;
+    {
+        mgr_status st = build_levels(h, false);
+        if (st != MGR_OK) { std::string m = h->err; mgr_free(h); return fail(nullptr, st, m); }
     }
-    mgr_status st = setup_amg(h, h->H, cur, h->opt.amg_num_functions);
-    if (st != MGR_OK) { std::string m = h->err; mgr_free(h); return fail(nullptr, st, m); }
+    if (transpose(h->A0, h->A0T, s, ar)) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "A^T"); }
     // Krylov workspace
     Krylov &K = h->kr;
     K.m = h->opt.restart; K.n = n; K.nblk = multidot_blocks(n);
@@ -553,32 +648,9 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
     if (!K.V || !K.Z || !K.r || !K.H || !K.partial || !K.stat || !K.hstat) {
         mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "Krylov workspace");
     }
-    // SELL-C-sigma copies of every matrix the solve phase multiplies with
+    // SELL-C-sigma copies of the outer operator and its transpose
     {
         int rc2 = 0;
-        auto sell_amg = [&](AmgH &G) {
-            for (int k = 0; k + 1 < G.namg && !rc2; k++) {
-                AmgLevel &A = G.amg[k];
-                DCSR *ms[] = {&A.A, &A.AT, &A.P, &A.R};
-                for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
-            }
-        };
-        for (int l = 0; l < h->nlev && !rc2; l++) {
-            MgrLevel &L = h->lev[l];
-            if (L.famg && L.famg->namg > 1) {
-                // A_FF and A_FF^T are the F hierarchy's level 0: one SELL copy
-                sell_amg(*L.famg);
-                L.AFF = L.famg->amg[0].A;
-                L.AFFT = L.famg->amg[0].AT;
-                DCSR *ms[] = {&L.ACF, &L.W, &L.ACFT, &L.WT};
-                for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
-            } else {
-                DCSR *ms[] = {&L.AFF, &L.ACF, &L.W, &L.AFFT, &L.ACFT, &L.WT};
-                for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
-            }
-            if (L.rtype == MGR_RESTRICT_JACOBI) rc2 |= build_sell(L.Z, s, ar) | build_sell(L.ZT, s, ar);
-        }
-        sell_amg(h->H);
         if (b == 1) {
             h->Aout.n = h->Aout.m = n;
             h->Aout.nnz = (int)nnzb;
@@ -588,16 +660,10 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
         rc2 |= build_sell(h->A0T, s, ar);
         if (rc2) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "SELL copies"); }
     }
-    {
-        const int rc3 = setup_tail(h, h->H, h->opt.amg_tail_nnz, s, ar);
-        if (rc3) {
-            mgr_free(h);
-            return fail(nullptr, rc3 == ST_NOMEM ? MGR_ERR_NOMEM : MGR_ERR_CUDA, "fused AMG tail");
-        }
-    }
     cudaStreamSynchronize(s);
     if (cudaGetLastError() != cudaSuccess) { mgr_free(h); return cuda_fail(nullptr, "setup"); }
     h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    h->ready = true;
     *out = h;
     return MGR_OK;
 }
@@ -1046,6 +1112,7 @@ static void outer_residual(mgr_handle h, const double *x, const double *bvec, do
 
 extern "C" mgr_status mgr_apply(mgr_handle h, const double *v, double *z) {
     if (!h || !v || !z) return fail(h, MGR_ERR_INVALID, "NULL argument");
+    if (!h->ready) return fail(h, MGR_ERR_INVALID, "no hierarchy (a refresh failed)");
     vcycle(h, v, z, 0);
     if (cudaGetLastError() != cudaSuccess) return cuda_fail(h, "mgr_apply");
     return MGR_OK;
@@ -1053,6 +1120,7 @@ extern "C" mgr_status mgr_apply(mgr_handle h, const double *v, double *z) {
 
 extern "C" mgr_status mgr_apply_transpose(mgr_handle h, const double *v, double *z) {
     if (!h || !v || !z) return fail(h, MGR_ERR_INVALID, "NULL argument");
+    if (!h->ready) return fail(h, MGR_ERR_INVALID, "no hierarchy (a refresh failed)");
     vcycle(h, v, z, 1);
     if (cudaGetLastError() != cudaSuccess) return cuda_fail(h, "mgr_apply_transpose");
     return MGR_OK;
@@ -1131,6 +1199,7 @@ static cudaError_t run_step(mgr_handle h, int j, int trans) {
 static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, int maxit, int trans,
                          mgr_solve_info *info) {
     if (!h || !b || !x) return fail(h, MGR_ERR_INVALID, "NULL argument");
+    if (!h->ready) return fail(h, MGR_ERR_INVALID, "no hierarchy (a refresh failed)");
     if (!(rtol >= 0.0)) return fail(h, MGR_ERR_INVALID, "rtol must be >= 0");
     auto t0 = std::chrono::steady_clock::now();
     Krylov &K = h->kr;
@@ -1242,12 +1311,15 @@ extern "C" mgr_status mgr_update_values(mgr_handle h, const double *val, int32_t
     if (!h || !val) return fail(h, MGR_ERR_INVALID, "NULL argument");
     cudaStream_t s = h->s;
     const long long nv = h->nnzb * h->b * h->b;
-    cudaMemcpyAsync(h->bval, val, sizeof(double) * nv,
-                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
-    launch_validate_bsr(h->nb, h->b, h->brp, h->bci, h->bval, h->errw, s);
-    if (read_errw(h)) return fail(h, MGR_ERR_INVALID, "non-finite matrix value");
-    // the transposed outer operator: same pattern, positions unchanged
     Arena tmp;
+    // validated in a scratch copy first: invalid values leave the handle as it was
+    double *nvv = tmp.alloc<double>(nv + 1);
+    if (!nvv) return fail(h, MGR_ERR_NOMEM, "update scratch");
+    cudaMemcpyAsync(nvv, val, sizeof(double) * nv, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+    launch_validate_bsr(h->nb, h->b, h->brp, h->bci, nvv, h->errw, s);
+    if (read_errw(h)) { tmp.free_all(); return fail(h, MGR_ERR_INVALID, "non-finite matrix value"); }
+    cudaMemcpyAsync(h->bval, nvv, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s);
+    // the transposed outer operator: same pattern, positions unchanged
     DCSR A0, T;
     A0.n = A0.m = h->n;
     A0.nnz = (int)nv;
@@ -1263,6 +1335,36 @@ extern "C" mgr_status mgr_update_values(mgr_handle h, const double *val, int32_t
     cudaStreamSynchronize(s);
     tmp.free_all();
     if (cudaGetLastError() != cudaSuccess) return cuda_fail(h, "mgr_update_values");
+    return MGR_OK;
+}
+
+extern "C" mgr_status mgr_refresh(mgr_handle h, const double *val, int32_t on_device) {
+    if (!h || !val) return fail(h, MGR_ERR_INVALID, "NULL argument");
+    if (h->in_batch) return fail(h, MGR_ERR_UNSUPPORTED, "handles of a batch are not refreshed one by one");
+    auto t0 = std::chrono::steady_clock::now();
+    mgr_status st = mgr_update_values(h, val, on_device);
+    if (st != MGR_OK) return st;
+    cudaStream_t s = h->s;
+    cudaStreamSynchronize(s);
+    // captured graphs and the fused tail point into the old hierarchy
+    for (int d = 0; d < 2; d++) {
+        for (auto g : h->kr.graphs[d]) if (g) cudaGraphExecDestroy(g);
+        h->kr.graphs[d].clear();
+    }
+    h->ready = false;
+    for (int l = 0; l < MGR_MAX_LEVELS; l++) {
+        AmgH *keep = h->lev[l].famg;
+        h->lev[l] = MgrLevel();
+        h->lev[l].famg = keep;
+    }
+    h->H = AmgH();
+    h->lar.free_all();
+    st = build_levels(h, true);
+    if (st != MGR_OK) return st;
+    cudaStreamSynchronize(s);
+    if (cudaGetLastError() != cudaSuccess) return cuda_fail(h, "mgr_refresh");
+    h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    h->ready = true;
     return MGR_OK;
 }
 
@@ -1288,9 +1390,11 @@ extern "C" void mgr_free(mgr_handle h) {
     if (!h) return;
     cudaStreamSynchronize(h->s);
     for (int l = 0; l < MGR_MAX_LEVELS; l++) {
+        if (h->lev[l].famg) h->lev[l].famg->ar.free_all();
         delete h->lev[l].famg;
         h->lev[l].famg = nullptr;
     }
+    h->lar.free_all();
     for (int d = 0; d < 2; d++)
         for (auto g : h->kr.graphs[d]) if (g) cudaGraphExecDestroy(g);
     if (h->kr.hstat) cudaFreeHost(h->kr.hstat);
@@ -1888,6 +1992,7 @@ extern "C" mgr_status mgr_setup_batched(int32_t nsys, const mgr_bsr *A, const mg
             snprintf(buf, sizeof buf, "system %d: ", s);
             return bfail(nullptr, st, buf + m);
         }
+        h->in_batch = true;
         bh->hs.push_back(h);
         bh->kmax = std::max(bh->kmax, h->H.namg - 1);
     }

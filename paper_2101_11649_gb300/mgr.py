@@ -90,6 +90,7 @@ def lib(build_if_missing: bool = True):
     L.mgr_solve_transpose.argtypes = [vp, vp, vp, dp, i32, C.POINTER(mgr_solve_info)]
     L.mgr_grad_values.argtypes = [vp, vp, vp, vp]
     L.mgr_update_values.argtypes = [vp, vp, i32]
+    L.mgr_refresh.argtypes = [vp, vp, i32]
     L.mgr_bsr_spmv.argtypes = [i32, i32, vp, vp, vp, vp, vp, dp, dp, vp]
     L.mgr_free.argtypes = [vp]
     L.mgr_free.restype = None
@@ -262,6 +263,18 @@ class MGRSolver:
         else:
             v = np.ascontiguousarray(val, np.float64)
             _check(lib().mgr_update_values(self.h, v.ctypes.data, 0), self.h)
+
+    def refresh(self, val):
+        """New values of A (same pattern): the MGR levels and the final AMG
+        hierarchy are rebuilt from them, AMG F-relaxation hierarchies are
+        kept (setup reuse)."""
+        import torch
+        if isinstance(val, torch.Tensor) and val.is_cuda:
+            v = val.to(torch.float64).contiguous()
+            _check(lib().mgr_refresh(self.h, _ptr(v), 1), self.h)
+        else:
+            v = np.ascontiguousarray(val, np.float64)
+            _check(lib().mgr_refresh(self.h, v.ctypes.data, 0), self.h)
 
     def grad_values(self, lam, x):
         import torch

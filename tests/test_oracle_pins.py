@@ -668,3 +668,66 @@ def test_jacobi_restriction_cycle_matches_dense_algorithm_1(sweeps, omega):
     v = np.random.default_rng(12).standard_normal(s.n)
     for got, ref in ((o.apply(v), Mi @ v), (o.apply_transpose(v), Mi.T @ v)):
         assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+# ------------------------------------------ setup reuse (Sec. 4.3, Sec. 5)
+def _perturbed(sysm, seed, touch_uu):
+    """The same pattern with new values: pressure rows and couplings scaled
+    by U[0.9, 1.1] per block; the displacement block A_uu too if touch_uu."""
+    import dataclasses
+    rng = np.random.default_rng(seed)
+    NN = (sysm.meta["ne"] + 1) ** 3
+    rows = np.repeat(np.arange(sysm.nb), np.diff(sysm.row_ptr))
+    cols = sysm.col_idx
+    sel = (rows >= NN) | (cols >= NN) | touch_uu
+    val = sysm.val.copy()
+    val[sel] *= rng.uniform(0.9, 1.1, int(sel.sum()))[:, None, None]
+    if sysm.n_pad:   # the padding dofs (F-points, identity rows) stay as they are
+        last = np.flatnonzero((rows == sysm.nb - 1) & (cols == sysm.nb - 1))[0]
+        for t in range(sysm.b - sysm.n_pad, sysm.b):
+            val[last, t, t] = sysm.val[last, t, t]
+    return dataclasses.replace(sysm, val=val)
+
+
+def _mgr_u_opts():
+    return O.Options(relax=["amg"], relax_functions=[3], max_coarse=32)
+
+
+def test_reuse_with_unchanged_A_uu_equals_a_fresh_setup():
+    """MGR_U keeps the displacement AMG hierarchy across Newton steps; when
+    A_uu did not change, the refreshed preconditioner is the one a fresh
+    setup builds (same coarse operators and final AMG, same cycle bits)."""
+    s1 = make_poromech(6, 4, strategy="mgr_u")
+    s2 = _perturbed(s1, 1, touch_uu=False)
+    o1 = O.Oracle(s1, _mgr_u_opts())
+    o2 = O.Oracle(s2, _mgr_u_opts(), reuse=o1)
+    f2 = O.Oracle(s2, _mgr_u_opts())
+    for lv in (0, 1):
+        assert np.array_equal(o2.mgr_matrix(lv, "A")[2], f2.mgr_matrix(lv, "A")[2])
+    assert o2.amg_nlevels == f2.amg_nlevels and o2.frelax_amg_nlevels(0) == f2.frelax_amg_nlevels(0)
+    v = np.random.default_rng(2).standard_normal(s1.n)
+    assert np.array_equal(o2.apply(v), f2.apply(v))
+    assert np.array_equal(o2.apply_transpose(v), f2.apply_transpose(v))
+
+
+def test_reuse_with_changed_A_uu_keeps_the_old_F_hierarchy():
+    """When A_uu changed, the F-relaxation still uses the hierarchy built from
+    the old A_uu while W, the coarse block and its AMG hierarchy follow the
+    new values; the stale preconditioner still converges."""
+    s1 = make_poromech(6, 4, strategy="mgr_u")
+    s2 = _perturbed(s1, 3, touch_uu=True)
+    o1 = O.Oracle(s1, _mgr_u_opts())
+    old_A0 = o1.amg_matrix(0, "A", frelax_level=0)
+    old_A1 = o1.amg_matrix(1, "A", frelax_level=0)
+    o2 = O.Oracle(s2, _mgr_u_opts(), reuse=o1)
+    f2 = O.Oracle(s2, _mgr_u_opts())
+    kept0 = o2.amg_matrix(0, "A", frelax_level=0)
+    assert np.array_equal(kept0[2], old_A0[2])
+    assert np.array_equal(o2.amg_matrix(1, "A", frelax_level=0)[2], old_A1[2])
+    assert not np.array_equal(kept0[2], o2.mgr_matrix(0, "AFF")[2])
+    assert np.array_equal(o2.mgr_matrix(0, "AFF")[2], f2.mgr_matrix(0, "AFF")[2])
+    assert np.array_equal(o2.mgr_matrix(1, "A")[2], f2.mgr_matrix(1, "A")[2])
+    for k in range(f2.amg_nlevels):
+        assert np.array_equal(o2.amg_matrix(k, "A")[2], f2.amg_matrix(k, "A")[2])
+    r = o2.solve(s2.rhs, rtol=1e-8, maxit=300)
+    assert r["status"] == 0 and r["relres"] <= 1e-8
