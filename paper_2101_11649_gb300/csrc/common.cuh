@@ -172,6 +172,12 @@ void launch_coarse_func(const int *cf, const int *func, const DCSR &P, int *cfun
 void launch_iota_mod(int *func, int n, int nf, cudaStream_t s);
 int dense_inverse(const DCSR &A, double *inv, int *errw, cudaStream_t s, Arena &ar);
 void launch_cast_f32(const double *in, float *out, long long n, cudaStream_t s);
+// src[q] = index into the BSR value array of entry q of the scalar transpose
+int transpose_sources(int nb, int b, const int *brp, const int *bci, long long nnzb, int *src,
+                      cudaStream_t s);
+void launch_gather_f64(const int *src, const double *in, double *out, long long n, cudaStream_t s);
+// 1 when the n values of a and b are bitwise equal, 0 when not, -1 on error
+int same_bits(const double *a, const double *b, long long n, cudaStream_t s, Arena &ar);
 
 // ------------------------------------------------------------- solve phase
 // BSR y = alpha A x + beta y (b in 1..4) on FP64

@@ -129,6 +129,7 @@ struct mgr_ctx {
     int *brp = nullptr, *bci = nullptr;
     double *bval = nullptr;
     DCSR A0T;  // scalar transpose of A (adjoint outer products)
+    int *a0t_src = nullptr;  // BSR value index of each A0T entry (value updates)
     DCSR Aout; // CSR view of A when b == 1 (the outer product runs on its SELL copy)
     int8_t *dlevel = nullptr;
     int nlev = 0;
@@ -452,6 +453,18 @@ static mgr_status build_levels(mgr_handle h, bool reuse) {
             L.famg = nullptr;
         }
         L.fshared = false;
+        if (keep) {
+            // an unchanged A_FF is shared with the kept hierarchy's level 0
+            // (no second transpose, FP32 or SELL copy)
+            const int same = same_bits(L.AFF.v, L.famg->amg[0].A.v, L.AFF.nnz, s, ar);
+            if (same < 0) return fail(h, MGR_ERR_CUDA, "A_FF comparison");
+            if (same) {
+                ar.release(L.AFF.rp); ar.release(L.AFF.ci); ar.release(L.AFF.v);
+                L.AFF = L.famg->amg[0].A;
+                L.AFFT = L.famg->amg[0].AT;
+                L.fshared = true;
+            }
+        }
         if (L.relax == MGR_RELAX_AMG && !keep) {
             // the F-relaxation's AMG hierarchy on A_FF (same AMG parameters as
             // the final coarse block), in an arena of its own so that a
@@ -468,7 +481,7 @@ static mgr_status build_levels(mgr_handle h, bool reuse) {
             L.AFF = L.famg->amg[0].A;
             L.AFFT = L.famg->amg[0].AT;
             L.fshared = true;
-        } else if (transpose(L.AFF, L.AFFT, s, ar)) {
+        } else if (!L.fshared && transpose(L.AFF, L.AFFT, s, ar)) {
             // (a kept hierarchy relaxes with the A_FF it was built from; the
             // level's own residuals use the new A_FF)
             return fail(h, MGR_ERR_NOMEM, "level transposes");
@@ -624,6 +637,10 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
         if (st != MGR_OK) { std::string m = h->err; mgr_free(h); return fail(nullptr, st, m); }
     }
     if (transpose(h->A0, h->A0T, s, ar)) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "A^T"); }
+    h->a0t_src = ar.alloc<int>((size_t)h->A0T.nnz + 1);
+    if (!h->a0t_src || transpose_sources(nb, b, h->brp, h->bci, nnzb, h->a0t_src, s)) {
+        mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "A^T sources");
+    }
     // Krylov workspace
     Krylov &K = h->kr;
     K.m = h->opt.restart; K.n = n; K.nblk = multidot_blocks(n);
@@ -1319,17 +1336,8 @@ extern "C" mgr_status mgr_update_values(mgr_handle h, const double *val, int32_t
     launch_validate_bsr(h->nb, h->b, h->brp, h->bci, nvv, h->errw, s);
     if (read_errw(h)) { tmp.free_all(); return fail(h, MGR_ERR_INVALID, "non-finite matrix value"); }
     cudaMemcpyAsync(h->bval, nvv, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s);
-    // the transposed outer operator: same pattern, positions unchanged
-    DCSR A0, T;
-    A0.n = A0.m = h->n;
-    A0.nnz = (int)nv;
-    A0.rp = tmp.alloc<int>(h->n + 1);
-    A0.ci = tmp.alloc<int>(nv + 1);
-    A0.v = tmp.alloc<double>(nv + 1);
-    if (!A0.rp || !A0.ci || !A0.v) { tmp.free_all(); return fail(h, MGR_ERR_NOMEM, "update scratch"); }
-    launch_bsr_to_csr(h->nb, h->b, h->brp, h->bci, h->bval, A0, s);
-    if (transpose(A0, T, s, tmp)) { tmp.free_all(); return fail(h, MGR_ERR_NOMEM, "update transpose"); }
-    cudaMemcpyAsync(h->A0T.v, T.v, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s);
+    // the transposed outer operator: same pattern, one gather of the new values
+    launch_gather_f64(h->a0t_src, h->bval, h->A0T.v, h->A0T.nnz, s);
     if (h->Aout.sptr) refresh_sell(h->Aout, s);
     if (h->A0T.sptr) refresh_sell(h->A0T, s);
     cudaStreamSynchronize(s);

@@ -1282,6 +1282,83 @@ void launch_cast_f32(const double *in, float *out, long long n, cudaStream_t s) 
     k_cast_f32<<<g > 8192 ? 8192 : g, 256, 0, s>>>(in, out, n);
 }
 
+// Positions of the scalar transpose's entries in the BSR value array: the
+// scalar CSR of a BSR whose values are their own indices, transposed; so
+// that new values reach A^T by one gather.
+__global__ void k_iota_f64(double *v, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        v[i] = (double)i;
+}
+
+__global__ void k_f64_to_i32(const double *in, int *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (int)in[i];
+}
+
+int transpose_sources(int nb, int b, const int *brp, const int *bci, long long nnzb, int *src,
+                      cudaStream_t s) {
+    Arena tmp;
+    const long long nv = nnzb * b * b;
+    double *idx = tmp.alloc<double>(nv + 1);
+    DCSR A;
+    A.n = A.m = nb * b;
+    A.nnz = (int)nv;
+    A.rp = tmp.alloc<int>(A.n + 1);
+    A.ci = tmp.alloc<int>(nv + 1);
+    A.v = tmp.alloc<double>(nv + 1);
+    if (!idx || !A.rp || !A.ci || !A.v) { tmp.free_all(); return ST_NOMEM; }
+    unsigned g = GRID(nv, 256);
+    k_iota_f64<<<g > 8192 ? 8192 : g, 256, 0, s>>>(idx, nv);
+    launch_bsr_to_csr(nb, b, brp, bci, idx, A, s);
+    DCSR T;
+    if (transpose(A, T, s, tmp)) { tmp.free_all(); return ST_NOMEM; }
+    k_f64_to_i32<<<g > 8192 ? 8192 : g, 256, 0, s>>>(T.v, src, nv);
+    cudaStreamSynchronize(s);
+    tmp.free_all();
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+__global__ void k_gather_f64(const int *src, const double *in, double *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = in[src[i]];
+}
+
+void launch_gather_f64(const int *src, const double *in, double *out, long long n, cudaStream_t s) {
+    if (n <= 0) return;
+    unsigned g = GRID(n, 256);
+    k_gather_f64<<<g > 8192 ? 8192 : g, 256, 0, s>>>(src, in, out, n);
+}
+
+// flag |= 1 when a and b differ in any bit of their n values
+__global__ void k_bits_differ(const unsigned long long *a, const unsigned long long *b, long long n,
+                              int *flag) {
+    int d = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        d |= a[i] != b[i];
+    if (__syncthreads_or(d) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+int same_bits(const double *a, const double *b, long long n, cudaStream_t s, Arena &ar) {
+    int *flag = ar.alloc<int>(1);
+    if (!flag) return -1;
+    int h = 1;
+    cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (n > 0) {
+        unsigned g = GRID(n, 256);
+        k_bits_differ<<<g > 8192 ? 8192 : g, 256, 0, s>>>((const unsigned long long *)a,
+                                                         (const unsigned long long *)b, n, flag);
+    }
+    cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    ar.release(flag);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    return h ? 0 : 1;
+}
+
 }  // namespace mgr
 
 namespace mgr {
