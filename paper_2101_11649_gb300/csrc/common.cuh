@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -82,14 +83,20 @@ enum { ST_OK = 0, ST_INVALID = 1, ST_NOMEM = 2, ST_CUDA = 3, ST_SINGULAR = 4,
 // Device error word bits written by setup kernels.
 enum { ERRW_SINGULAR = 1, ERRW_INVALID = 2, ERRW_OVERFLOW = 4 };
 
-// Simple device allocator that remembers what it handed out.
+// Device memory of one owner.  Released blocks stay in a pool and serve
+// later requests of about the same size (all work of an owner runs on one
+// stream, so stream order protects a reused block); recycle() returns every
+// block to the pool, trim() gives the pool back to the driver.
 struct Arena {
-    std::vector<void *> blocks;
+    std::vector<std::pair<void *, size_t>> blocks;  // live
+    std::multimap<size_t, void *> pool;             // released, kept for reuse
     size_t bytes = 0;
     int status = ST_OK;
     void *get(size_t nbytes);
     template <class T> T *alloc(size_t count) { return (T *)get(count * sizeof(T)); }
     void release(void *p);
+    void recycle();
+    void trim();
     void free_all();
 };
 

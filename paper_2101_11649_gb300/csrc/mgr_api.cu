@@ -679,6 +679,11 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
     }
     cudaStreamSynchronize(s);
     if (cudaGetLastError() != cudaSuccess) { mgr_free(h); return cuda_fail(nullptr, "setup"); }
+    // setup temporaries go back to the driver
+    h->ar.trim();
+    h->lar.trim();
+    for (int l = 0; l < h->nlev; l++)
+        if (h->lev[l].famg) h->lev[l].famg->ar.trim();
     h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     h->ready = true;
     *out = h;
@@ -1366,10 +1371,13 @@ extern "C" mgr_status mgr_refresh(mgr_handle h, const double *val, int32_t on_de
         h->lev[l].famg = keep;
     }
     h->H = AmgH();
-    h->lar.free_all();
+    h->lar.recycle();  // the new hierarchy has the old one's sizes: reuse its blocks
     st = build_levels(h, true);
     if (st != MGR_OK) return st;
     cudaStreamSynchronize(s);
+    h->lar.trim();
+    for (int l = 0; l < h->nlev; l++)
+        if (h->lev[l].famg) h->lev[l].famg->ar.trim();
     if (cudaGetLastError() != cudaSuccess) return cuda_fail(h, "mgr_refresh");
     h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     h->ready = true;

@@ -18,15 +18,29 @@ namespace mgr {
 
 // ------------------------------------------------------------------ arena
 void *Arena::get(size_t nbytes) {
-    if (nbytes == 0) nbytes = 16;
+    nbytes = (nbytes + 255) & ~(size_t)255;
+    if (nbytes == 0) nbytes = 256;
+    // a pooled block at most 1/8 (plus 64 KiB) larger than the request
+    auto it = pool.lower_bound(nbytes);
+    if (it != pool.end() && it->first <= nbytes + nbytes / 8 + (64u << 10)) {
+        void *p = it->second;
+        blocks.push_back({p, it->first});
+        pool.erase(it);
+        return p;
+    }
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e != cudaSuccess && !pool.empty()) {
+        cudaGetLastError();
+        trim();
+        e = cudaMalloc(&p, nbytes);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         status = ST_NOMEM;
         return nullptr;
     }
-    blocks.push_back(p);
+    blocks.push_back({p, nbytes});
     bytes += nbytes;
     return p;
 }
@@ -34,16 +48,30 @@ void *Arena::get(size_t nbytes) {
 void Arena::release(void *p) {
     if (!p) return;
     for (size_t i = 0; i < blocks.size(); i++)
-        if (blocks[i] == p) {
-            cudaFree(p);
+        if (blocks[i].first == p) {
+            pool.insert({blocks[i].second, p});
             blocks[i] = blocks.back();
             blocks.pop_back();
             return;
         }
 }
 
+void Arena::recycle() {
+    for (auto &b : blocks) pool.insert({b.second, b.first});
+    blocks.clear();
+}
+
+void Arena::trim() {
+    for (auto &q : pool) {
+        cudaFree(q.second);
+        bytes -= q.first;
+    }
+    pool.clear();
+}
+
 void Arena::free_all() {
-    for (void *p : blocks) cudaFree(p);
+    trim();
+    for (auto &b : blocks) cudaFree(b.first);
     blocks.clear();
     bytes = 0;
 }
@@ -1164,7 +1192,7 @@ void launch_iota_mod(int *func, int n, int nf, cudaStream_t s) {
 }
 
 // ------------------------------------------------------- coarsest inverse
-// Gauss-Jordan with partial pivoting on [A | I] (one CTA), n <= 1024.
+// Gauss-Jordan with partial pivoting on [A | I].
 __global__ void k_dense_fill(int n, const int *rp, const int *ci, const double *v, double *M) {
     int i = blockIdx.x;
     if (i >= n) return;
@@ -1175,62 +1203,123 @@ __global__ void k_dense_fill(int n, const int *rp, const int *ci, const double *
 }
 
 // Gauss-Jordan inverse with partial pivoting (the largest |entry| of the
-// column, ties to the lower row), one launch per pivot column over the whole
-// grid.  Step c reads the augmented matrix [A | I] from Min and writes Mout
-// (the two alternate, so no CTA reads a row another CTA is writing): every
-// CTA finds the same pivot p, stages the pivot row scaled by 1/a_pc in
-// shared memory, and updates its share of the entries; row c takes the
-// scaled pivot row, row p the eliminated old row c, and column c becomes
-// e_c.  The operations per entry are those of the one-CTA sweep (a division
-// for the pivot row, a separately rounded multiply and subtract elsewhere).
-static constexpr int GJ_THREADS = 256;
+// column, ties to the lower row), one launch per pivot column over at most
+// one CTA per SM.  Step c reads the augmented matrix [A | I] from Min and
+// writes Mout (the two alternate, so no CTA reads a row another CTA is
+// writing): every CTA takes the pivot p from the per-CTA candidates of the
+// previous step, stages the pivot row scaled by 1/a_pc in shared memory,
+// and updates its share of the entries; row c takes the scaled pivot row,
+// row p the eliminated old row c, and column c becomes e_c.  While it
+// writes column c + 1 it also records its best pivot candidate there, so a
+// step reads 16 bytes per CTA instead of the whole column.  The operations
+// per entry are a division for the pivot row and a separately rounded
+// multiply and subtract elsewhere.
+static constexpr int GJ_THREADS = 512;
 
-__global__ void __launch_bounds__(GJ_THREADS) k_gj_step(int n, int c, const double *__restrict__ Min,
-                                                        double *__restrict__ Mout, int *errw) {
-    extern __shared__ double prow[];  // [2n] scaled pivot row
-    __shared__ double red_v[GJ_THREADS];
-    __shared__ int red_i[GJ_THREADS];
-    const int tid = threadIdx.x;
+struct GJCand {
+    double v;  // |entry|, -1 when the CTA saw no candidate
+    int r;
+    int pad;
+};
+
+__device__ __forceinline__ bool gj_better(double b, int ib, double a, int ia) {
+    return b > a || (b == a && ib < ia);
+}
+
+// CTA-wide best candidate -> cand[blockIdx.x]
+__device__ void gj_block_best(double best, int bi, GJCand *cand) {
+    __shared__ double rv[GJ_THREADS / 32];
+    __shared__ int ri[GJ_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const double b = __shfl_down_sync(0xffffffffu, best, o);
+        const int ib = __shfl_down_sync(0xffffffffu, bi, o);
+        if (gj_better(b, ib, best, bi)) { best = b; bi = ib; }
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { rv[w] = best; ri[w] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = rv[0];
+        int ib = ri[0];
+        for (int q = 1; q < GJ_THREADS / 32; q++)
+            if (gj_better(rv[q], ri[q], b, ib)) { b = rv[q]; ib = ri[q]; }
+        cand[blockIdx.x].v = b;
+        cand[blockIdx.x].r = ib;
+    }
+}
+
+// candidates of column 0 (rows 0..n-1), in the layout the steps use
+__global__ void __launch_bounds__(GJ_THREADS) k_gj_first(int n, const double *__restrict__ M,
+                                                         GJCand *cand) {
     const long long ld = 2LL * n;
     double best = -1.0;
-    int bi = c;
-    for (int r = c + tid; r < n; r += GJ_THREADS) {
-        const double x = fabs(Min[r * ld + c]);
-        if (x > best || (x == best && r < bi)) { best = x; bi = r; }
+    int bi = 0x7fffffff;
+    for (int r = blockIdx.x * GJ_THREADS + threadIdx.x; r < n; r += gridDim.x * GJ_THREADS) {
+        const double x = fabs(M[r * ld]);
+        if (gj_better(x, r, best, bi)) { best = x; bi = r; }
     }
-    red_v[tid] = best;
-    red_i[tid] = bi;
-    __syncthreads();
-    for (int o = GJ_THREADS / 2; o > 0; o >>= 1) {
-        if (tid < o) {
-            const double a = red_v[tid], b = red_v[tid + o];
-            const int ia = red_i[tid], ib = red_i[tid + o];
-            if (b > a || (b == a && ib < ia)) { red_v[tid] = b; red_i[tid] = ib; }
+    gj_block_best(best, bi, cand);
+}
+
+__global__ void __launch_bounds__(GJ_THREADS) k_gj_step(int n, int c, const double *__restrict__ Min,
+                                                        double *__restrict__ Mout,
+                                                        const GJCand *__restrict__ cin, GJCand *cout,
+                                                        int ncand, int *errw) {
+    extern __shared__ double prow[];  // [2n] scaled pivot row, then [nr] row factors
+    __shared__ int piv;
+    pdl_wait();
+    pdl_launch_dependents();
+    const int tid = threadIdx.x;
+    const long long ld = 2LL * n;
+    if (tid < 32) {
+        double best = -1.0;
+        int bi = 0x7fffffff;
+        for (int q = tid; q < ncand; q += 32)
+            if (gj_better(cin[q].v, cin[q].r, best, bi)) { best = cin[q].v; bi = cin[q].r; }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double b = __shfl_down_sync(0xffffffffu, best, o);
+            const int ib = __shfl_down_sync(0xffffffffu, bi, o);
+            if (gj_better(b, ib, best, bi)) { best = b; bi = ib; }
         }
-        __syncthreads();
+        if (tid == 0) piv = (bi >= c && bi < n) ? bi : c;
     }
-    const int p = red_i[0];
+    __syncthreads();
+    const int p = piv;
     const double pv = Min[p * ld + c];
     if (pv == 0.0) {
         if (blockIdx.x == 0 && tid == 0) atomicOr(errw, ERRW_SINGULAR);
         return;
     }
+    // rows r_k = blockIdx.x + k gridDim.x (k < nr) to this CTA, columns to threads;
+    // after the swap row p holds the old row c
+    const int nr = (n - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
+    double *fk = prow + 2 * n;
     for (int t = tid; t < 2 * n; t += GJ_THREADS) prow[t] = Min[p * ld + t] / pv;
-    __syncthreads();
-    const long long tot = (long long)n * ld;
-    for (long long e = (long long)blockIdx.x * GJ_THREADS + tid; e < tot; e += (long long)gridDim.x * GJ_THREADS) {
-        const int r = (int)(e / ld), t = (int)(e % ld);
-        double out;
-        if (r == c) {
-            out = prow[t];
-        } else if (t == c) {
-            out = 0.0;
-        } else {
-            const int src = (r == p) ? c : r;  // after the swap row p holds the old row c
-            out = Min[src * ld + t] - Min[src * ld + c] * prow[t];
-        }
-        Mout[e] = out;
+    for (int k = tid; k < nr; k += GJ_THREADS) {
+        const int r = blockIdx.x + k * gridDim.x;
+        fk[k] = Min[(long long)(r == p ? c : r) * ld + c];
     }
+    __syncthreads();
+    const int cn = c + 1;  // the next pivot column
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int t = tid; t < 2 * n; t += GJ_THREADS) {
+        const double pt = prow[t];
+#pragma unroll 4
+        for (int k = 0; k < nr; k++) {
+            const int r = blockIdx.x + k * gridDim.x;
+            double out;
+            if (r == c) out = pt;
+            else if (t == c) out = 0.0;
+            else out = Min[(long long)(r == p ? c : r) * ld + t] - fk[k] * pt;
+            Mout[r * ld + t] = out;
+            if (t == cn && r >= cn) {
+                const double x = fabs(out);
+                if (gj_better(x, r, best, bi)) { best = x; bi = r; }
+            }
+        }
+    }
+    if (cn < n) gj_block_best(best, bi, cout);
 }
 
 __global__ void k_gj_extract(int n, const double *M, double *inv) {
@@ -1247,19 +1336,33 @@ int dense_inverse(const DCSR &A, double *inv, int *errw, cudaStream_t s, Arena &
     if (n <= 0) return ST_OK;
     double *M = ar.alloc<double>((size_t)n * 2 * n + 1);
     double *M2 = ar.alloc<double>((size_t)n * 2 * n + 1);
-    if (!M || !M2) return ST_NOMEM;
-    k_dense_fill<<<n, 256, 0, s>>>(n, A.rp, A.ci, A.v, M);
     const long long tot = 2LL * n * n;
-    long long blocks = (tot + GJ_THREADS * 8 - 1) / (GJ_THREADS * 8);
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    long long blocks = (tot + GJ_THREADS * 16 - 1) / (GJ_THREADS * 16);
+    if (blocks > n) blocks = n;
+    if (blocks > 152) blocks = 152;
     if (blocks < 1) blocks = 1;
-    const size_t sh = (size_t)2 * n * sizeof(double);
+    GJCand *cand = ar.alloc<GJCand>(2 * blocks);
+    if (!M || !M2 || !cand) return ST_NOMEM;
+    k_dense_fill<<<n, 256, 0, s>>>(n, A.rp, A.ci, A.v, M);
+    k_gj_first<<<(unsigned)blocks, GJ_THREADS, 0, s>>>(n, M, cand);
+    const size_t sh = (size_t)(2 * n + (n + blocks - 1) / blocks) * sizeof(double);
     if (sh > 48 * 1024 &&
         cudaFuncSetAttribute(k_gj_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh) != cudaSuccess)
         return ST_CUDA;
     double *a = M, *b = M2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(GJ_THREADS);
+    cfg.dynamicSmemBytes = sh;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_on() ? 1 : 0;  // the next step's launch overlaps this one's tail
     for (int c = 0; c < n; c++) {
-        k_gj_step<<<(unsigned)blocks, GJ_THREADS, sh, s>>>(n, c, a, b, errw);
+        GJCand *ci = cand + (c & 1) * blocks, *co = cand + ((c + 1) & 1) * blocks;
+        cudaLaunchKernelEx(&cfg, k_gj_step, n, c, (const double *)a, b, (const GJCand *)ci, co, (int)blocks, errw);
         double *t = a;
         a = b;
         b = t;
@@ -1268,6 +1371,7 @@ int dense_inverse(const DCSR &A, double *inv, int *errw, cudaStream_t s, Arena &
     cudaStreamSynchronize(s);
     ar.release(M);
     ar.release(M2);
+    ar.release(cand);
     return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
 }
 
