@@ -289,6 +289,15 @@ mgr_status mgr_get_dinv(mgr_handle h, int32_t level, double *dinv, int32_t *gsiz
 /* Level counts: out[0] = MGR levels, out[1] = AMG levels, out[2] = n. */
 mgr_status mgr_get_info(mgr_handle h, int32_t *out);
 
+/* Structure check of the built hierarchy, in place of a memory checker:
+ * every index array the solve phase reads through (CSR row offsets and
+ * columns, SELL-C-sigma slice offsets, widths, row maps and columns, the
+ * C/F index maps, D_FF block descriptors) is checked on the device against
+ * the size of the array it indexes, and consecutive operators against each
+ * other's shapes.  *violations (host) receives the number of violations
+ * (0 for a sound hierarchy).  Synchronises the stream. */
+mgr_status mgr_check_hierarchy(mgr_handle h, int64_t *violations);
+
 /* ------------------------------------------------------- instrumentation
  * Kernel launches this library has made (all handles, solve-phase kernels,
  * counted on the host when enqueued).  */

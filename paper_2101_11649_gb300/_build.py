@@ -26,6 +26,7 @@ UNITS = {
     "mgr_api.cu": [],
     "noalloc.cu": [],
     "tail.cu": [],
+    "check.cu": [],
 }
 
 

@@ -183,6 +183,12 @@ void launch_cast_f32(const double *in, float *out, long long n, cudaStream_t s);
 int transpose_sources(int nb, int b, const int *brp, const int *bci, long long nnzb, int *src,
                       cudaStream_t s);
 void launch_gather_f64(const int *src, const double *in, double *out, long long n, cudaStream_t s);
+// structure checks (check.cu): violations are added to *bad (device)
+int check_csr(const DCSR &M, unsigned long long *bad, cudaStream_t s, Arena &ar);
+int check_split(int n, const int *fidx, int nF, const int *cidx, int nC, const int *gstart,
+                const int *gsize, unsigned long long *bad, cudaStream_t s, Arena &ar);
+int check_add(unsigned long long *bad, unsigned long long v, cudaStream_t s);
+int check_iota(const int *a, int n, unsigned long long *bad, cudaStream_t s);
 // 1 when the n values of a and b are bitwise equal, 0 when not, -1 on error
 int same_bits(const double *a, const double *b, long long n, cudaStream_t s, Arena &ar);
 

@@ -1499,6 +1499,72 @@ extern "C" mgr_status mgr_get_dinv(mgr_handle h, int32_t level, double *dinv, in
     return MGR_OK;
 }
 
+// Every index array of the hierarchy against the size of what it indexes
+// (check.cu), and the shapes of consecutive operators.
+static int check_amg(const AmgH &G, unsigned long long *bad, cudaStream_t s, Arena &ar) {
+    int rc = 0;
+    unsigned long long hb = 0;
+    for (int k = 0; k < G.namg; k++) {
+        const AmgLevel &L = G.amg[k];
+        rc |= check_csr(L.A, bad, s, ar);
+        rc |= check_csr(L.AT, bad, s, ar);
+        hb += L.A.n != L.A.m || L.AT.n != L.A.n || L.AT.nnz != L.A.nnz;
+        if (k + 1 < G.namg) {
+            const int nc = G.amg[k + 1].A.n;
+            rc |= check_csr(L.P, bad, s, ar);
+            rc |= check_csr(L.R, bad, s, ar);
+            hb += L.P.n != L.A.n || L.P.m != nc || L.R.n != nc || L.R.m != L.A.n;
+        }
+    }
+    hb += G.namg < 1 || G.nco != G.amg[G.namg - 1].A.n;
+    rc |= check_add(bad, hb, s);
+    return rc;
+}
+
+extern "C" mgr_status mgr_check_hierarchy(mgr_handle h, int64_t *violations) {
+    if (!h || !violations) return fail(h, MGR_ERR_INVALID, "NULL argument");
+    if (!h->ready) return fail(h, MGR_ERR_INVALID, "no hierarchy (a refresh failed)");
+    cudaStream_t s = h->s;
+    Arena tmp;
+    unsigned long long *bad = tmp.alloc<unsigned long long>(1);
+    if (!bad) return fail(h, MGR_ERR_NOMEM, "check scratch");
+    cudaMemsetAsync(bad, 0, sizeof(*bad), s);
+    int rc = 0;
+    unsigned long long hb = 0;
+    for (int l = 0; l < h->nlev; l++) {
+        const MgrLevel &L = h->lev[l];
+        const DCSR *ms[] = {&L.AFF, &L.ACF, &L.W, &L.AFFT, &L.ACFT, &L.WT};
+        for (const DCSR *m : ms) rc |= check_csr(*m, bad, s, tmp);
+        hb += L.AFF.n != L.nF || L.AFF.m != L.nF || L.ACF.n != L.nC || L.ACF.m != L.nF ||
+              L.W.n != L.nF || L.W.m != L.nC;
+        if (L.rtype == MGR_RESTRICT_JACOBI) {
+            rc |= check_csr(L.Z, bad, s, tmp) | check_csr(L.ZT, bad, s, tmp);
+            hb += L.Z.n != L.nC || L.Z.m != L.nF || L.ZT.n != L.nF || L.ZT.m != L.nC;
+        }
+        const int nnext = l + 1 < h->nlev ? h->lev[l + 1].n : h->H.amg[0].A.n;
+        hb += nnext != L.nC;
+        rc |= check_split(L.n, L.fidx, L.nF, L.cidx, L.nC, L.gstart, L.gsize, bad, s, tmp);
+        rc |= check_iota(L.fiota, L.nF, bad, s);
+        if (L.famg) {
+            rc |= check_amg(*L.famg, bad, s, tmp);
+            hb += L.famg->amg[0].A.n != L.nF;
+        }
+    }
+    rc |= check_amg(h->H, bad, s, tmp);
+    rc |= check_csr(h->A0T, bad, s, tmp);
+    hb += h->A0T.n != h->n || h->A0T.m != h->n;
+    if (h->b == 1) rc |= check_csr(h->Aout, bad, s, tmp);
+    rc |= check_add(bad, hb, s);
+    unsigned long long tot = 0;
+    cudaMemcpyAsync(&tot, bad, sizeof(tot), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    tmp.free_all();
+    if (rc == ST_NOMEM) return fail(h, MGR_ERR_NOMEM, "check scratch");
+    if (rc || cudaGetLastError() != cudaSuccess) return cuda_fail(h, "mgr_check_hierarchy");
+    *violations = (int64_t)tot;
+    return MGR_OK;
+}
+
 extern "C" mgr_status mgr_get_info(mgr_handle h, int32_t *out) {
     if (!h || !out) return fail(h, MGR_ERR_INVALID, "NULL argument");
     out[0] = h->nlev; out[1] = h->H.namg; out[2] = h->n;

@@ -103,6 +103,7 @@ def lib(build_if_missing: bool = True):
     L.mgr_get_amg_levels.restype = i32
     L.mgr_get_dinv.argtypes = [vp, i32, vp, vp]
     L.mgr_get_info.argtypes = [vp, vp]
+    L.mgr_check_hierarchy.argtypes = [vp, C.POINTER(C.c_int64)]
     L.mgr_residual_norm_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mgr_launch_count.argtypes = []
     L.mgr_launch_count.restype = C.c_int64
@@ -328,6 +329,13 @@ class MGRSolver:
         cf = np.zeros(n, np.int32)
         st = lib().mgr_get_amg_cf(self.h, amg, int(level), cf.ctypes.data)
         return cf if st == MGR_OK else None
+
+    def check(self):
+        """Number of index-range and shape violations in the built hierarchy
+        (0 for a sound one)."""
+        v = C.c_int64(-1)
+        _check(lib().mgr_check_hierarchy(self.h, C.byref(v)), self.h)
+        return int(v.value)
 
     def frelax_amg_levels(self, level):
         """AMG levels of MGR level ``level``'s F-relaxation (0: not AMG)."""

@@ -71,6 +71,7 @@ def test_batched_member_handles_and_gradients(small_batch):
     xs, infos = batch.solve([t(s.rhs) for s in systems], rtol=1e-12, maxit=1000)
     i = 1
     sv = batch.system(i)
+    assert all(batch.system(k).check() == 0 for k in range(len(systems)))
     lam, info = sv.solve(t(weights[i]), rtol=1e-12, transpose=True)
     ro = O.Oracle(systems[i]).solve(weights[i], rtol=1e-12, trans=True)
     assert info["status"] == 0

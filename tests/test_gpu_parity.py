@@ -244,6 +244,20 @@ def _same_frelax_hierarchies(g, o, s):
                 assert np.array_equal(g.amg_cf(k, frelax_level=l), o.amg_cf(k, frelax_level=l))
 
 
+@pytest.mark.parametrize("name", list(SMALL))
+@pytest.mark.parametrize("restrict", ["injection", "jacobi"])
+def test_hierarchy_index_structure(name, restrict):
+    """Every index array of the built hierarchy lies inside the array it
+    indexes, and consecutive operators have matching shapes (the device-side
+    check that stands in for a memory checker)."""
+    s = SMALL[name]()
+    if restrict == "jacobi" and "block_jacobi" in s.relax:
+        pytest.skip("the restriction of Eq. 5 takes a diagonal D")
+    for prec in ("fp64", "fp32"):
+        g = solver(s, precision=prec, max_coarse=SMALL_COARSE, restrict=[restrict] * s.num_levels)
+        assert g.check() == 0
+
+
 # -------------------------------------------------------- V-cycle, solve
 @pytest.mark.parametrize("name", list(SMALL))
 def test_vcycle_parity(name):
@@ -274,6 +288,30 @@ def test_amg_frelax_sweeps_and_weight(name, precision, sweeps, omega):
         zg = g.apply(t(v), transpose=trans).cpu().numpy()
         zo = o.apply_transpose(v) if trans else o.apply(v)
         assert np.linalg.norm(zg - zo) <= tol * np.linalg.norm(zo), (trans, np.linalg.norm(zg - zo) / np.linalg.norm(zo))
+
+
+@pytest.mark.parametrize("name", ["poromech_mgr_u", "two_phase_amg_relax", "compositional_4level"])
+@pytest.mark.parametrize("restrict", ["injection", "jacobi"])
+def test_amg_frelax_single_level_hierarchy(name, restrict):
+    """AMG F-relaxations whose A_FF is small enough to be the coarsest grid
+    (one dense level, no SELL copy shared with the hierarchy): cycle parity
+    forward and transposed, and solve parity."""
+    s = SMALL[name]()
+    rs = [restrict] * s.num_levels
+    g = solver(s, max_coarse=4096, restrict=rs)
+    o = oracle_of(s, max_coarse=4096, restrict=rs)
+    for l in range(s.num_levels):
+        if s.relax[l] == "amg":
+            assert g.frelax_amg_levels(l) == o.frelax_amg_nlevels(l) == 1
+    rng = np.random.default_rng(31)
+    for trans in (False, True):
+        v = rng.standard_normal(s.n)
+        zg = g.apply(t(v), transpose=trans).cpu().numpy()
+        zo = o.apply_transpose(v) if trans else o.apply(v)
+        assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo)
+    ro = o.solve(s.rhs, rtol=1e-10, maxit=300)
+    _, ig = g.solve(t(s.rhs), rtol=1e-10, maxit=300)
+    assert ig["status"] == 0 and abs(ig["iterations"] - ro["iters"]) <= 1
 
 
 def test_mgr_u_fewer_iterations_than_mgr_p_on_gpu():
@@ -494,6 +532,7 @@ def test_full_size(name):
     g = solver(s)
     o = O.Oracle(s)
     assert g.info()["mgr_levels"] == o.mgr_nlevels and g.info()["amg_levels"] == o.amg_nlevels
+    assert g.check() == 0
     for l in range(s.num_levels + 1):
         _same_csr(g.matrix(0, l, 0), o.mgr_matrix(l, "A"), f"MGR A_{l}")
     for k in range(o.amg_nlevels):

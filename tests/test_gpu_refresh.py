@@ -32,6 +32,7 @@ def test_refresh_matches_oracle_reuse(touch_uu, restrict):
     s1, s2 = _pair(touch_uu)
     g = solver(s1, max_coarse=COARSE, restrict=[restrict])
     g.refresh(s2.val)
+    assert g.check() == 0
     o1 = oracle_of(s1, max_coarse=COARSE, restrict=[restrict])
     o2 = O.Oracle(s2, O.Options(relax=list(s2.relax), relax_functions=list(s2.relax_functions),
                                 num_functions=s2.num_functions, max_coarse=COARSE,
