@@ -90,6 +90,10 @@ enum { MGR_PREC_FP64 = 0, MGR_PREC_FP32 = 1 };
  * R~ A P~ and the cycle restricts v_C - A_CF z_F + Z (v_F - A_FF z_F),
  * Z = -A_CF D^{-1}.  It needs a diagonal D (not block-Jacobi:
  * MGR_ERR_UNSUPPORTED); batched solves restrict by injection only.
+ * spin_limit: polls before a grid-barrier wait of the fused AMG tail gives
+ * up (0: the default, about half a second); a test knob that makes the wait
+ * run out on purpose, so that the MGR_ERR_TIMEOUT path can be exercised
+ * without a GPU fault.
  * AMG: strength threshold theta, level and coarse-size limits, max
  * interpolation entries per row (0 = no truncation), number of functions
  * of the unknown approach (function of a coarse-block dof = its index mod
@@ -116,6 +120,7 @@ typedef struct {
     int32_t amg_tail_nnz;
     int32_t relax_functions[MGR_MAX_LEVELS];
     int32_t restrict_type[MGR_MAX_LEVELS];
+    int32_t spin_limit;
 } mgr_options;
 
 /* Solve report.  level_rows/level_nnz list the MGR levels, then the AMG levels. */
@@ -132,7 +137,7 @@ typedef struct {
 /* Defaults: Jacobi, 1 sweep, omega 1 on every level; theta 0.25, 25 AMG
  * levels, coarsest <= 1024 rows, P_max 4, 1 function; FP64; m = 30; graphs on;
  * no fused AMG tail; 1 function in every F-relaxation AMG hierarchy;
- * injection restriction on every level. */
+ * injection restriction on every level; the default barrier wait limit. */
 void mgr_options_default(mgr_options *opt);
 
 /*
@@ -297,6 +302,13 @@ mgr_status mgr_get_info(mgr_handle h, int32_t *out);
  * other's shapes.  *violations (host) receives the number of violations
  * (0 for a sound hierarchy).  Synchronises the stream. */
 mgr_status mgr_check_hierarchy(mgr_handle h, int64_t *violations);
+
+/* Relative residuals of the handle's last solve: out[0] = ||b - A x0|| / ||b||,
+ * out[i] = the Arnoldi estimate |g_{i}| / ||b|| after preconditioner
+ * application i (restarts included), as the oracle's history.  Copies at
+ * most cap values to out (host; may be NULL) and returns the count
+ * (iterations + 1). */
+int32_t mgr_solve_history(mgr_handle h, double *out, int32_t cap);
 
 /* ------------------------------------------------------- instrumentation
  * Kernel launches this library has made (all handles, solve-phase kernels,

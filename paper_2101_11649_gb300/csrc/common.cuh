@@ -130,6 +130,7 @@ struct TailPhase {
 };
 struct TailPlan {
     int nphase = 0;
+    long long spin = 0;  // polls before a barrier wait gives up (0: the default)
     TailPhase ph[TAIL_MAX_PHASES];
 };
 // sync: 3 device words (arrivals, generation, error), zero before the first

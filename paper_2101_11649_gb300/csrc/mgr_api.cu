@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mgr_gb300.h"
 #include "common.cuh"
 #include "sell.cuh"
@@ -95,6 +97,7 @@ struct Krylov {
     int *flag = nullptr;
     double *tol = nullptr;     // device copy of rtol * |b|
     long long graph_kernels[2][32] = {};
+    std::vector<double> hist;  // relative residuals of the last solve (mgr_solve_history)
     double *hstat = nullptr;  // pinned host mirror of stat
     std::vector<cudaGraphExec_t> graphs[2];
 };
@@ -113,6 +116,13 @@ struct Prof {
 };
 
 static std::atomic<long long> g_launches{0};
+
+// NVTX range over a phase (setup, each MGR level, each AMG hierarchy, solve,
+// refresh); free unless a profiler is attached.
+struct Nvtx {
+    explicit Nvtx(const char *name) { nvtxRangePushA(name); }
+    ~Nvtx() { nvtxRangePop(); }
+};
 
 }  // namespace mgr
 
@@ -235,6 +245,7 @@ extern "C" void mgr_options_default(mgr_options *o) {
         o->relax_functions[l] = 1;
         o->restrict_type[l] = MGR_RESTRICT_INJECTION;
     }
+    o->spin_limit = 0;
 }
 
 // ---------------------------------------------------------------- helpers
@@ -275,6 +286,7 @@ static int copy_csr(const DCSR &A, DCSR &out, Arena &ar, cudaStream_t s) {
 // nfunc functions of the unknown approach, allocated from ar.  own_copy:
 // level 0 holds a copy of A0 (a hierarchy that outlives A0's arena).
 static mgr_status setup_amg(mgr_handle h, AmgH &G, DCSR A0, int nfunc, Arena &ar, bool own_copy) {
+    Nvtx nv(G.frelax ? "mgr AMG setup (F-relaxation)" : "mgr AMG setup (coarse block)");
     cudaStream_t s = h->s;
     const mgr_options &o = h->opt;
     int maxl = o.amg_max_levels < 1 ? 1 : (o.amg_max_levels > 32 ? 32 : o.amg_max_levels);
@@ -363,6 +375,7 @@ static mgr_status setup_amg(mgr_handle h, AmgH &G, DCSR A0, int nfunc, Arena &ar
 // left (mgr_refresh).  On failure the handle is not usable (ready stays
 // false).
 static mgr_status build_levels(mgr_handle h, bool reuse) {
+    Nvtx nv(reuse ? "mgr hierarchy (refresh)" : "mgr hierarchy");
     Arena &ar = h->lar;
     cudaStream_t s = h->s;
     const int nb = h->nb, b = h->b, n = h->n;
@@ -381,6 +394,9 @@ static mgr_status build_levels(mgr_handle h, bool reuse) {
     int *gdof = nullptr;
     for (int l = 0; l < h->nlev; l++) {
         MgrLevel &L = h->lev[l];
+        char nvn[32];
+        snprintf(nvn, sizeof nvn, "mgr level %d", l);
+        Nvtx nvl(nvn);
         L.A = cur; L.gdof = gdof; L.n = cur.n;
         L.relax = h->opt.relax_type[l];
         L.sweeps = h->opt.relax_sweeps[l] < 1 ? 1 : h->opt.relax_sweeps[l];
@@ -421,10 +437,23 @@ static mgr_status build_levels(mgr_handle h, bool reuse) {
         L.gstart = ar.alloc<int>(nF + 1); L.gsize = ar.alloc<int>(nF + 1);
         L.dinv = ar.alloc<double>((size_t)nF * 4 + 4); L.dinv32 = ar.alloc<float>((size_t)nF * 4 + 4);
         if (rc || !L.gstart || !L.gsize || !L.dinv || !L.dinv32) { return fail(h, MGR_ERR_NOMEM, "level blocks"); }
+        {
+            const int none = 0x7fffffff;  // errw[1]: the first singular F point
+            cudaMemcpyAsync(h->errw + 1, &none, sizeof(int), cudaMemcpyHostToDevice, s);
+        }
         mgr_dinv(L.AFF, L.fidx, gdof, b, L.relax, L.gstart, L.gsize, L.dinv, h->errw, s);
         if (read_errw(h) & ERRW_SINGULAR) {
-            char buf[128];
-            snprintf(buf, sizeof buf, "singular D_FF (zero diagonal or singular block) at MGR level %d", l);
+            int f = -1, loc = -1, dof = -1;
+            cudaMemcpy(&f, h->errw + 1, sizeof(int), cudaMemcpyDeviceToHost);
+            if (f >= 0 && f < nF) {
+                cudaMemcpy(&loc, L.fidx + f, sizeof(int), cudaMemcpyDeviceToHost);
+                dof = loc;
+                if (gdof && loc >= 0) cudaMemcpy(&dof, gdof + loc, sizeof(int), cudaMemcpyDeviceToHost);
+            }
+            char buf[192];
+            snprintf(buf, sizeof buf,
+                     "singular D_FF (zero diagonal or singular block) at MGR level %d, first at F point %d (dof %d)",
+                     l, f, dof);
             return fail(h, MGR_ERR_SINGULAR, buf);
         }
         launch_cast_f32(L.dinv, L.dinv32, (long long)nF * 4, s);
@@ -570,6 +599,7 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
         return fail(nullptr, MGR_ERR_UNSUPPORTED, "matrix too large for 32-bit scalar indices");
     if (cf->num_levels < 0 || cf->num_levels > MGR_MAX_LEVELS)
         return fail(nullptr, MGR_ERR_INVALID, "num_levels out of range");
+    Nvtx nv("mgr_setup");
     auto t0 = std::chrono::steady_clock::now();
     mgr_handle h = new mgr_ctx();
     cudaGetDevice(&h->dev);
@@ -812,6 +842,7 @@ static int setup_tail(mgr_handle h, AmgH &G, int tail_nnz, cudaStream_t s, Arena
     G.tail_k = kt;
     for (int trans = 0; trans < 2; trans++) {
         TailPlan plan;
+        plan.spin = h->opt.spin_limit > 0 ? h->opt.spin_limit : 0;
         const bool ok = h->opt.precision == MGR_PREC_FP32 ? build_tail_plan<float>(G, trans, plan)
                                                           : build_tail_plan<double>(G, trans, plan);
         if (!ok) {
@@ -1223,6 +1254,7 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
     if (!h || !b || !x) return fail(h, MGR_ERR_INVALID, "NULL argument");
     if (!h->ready) return fail(h, MGR_ERR_INVALID, "no hierarchy (a refresh failed)");
     if (!(rtol >= 0.0)) return fail(h, MGR_ERR_INVALID, "rtol must be >= 0");
+    Nvtx nv(trans ? "mgr_solve_transpose" : "mgr_solve");
     auto t0 = std::chrono::steady_clock::now();
     Krylov &K = h->kr;
     cudaStream_t s = h->s;
@@ -1239,6 +1271,7 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
     double relres = 0.0;
     mgr_status st = MGR_ERR_NOT_CONVERGED;
     if (bn == 0.0) {
+        K.hist.assign(1, 0.0);
         cudaMemsetAsync(x, 0, sizeof(double) * n, s);
         cudaStreamSynchronize(s);
         relres = 0.0;
@@ -1246,6 +1279,7 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
     } else {
         double tol_abs = rtol * bn;
         cudaMemcpyAsync(K.tol, &tol_abs, sizeof(double), cudaMemcpyHostToDevice, s);
+        K.hist.clear();
         for (;;) {
             outer_residual(h, x, b, K.r, trans);
             { KScope ks(h, "norm", -1, n * 8.0);
@@ -1255,6 +1289,7 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
             cudaStreamSynchronize(s);
             if (cudaGetLastError() != cudaSuccess) return cuda_fail(h, "solve residual");
             relres = beta / bn;
+            if (it == 0) K.hist.push_back(relres);
             if (!isfinite(beta)) { st = MGR_ERR_INVALID; h->err = "residual is not finite"; break; }
             if (beta <= tol_abs) { st = MGR_OK; break; }
             if (it >= maxit) break;
@@ -1270,6 +1305,7 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
                 it++;
                 k = j + 1;
                 double est = K.hstat[0];
+                K.hist.push_back(est / bn);
                 int conv = K.hstat[1] != 0.0, brk = K.hstat[2] != 0.0;
                 if (!isfinite(est)) { st = MGR_ERR_INVALID; break; }
                 if (K.hstat[4] != 0.0) reorth++;
@@ -1354,6 +1390,7 @@ extern "C" mgr_status mgr_update_values(mgr_handle h, const double *val, int32_t
 extern "C" mgr_status mgr_refresh(mgr_handle h, const double *val, int32_t on_device) {
     if (!h || !val) return fail(h, MGR_ERR_INVALID, "NULL argument");
     if (h->in_batch) return fail(h, MGR_ERR_UNSUPPORTED, "handles of a batch are not refreshed one by one");
+    Nvtx nv("mgr_refresh");
     auto t0 = std::chrono::steady_clock::now();
     mgr_status st = mgr_update_values(h, val, on_device);
     if (st != MGR_OK) return st;
@@ -1569,6 +1606,14 @@ extern "C" mgr_status mgr_get_info(mgr_handle h, int32_t *out) {
     if (!h || !out) return fail(h, MGR_ERR_INVALID, "NULL argument");
     out[0] = h->nlev; out[1] = h->H.namg; out[2] = h->n;
     return MGR_OK;
+}
+
+extern "C" int32_t mgr_solve_history(mgr_handle h, double *out, int32_t cap) {
+    if (!h) return 0;
+    const auto &v = h->kr.hist;
+    const int32_t cnt = (int32_t)v.size();
+    for (int32_t i = 0; out && i < cnt && i < cap; i++) out[i] = v[i];
+    return cnt;
 }
 
 extern "C" int64_t mgr_launch_count(void) { return g_launches.load(); }

@@ -355,7 +355,12 @@ __global__ void k_mgr_dinv(int nF, const int *rp, const int *ci, const double *v
             d = aii < 0.0 ? aii - s : aii + s;
         }
         gstart[f] = f; gsize[f] = 1;
-        if (d == 0.0) { atomicOr(errw, ERRW_SINGULAR); dinv[(long long)f * 4] = 0.0; return; }
+        if (d == 0.0) {
+            atomicOr(errw, ERRW_SINGULAR);
+            atomicMin(errw + 1, f);  // the first singular F point
+            dinv[(long long)f * 4] = 0.0;
+            return;
+        }
         dinv[(long long)f * 4] = 1.0 / d;
         dinv[(long long)f * 4 + 1] = dinv[(long long)f * 4 + 2] = dinv[(long long)f * 4 + 3] = 0.0;
         return;
@@ -373,6 +378,7 @@ __global__ void k_mgr_dinv(int nF, const int *rp, const int *ci, const double *v
     int rr = f - g0;
     if (block_inverse(k, B, inv)) {
         atomicOr(errw, ERRW_SINGULAR);
+        atomicMin(errw + 1, f);
         for (int c = 0; c < 4; c++) dinv[(long long)f * 4 + c] = 0.0;
         return;
     }

@@ -33,7 +33,7 @@ struct XCg {
 // this CTA's arrival); the last arrival resets the count and advances the
 // generation; the others poll it.  false: this CTA must stop (a wait ran out
 // here or elsewhere).
-__device__ __forceinline__ bool grid_barrier(unsigned *sync) {
+__device__ __forceinline__ bool grid_barrier(unsigned *sync, long long spin) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -50,7 +50,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *sync) {
         } else {
             long long i = 0;
             while (*gen == g) {
-                if (++i > TAIL_SPIN || *err) {
+                if (++i > spin || *err) {
                     ok = 0;
                     atomicOr(sync + 2, 1u);
                     break;
@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_amg_tail(const TailPlan *__
     const int gw = (int)blockIdx.x * (TAIL_THREADS / 32) + (int)(threadIdx.x >> 5);
     const int W = (int)gridDim.x * (TAIL_THREADS / 32);
     const int np = plan->nphase;
+    const long long spin = plan->spin > 0 ? plan->spin : TAIL_SPIN;
     for (int p = 0; p < np; p++) {
         const TailPhase &P = plan->ph[p];
         const int kind = P.kind;
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_amg_tail(const TailPlan *__
                     break;
             }
         }
-        if (p + 1 < np && !grid_barrier(sync)) return;
+        if (p + 1 < np && !grid_barrier(sync, spin)) return;
     }
 }
 

@@ -46,7 +46,7 @@ class mgr_options(C.Structure):
                 ("amg_pmax", C.c_int32), ("amg_num_functions", C.c_int32),
                 ("precision", C.c_int32), ("restart", C.c_int32), ("use_graphs", C.c_int32),
                 ("amg_tail_nnz", C.c_int32), ("relax_functions", C.c_int32 * MAX_LEVELS),
-                ("restrict_type", C.c_int32 * MAX_LEVELS)]
+                ("restrict_type", C.c_int32 * MAX_LEVELS), ("spin_limit", C.c_int32)]
 
 
 class mgr_solve_info(C.Structure):
@@ -104,6 +104,8 @@ def lib(build_if_missing: bool = True):
     L.mgr_get_dinv.argtypes = [vp, i32, vp, vp]
     L.mgr_get_info.argtypes = [vp, vp]
     L.mgr_check_hierarchy.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.mgr_solve_history.argtypes = [vp, vp, i32]
+    L.mgr_solve_history.restype = i32
     L.mgr_residual_norm_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mgr_launch_count.argtypes = []
     L.mgr_launch_count.restype = C.c_int64
@@ -135,7 +137,7 @@ def _ptr(t):
 
 def options(relax=("jacobi",), sweeps=(), weights=(), theta=0.25, max_levels=25, max_coarse=1024,
             pmax=4, num_functions=1, precision="fp64", restart=30, use_graphs=True,
-            tail_nnz=None, relax_functions=(), restrict=()) -> mgr_options:
+            tail_nnz=None, relax_functions=(), restrict=(), spin_limit=None) -> mgr_options:
     o = mgr_options()
     lib().mgr_options_default(C.byref(o))
     for l, r in enumerate(relax):
@@ -158,6 +160,8 @@ def options(relax=("jacobi",), sweeps=(), weights=(), theta=0.25, max_levels=25,
         o.relax_functions[l] = int(f)
     for l, r in enumerate(restrict):
         o.restrict_type[l] = RESTRICT[r] if isinstance(r, str) else int(r)
+    if spin_limit is not None:
+        o.spin_limit = int(spin_limit)
     return o
 
 
@@ -329,6 +333,14 @@ class MGRSolver:
         cf = np.zeros(n, np.int32)
         st = lib().mgr_get_amg_cf(self.h, amg, int(level), cf.ctypes.data)
         return cf if st == MGR_OK else None
+
+    def history(self):
+        """Relative residuals of the last solve: the initial true residual,
+        then the Arnoldi estimate after every preconditioner application."""
+        n = lib().mgr_solve_history(self.h, None, 0)
+        out = np.zeros(max(n, 1))
+        lib().mgr_solve_history(self.h, out.ctypes.data, n)
+        return out[:n]
 
     def check(self):
         """Number of index-range and shape violations in the built hierarchy

@@ -483,6 +483,38 @@ def test_singular_f_block_reports_singular():
         M.MGRSolver(s.row_ptr, s.col_idx, v, s.b, s.dof_level, s.num_levels,
                     M.options(relax=("jacobi",)))
     assert e.value.status == M.MGR_ERR_SINGULAR
+    assert "dof 9" in str(e.value), str(e.value)   # block row 4, second unknown
+
+
+def test_tail_barrier_timeout_is_reported_and_the_context_survives():
+    """A grid-barrier wait of the fused AMG tail that runs out (forced with a
+    spin limit of one poll) ends the kernel, and the solve reports
+    MGR_ERR_TIMEOUT; the next solve on a handle with the default limit
+    converges normally."""
+    s = TAIL_SYSTEMS["mimetic24"]()
+    g = solver(s, tail_nnz=400000, spin_limit=1)
+    _, info = g.solve(t(s.rhs), rtol=1e-8, maxit=3, check=False)
+    assert info["status"] == M.MGR_ERR_TIMEOUT, info
+    ok = solver(s, tail_nnz=400000)
+    _, info2 = ok.solve(t(s.rhs), rtol=1e-8)
+    assert info2["status"] == 0 and info2["rel_residual"] <= 1e-8
+
+
+@pytest.mark.parametrize("name", ["two_phase", "poromech_mgr_u"])
+def test_solve_history_matches_oracle(name):
+    """The residual history of a solve (initial true residual, then the
+    Arnoldi estimate per iteration) against the oracle's."""
+    s = SMALL[name]()
+    g = solver(s, max_coarse=SMALL_COARSE)
+    o = oracle_of(s, max_coarse=SMALL_COARSE)
+    _, ig = g.solve(t(s.rhs), rtol=1e-10, maxit=300)
+    ro = o.solve(s.rhs, rtol=1e-10, maxit=300)
+    hg, ho = g.history(), ro["hist"]
+    assert hg.size == ig["iterations"] + 1 and ho.size == ro["iters"] + 1
+    assert hg[0] == pytest.approx(1.0) and ho[0] == pytest.approx(1.0)
+    k = min(hg.size, ho.size)
+    assert np.all(np.abs(hg[:k] - ho[:k]) <= 1e-6 * ho[:k] + 1e-14), np.max(np.abs(hg[:k] - ho[:k]) / ho[:k])
+    assert np.all(np.diff(hg[1:]) <= 1e-12)   # GMRES residual estimates never increase within a cycle
 
 
 def test_maxit_and_zero_rhs():
