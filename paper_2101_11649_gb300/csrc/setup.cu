@@ -495,6 +495,26 @@ __device__ __forceinline__ void spgemm_insert(int *key, double *val, unsigned ca
     atomicOr(errw, ERRW_OVERFLOW);  // table full: cannot happen when cap >= 2 * distinct
 }
 
+// The slot of column j in the row's table, claimed when absent (fresh).
+// -1 when the table is full (cannot happen when cap >= 2 * distinct).
+__device__ __forceinline__ int spgemm_slot(int *key, unsigned cap, int j, bool &fresh, int *errw) {
+    unsigned h = hash_col(j) & (cap - 1);
+    for (unsigned probe = 0; probe < cap; probe++) {
+        int kk = ((volatile int *)key)[h];
+        if (kk < 0) {
+            kk = atomicCAS(key + h, -1, j);
+            if (kk < 0) {
+                fresh = true;
+                return (int)h;
+            }
+        }
+        if (kk == j) return (int)h;
+        h = (h + 1) & (cap - 1);
+    }
+    atomicOr(errw, ERRW_OVERFLOW);
+    return -1;
+}
+
 template <bool NUMERIC>
 __global__ void k_spgemm_row(int r0, int r1, const int *arp, const int *aci, const double *av,
                              const int *brp, const int *bci, const double *bv, const int *erp,
@@ -513,13 +533,71 @@ __global__ void k_spgemm_row(int r0, int r1, const int *arp, const int *aci, con
     for (unsigned t = lane; t < cap; t += 32) key[t] = -1;
     __syncwarp();
     int claimed = 0;
-    for (int p = arp[i]; p < arp[i + 1]; p++) {
-        const int k = aci[p];
-        const double a = NUMERIC ? av[p] : 0.0;
-        const int q1 = brp[k + 1];
-        for (int q = brp[k] + lane; q < q1; q += 32)
-            spgemm_insert(key, val, cap, bci[q], NUMERIC ? a * bv[q] : 0.0, NUMERIC, claimed, errw);
+    // The products a_ip b_pj in (p, j) order, 32 at a time: a chunk may span
+    // several short rows of B.  Lanes of a chunk with the same column form a
+    // group (__match_any_sync); its lowest lane adds the group's products in
+    // lane order, which is ascending p, so every entry still receives its
+    // contributions in the order of the row-by-row definition.
+    __shared__ int own_s[8][32], bef_s[8][32];
+    __shared__ double prod_s[8][32];
+    const int wib = threadIdx.x >> 5;
+    int p = arp[i], qoff = 0;  // next product: entry qoff of B's row a_p
+    const int pe = arp[i + 1];
+    while (p < pe) {
+        const int pl = p + lane;
+        int len = 0;
+        if (pl < pe) {
+            const int kk = aci[pl];
+            len = brp[kk + 1] - brp[kk] - (lane == 0 ? qoff : 0);
+        }
+        int cum = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, cum, o);
+            if (lane >= o) cum += y;
+        }
+        const int before = cum - len;
+        const int total = __shfl_sync(FULL, cum, 31);
+        const int nprod = total < 32 ? total : 32;
+        bef_s[wib][lane] = before;
+        for (int t = before; t < cum && t < 32; t++) own_s[wib][t] = lane;
         __syncwarp();
+        int j = -1;
+        if (lane < nprod) {
+            const int l = own_s[wib][lane];
+            const int pp = p + l;
+            const int kk = aci[pp];
+            const int q = brp[kk] + (l == 0 ? qoff : 0) + (lane - bef_s[wib][l]);
+            j = bci[q];
+            prod_s[wib][lane] = NUMERIC ? av[pp] * bv[q] : 0.0;
+        }
+        const unsigned act = __ballot_sync(FULL, lane < nprod);
+        __syncwarp();
+        if (lane < nprod) {
+            const unsigned grp = __match_any_sync(act, j);
+            if ((grp & ((1u << lane) - 1u)) == 0u) {  // the group's lowest lane
+                bool fresh = false;
+                const int h = spgemm_slot(key, cap, j, fresh, errw);
+                if (h >= 0) {
+                    if (fresh) claimed++;
+                    if (NUMERIC) {
+                        double acc = fresh ? 0.0 : val[h];
+                        for (unsigned rest = grp; rest; rest &= rest - 1u) acc = acc + prod_s[wib][__ffs(rest) - 1];
+                        val[h] = acc;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (total <= 32) {
+            p += 32;
+            qoff = 0;
+        } else {
+            const int ls = __ffs(__ballot_sync(FULL, cum > 32)) - 1;  // first row not used up
+            const int bls = __shfl_sync(FULL, before, ls);
+            qoff = (ls == 0 ? qoff : 0) + (32 - bls);
+            p += ls;
+        }
     }
     if (erp) {
         for (int q = erp[i] + lane; q < erp[i + 1]; q += 32)
@@ -649,14 +727,17 @@ __global__ void k_col_count(int nnz, const int *ci, int *cnt) {
         atomicAdd(&cnt[ci[p]], 1);
 }
 
+// one warp per source row (the order inside a row of the transpose is
+// fixed by k_row_sort afterwards)
 __global__ void k_tr_fill(int n, const int *rp, const int *ci, const double *v, const int *trp,
                           int *cursor, int *tci, double *tv) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= n) return;
-    for (int p = rp[i]; p < rp[i + 1]; p++) {
-        int j = ci[p];
-        int q = trp[j] + atomicAdd(&cursor[j], 1);
-        tci[q] = i;
+    for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+        const int j = ci[p];
+        const int q = trp[j] + atomicAdd(&cursor[j], 1);
+        tci[q] = (int)i;
         if (v) tv[q] = v[p];
     }
 }
@@ -696,7 +777,7 @@ int transpose(const DCSR &A, DCSR &T, cudaStream_t s, Arena &ar) {
     int rc = scan_exclusive(cnt, T.rp, A.m, s, ar, nullptr);
     if (rc) return rc;
     cudaMemsetAsync(cnt, 0, sizeof(int) * (A.m + 1), s);
-    k_tr_fill<<<GRID(A.n, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, T.rp, cnt, T.ci, T.v);
+    k_tr_fill<<<GRID((long long)A.n * 32, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, T.rp, cnt, T.ci, T.v);
     k_row_sort<<<GRID(A.m, 128), 128, 0, s>>>(A.m, T.rp, T.ci, T.v);
     cudaStreamSynchronize(s);
     ar.release(cnt);
