@@ -742,11 +742,43 @@ __global__ void k_tr_fill(int n, const int *rp, const int *ci, const double *v, 
     }
 }
 
-// sort each row by column (source row index); insertion sort (rows are short)
+// sort each row by column (source row index; the keys of a row are
+// distinct).  One warp per row: rows of up to 128 entries by rank (each
+// lane holds up to 4 entries, counts the smaller keys of the row, and all
+// writes wait for all reads); longer rows by one lane's shell sort.
 __global__ void k_row_sort(int n, const int *rp, int *ci, double *v) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned FULL = 0xffffffffu;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= n) return;
-    int o = rp[i], len = rp[i + 1] - o;
+    const int o = rp[i], len = rp[i + 1] - o;
+    if (len <= 128) {
+        int key[4], rank[4];
+        double val[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int e = lane + 32 * u;
+            key[u] = e < len ? ci[o + e] : 0;
+            val[u] = (e < len && v) ? v[o + e] : 0.0;
+            rank[u] = 0;
+        }
+        for (int f = 0; f < len; f++) {
+            const int kf = ci[o + f];
+#pragma unroll
+            for (int u = 0; u < 4; u++) rank[u] += kf < key[u];
+        }
+        __syncwarp(FULL);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int e = lane + 32 * u;
+            if (e < len) {
+                ci[o + rank[u]] = key[u];
+                if (v) v[o + rank[u]] = val[u];
+            }
+        }
+        return;
+    }
+    if (lane != 0) return;
     const int gaps[8] = {701, 301, 132, 57, 23, 10, 4, 1};
     for (int gi = 0; gi < 8; gi++) {
         int g = gaps[gi];
@@ -778,7 +810,7 @@ int transpose(const DCSR &A, DCSR &T, cudaStream_t s, Arena &ar) {
     if (rc) return rc;
     cudaMemsetAsync(cnt, 0, sizeof(int) * (A.m + 1), s);
     k_tr_fill<<<GRID((long long)A.n * 32, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, T.rp, cnt, T.ci, T.v);
-    k_row_sort<<<GRID(A.m, 128), 128, 0, s>>>(A.m, T.rp, T.ci, T.v);
+    k_row_sort<<<GRID((long long)A.m * 32, 256), 256, 0, s>>>(A.m, T.rp, T.ci, T.v);
     cudaStreamSynchronize(s);
     ar.release(cnt);
     return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
@@ -787,44 +819,67 @@ int transpose(const DCSR &A, DCSR &T, cudaStream_t s, Arena &ar) {
 // --------------------------------------------------------------- strength
 // s_i = -1 if a_ii < 0 else +1; m_i = max over off-diagonal same-function j
 // of -s_i a_ij (from 0); j strong iff m_i > 0 and -s_i a_ij >= theta m_i.
+// One warp per row.  s_i = sign(a_ii); m_i = max over same-function j != i
+// of -s_i a_ij; j is strong when m_i > 0 and -s_i a_ij >= theta m_i.  The
+// maximum and the comparisons do not depend on the order of the entries.
 __global__ void k_strength(int n, const int *rp, const int *ci, const double *v, const int *func,
                            double theta, uint8_t *sflag, int *cnt) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned FULL = 0xffffffffu;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= n) return;
+    const int a = rp[i], e = rp[i + 1];
     double aii = 0.0;
-    for (int p = rp[i]; p < rp[i + 1]; p++)
+    for (int p = a + lane; p < e; p += 32)
         if (ci[p] == i) aii = v[p];
-    bool neg = aii < 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_xor_sync(FULL, aii, o);
+        if (y != 0.0) aii = y;  // the one diagonal entry (or zero)
+    }
+    const bool neg = aii < 0.0;
+    const int fi = func[i];
     double m = 0.0;
-    int fi = func[i];
-    for (int p = rp[i]; p < rp[i + 1]; p++) {
-        int j = ci[p];
+    for (int p = a + lane; p < e; p += 32) {
+        const int j = ci[p];
         if (j == i || func[j] != fi) continue;
-        double val = neg ? v[p] : -v[p];
+        const double val = neg ? v[p] : -v[p];
         if (val > m) m = val;
     }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(FULL, m, o));
+    const double thr = theta * m;
     int c = 0;
-    double thr = theta * m;
-    for (int p = rp[i]; p < rp[i + 1]; p++) {
-        int j = ci[p];
-        uint8_t st = 0;
-        if (m > 0.0 && j != i && func[j] == fi) {
-            double val = neg ? v[p] : -v[p];
-            st = val >= thr;
+    for (int p0 = a; p0 < e; p0 += 32) {
+        const int p = p0 + lane;
+        bool st = false;
+        if (p < e) {
+            const int j = ci[p];
+            if (m > 0.0 && j != i && func[j] == fi) {
+                const double val = neg ? v[p] : -v[p];
+                st = val >= thr;
+            }
+            sflag[p] = st;
         }
-        sflag[p] = st;
-        c += st;
+        c += __popc(__ballot_sync(FULL, st));
     }
-    cnt[i] = c;
+    if (lane == 0) cnt[i] = c;
 }
 
+// one warp per row: strong entries in row order
 __global__ void k_strength_fill(int n, const int *rp, const int *ci, const uint8_t *sflag,
                                 const int *srp, int *sci) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned FULL = 0xffffffffu;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= n) return;
     int q = srp[i];
-    for (int p = rp[i]; p < rp[i + 1]; p++)
-        if (sflag[p]) sci[q++] = ci[p];
+    const int e = rp[i + 1];
+    for (int p0 = rp[i]; p0 < e; p0 += 32) {
+        const int p = p0 + lane;
+        const bool st = p < e && sflag[p];
+        const unsigned b = __ballot_sync(FULL, st);
+        if (st) sci[q + __popc(b & ((1u << lane) - 1u))] = ci[p];
+        q += __popc(b);
+    }
 }
 
 int amg_strength(const DCSR &A, const int *func, double theta, uint8_t *sflag, DCSR &S,
@@ -834,7 +889,7 @@ int amg_strength(const DCSR &A, const int *func, double theta, uint8_t *sflag, D
     S.rp = ar.alloc<int>(n + 1);
     int *cnt = ar.alloc<int>(n + 1);
     if (!S.rp || !cnt) return ST_NOMEM;
-    k_strength<<<GRID(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, func, theta, sflag, cnt);
+    k_strength<<<GRID((long long)n * 32, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, func, theta, sflag, cnt);
     int tot = 0;
     int rc = scan_exclusive(cnt, S.rp, n, s, ar, &tot);
     ar.release(cnt);
@@ -843,7 +898,7 @@ int amg_strength(const DCSR &A, const int *func, double theta, uint8_t *sflag, D
     S.ci = ar.alloc<int>(tot + 1);
     S.v = nullptr;
     if (!S.ci) return ST_NOMEM;
-    k_strength_fill<<<GRID(n, 128), 128, 0, s>>>(n, A.rp, A.ci, sflag, S.rp, S.ci);
+    k_strength_fill<<<GRID((long long)n * 32, 256), 256, 0, s>>>(n, A.rp, A.ci, sflag, S.rp, S.ci);
     return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
 }
 
