@@ -86,7 +86,7 @@ enum { ERRW_SINGULAR = 1, ERRW_INVALID = 2, ERRW_OVERFLOW = 4 };
 // Device memory of one owner.  Released blocks stay in a pool and serve
 // later requests of about the same size (all work of an owner runs on one
 // stream, so stream order protects a reused block); recycle() returns every
-// block to the pool, trim() gives the pool back to the driver.
+// block to the pool, trim() frees the pooled blocks (cudaFree).
 struct Arena {
     std::vector<std::pair<void *, size_t>> blocks;  // live
     std::multimap<size_t, void *> pool;             // released, kept for reuse

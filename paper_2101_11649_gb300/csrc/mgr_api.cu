@@ -709,7 +709,7 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
     }
     cudaStreamSynchronize(s);
     if (cudaGetLastError() != cudaSuccess) { mgr_free(h); return cuda_fail(nullptr, "setup"); }
-    // setup temporaries go back to the driver
+    // setup temporaries are freed (cudaFree)
     h->ar.trim();
     h->lar.trim();
     for (int l = 0; l < h->nlev; l++)

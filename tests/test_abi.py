@@ -40,6 +40,13 @@ def test_options_default_and_null_handling():
     lib.mgr_options_default(ctypes.byref(o))
     assert o.amg_theta == 0.25 and o.amg_max_coarse == 1024 and o.amg_pmax == 4 and o.restart == 30
     assert list(o.relax_sweeps)[:2] == [1, 1] and o.relax_weight[0] == 1.0
+    # the fields after the AMG block: a layout mismatch between the ctypes
+    # mirror and the C struct would show here
+    assert o.amg_num_functions == 1 and o.precision == 0 and o.use_graphs == 1
+    assert o.amg_tail_nnz == 0 and o.spin_limit == 0
+    assert list(o.relax_functions) == [1] * M.MAX_LEVELS
+    assert list(o.restrict_type) == [0] * M.MAX_LEVELS
+    assert ctypes.sizeof(o) == 8 * 4 + 8 * 4 + 8 * 8 + 8 + 4 * 4 + 4 * 4 + 8 * 4 + 8 * 4 + 4 + 4
     lib.mgr_free(None)  # no-op
     lib.mgr_setup.restype = ctypes.c_int
     # NULL out pointer -> INVALID, no CUDA call made
