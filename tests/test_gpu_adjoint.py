@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from paper_2101_11649_gb300.synth import make_batch, make_two_phase
+from paper_2101_11649_gb300.synth import make_batch, make_poromech, make_two_phase
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +59,27 @@ def test_autograd_matches_dense_gradient():
     assert np.linalg.norm(db - lam_ref) <= 1e-9 * np.linalg.norm(lam_ref)
     g_ref = grads_from(s, lam_ref, x_ref)
     assert np.max(np.abs(dA - g_ref)) <= 1e-9 * np.max(np.abs(g_ref))
+
+
+@pytest.mark.parametrize("restrict", ["injection", "jacobi"])
+def test_autograd_mgr_u_matches_dense_gradient(restrict):
+    """The adjoint through an AMG F-relaxation (MGR_U) and, optionally, the
+    restriction of Eq. 5: gradients against dense LU."""
+    s = make_poromech(6, 4, strategy="mgr_u")
+    w = np.random.default_rng(17).standard_normal(s.n)
+    A = dense_of(s)
+    x_ref = O.dense_solve(A, s.rhs)
+    lam_ref = O.dense_solve(A.T.copy(), w)
+    solver = M.MGRSolver.from_system(s, restrict=[restrict], max_coarse=32)
+    vals = torch.as_tensor(s.val, device=DEV).requires_grad_(True)
+    rhs = torch.as_tensor(s.rhs, device=DEV).requires_grad_(True)
+    x = mgr_solve_fn(vals, rhs, solver, 1e-12, 2000)
+    (torch.as_tensor(w, device=DEV) * x).sum().backward()
+    assert np.linalg.norm(x.detach().cpu().numpy() - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+    db = rhs.grad.cpu().numpy()
+    assert np.linalg.norm(db - lam_ref) <= 1e-9 * np.linalg.norm(lam_ref)
+    g_ref = grads_from(s, lam_ref, x_ref)
+    assert np.max(np.abs(vals.grad.cpu().numpy() - g_ref)) <= 1e-8 * np.max(np.abs(g_ref))
 
 
 @pytest.fixture(scope="module")
