@@ -1410,7 +1410,16 @@ extern "C" mgr_status mgr_refresh(mgr_handle h, const double *val, int32_t on_de
     h->H = AmgH();
     h->lar.recycle();  // the new hierarchy has the old one's sizes: reuse its blocks
     st = build_levels(h, true);
-    if (st != MGR_OK) return st;
+    if (st != MGR_OK) {
+        // a partly built F-relaxation hierarchy must not be kept by a later refresh
+        for (int l = 0; l < MGR_MAX_LEVELS; l++) {
+            if (h->lev[l].famg) h->lev[l].famg->ar.free_all();
+            delete h->lev[l].famg;
+            h->lev[l].famg = nullptr;
+        }
+        h->lar.trim();
+        return st;
+    }
     cudaStreamSynchronize(s);
     h->lar.trim();
     for (int l = 0; l < h->nlev; l++)
