@@ -731,3 +731,26 @@ def test_reuse_with_changed_A_uu_keeps_the_old_F_hierarchy():
         assert np.array_equal(o2.amg_matrix(k, "A")[2], f2.amg_matrix(k, "A")[2])
     r = o2.solve(s2.rhs, rtol=1e-8, maxit=300)
     assert r["status"] == 0 and r["relres"] <= 1e-8
+
+
+def test_paper_strategies_converge_mesh_independently():
+    """Qualitative pin (Sec. 5.2-5.4, Tables 4 and 7): the iteration counts of
+    MGR_U, the 4-level compositional order and MGR_Pi on TPFA stay bounded
+    as the grids grow."""
+    cases = {
+        "mgr_u": [make_poromech(8, 4, strategy="mgr_u"), make_poromech(16, 8, strategy="mgr_u"),
+                  make_poromech(24, 12, strategy="mgr_u")],
+        "mgr4": [make_compositional(16, 16, 4, strategy="mgr4"),
+                 make_compositional(32, 32, 8, strategy="mgr4"),
+                 make_compositional(48, 48, 12, strategy="mgr4")],
+        "mgr_pi": [make_mimetic(12, 12, 12, scheme="tpfa", strategy="mgr_pi"),
+                   make_mimetic(20, 20, 20, scheme="tpfa", strategy="mgr_pi"),
+                   make_mimetic(28, 28, 28, scheme="tpfa", strategy="mgr_pi")],
+    }
+    for name, systems in cases.items():
+        its = []
+        for sysm in systems:
+            r = O.Oracle(sysm).solve(sysm.rhs, rtol=1e-8, maxit=300)
+            assert r["status"] == 0, name
+            its.append(r["iters"])
+        assert max(its) - min(its) <= 8 and max(its) <= 40, (name, its)
