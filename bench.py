@@ -33,7 +33,9 @@ METRIC = "time to 1e-8 rel. residual, FP64 vs FP32-MGR; V-cycle HBM GB/s vs 8 TB
 # GB300 FP64 peak (nominal, 2 flops per FMA): FP64 sparse kernels with fewer
 # than ~10.7 bytes per FMA are bound by it rather than by HBM.
 FP64_PEAK_GFLOPS = 1250.0
-WORKLOAD = "hybrid mimetic single-phase 64^3 (1,060,864 unknowns), MGR_P + AMG V(1,1), FGMRES(30)"
+def workload(grid, n):
+    return (f"hybrid mimetic single-phase {grid}^3 ({n:,} unknowns), MGR_P + AMG V(1,1), "
+            f"FGMRES(30)")
 
 
 def newton_values(cs, k):
@@ -253,7 +255,7 @@ def run_reference(args, world, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": args.grid, "rtol": args.rtol},
+            "config": {"workload": workload(args.grid, sysm.n), "grid": args.grid, "rtol": args.rtol},
             "iterations": its[-1] if its else None,
             "cpu_baseline": {"value": round(ms, 3), "unit": "ms", "cores": 1, "kind": "oracle",
                              "sample": sample},
@@ -550,7 +552,7 @@ def run_gb300(args, world, rank, local):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms64, 3),
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "grid": args.grid, "rtol": args.rtol,
+                "config": {"workload": workload(args.grid, sysm.n), "grid": args.grid, "rtol": args.rtol,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "256 MB write before every timed step",
                            "solves_per_s_job": round(world * 1e3 / ms64, 2)},
