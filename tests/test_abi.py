@@ -53,3 +53,16 @@ def test_options_default_and_null_handling():
     assert lib.mgr_setup(None, None, None, None, None) == 1
     lib.mgr_last_error.restype = ctypes.c_char_p
     assert b"NULL" in lib.mgr_last_error(None)
+
+
+def test_python_options_mapping():
+    """Names and per-level lists of the Python options() reach the C struct."""
+    from paper_2101_11649_gb300 import mgr as M
+    o = M.options(relax=("amg", "l1_jacobi", "block_jacobi"), sweeps=(2,), weights=(0.8,),
+                  relax_functions=(3,), restrict=("jacobi", "injection"), spin_limit=7,
+                  max_coarse=32, precision="fp32", tail_nnz=1000)
+    assert list(o.relax_type)[:3] == [M.RELAX["amg"], M.RELAX["l1_jacobi"], M.RELAX["block_jacobi"]]
+    assert o.relax_sweeps[0] == 2 and o.relax_sweeps[1] == 1 and o.relax_weight[0] == 0.8
+    assert o.relax_functions[0] == 3 and o.relax_functions[1] == 1
+    assert list(o.restrict_type)[:2] == [1, 0] and o.spin_limit == 7
+    assert o.amg_max_coarse == 32 and o.precision == 1 and o.amg_tail_nnz == 1000

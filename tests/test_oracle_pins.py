@@ -754,3 +754,11 @@ def test_paper_strategies_converge_mesh_independently():
             assert r["status"] == 0, name
             its.append(r["iters"])
         assert max(its) - min(its) <= 8 and max(its) <= 40, (name, its)
+
+
+def test_oracle_refuses_eq5_restriction_with_block_jacobi():
+    """The restriction of Eq. 5 is stated for D_FF = diag(A_FF): a block-Jacobi
+    level with it is refused."""
+    s = make_compositional(6, 5, 2, nwell_side=2)
+    with pytest.raises(RuntimeError):
+        O.Oracle(s, O.Options(relax=["block_jacobi", "block_jacobi"], restrict=["jacobi"]))
