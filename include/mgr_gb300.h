@@ -106,7 +106,11 @@ enum { MGR_PREC_FP64 = 0, MGR_PREC_FP32 = 1 };
  * separated by grid-wide barriers (same arithmetic, bitwise the same result
  * as one launch per step); 0 (the default) runs every step as its own
  * launch.  Devices without cooperative launches ignore it.  A barrier wait
- * that runs out (it should not) makes mgr_solve return MGR_ERR_TIMEOUT.
+ * that runs out (it should not) makes mgr_solve, mgr_apply and
+ * mgr_apply_transpose return MGR_ERR_TIMEOUT; with the tail on, the two
+ * apply calls synchronise the stream to read its error word, and a solve
+ * stops at the first step whose tail gave up, leaving x as it was at the
+ * last restart.
  */
 typedef struct {
     int32_t relax_type[MGR_MAX_LEVELS];
@@ -154,7 +158,8 @@ void mgr_options_default(mgr_options *opt);
 mgr_status mgr_setup(const mgr_bsr *A, const mgr_labels *cf, const mgr_options *opt,
                      void *stream, mgr_handle *out);
 
-/* z = M^{-1} v: one MGR V-cycle (Algorithm 1 without global relaxation). device v, z. */
+/* z = M^{-1} v: one MGR V-cycle (Algorithm 1 without global relaxation).
+ * device v, z.  TIMEOUT when a fused AMG tail (amg_tail_nnz) gave up. */
 mgr_status mgr_apply(mgr_handle h, const double *v, double *z);
 
 /* z = M^{-T} v: the exact transpose of mgr_apply's operator. device v, z. */
@@ -211,10 +216,11 @@ mgr_status mgr_bsr_spmv(int32_t nb, int32_t b, const int32_t *row_ptr, const int
 
 /*
  * Residual r = bvec - A x and its norm without any allocation (the paper has
- * no counterpart; this serves callers that cannot call cudaMalloc: code
- * running while a CUDA graph is being captured, plug-ins whose host
- * application owns all device memory, loops that must not enter the
- * allocator).  A is a block-CSR matrix on the device (as mgr_bsr_spmv);
+ * no counterpart; this serves callers that cannot call cudaMalloc: plug-ins
+ * whose host application owns all device memory through its own pool and
+ * forbids allocations behind its back, and real-time loops that must never
+ * enter the allocator, whose calls can block or fail at any moment).  A is
+ * a block-CSR matrix on the device (as mgr_bsr_spmv);
  * x, bvec, r (length n = nb*b) and norm_out (one double, = ||r||_2) are
  * caller-owned device memory.  The reduction's only scratch is a file-scope
  * static device array of MGR_NOALLOC_MAX_BLOCKS partial sums plus a ticket

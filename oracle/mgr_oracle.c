@@ -1256,6 +1256,15 @@ int or_amg_cf(or_ctx *c, int amg, int k, int *cf) {
     return OR_OK;
 }
 
+/* 1/d_i of the l1-Jacobi smoother of AMG level k (every level but the
+ * coarsest) of hierarchy amg (as above) */
+int or_amg_dinv(or_ctx *c, int amg, int k, double *dinv) {
+    amg_h *H = amg_of(c, amg);
+    if (!H || k < 0 || k >= H->nlev - 1 || !H->lev[k].dl1inv) return OR_INVALID;
+    memcpy(dinv, H->lev[k].dl1inv, (size_t)H->lev[k].A.n * sizeof(double));
+    return OR_OK;
+}
+
 /* AMG levels of hierarchy amg (as above); 0 when there is none */
 int or_amg_nlevels_of(or_ctx *c, int amg) {
     amg_h *H = amg_of(c, amg);

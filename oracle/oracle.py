@@ -61,6 +61,7 @@ def lib():
         L.or_mat_copy.argtypes = [vp, ip, ip, ip, vp, vp, vp]
         L.or_mgr_dinv.argtypes = [vp, ip, vp, vp]
         L.or_amg_cf.argtypes = [vp, ip, ip, vp]
+        L.or_amg_dinv.argtypes = [vp, ip, ip, vp]
         L.or_amg_nlevels_of.argtypes = [vp, ip]
         L.or_amg_split_interp.argtypes = [ip, vp, vp, vp, vp, dp, ip, ip, vp, vp, vp, vp, ip, vp]
         L.or_amg_strength.argtypes = [ip, vp, vp, vp, vp, dp, vp, vp, ip]
@@ -224,6 +225,15 @@ class Oracle:
         if lib().or_amg_cf(self.h, amg, k, _p(cf)):
             return None
         return cf
+
+    def amg_dinv(self, k, frelax_level=None):
+        """1/d_i of the l1-Jacobi smoother of AMG level k (not the coarsest)."""
+        amg = 1 if frelax_level is None else 2 + frelax_level
+        n = self.amg_matrix(k, "A", frelax_level)[3][0]
+        d = np.zeros(n)
+        if lib().or_amg_dinv(self.h, amg, k, _p(d)):
+            return None
+        return d
 
     def frelax_amg_nlevels(self, lvl):
         """AMG levels of MGR level ``lvl``'s F-relaxation (0: not AMG)."""

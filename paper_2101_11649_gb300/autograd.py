@@ -14,12 +14,20 @@ from .mgr import MGRSolver
 class MGRSolveFn(torch.autograd.Function):
     """forward(values, b, solver, rtol, maxit) -> x.
 
-    `values` is the (nnzb, b, b) tensor of A's stored blocks the solver was
-    built from; it is an input only so autograd can return dL/dA for it.
+    `values` is the (nnzb, b, b) tensor of A's stored blocks.  When they are
+    not the values the solver last took (at setup, refresh or update), they
+    are handed to the solver's outer operator first (mgr_update_values), so x
+    and the gradients always belong to `values`; the hierarchy built before
+    stays the preconditioner (call solver.refresh to rebuild it).
     """
 
     @staticmethod
     def forward(ctx, values, rhs, solver: MGRSolver, rtol: float, maxit: int):
+        if tuple(values.shape) != (solver.nnzb, solver.b, solver.b):
+            raise ValueError(f"values has shape {tuple(values.shape)}, the solver's pattern "
+                             f"holds ({solver.nnzb}, {solver.b}, {solver.b}) blocks")
+        if not solver.holds_values(values):
+            solver.update_values(values.detach())
         x, info = solver.solve(rhs.contiguous(), rtol=rtol, maxit=maxit)
         if info["status"] != 0:
             raise RuntimeError(f"forward solve did not converge: {info}")

@@ -257,6 +257,20 @@ static int read_errw(mgr_handle h) {
     return e;
 }
 
+// The fused AMG tail's error word (nonzero once one of its grid-barrier
+// waits ran out).  Synchronises the stream to read it; a set word is cleared
+// with the barrier's other words so that later launches start clean.
+static bool tail_timed_out(mgr_handle h) {
+    if (!h->H.tail_sync) return false;
+    unsigned terr = 0;
+    cudaMemcpyAsync(&terr, h->H.tail_sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, h->s);
+    cudaStreamSynchronize(h->s);
+    if (!terr) return false;
+    cudaMemsetAsync(h->H.tail_sync, 0, 4 * sizeof(unsigned), h->s);
+    cudaStreamSynchronize(h->s);
+    return true;
+}
+
 static int to_f32(Arena &ar, DCSR &M, cudaStream_t s) {
     if (M.nnz == 0) { M.v32 = ar.alloc<float>(1); return M.v32 ? 0 : ST_NOMEM; }
     M.v32 = ar.alloc<float>(M.nnz);
@@ -1168,6 +1182,8 @@ extern "C" mgr_status mgr_apply(mgr_handle h, const double *v, double *z) {
     if (!h->ready) return fail(h, MGR_ERR_INVALID, "no hierarchy (a refresh failed)");
     vcycle(h, v, z, 0);
     if (cudaGetLastError() != cudaSuccess) return cuda_fail(h, "mgr_apply");
+    if (tail_timed_out(h))
+        return fail(h, MGR_ERR_TIMEOUT, "a grid barrier of the fused AMG tail ran out of time");
     return MGR_OK;
 }
 
@@ -1176,6 +1192,8 @@ extern "C" mgr_status mgr_apply_transpose(mgr_handle h, const double *v, double 
     if (!h->ready) return fail(h, MGR_ERR_INVALID, "no hierarchy (a refresh failed)");
     vcycle(h, v, z, 1);
     if (cudaGetLastError() != cudaSuccess) return cuda_fail(h, "mgr_apply_transpose");
+    if (tail_timed_out(h))
+        return fail(h, MGR_ERR_TIMEOUT, "a grid barrier of the fused AMG tail ran out of time");
     return MGR_OK;
 }
 
@@ -1213,6 +1231,8 @@ static void arnoldi_step(mgr_handle h, int j, int trans) {
     { KScope ks(h, "givens", -1, 0.0);
       launch_arnoldi_finish(j, K.m, K.h1, K.h2, K.nrm2, K.nrmB, K.flag, K.H, K.cs, K.sn, K.g, K.hn, K.stat, K.tol, s); }
     cudaMemcpyAsync(K.hstat, K.stat, 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (h->H.tail_sync)  // the fused tail's error word, read after every step
+        cudaMemcpyAsync(K.hstat + 6, h->H.tail_sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     { KScope ks(h, "vec_scale", -1, nd * 16);
       launch_vec_scale(w, w, K.hn, nullptr, 1, (int)n, s); }
 }
@@ -1280,6 +1300,7 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
         double tol_abs = rtol * bn;
         cudaMemcpyAsync(K.tol, &tol_abs, sizeof(double), cudaMemcpyHostToDevice, s);
         K.hist.clear();
+        K.hstat[6] = 0.0;
         for (;;) {
             outer_residual(h, x, b, K.r, trans);
             { KScope ks(h, "norm", -1, n * 8.0);
@@ -1309,9 +1330,14 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
                 int conv = K.hstat[1] != 0.0, brk = K.hstat[2] != 0.0;
                 if (!isfinite(est)) { st = MGR_ERR_INVALID; break; }
                 if (K.hstat[4] != 0.0) reorth++;
+                unsigned tail_err = 0;
+                memcpy(&tail_err, K.hstat + 6, sizeof(unsigned));
+                if (tail_err) { st = MGR_ERR_TIMEOUT; break; }
                 if (conv || brk) break;
             }
             if (st == MGR_ERR_INVALID) { h->err = "preconditioned residual is not finite"; break; }
+            // a preconditioner that left its tail early is not applied to x
+            if (st == MGR_ERR_TIMEOUT) break;
             { KScope ks(h, "givens", -1, 0.0);
               launch_solve_upper(k, m, K.H, K.g, K.y, s); }
             { KScope ks(h, "update_x", -1, (k + 2.0) * n * 8, (double)k * n);
@@ -1319,16 +1345,9 @@ static mgr_status fgmres(mgr_handle h, const double *b, double *x, double rtol, 
         }
     }
     cudaStreamSynchronize(s);
-    if (h->H.tail_sync) {
-        unsigned terr = 0;
-        cudaMemcpyAsync(&terr, h->H.tail_sync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
-        if (terr) {
-            cudaMemsetAsync(h->H.tail_sync, 0, 4 * sizeof(unsigned), s);
-            cudaStreamSynchronize(s);
-            st = MGR_ERR_TIMEOUT;
-            h->err = "a grid barrier of the fused AMG tail ran out of time";
-        }
+    if (tail_timed_out(h) || st == MGR_ERR_TIMEOUT) {
+        st = MGR_ERR_TIMEOUT;
+        h->err = "a grid barrier of the fused AMG tail ran out of time";
     }
     double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) {

@@ -1,10 +1,10 @@
 // Residual and residual norm without any device allocation.
 //
-// Some callers cannot call cudaMalloc when they need a residual check: code
-// that runs while another part of the application is capturing a CUDA graph
-// (an allocation there breaks the capture), plug-ins whose host application
-// owns all device memory through its own pool, and latency-critical loops
-// that must never enter the allocator.  This entry point serves them: the
+// Some callers cannot call cudaMalloc when they need a residual check:
+// plug-ins whose host application owns all device memory through its own
+// pool and forbids allocations behind its back, and latency-critical loops
+// that must never enter the allocator (a cudaMalloc can block on the device
+// or fail when memory is exhausted).  This entry point serves them: the
 // caller passes the matrix, the vectors and the outputs, and the only
 // scratch the reduction needs (one partial sum per block and the ticket that
 // elects the last block) lives in the file-scope static device array below.

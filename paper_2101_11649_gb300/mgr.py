@@ -135,6 +135,16 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _value_key(val):
+    """Identity of a values tensor for MGRSolver.holds_values: its storage
+    address, shape, dtype and in-place version counter (None for arrays that
+    are not torch tensors, which the solver copies and cannot track)."""
+    import torch
+    if not isinstance(val, torch.Tensor):
+        return None
+    return (val.data_ptr(), tuple(val.shape), val.dtype, val._version)
+
+
 def options(relax=("jacobi",), sweeps=(), weights=(), theta=0.25, max_levels=25, max_coarse=1024,
             pmax=4, num_functions=1, precision="fp64", restart=30, use_graphs=True,
             tail_nnz=None, relax_functions=(), restrict=(), spin_limit=None) -> mgr_options:
@@ -207,6 +217,7 @@ class MGRSolver:
         self.n = nb * self.b
         self.nb = nb
         self.nnzb = nnzb
+        self._held = _value_key(val)
 
     @classmethod
     def from_system(cls, sysm, precision="fp64", **kw):
@@ -258,6 +269,11 @@ class MGRSolver:
         d["status"] = int(st)
         return x, d
 
+    def holds_values(self, val):
+        """True when `val` is the tensor the solver last took its values from
+        (setup, refresh or update_values) and has not been modified since."""
+        return self._held is not None and _value_key(val) == self._held
+
     def update_values(self, val):
         """New values of A (same pattern) for the outer operator; the
         hierarchy from setup stays the preconditioner."""
@@ -268,18 +284,21 @@ class MGRSolver:
         else:
             v = np.ascontiguousarray(val, np.float64)
             _check(lib().mgr_update_values(self.h, v.ctypes.data, 0), self.h)
+        self._held = _value_key(val)
 
     def refresh(self, val):
         """New values of A (same pattern): the MGR levels and the final AMG
         hierarchy are rebuilt from them, AMG F-relaxation hierarchies are
         kept (setup reuse)."""
         import torch
+        self._held = None
         if isinstance(val, torch.Tensor) and val.is_cuda:
             v = val.to(torch.float64).contiguous()
             _check(lib().mgr_refresh(self.h, _ptr(v), 1), self.h)
         else:
             v = np.ascontiguousarray(val, np.float64)
             _check(lib().mgr_refresh(self.h, v.ctypes.data, 0), self.h)
+        self._held = _value_key(val)
 
     def grad_values(self, lam, x):
         import torch
@@ -379,9 +398,9 @@ def launch_count() -> int:
 
 def residual_norm_noalloc(row_ptr, col_idx, val, b, x, bvec, r=None, norm=None, stream=None):
     """r = bvec - A x and ||r||_2 (device tensors) through the allocation-free
-    entry point: its reduction scratch is a static device array, so it can run
-    where cudaMalloc cannot be called (torch may still allocate r and norm
-    here when they are not passed in)."""
+    entry point: its reduction scratch is a static device array, so the call
+    itself never allocates (torch allocates r and norm here when they are not
+    passed in)."""
     import torch
     r = torch.empty_like(x) if r is None else r
     norm = torch.empty(1, dtype=torch.float64, device=x.device) if norm is None else norm
@@ -401,6 +420,7 @@ class _BorrowedSolver(MGRSolver):
         self.h = h
         self.n, self.nb, self.b, self.nnzb = n, nb, b, nnzb
         self.device = device
+        self._held = None
 
     def close(self):
         self.h = C.c_void_p()

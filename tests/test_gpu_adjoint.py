@@ -1,6 +1,8 @@
 """Adjoint form: gradients of L = w . x, x = A^{-1} b, through the autograd
 Function (transposed MGR cycle on the GPU), checked against the dense
 gradient, the CPU oracle's gradient and central finite differences."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -161,3 +163,28 @@ def test_autograd_matches_central_differences_16cubed(member16):
         err = abs(fd - ad) / max(abs(ad), 1e-8 * gmax)
         worst = max(worst, err)
     assert worst <= 1e-5, worst
+
+
+def test_autograd_follows_the_values_it_is_given():
+    """Values that differ from the ones the solver was built from (a later
+    Newton step) reach the outer operator before the forward solve, so x and
+    the gradients belong to them; a wrong shape is refused."""
+    s = make_two_phase(6, 5, 4)
+    solver = M.MGRSolver.from_system(s)
+    rng = np.random.default_rng(11)
+    val2 = s.val * rng.uniform(0.9, 1.1, s.val.shape[0])[:, None, None]
+    s2 = dataclasses.replace(s, val=val2)
+    w = rng.standard_normal(s.n)
+    A2 = dense_of(s2)
+    x_ref = O.dense_solve(A2, s.rhs)
+    lam_ref = O.dense_solve(A2.T.copy(), w)
+    vals = torch.as_tensor(val2, device=DEV).requires_grad_(True)
+    rhs = torch.as_tensor(s.rhs, device=DEV).requires_grad_(True)
+    x = mgr_solve_fn(vals, rhs, solver, 1e-12, 2000)
+    (torch.as_tensor(w, device=DEV) * x).sum().backward()
+    assert np.linalg.norm(x.detach().cpu().numpy() - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+    g_ref = grads_from(s2, lam_ref, x_ref)
+    assert np.max(np.abs(vals.grad.cpu().numpy() - g_ref)) <= 1e-9 * np.max(np.abs(g_ref))
+    assert solver.holds_values(vals)
+    with pytest.raises(ValueError):
+        mgr_solve_fn(vals[:-1], rhs, solver, 1e-12, 2000)

@@ -2,9 +2,11 @@
 
 Setup is compared bit for bit (both sides follow the same stated operation
 order without fused multiply-add); the solve phase within the tolerances of
-the FP64 arithmetic: SpMV per entry relative to sum_j |a_ij x_j| (1e-13),
-V-cycle 1e-11 relative, FGMRES iterations +-1 and solutions 1e-8 relative
-when both are converged to 1e-12.
+the FP64 arithmetic: SpMV per entry relative to sum_j |a_ij x_j| (1e-13);
+V-cycle outputs entry by entry, per MGR level's F set and per final coarse
+block, within 1e-11 of the set's largest entry (1e-4 for the FP32 cycle);
+FGMRES iterations +-1; solutions converged to 1e-12 within 1e-8 in the
+2-norm and per set.
 """
 import dataclasses
 
@@ -22,6 +24,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from paper_2101_11649_gb300 import mgr as M  # noqa: E402
+from parity_checks import cycle_close  # noqa: E402
 
 DEV = torch.device("cuda:0")
 
@@ -133,9 +136,9 @@ def test_sell_products_over_row_shapes(n, K, keep):
         o = O.Oracle(s)
         zo = o.apply(x)
         zg = g.apply(t(x)).cpu().numpy()
-        assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo)
+        cycle_close(s, zg, zo, 1e-11, "fp64")
         z32 = solver(s, precision="fp32").apply(t(x)).cpu().numpy()
-        assert np.linalg.norm(z32 - zo) <= 1e-4 * np.linalg.norm(zo)
+        cycle_close(s, z32, zo, 1e-4, "fp32")
 
 
 # ------------------------------------------------------- fused AMG tail
@@ -269,7 +272,7 @@ def test_vcycle_parity(name):
         v = rng.standard_normal(s.n)
         zg = g.apply(t(v), transpose=trans).cpu().numpy()
         zo = o.apply_transpose(v) if trans else o.apply(v)
-        assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo), (trans, np.linalg.norm(zg - zo) / np.linalg.norm(zo))
+        cycle_close(s, zg, zo, 1e-11, f"trans={trans}")
 
 
 @pytest.mark.parametrize("name", ["poromech_mgr_u", "two_phase_amg_relax"])
@@ -287,7 +290,7 @@ def test_amg_frelax_sweeps_and_weight(name, precision, sweeps, omega):
         v = rng.standard_normal(s.n)
         zg = g.apply(t(v), transpose=trans).cpu().numpy()
         zo = o.apply_transpose(v) if trans else o.apply(v)
-        assert np.linalg.norm(zg - zo) <= tol * np.linalg.norm(zo), (trans, np.linalg.norm(zg - zo) / np.linalg.norm(zo))
+        cycle_close(s, zg, zo, tol, f"trans={trans}")
 
 
 @pytest.mark.parametrize("name", ["poromech_mgr_u", "two_phase_amg_relax", "compositional_4level"])
@@ -308,7 +311,7 @@ def test_amg_frelax_single_level_hierarchy(name, restrict):
         v = rng.standard_normal(s.n)
         zg = g.apply(t(v), transpose=trans).cpu().numpy()
         zo = o.apply_transpose(v) if trans else o.apply(v)
-        assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo)
+        cycle_close(s, zg, zo, 1e-11, f"trans={trans}")
     ro = o.solve(s.rhs, rtol=1e-10, maxit=300)
     _, ig = g.solve(t(s.rhs), rtol=1e-10, maxit=300)
     assert ig["status"] == 0 and abs(ig["iterations"] - ro["iters"]) <= 1
@@ -369,7 +372,7 @@ def test_jacobi_restriction_vcycle_parity(name, sweeps, omega, precision):
         v = rng.standard_normal(s.n)
         zg = g.apply(t(v), transpose=trans).cpu().numpy()
         zo = o.apply_transpose(v) if trans else o.apply(v)
-        assert np.linalg.norm(zg - zo) <= tol * np.linalg.norm(zo), (trans, np.linalg.norm(zg - zo) / np.linalg.norm(zo))
+        cycle_close(s, zg, zo, tol, f"trans={trans}")
 
 
 @pytest.mark.parametrize("name", RESTRICT_CASES)
@@ -413,6 +416,7 @@ def test_solve_parity(name):
     xg, ig = g.solve(t(s.rhs), rtol=1e-12, maxit=1000)
     xo = ro["x"]
     assert np.linalg.norm(xg.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
+    cycle_close(s, xg.cpu().numpy(), xo, 1e-8, "solution")
 
 
 @pytest.mark.parametrize("name", list(SMALL))
@@ -428,6 +432,7 @@ def test_fp32_preconditioner_reaches_fp64_tolerance(name):
     xo = ro["x"]
     rel = np.linalg.norm(xg.cpu().numpy() - xo) / np.linalg.norm(xo)
     assert rel <= 1e-5, rel
+    cycle_close(s, xg.cpu().numpy(), xo, 1e-5, "fp32 solution")
 
 
 def test_transpose_solve_and_gradient():
@@ -493,8 +498,18 @@ def test_tail_barrier_timeout_is_reported_and_the_context_survives():
     converges normally."""
     s = TAIL_SYSTEMS["mimetic24"]()
     g = solver(s, tail_nnz=400000, spin_limit=1)
-    _, info = g.solve(t(s.rhs), rtol=1e-8, maxit=3, check=False)
+    x = torch.zeros(s.n, dtype=torch.float64, device=DEV)
+    _, info = g.solve(t(s.rhs), x, rtol=1e-8, maxit=3, check=False)
     assert info["status"] == M.MGR_ERR_TIMEOUT, info
+    # the solve stops at the first step whose tail gave up, and the broken
+    # preconditioner output never reaches x
+    assert info["iterations"] == 1 and float(x.abs().max()) == 0.0
+    # a single cycle reports the timeout too, in both orientations
+    v = t(np.random.default_rng(3).standard_normal(s.n))
+    for trans in (False, True):
+        with pytest.raises(M.MGRError) as e:
+            g.apply(v, transpose=trans)
+        assert e.value.status == M.MGR_ERR_TIMEOUT
     ok = solver(s, tail_nnz=400000)
     _, info2 = ok.solve(t(s.rhs), rtol=1e-8)
     assert info2["status"] == 0 and info2["rel_residual"] <= 1e-8
@@ -582,7 +597,10 @@ def test_full_size(name):
     v = rng.standard_normal(s.n)
     zg = g.apply(t(v)).cpu().numpy()
     zo = o.apply(v)
-    assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo)
+    cycle_close(s, zg, zo, 1e-11, "fp64")
+    # the FP32 cycle entry by entry against the FP64 oracle
+    z32 = solver(s, precision="fp32").apply(t(v)).cpu().numpy()
+    cycle_close(s, z32, zo, 1e-4, "fp32")
     ro = o.solve(s.rhs, rtol=1e-8)
     bn = np.linalg.norm(s.rhs)
     for prec in ("fp64", "fp32"):

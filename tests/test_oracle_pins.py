@@ -332,6 +332,112 @@ def test_amg_vcycle_convergence_factor_poisson():
     assert rate < 0.3, rate
 
 
+
+def _amg_only(rp, ci, v, rhs=None):
+    """A scalar system whose every dof belongs to the final coarse block, so
+    the oracle's preconditioner is the AMG V(1,1) cycle alone."""
+    from paper_2101_11649_gb300.synth.bsr import BlockSystem
+    n = rp.size - 1
+    rhs = np.zeros(n) if rhs is None else rhs
+    return BlockSystem("amg", 1, rp, ci, v.reshape(-1, 1, 1), np.zeros(n, np.int8), 0, rhs)
+
+
+def test_amg_l1_smoother_hand_example():
+    """The l1-Jacobi smoother of an AMG level (Sec. 5.1 names an l1
+    smoother): d_i = a_ii + sign(a_ii) sum_{j != i} |a_ij| over the whole row,
+    sign(0) = +1.  Expected 1/d_i worked out by hand: row 1 has a negative
+    diagonal, row 2 sums to zero, row 5 couples across the whole grid."""
+    from paper_2101_11649_gb300.synth.bsr import assemble_bsr
+    A = np.array([[4.0, -1.0, 0.0, 0.0, 0.0, -2.0],
+                  [-1.0, -3.0, 0.5, 0.0, 0.0, 0.0],
+                  [0.0, -1.0, 2.0, -1.0, 0.0, 0.0],
+                  [0.0, 0.0, -1.0, 3.0, -0.5, 0.0],
+                  [0.0, 0.0, 0.0, -2.0, 5.0, -1.0],
+                  [-0.25, 0.0, 0.0, 0.0, -1.0, 2.0]])
+    # d = 4+3, -3-1.5, 2+2, 3+1.5, 5+3, 2+1.25
+    expected = np.array([1 / 7, -2 / 9, 1 / 4, 2 / 9, 1 / 8, 4 / 13])
+    r, c = np.nonzero(A)
+    rp, ci, v = assemble_bsr(6, 1, r, c, A[r, c])
+    o = O.Oracle(_amg_only(rp, ci, v.ravel()), O.Options(relax=[], max_coarse=1))
+    assert o.amg_nlevels >= 2  # level 0 is smoothed, not the coarsest grid
+    np.testing.assert_allclose(o.amg_dinv(0), expected, rtol=1e-15, atol=0)
+
+
+def _row_l1_inverse(A):
+    """1/d_i of the l1 smoother by the reading, from a dense matrix."""
+    dg = np.diag(A).copy()
+    off = np.abs(A).sum(axis=1) - np.abs(dg)
+    return 1.0 / np.where(dg < 0, dg - off, dg + off)
+
+
+def _vcycle_dense(A, Ps):
+    """Dense operator B of the AMG V(1,1) cycle x = B r from x = 0 on A with
+    the interpolation matrices Ps (one per level, coarsest solved exactly):
+    x1 = D r; x2 = x1 + P B_c P^T (r - A x1); x = x2 + D (r - A x2), with
+    B_c the cycle on the Galerkin operator P^T A P and D the l1 inverse
+    diagonal of A.  Built from the definitions only."""
+    if not Ps:
+        return np.linalg.inv(A)
+    P = Ps[0]
+    D = np.diag(_row_l1_inverse(A))
+    Bc = _vcycle_dense(P.T @ A @ P, Ps[1:])
+    I = np.eye(A.shape[0])
+    X2 = D + P @ Bc @ P.T @ (I - A @ D)
+    return X2 + D @ (I - A @ X2)
+
+
+def _convection_diffusion(nx, ny, seed):
+    """2D 5-point diffusion plus an upwinded convection term (nonsymmetric)
+    with every third row's sign flipped (negative diagonals)."""
+    from paper_2101_11649_gb300.synth.bsr import assemble_bsr
+    rp, ci, v = poisson(nx, ny)
+    n = rp.size - 1
+    rng = np.random.default_rng(seed)
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, ci[rp[i]:rp[i + 1]]] = v[rp[i]:rp[i + 1]]
+    for i in range(n):  # upwind convection to the left neighbour
+        if i % nx:
+            w = 0.6 * rng.random()
+            A[i, i - 1] -= w
+            A[i, i] += w
+    A[::3] *= -1.0
+    r, c = np.nonzero(A)
+    rp, ci, v = assemble_bsr(n, 1, r, c, A[r, c])
+    return rp, ci, v.ravel(), A
+
+
+@pytest.mark.parametrize("max_coarse,nfunc", [(150, 1), (40, 1), (40, 2)])
+def test_amg_vcycle_equals_dense_multigrid_operator(max_coarse, nfunc):
+    """The oracle's AMG V(1,1) cycle, forward and transposed, equals the
+    dense composition of its definition (l1 pre-smoothing from zero,
+    restriction by P^T, Galerkin coarse operators, exact coarsest solve,
+    prolongation, l1 post-smoothing) built in the test from the oracle's
+    interpolation matrices alone: two levels (max_coarse 150) and three or
+    more (40), with the unknown approach's two functions, on a nonsymmetric
+    matrix with negative diagonals."""
+    rp, ci, v, A = _convection_diffusion(16, 12, 3)
+    o = O.Oracle(_amg_only(rp, ci, v), O.Options(relax=[], max_coarse=max_coarse,
+                                                 num_functions=nfunc))
+    nl = o.amg_nlevels
+    assert nl >= (2 if max_coarse == 150 else 3)
+    Ps = [csr_dense(o.amg_matrix(k, "P")) for k in range(nl - 1)]
+    # the smoother of every level is the reading's l1 row scaling of its
+    # Galerkin operator (all functions counted)
+    Ak = A
+    for k in range(nl - 1):
+        np.testing.assert_allclose(o.amg_dinv(k), _row_l1_inverse(Ak), rtol=1e-13)
+        Ak = Ps[k].T @ Ak @ Ps[k]
+    B = _vcycle_dense(A, Ps)
+    rng = np.random.default_rng(11)
+    for _ in range(2):
+        r = rng.standard_normal(A.shape[0])
+        z = o.apply(r)
+        zt = o.apply_transpose(r)
+        ref, reft = B @ r, B.T @ r
+        assert np.max(np.abs(z - ref)) <= 1e-12 * np.max(np.abs(ref))
+        assert np.max(np.abs(zt - reft)) <= 1e-12 * np.max(np.abs(reft))
+
 # ------------------------------------------------- transposed cycle (adjoint)
 @pytest.mark.parametrize("make,opts", [
     (lambda: make_two_phase(6, 5, 3), None),

@@ -1,8 +1,9 @@
 """The allocation-free residual entry point (collected last on purpose).
 
-mgr_residual_norm_noalloc serves callers that cannot call cudaMalloc (for
-example while a CUDA graph is being captured, or inside an application that
-owns all device memory): its reduction scratch is a static device array.
+mgr_residual_norm_noalloc serves callers that cannot call cudaMalloc (a
+plug-in whose host application owns all device memory, a real-time loop that
+must never enter the allocator): its reduction scratch is a static device
+array.
 Checked through the C ABI against the entry points that do allocate: the
 residual against b - mgr_spmv(x), the norm against the true residual that
 mgr_solve reports, on two calls in a row (the static scratch is reused).
