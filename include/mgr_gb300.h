@@ -337,6 +337,13 @@ mgr_status mgr_profile_entry(mgr_handle h, int32_t i, char *name, int32_t name_c
                              double *total_ms, int64_t *launches, double *bytes_per_launch,
                              double *fp64_fma_per_launch);
 
+/* Measured FP64 fused-multiply-add rate of the current device (FMA per
+ * second, best of reps timed launches after one warm-up, on stream): every
+ * thread of a full-occupancy grid runs independent FMA chains in registers.
+ * Instrumentation, not part of the method: the roofline denominator of the
+ * FP64 products, which issue one FMA per stored entry.  Synchronises. */
+mgr_status mgr_measure_fp64_fma(void *stream, int32_t reps, double *fma_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,7 +1,7 @@
 /*
  * mgr_oracle.c -- TEST INFRASTRUCTURE ONLY.
  *
- * A plain, slow, single-threaded FP64 restatement of multigrid-reduction
+ * A plain, slow FP64 restatement of multigrid-reduction
  * (MGR) preconditioned FGMRES, written from the paper (arXiv 2101.11649) so
  * that the CUDA path can be checked against it.  Only tests/, the smoke
  * check and the benchmark's CPU-baseline leg may load this library; the
@@ -21,6 +21,18 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Solve-phase loops whose iterations are independent (row products, vector
+ * updates, gathers and scatters over disjoint index sets) run OpenMP-parallel
+ * when built with -fopenmp; every entry is computed by the same operations
+ * in the same order as in a single thread.  Setup stays sequential. */
+#ifdef _OPENMP
+#include <omp.h>
+#define OR_PRAGMA(x) _Pragma(#x)
+#define PAR_FOR(n) OR_PRAGMA(omp parallel for schedule(static) if ((n) > 8192))
+#else
+#define PAR_FOR(n)
+#endif
 
 enum { OR_OK = 0, OR_INVALID = 1, OR_NOMEM = 2, OR_SINGULAR = 4, OR_NOT_CONVERGED = 5 };
 enum { OR_JACOBI = 0, OR_L1_JACOBI = 1, OR_BLOCK_JACOBI = 2, OR_AMG_RELAX = 3 };
@@ -50,6 +62,7 @@ static int csr_alloc(csr *a, int n, int m, int nnz) {
 
 /* y = A x  (row i: sum over entries in ascending column order) */
 static void csr_matvec(const csr *a, const double *x, double *y) {
+    PAR_FOR(a->n)
     for (int i = 0; i < a->n; i++) {
         double s = 0.0;
         for (int p = a->rp[i]; p < a->rp[i + 1]; p++) s += a->v[p] * x[a->ci[p]];
@@ -180,6 +193,7 @@ static int bsr_to_csr(int nb, int b, const int *rp, const int *ci, const double 
 /* y = A x for the block matrix itself (definition of the product). */
 void or_spmv_bsr(int nb, int b, const int *rp, const int *ci, const double *val,
                  const double *x, double *y) {
+    PAR_FOR(nb)
     for (int I = 0; I < nb; I++)
         for (int r = 0; r < b; r++) {
             double s = 0.0;
@@ -649,8 +663,10 @@ static void amg_vcycle(amg_h *h, int k, const double *rhs, double *x, int trans)
     int n = L->A.n;
     const csr *A = trans ? &L->AT : &L->A;
     if (k == h->nlev - 1) { lu_solve(h->nco, h->lu, h->piv, rhs, x, trans); return; }
+    PAR_FOR(n)
     for (int i = 0; i < n; i++) x[i] = L->dl1inv[i] * rhs[i];
     csr_matvec(A, x, L->t);
+    PAR_FOR(n)
     for (int i = 0; i < n; i++) L->r[i] = rhs[i] - L->t[i];
     amg_level *C = &h->lev[k + 1];
     double *rc = (double *)malloc(((size_t)C->A.n + 1) * sizeof(double));
@@ -658,8 +674,10 @@ static void amg_vcycle(amg_h *h, int k, const double *rhs, double *x, int trans)
     csr_matvec(&L->R, L->r, rc);
     amg_vcycle(h, k + 1, rc, ec, trans);
     csr_matvec(&L->P, ec, L->t);
+    PAR_FOR(n)
     for (int i = 0; i < n; i++) x[i] = x[i] + L->t[i];
     csr_matvec(A, x, L->t);
+    PAR_FOR(n)
     for (int i = 0; i < n; i++) x[i] = x[i] + L->dl1inv[i] * (rhs[i] - L->t[i]);
     free(rc); free(ec);
 }
@@ -991,16 +1009,21 @@ or_ctx *or_setup(int nb, int b, const int *rp, const int *ci, const double *val,
 static void mgr_frelax(mgr_level *L, const double *y, int trans) {
     const csr *AFF = trans ? &L->AFFT : &L->AFF;
     int nF = L->nF;
+    PAR_FOR(nF)
     for (int f = 0; f < nF; f++) L->zF[f] = 0.0;
     for (int s = 0; s < L->sweeps; s++) {
         csr_matvec(AFF, L->zF, L->tF);
+        PAR_FOR(nF)
         for (int f = 0; f < nF; f++) L->rF[f] = y[f] - L->tF[f];
         if (L->relax == OR_AMG_RELAX) {
             amg_vcycle(&L->famg, 0, L->rF, L->tF, trans);
+            PAR_FOR(nF)
             for (int f = 0; f < nF; f++) L->tF[f] = L->omega * L->tF[f];
+            PAR_FOR(nF)
             for (int f = 0; f < nF; f++) L->zF[f] = L->zF[f] + L->tF[f];
             continue;
         }
+        PAR_FOR(nF)
         for (int f = 0; f < nF; f++) {
             int g = L->gstart[f], k = L->gsize[f], r = f - g;
             double s2 = 0.0;
@@ -1010,6 +1033,7 @@ static void mgr_frelax(mgr_level *L, const double *y, int trans) {
             }
             L->tF[f] = L->omega * s2;
         }
+        PAR_FOR(nF)
         for (int f = 0; f < nF; f++) L->zF[f] = L->zF[f] + L->tF[f];
     }
 }
@@ -1024,16 +1048,20 @@ static void mgr_vcycle(or_ctx *c, int l, const double *v, double *z) {
     if (l == c->nlev) { amg_vcycle(&c->amg, 0, v, z, 0); return; }
     mgr_level *L = &c->lev[l];
     double *yF = (double *)malloc(((size_t)L->nF + 1) * sizeof(double));
+    PAR_FOR(L->nF)
     for (int f = 0; f < L->nF; f++) yF[f] = v[L->fidx[f]];
     mgr_frelax(L, yF, 0);
     csr_matvec(&L->ACF, L->zF, L->vC);
+    PAR_FOR(L->nC)
     for (int t = 0; t < L->nC; t++) L->vC[t] = v[L->cidx[t]] - L->vC[t];
     if (L->rtype == OR_RESTRICT_JACOBI) {
         /* r_C += Z r_F with r_F = v_F - A_FF z_F (Alg. 1 line 5, R~ of Eq. 5) */
         double *sC = (double *)malloc(((size_t)L->nC + 1) * sizeof(double));
         csr_matvec(&L->AFF, L->zF, L->tF);
+        PAR_FOR(L->nF)
         for (int f = 0; f < L->nF; f++) L->rF[f] = yF[f] - L->tF[f];
         csr_matvec(&L->Z, L->rF, sC);
+        PAR_FOR(L->nC)
         for (int t = 0; t < L->nC; t++) L->vC[t] = L->vC[t] + sC[t];
         free(sC);
     }
@@ -1045,7 +1073,9 @@ static void mgr_vcycle(or_ctx *c, int l, const double *v, double *z) {
     mgr_vcycle(c, l + 1, vC, eC);
     double *we = (double *)malloc(((size_t)L->nF + 1) * sizeof(double));
     csr_matvec(&L->W, eC, we);
+    PAR_FOR(L->nC)
     for (int t = 0; t < L->nC; t++) z[L->cidx[t]] = eC[t];
+    PAR_FOR(L->nF)
     for (int f = 0; f < L->nF; f++) z[L->fidx[f]] = zF[f] + we[f];
     free(yF); free(vC); free(eC); free(zF); free(we);
 }
@@ -1065,23 +1095,30 @@ static void mgr_vcycle_t(or_ctx *c, int l, const double *v, double *z) {
     double *rC = (double *)malloc(((size_t)L->nC + 1) * sizeof(double));
     double *eC = (double *)malloc(((size_t)L->nC + 1) * sizeof(double));
     double *tF = (double *)malloc(((size_t)L->nF + 1) * sizeof(double));
+    PAR_FOR(L->nF)
     for (int f = 0; f < L->nF; f++) vF[f] = v[L->fidx[f]];
     csr_matvec(&L->WT, vF, rC);
+    PAR_FOR(L->nC)
     for (int t = 0; t < L->nC; t++) rC[t] = v[L->cidx[t]] + rC[t];
     mgr_vcycle_t(c, l + 1, rC, eC);
     csr_matvec(&L->ACFT, eC, tF);
+    PAR_FOR(L->nF)
     for (int f = 0; f < L->nF; f++) tF[f] = vF[f] - tF[f];
     if (L->rtype == OR_RESTRICT_JACOBI) {
         double *sF = (double *)malloc(((size_t)L->nF + 1) * sizeof(double));
         csr_matvec(&L->ZT, eC, L->qF);
         csr_matvec(&L->AFFT, L->qF, sF);
+        PAR_FOR(L->nF)
         for (int f = 0; f < L->nF; f++) tF[f] = tF[f] - sF[f];
         free(sF);
     }
     mgr_frelax(L, tF, 1);
     if (L->rtype == OR_RESTRICT_JACOBI)
+        PAR_FOR(L->nF)
         for (int f = 0; f < L->nF; f++) L->zF[f] = L->zF[f] + L->qF[f];
+    PAR_FOR(L->nC)
     for (int t = 0; t < L->nC; t++) z[L->cidx[t]] = eC[t];
+    PAR_FOR(L->nF)
     for (int f = 0; f < L->nF; f++) z[L->fidx[f]] = L->zF[f];
     free(vF); free(rC); free(eC); free(tF);
 }
@@ -1089,9 +1126,24 @@ static void mgr_vcycle_t(or_ctx *c, int l, const double *v, double *z) {
 int or_apply(or_ctx *c, const double *v, double *z) { mgr_vcycle(c, 0, v, z); return OR_OK; }
 int or_apply_transpose(or_ctx *c, const double *v, double *z) { mgr_vcycle_t(c, 0, v, z); return OR_OK; }
 
+/* Inner product summed in fixed chunks of DOT_CHUNK entries: each chunk in
+ * ascending order, then the chunk sums in ascending chunk order.  The paper
+ * fixes no summation order; this one does not depend on the thread count. */
+#define DOT_CHUNK 4096
 static double dot(int n, const double *x, const double *y) {
+    int nch = (n + DOT_CHUNK - 1) / DOT_CHUNK;
+    double part_local[64];
+    double *part = nch <= 64 ? part_local : (double *)malloc((size_t)nch * sizeof(double));
+    PAR_FOR(n)
+    for (int c = 0; c < nch; c++) {
+        int i1 = (c + 1) * DOT_CHUNK < n ? (c + 1) * DOT_CHUNK : n;
+        double s = 0.0;
+        for (int i = c * DOT_CHUNK; i < i1; i++) s += x[i] * y[i];
+        part[c] = s;
+    }
     double s = 0.0;
-    for (int i = 0; i < n; i++) s += x[i] * y[i];
+    for (int c = 0; c < nch; c++) s += part[c];
+    if (part != part_local) free(part);
     return s;
 }
 
@@ -1125,12 +1177,14 @@ int or_solve(or_ctx *c, const double *b, double *x, double rtol, int maxit, int 
     }
     for (;;) {
         csr_matvec(A, x, r);
+        PAR_FOR(n)
         for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
         double beta = sqrt(dot(n, r, r));
         *relres = beta / bn;
         if (hist && it == 0) hist[0] = *relres;
         if (beta <= rtol * bn) { rc = OR_OK; break; }
         if (it >= maxit) break;
+        PAR_FOR(n)
         for (int i = 0; i < n; i++) V[i] = r[i] / beta;
         for (int t = 0; t <= m; t++) g[t] = 0.0;
         g[0] = beta;
@@ -1146,6 +1200,7 @@ int or_solve(or_ctx *c, const double *b, double *x, double rtol, int maxit, int 
                 double *vi = V + (size_t)i * n;
                 double h = dot(n, w, vi);
                 H[(size_t)i * m + j] = h;
+                PAR_FOR(n)
                 for (int e = 0; e < n; e++) w[e] -= h * vi[e];
             }
             double hn = sqrt(dot(n, w, w));
@@ -1165,6 +1220,7 @@ int or_solve(or_ctx *c, const double *b, double *x, double rtol, int maxit, int 
             if (hist) hist[it] = fabs(g[j + 1]) / bn;
             if (fabs(g[j + 1]) <= rtol * bn || hn <= 1e-14 * w0) break;
             double *vn = V + (size_t)(j + 1) * n;
+            PAR_FOR(n)
             for (int e = 0; e < n; e++) vn[e] = w[e] / hn;
         }
         for (int i = k - 1; i >= 0; i--) {
@@ -1172,10 +1228,10 @@ int or_solve(or_ctx *c, const double *b, double *x, double rtol, int maxit, int 
             for (int t = i + 1; t < k; t++) s -= H[(size_t)i * m + t] * y[t];
             y[i] = s / H[(size_t)i * m + i];
         }
-        for (int i = 0; i < k; i++) {
-            double *zi = Z + (size_t)i * n;
-            for (int e = 0; e < n; e++) x[e] += y[i] * zi[e];
-        }
+        /* x_e += y_i z_i,e for i ascending (per entry, as one loop over i) */
+        PAR_FOR(n)
+        for (int e = 0; e < n; e++)
+            for (int i = 0; i < k; i++) x[e] += y[i] * Z[(size_t)i * n + e];
     }
     *iters = it;
 done:
@@ -1184,6 +1240,17 @@ done:
 }
 
 /* ------------------------------------------------------- inspection */
+/* threads of the parallel solve-phase loops (1 without OpenMP) */
+int or_set_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
 int or_n(or_ctx *c) { return c->n; }
 int or_mgr_nlevels(or_ctx *c) { return c->nlev; }
 int or_amg_nlevels(or_ctx *c) { return c->amg.nlev; }

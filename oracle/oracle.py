@@ -2,9 +2,12 @@
 
 Only tests, the smoke check and the benchmark's CPU-baseline leg use this
 module.  It never touches the CUDA library and the CUDA library never calls
-it.  Building it is plain ``gcc -O2 -ffp-contract=off`` (no fused
+it.  Building it is plain ``gcc -O2 -ffp-contract=off -fopenmp`` (no fused
 multiply-add, no fast-math), so setup arithmetic follows the C source's
-stated operation order exactly.
+stated operation order exactly; the solve phase's independent loops run on
+all cores of the process's affinity set (``set_threads`` changes that),
+with results that do not depend on the thread count.  Without OpenMP the
+same source builds single-threaded.
 """
 from __future__ import annotations
 
@@ -30,10 +33,26 @@ def build(force: bool = False) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", SRC, "-lm", "-o", tmp])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+        r = subprocess.run(base + ["-fopenmp", SRC, "-lm", "-o", tmp], capture_output=True)
+        if r.returncode != 0:  # a toolchain without OpenMP: the same source, one thread
+            subprocess.check_call(base + [SRC, "-lm", "-o", tmp])
         os.replace(tmp, LIB)
     return LIB
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's parallel solve loops (n <= 0: keep); returns
+    the count in effect."""
+    return int(lib().or_set_threads(int(n)))
+
+
+def affinity_cores() -> int:
+    """Cores of this process's affinity set (the oracle's default thread count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 _lib = None
@@ -53,6 +72,8 @@ def lib():
         L.or_solve.argtypes = [vp, vp, vp, dp, ip, ip, ip, ip, vp, vp, vp]
         L.or_spmv_bsr.argtypes = [ip, ip, vp, vp, vp, vp, vp]
         L.or_dense_solve.argtypes = [ip, vp, vp, vp]
+        L.or_set_threads.argtypes = [ip]
+        L.or_set_threads.restype = ip
         L.or_pmis_u01.restype = dp
         L.or_pmis_u01.argtypes = [C.c_uint, C.c_uint]
         for nm in ("or_n", "or_mgr_nlevels", "or_amg_nlevels", "or_amg_coarse_n"):
@@ -65,6 +86,8 @@ def lib():
         L.or_amg_nlevels_of.argtypes = [vp, ip]
         L.or_amg_split_interp.argtypes = [ip, vp, vp, vp, vp, dp, ip, ip, vp, vp, vp, vp, ip, vp]
         L.or_amg_strength.argtypes = [ip, vp, vp, vp, vp, dp, vp, vp, ip]
+        # all cores of the affinity set (OpenMP's default may count others)
+        L.or_set_threads(affinity_cores())
         _lib = L
     return _lib
 

@@ -27,6 +27,7 @@ UNITS = {
     "noalloc.cu": [],
     "tail.cu": [],
     "check.cu": [],
+    "peak.cu": [],
 }
 
 

@@ -107,6 +107,7 @@ def lib(build_if_missing: bool = True):
     L.mgr_solve_history.argtypes = [vp, vp, i32]
     L.mgr_solve_history.restype = i32
     L.mgr_residual_norm_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.mgr_measure_fp64_fma.argtypes = [vp, i32, C.POINTER(C.c_double)]
     L.mgr_launch_count.argtypes = []
     L.mgr_launch_count.restype = C.c_int64
     L.mgr_profile.argtypes = [vp, i32]
@@ -389,6 +390,13 @@ def bsr_spmv(row_ptr, col_idx, val, b, x, y=None, alpha=1.0, beta=0.0, stream=No
     _check(lib().mgr_bsr_spmv(nb, int(b), _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x), _ptr(y),
                               float(alpha), float(beta), _stream_ptr(stream)))
     return y
+
+
+def measure_fp64_fma(reps=10, stream=None) -> float:
+    """Measured FP64 FMA rate of the current device (FMA/s, best of reps)."""
+    out = C.c_double()
+    _check(lib().mgr_measure_fp64_fma(_stream_ptr(stream), int(reps), C.byref(out)))
+    return out.value
 
 
 def launch_count() -> int:

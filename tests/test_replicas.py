@@ -53,7 +53,8 @@ def test_barrier_and_max_over_ranks_gloo():
 def test_reference_arm_two_ranks_prints_once():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py",
-           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--grid", "10"]
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
+           "--config", "two_phase_16x16x8"]
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600,
                        env=dict(os.environ, OMP_NUM_THREADS="1"))
     assert r.returncode == 0, r.stderr[-2000:]
@@ -62,3 +63,11 @@ def test_reference_arm_two_ranks_prints_once():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["higher_is_better"] is False
     assert d["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] == 0
+    # the GPU arm prints the same config dict for the same arguments
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2101_11649_gb300.synth import CONFIGS
+
+    class A:
+        rtol = 1e-8
+    assert d["config"] == bench.config_dict(A, "two_phase_16x16x8", CONFIGS["two_phase_16x16x8"]().n, 2)
