@@ -35,6 +35,7 @@ struct DCSR {
     double *sv = nullptr;        // padded values (FP64)
     float *sv32 = nullptr;       // padded values (FP32)
     long long sell_stored = 0;   // stored entries including padding
+    int sched = 0;               // slice order of the product kernel: 0 grid-stride, 1 contiguous per block
 };
 
 
@@ -141,8 +142,21 @@ int launch_amg_tail(const TailPlan *plan_device, int grid, unsigned *sync, cudaS
 // device cannot run it (the cycle then launches the levels one at a time).
 int amg_tail_grid(void);
 
-// SELL-C-sigma build from the CSR arrays (values of both precisions when present)
-int build_sell(DCSR &M, cudaStream_t s, Arena &ar);
+// Slice-order tuning of a SELL product: the values' precision, a flush
+// buffer larger than L2 and an event pair (owned by the caller)
+struct SellTune {
+    int fp32 = 0;
+    void *flush = nullptr;
+    size_t flush_bytes = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+constexpr int SELL_TUNE_MIN_SLICES = 4096;
+constexpr size_t SELL_TUNE_FLUSH_BYTES = 192u << 20;
+// SELL-C-sigma build from the CSR arrays (values of both precisions when
+// present); with tn, the product is then timed in both slice orders with the
+// values of tn's precision and the faster order kept (sell_tune)
+int build_sell(DCSR &M, cudaStream_t s, Arena &ar, const SellTune *tn = nullptr);
+int sell_tune(DCSR &M, const SellTune &tn, cudaStream_t s, Arena &ar);
 // re-copy the values of a built SELL layout after the CSR values changed
 void refresh_sell(DCSR &M, cudaStream_t s);
 

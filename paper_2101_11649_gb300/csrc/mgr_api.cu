@@ -159,6 +159,36 @@ struct mgr_ctx {
 
 static thread_local std::string g_last_error;
 
+// Setup of the members of a batch skips the slice-order timing (the batched
+// solve does not use SELL products; the members keep the grid-stride order).
+static thread_local bool g_no_tune = false;
+
+// Resources of the slice-order timing of SELL products (sell_tune): a flush
+// buffer larger than L2 and an event pair, held only while a setup builds its
+// SELL copies.  nullptr when tuning is off or a resource is missing (every
+// product then keeps the grid-stride order).
+static const SellTune *tune_begin(SellTune &t) {
+    if (g_no_tune) return nullptr;
+    t.flush_bytes = SELL_TUNE_FLUSH_BYTES;
+    if (cudaMalloc(&t.flush, t.flush_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        t.flush = nullptr;
+        return nullptr;
+    }
+    if (cudaEventCreate(&t.e0) != cudaSuccess || cudaEventCreate(&t.e1) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return &t;
+}
+
+static void tune_end(SellTune &t) {
+    if (t.flush) cudaFree(t.flush);
+    if (t.e0) cudaEventDestroy(t.e0);
+    if (t.e1) cudaEventDestroy(t.e1);
+    t = SellTune();
+}
+
 static int setup_tail(mgr_handle h, AmgH &G, int tail_nnz, cudaStream_t s, Arena &ar);
 
 static mgr_status fail(mgr_handle h, mgr_status st, const std::string &msg) {
@@ -565,15 +595,19 @@ static mgr_status build_levels(mgr_handle h, bool reuse) {
     }
     mgr_status st = setup_amg(h, h->H, cur, h->opt.amg_num_functions, ar, false);
     if (st != MGR_OK) return st;
-    // SELL-C-sigma copies of every matrix the solve phase multiplies with
+    // SELL-C-sigma copies of every matrix the solve phase multiplies with,
+    // each with the slice order its product runs fastest in (timed here)
     {
+        SellTune tune;
+        tune.fp32 = h->opt.precision == MGR_PREC_FP32 ? 1 : 0;
+        const SellTune *prec = tune_begin(tune);
         int rc2 = 0;
         auto sell_amg = [&](AmgH &G, Arena &gar) {
             if (G.sell) return;
             for (int k = 0; k + 1 < G.namg && !rc2; k++) {
                 AmgLevel &A = G.amg[k];
                 DCSR *ms[] = {&A.A, &A.AT, &A.P, &A.R};
-                for (DCSR *m : ms) rc2 |= build_sell(*m, s, gar);
+                for (DCSR *m : ms) rc2 |= build_sell(*m, s, gar, prec);
             }
             G.sell = !rc2;
         };
@@ -585,14 +619,15 @@ static mgr_status build_levels(mgr_handle h, bool reuse) {
                 L.AFF = L.famg->amg[0].A;
                 L.AFFT = L.famg->amg[0].AT;
                 DCSR *ms[] = {&L.ACF, &L.W, &L.ACFT, &L.WT};
-                for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
+                for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar, prec);
             } else {
                 DCSR *ms[] = {&L.AFF, &L.ACF, &L.W, &L.AFFT, &L.ACFT, &L.WT};
-                for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar);
+                for (DCSR *m : ms) rc2 |= build_sell(*m, s, ar, prec);
             }
-            if (L.rtype == MGR_RESTRICT_JACOBI) rc2 |= build_sell(L.Z, s, ar) | build_sell(L.ZT, s, ar);
+            if (L.rtype == MGR_RESTRICT_JACOBI) rc2 |= build_sell(L.Z, s, ar, prec) | build_sell(L.ZT, s, ar, prec);
         }
         sell_amg(h->H, ar);
+        tune_end(tune);
         if (rc2) return fail(h, MGR_ERR_NOMEM, "SELL copies");
     }
     {
@@ -711,14 +746,17 @@ extern "C" mgr_status mgr_setup(const mgr_bsr *Ain, const mgr_labels *cf, const 
     }
     // SELL-C-sigma copies of the outer operator and its transpose
     {
+        SellTune tune;  // the outer products are FP64 in both forms
+        const SellTune *tp = tune_begin(tune);
         int rc2 = 0;
         if (b == 1) {
             h->Aout.n = h->Aout.m = n;
             h->Aout.nnz = (int)nnzb;
             h->Aout.rp = h->brp; h->Aout.ci = h->bci; h->Aout.v = h->bval;
-            rc2 |= build_sell(h->Aout, s, ar);
+            rc2 |= build_sell(h->Aout, s, ar, tp);
         }
-        rc2 |= build_sell(h->A0T, s, ar);
+        rc2 |= build_sell(h->A0T, s, ar, tp);
+        tune_end(tune);
         if (rc2) { mgr_free(h); return fail(nullptr, MGR_ERR_NOMEM, "SELL copies"); }
     }
     cudaStreamSynchronize(s);
@@ -2139,7 +2177,9 @@ extern "C" mgr_status mgr_setup_batched(int32_t nsys, const mgr_bsr *A, const mg
             return bfail(nullptr, MGR_ERR_INVALID, "all systems of a batch need the same block size and MGR level count");
         }
         mgr_handle h = nullptr;
+        g_no_tune = true;
         mgr_status st = mgr_setup(&A[s], &cf[s], &o, bh->s, &h);
+        g_no_tune = false;
         if (st != MGR_OK) {
             std::string m = g_last_error;
             mgr_free_batched(bh);

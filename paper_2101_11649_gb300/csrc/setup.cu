@@ -1696,9 +1696,11 @@ __global__ void k_sell_fill(int nsl, int G, const int *rp, const int *ci, const 
 }
 
 // Lanes per row (rules fitted to timings of the solve-phase kernels on
-// GB300 over the AMG levels of a 1M-unknown system).  A lane's chain should
-// hold <= 24 entries on average and, while lanes keep >= 4 entries, <= 64 in
-// the longest row; a matrix with fewer than 64 warps per SM spreads rows
+// GB300 over the AMG levels of a 1M-unknown system, and of the 2M-unknown
+// compositional system whose pressure block has a few well-coupled rows
+// seven times longer than the rest).  A lane's chain should hold <= 24
+// entries on average and, while lanes keep >= 4 entries, <= 128 in the
+// longest row; a matrix with fewer than 64 warps per SM spreads rows
 // over more lanes while chains keep >= 16 entries; and a matrix too small
 // to give every SM 8 warps is bound by the dependent load-then-gather
 // rounds of its longest row, which are cut to <= 8 entries.
@@ -1707,7 +1709,7 @@ static int sell_lanes(double avg, int maxlen, long long n) {
     while (G < 32) {
         const double steps = avg / G, longest = (double)maxlen / G;
         const long long warps = n * G / 32;
-        const bool more = steps > 24.0 || (steps >= 4.0 && longest > 64.0) ||
+        const bool more = steps > 24.0 || (steps >= 4.0 && longest > 128.0) ||
                           (warps < 152LL * 64 && steps >= 16.0) || (warps < 152LL * 8 && longest > 8.0);
         if (!more) break;
         G *= 2;
@@ -1715,8 +1717,9 @@ static int sell_lanes(double avg, int maxlen, long long n) {
     return G;
 }
 
-int build_sell(DCSR &M, cudaStream_t s, Arena &ar) {
+int build_sell(DCSR &M, cudaStream_t s, Arena &ar, const SellTune *tn) {
     if (M.n <= 0) return ST_OK;
+    M.sched = 0;
     const int nwin = (M.n + SELL_WIN - 1) / SELL_WIN;
     M.perm = ar.alloc<int>((size_t)nwin * SELL_WIN);
     int *dmax = ar.alloc<int>(1);
@@ -1748,7 +1751,8 @@ int build_sell(DCSR &M, cudaStream_t s, Arena &ar) {
     M.sv32 = M.v32 ? ar.alloc<float>(tot + 1) : nullptr;
     if (!M.sci || (M.v && !M.sv) || (M.v32 && !M.sv32)) return ST_NOMEM;
     refresh_sell(M, s);
-    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return ST_CUDA;
+    return tn ? sell_tune(M, *tn, s, ar) : ST_OK;
 }
 
 void refresh_sell(DCSR &M, cudaStream_t s) {

@@ -296,6 +296,46 @@ void launch_dense_matvec(int n, const double *inv, const TV *r, TV *x, cudaStrea
 }
 
 
+// ------------------------------------------------------------ SELL tuning
+// Time y = M x in both slice orders of k_sell (grid-stride, contiguous per
+// block) and keep the faster one in M.sched.  Each timed launch follows a
+// write of the flush buffer (larger than L2), so the matrix streams from
+// HBM as it does inside a V-cycle; the orders alternate and each keeps its
+// best of two launches; the contiguous order must win by 5%.  The choice
+// only changes which warp sums which row, never a result.
+template <class T>
+static int sell_tune_t(DCSR &M, const T *vals, cudaStream_t s, Arena &ar, const SellTune &tn) {
+    T *x = ar.alloc<T>((size_t)(M.m > 0 ? M.m : 1));
+    T *y = ar.alloc<T>((size_t)(M.n > 0 ? M.n : 1));
+    if (!x || !y) return ST_NOMEM;
+    cudaMemsetAsync(x, 0, sizeof(T) * (M.m > 0 ? M.m : 1), s);
+    float best[2] = {1e30f, 1e30f};
+    for (int round = 0; round < 4; round++) {
+        const int mode = round & 1;
+        M.sched = mode;
+        cudaMemsetAsync(tn.flush, round, tn.flush_bytes, s);
+        cudaEventRecord(tn.e0, s);
+        spmv_rows<T>(M, vals, XPlain<T, T>{x}, EStore<T, T>{y}, s);
+        cudaEventRecord(tn.e1, s);
+        if (cudaEventSynchronize(tn.e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, tn.e0, tn.e1);
+        if (ms < best[mode]) best[mode] = ms;
+    }
+    ar.release(x);
+    ar.release(y);
+    M.sched = best[1] < 0.95f * best[0] ? 1 : 0;
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+int sell_tune(DCSR &M, const SellTune &tn, cudaStream_t s, Arena &ar) {
+    M.sched = 0;
+    // a product of fewer slices than one wave of warps runs the same in both orders
+    if (!M.sptr || M.nsl < SELL_TUNE_MIN_SLICES || !tn.flush) return ST_OK;
+    if (tn.fp32) return M.sv32 ? sell_tune_t<float>(M, M.sv32, s, ar, tn) : ST_OK;
+    return M.sv ? sell_tune_t<double>(M, M.sv, s, ar, tn) : ST_OK;
+}
+
 // ------------------------------------------------------- instantiations
 #define INST_T_TV(T, TV)                                                                          \
     template void launch_frelax_first<T, TV>(int, const int *, const int *, const int *,          \

@@ -118,10 +118,15 @@ static void csr_chunk(int n, long long nnz, const int *rp, const int *ci, const 
 }
 
 // ---------------------------------------------------------- SELL-C-sigma
-// k_sell: one warp per slice (layout and row sums in sell.cuh), grid-stride
-// over slices; FP32 (PF) starts a slice's epilogue loads and the next
-// slice's offsets before the slice's products.
-template <int G, class T, class XF, class EPI>
+// k_sell: one warp per slice (layout and row sums in sell.cuh); FP32 (PF)
+// starts a slice's epilogue loads and the next slice's offsets before the
+// slice's products.  Slices reach the warps in one of two orders, chosen per
+// matrix at setup by timing both (DCSR::sched): grid-stride over all slices
+// (CONTIG = 0), or a contiguous range of slices per block whose warps
+// interleave inside it (CONTIG = 1), so that the warps of an SM gather from
+// neighbouring rows and L1 keeps the vector lines they share (a structured
+// stencil's neighbouring grid lines).  Every row's sum is the same either way.
+template <int G, class T, class XF, class EPI, int CONTIG>
 __global__ void __launch_bounds__(256, SELL_BLOCKS)
     k_sell(int nsl, const long long *__restrict__ sptr, const int *__restrict__ slen,
            const int *__restrict__ perm, const int *__restrict__ sci, const T *__restrict__ sv, XF xf,
@@ -129,8 +134,17 @@ __global__ void __launch_bounds__(256, SELL_BLOCKS)
     constexpr int PF = SellCfg<T>::PF;
     constexpr int C = 32 / G;
     const int lane = threadIdx.x & 31;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nw, sl;
+    if (CONTIG) {
+        const int per = (nsl + gridDim.x - 1) / gridDim.x;
+        const int s0 = blockIdx.x * per;
+        nsl = min(nsl, s0 + per);
+        nw = blockDim.x >> 5;
+        sl = s0 + (threadIdx.x >> 5);
+    } else {
+        nw = (gridDim.x * blockDim.x) >> 5;
+        sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    }
     if (sl >= nsl) return;
     int L = __ldg(slen + sl);
     long long base = __ldg(sptr + sl) + lane;
@@ -163,13 +177,18 @@ __global__ void __launch_bounds__(256, SELL_BLOCKS)
     }
 }
 
+// grid: two waves of resident blocks for the grid-stride order, one for the
+// contiguous order (each block's range is its whole share)
 template <int G, class T, class XF, class EPI>
 static void sell_launch(const DCSR &M, const T *vals, XF xf, EPI epi, cudaStream_t s) {
     long long blocks = ((long long)M.nsl * 32 + 255) / 256;
-    const long long cap = (long long)NUM_SMS * SELL_BLOCKS * 2;
+    const long long cap = (long long)NUM_SMS * SELL_BLOCKS * (M.sched ? 1 : 2);
     if (blocks > cap) blocks = cap;
-    launch_k(k_sell<G, T, XF, EPI>, dim3((unsigned)(blocks < 1 ? 1 : blocks)), dim3(256), s, M.nsl, M.sptr,
-             M.slen, M.perm, M.sci, vals, xf, epi);
+    const dim3 grid((unsigned)(blocks < 1 ? 1 : blocks));
+    if (M.sched)
+        launch_k(k_sell<G, T, XF, EPI, 1>, grid, dim3(256), s, M.nsl, M.sptr, M.slen, M.perm, M.sci, vals, xf, epi);
+    else
+        launch_k(k_sell<G, T, XF, EPI, 0>, grid, dim3(256), s, M.nsl, M.sptr, M.slen, M.perm, M.sci, vals, xf, epi);
 }
 
 // Row products over a matrix: SELL-C-sigma when built, else the chunk engine.
