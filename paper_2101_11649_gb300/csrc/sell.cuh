@@ -33,9 +33,15 @@ __device__ __forceinline__ T group_sum(T s) {
 // offsets before the products, so they overlap them.  Both stay within 48
 // registers (5 blocks, 40 warps per SM).
 template <class T>
-struct SellCfg { static constexpr int U = 4, PF = 0; };
+struct SellCfg { static constexpr int U = 4, PF = 0, BP = 0; };
 template <>
-struct SellCfg<float> { static constexpr int U = 8, PF = 1; };
+struct SellCfg<float> { static constexpr int U = 6, PF = 1, BP = 1; };
+
+// one bulk request that brings [p, p + bytes) into L2 (16-byte aligned
+// address, size a multiple of 16; no completion to wait for)
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 constexpr int SELL_BLOCKS = 5;
 
 template <class T>

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256, SELL_BLOCKS)
     k_sell(int nsl, const long long *__restrict__ sptr, const int *__restrict__ slen,
            const int *__restrict__ perm, const int *__restrict__ sci, const T *__restrict__ sv, XF xf,
            EPI epi) {
-    constexpr int PF = SellCfg<T>::PF;
+    constexpr int PF = SellCfg<T>::PF, BP = SellCfg<T>::BP;
     constexpr int C = 32 / G;
     const int lane = threadIdx.x & 31;
     int nw, sl;
@@ -146,6 +146,46 @@ __global__ void __launch_bounds__(256, SELL_BLOCKS)
         sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     }
     if (sl >= nsl) return;
+    if (BP) {
+        // the next slice's header two slices ahead, so that its values and
+        // columns can be prefetched to L2 (one bulk request each, from lane
+        // 0) while this slice is summed
+        int L = __ldg(slen + sl);
+        long long base = __ldg(sptr + sl) + lane;
+        int row = __ldg(perm + (long long)sl * C + lane / G);
+        int nx = sl + nw, L2 = 0, row2 = -1;
+        long long s2 = 0;
+        if (nx < nsl) {
+            L2 = __ldg(slen + nx);
+            s2 = __ldg(sptr + nx);
+            row2 = __ldg(perm + (long long)nx * C + lane / G);
+        }
+        pdl_wait();  // slice offsets and rows above are read-only
+        pdl_launch_dependents();
+        for (;;) {
+            const bool own = (lane % G == 0) && row >= 0;
+            typename EPI::Pre pre{};
+            if (own) pre = epi.pre(row);
+            const int nx2 = nx + nw;
+            int L3 = 0, row3 = -1;
+            long long s3 = 0;
+            if (nx2 < nsl) {
+                L3 = __ldg(slen + nx2);
+                s3 = __ldg(sptr + nx2);
+                row3 = __ldg(perm + (long long)nx2 * C + lane / G);
+            }
+            if (lane == 0 && nx < nsl && L2 > 0) {
+                prefetch_l2(sv + s2, (unsigned)(L2 * 32 * (int)sizeof(T)));
+                prefetch_l2(sci + s2, (unsigned)(L2 * 32 * 4));
+            }
+            const T acc = sell_rows<G, T>(L, base, sci, sv, xf);
+            if (own) epi.put(row, acc, pre);
+            if (nx >= nsl) break;
+            sl = nx; L = L2; base = s2 + lane; row = row2;
+            nx = nx2; L2 = L3; s2 = s3; row2 = row3;
+        }
+        return;
+    }
     int L = __ldg(slen + sl);
     long long base = __ldg(sptr + sl) + lane;
     int row = __ldg(perm + (long long)sl * C + lane / G);
