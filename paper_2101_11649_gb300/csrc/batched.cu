@@ -171,6 +171,75 @@ void launch_bchunk<double, double>(int op, const BJob *jobs, const long long *pr
     }
 }
 
+// SELL row products of a batch: work item g is one slice of one member's
+// matrix; each member keeps its own lanes per row (sg) and layout, and a
+// row's sum is the chain and tree of the single-system kernel (sell.cuh), so
+// a member's products give the bits its own handle gives.
+template <class T, class TV, int OP>
+__global__ void __launch_bounds__(256) k_bsell(const BJob *__restrict__ jobs,
+                                               const long long *__restrict__ prefix, int njobs,
+                                               int js) {
+    pdl_wait();
+    pdl_launch_dependents();
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long total = prefix[njobs];
+    for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += nwarps) {
+        const int j = find_job(prefix, njobs, g);
+        const BJob &J = jobs[j];
+        if (job_off(J)) continue;
+        const int sl = (int)(g - prefix[j]);
+        const int G = J.sg, C = 32 / G;
+        const int L = __ldg(J.slen + sl);
+        const long long base = __ldg(J.sptr + sl) + lane;
+        const int row = __ldg(J.perm + (long long)sl * C + lane / G);
+        const auto xf = BOpT<T, TV, OP>::xf(J, js);
+        const auto epi = BOpT<T, TV, OP>::epi(J, js);
+        T acc = sell_chain<T>(L, base, J.sci, (const T *)J.sv, xf);
+        if (G > 1) acc = group_sum_rt<T>(acc, G);
+        if (lane % G == 0 && row >= 0) epi(row, acc);
+    }
+}
+
+template <class T, class TV, int OP>
+static void bsell_dispatch(const BJob *jobs, const long long *prefix, int njobs, long long total, int js,
+                           cudaStream_t s) {
+    if (total <= 0) return;
+    long long blocks = (total + 7) / 8;
+    if (blocks > NUM_SMS * 16) blocks = NUM_SMS * 16;
+    launch_plain(k_bsell<T, TV, OP>, dim3((unsigned)(blocks < 1 ? 1 : blocks)), dim3(256), s, jobs, prefix,
+                 njobs, js);
+}
+
+template <class T, class TV>
+void launch_bsell(int op, const BJob *jobs, const long long *prefix, int njobs, long long total, int js,
+                  cudaStream_t s) {
+    switch (op) {
+        case BOP_RESID: bsell_dispatch<T, TV, BOP_RESID>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_RESTRICT: bsell_dispatch<T, TV, BOP_RESTRICT>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_PROLONG: bsell_dispatch<T, TV, BOP_PROLONG>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_POST: bsell_dispatch<T, TV, BOP_POST>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_MGR_RESTRICT: bsell_dispatch<T, TV, BOP_MGR_RESTRICT>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_MGR_INTERP: bsell_dispatch<T, TV, BOP_MGR_INTERP>(jobs, prefix, njobs, total, js, s); break;
+        default: break;
+    }
+}
+
+template <>
+void launch_bsell<double, double>(int op, const BJob *jobs, const long long *prefix, int njobs,
+                                  long long total, int js, cudaStream_t s) {
+    switch (op) {
+        case BOP_RESID: bsell_dispatch<double, double, BOP_RESID>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_RESTRICT: bsell_dispatch<double, double, BOP_RESTRICT>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_PROLONG: bsell_dispatch<double, double, BOP_PROLONG>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_POST: bsell_dispatch<double, double, BOP_POST>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_MGR_RESTRICT: bsell_dispatch<double, double, BOP_MGR_RESTRICT>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_MGR_INTERP: bsell_dispatch<double, double, BOP_MGR_INTERP>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_OUTER_CSR: bsell_dispatch<double, double, BOP_OUTER_CSR>(jobs, prefix, njobs, total, js, s); break;
+        default: break;
+    }
+}
+
 static inline unsigned elem_grid(long long total) {
     long long g = (total + 255) / 256;
     if (g > NUM_SMS * 8) g = NUM_SMS * 8;
@@ -501,6 +570,8 @@ void launch_bupdate_norm(int k, const BJob *jobs, const long long *bprefix, int 
 
 template void launch_bchunk<float, float>(int, const BJob *, const long long *, int, long long, int, int, cudaStream_t);
 template void launch_bchunk<float, double>(int, const BJob *, const long long *, int, long long, int, int, cudaStream_t);
+template void launch_bsell<float, float>(int, const BJob *, const long long *, int, long long, int, cudaStream_t);
+template void launch_bsell<float, double>(int, const BJob *, const long long *, int, long long, int, cudaStream_t);
 template void launch_bfrelax_first<double, double>(const BJob *, const long long *, int, long long, double, int, cudaStream_t);
 template void launch_bfrelax_first<float, double>(const BJob *, const long long *, int, long long, float, int, cudaStream_t);
 template void launch_bfrelax_first<float, float>(const BJob *, const long long *, int, long long, float, int, cudaStream_t);

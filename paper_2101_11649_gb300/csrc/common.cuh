@@ -301,6 +301,11 @@ struct BJob {
     unsigned *ticket = nullptr;
     int *flag = nullptr;
     int nblk = 0;
+    // the matrix's SELL-C-sigma copy (row products of the SELL table kind)
+    const long long *sptr = nullptr;
+    const int *slen = nullptr, *perm = nullptr, *sci = nullptr;
+    const void *sv = nullptr;
+    int nsl = 0, sg = 1;
 };
 
 // batched table launches (T = value type, TV = top-level vector type)
@@ -309,6 +314,10 @@ enum BOp { BOP_RESID, BOP_RESTRICT, BOP_PROLONG, BOP_POST, BOP_MGR_RESTRICT, BOP
 template <class T, class TV>
 void launch_bchunk(int op, const BJob *jobs, const long long *prefix, int njobs, long long total,
                    int R, int jsel, cudaStream_t s);
+// the same row products over the members' SELL copies: one work item per slice
+template <class T, class TV>
+void launch_bsell(int op, const BJob *jobs, const long long *prefix, int njobs, long long total,
+                  int jsel, cudaStream_t s);
 template <class T, class TV>
 void launch_bfrelax_first(const BJob *jobs, const long long *prefix, int njobs, long long total,
                           T omega, int jsel, cudaStream_t s);

@@ -1732,7 +1732,10 @@ struct BTable {
     int njobs = 0;
     long long total = 0;
     int R = 1;
-    int kind = 0;  // 0 chunk (warp-chunks of R rows), 1 elements, 2 reduction blocks
+    // 0 chunk (warp-chunks of R rows), 1 elements, 2 reduction blocks,
+    // 3 SELL slices (the same row products over the members' SELL copies)
+    int kind = 0;
+    bool sell_ok = false;  // every member's matrix has a SELL copy (kind 0 may become 3)
     std::vector<BJob> host;
 };
 
@@ -1825,7 +1828,18 @@ static mgr_status bfail(mgr_batch bh, mgr_status st, const std::string &msg) {
 static long long job_items(const BTable &t, const BJob &j, int R) {
     if (t.kind == 0) return (j.n + R - 1) / R;
     if (t.kind == 2) return j.nblk;
+    if (t.kind == 3) return j.n > 0 ? j.nsl : 0;
     return j.n;
+}
+
+// the SELL copy of M (values of precision T) into job J; false when M has none
+template <class T>
+static bool job_sell(BJob &J, const DCSR &M) {
+    const void *sv = sizeof(T) == 8 ? (const void *)M.sv : (const void *)M.sv32;
+    if (M.n > 0 && (!M.sptr || !sv)) return false;
+    J.sptr = M.sptr; J.slen = M.slen; J.perm = M.perm; J.sci = M.sci; J.sv = sv;
+    J.nsl = M.nsl; J.sg = M.sg;
+    return true;
 }
 
 static int upload_table(mgr_batch bh, BTable &t) {
@@ -1870,6 +1884,10 @@ static int build_tables(mgr_batch bh) {
     bh->mgr_interp.assign(L, BTable()); bh->mgr_scatter.assign(L, BTable());
     bh->amg_resid.assign(bh->kmax, BTable()); bh->amg_restrict.assign(bh->kmax, BTable());
     bh->amg_prolong.assign(bh->kmax, BTable()); bh->amg_post.assign(bh->kmax, BTable());
+    std::vector<char> sell_all[2] = {std::vector<char>(L, 1), std::vector<char>(L, 1)};
+    std::vector<char> sell_amg[4];
+    for (auto &v : sell_amg) v.assign(bh->kmax, 1);
+    bool sell_outer = bh->b == 1;
     for (int s = 0; s < bh->nsys; s++) {
         mgr_handle h = bh->hs[s];
         Krylov &K = h->kr;
@@ -1884,6 +1902,7 @@ static int build_tables(mgr_batch bh) {
             f.gz = M.gsize; f.idx = M.fidx; f.o1 = sel<T>(M.zF, M.zF32); f.active = act;
             bh->mgr_first[l].host.push_back(f);
             BJob r; r.n = M.nC; r.rp = M.ACF.rp; r.ci = M.ACF.ci; r.v = vals_of<T>(M.ACF);
+            sell_all[0][l] &= (char)job_sell<T>(r, M.ACF);
             r.x = sel<T>(M.zF, M.zF32); r.idx = M.cidx; r.r = vin; r.sr = st;
             r.o1 = sel<T>(M.vC, M.vC32); r.active = act;
             if (l + 1 == L && h->H.namg > 1) {
@@ -1892,6 +1911,7 @@ static int build_tables(mgr_batch bh) {
             }
             bh->mgr_restrict[l].host.push_back(r);
             BJob w; w.n = M.nF; w.rp = M.W.rp; w.ci = M.W.ci; w.v = vals_of<T>(M.W);
+            sell_all[1][l] &= (char)job_sell<T>(w, M.W);
             w.x = sel<T>(M.eC, M.eC32); w.idx = M.fidx; w.zF = sel<T>(M.zF, M.zF32);
             w.o1 = zout; w.so1 = st; w.active = act;
             bh->mgr_interp[l].host.push_back(w);
@@ -1908,16 +1928,20 @@ static int build_tables(mgr_batch bh) {
             void *rc, *xc;
             amg_io<T>(h, k + 1, &rc, &xc);
             BJob e; e.n = A.A.n; e.rp = A.A.rp; e.ci = A.A.ci; e.v = vals_of<T>(A.A);
+            sell_amg[0][k] &= (char)job_sell<T>(e, A.A);
             e.x = sel<T>(A.xw, A.xw32); e.r = rk; e.o1 = sel<T>(A.res, A.res32); e.active = act;
             bh->amg_resid[k].host.push_back(e);
             BJob q; q.n = A.R.n; q.rp = A.R.rp; q.ci = A.R.ci; q.v = vals_of<T>(A.R);
+            sell_amg[1][k] &= (char)job_sell<T>(q, A.R);
             q.x = sel<T>(A.res, A.res32); q.o1 = rc; q.active = act;
             if (k + 1 < cl) { q.d = sel<T>(C.dinv, C.dinv32); q.o2 = sel<T>(C.xw, C.xw32); }
             bh->amg_restrict[k].host.push_back(q);
             BJob pr; pr.n = A.P.n; pr.rp = A.P.rp; pr.ci = A.P.ci; pr.v = vals_of<T>(A.P);
+            sell_amg[2][k] &= (char)job_sell<T>(pr, A.P);
             pr.x = xc; pr.o1 = sel<T>(A.xw, A.xw32); pr.active = act;
             bh->amg_prolong[k].host.push_back(pr);
             BJob po; po.n = A.A.n; po.rp = A.A.rp; po.ci = A.A.ci; po.v = vals_of<T>(A.A);
+            sell_amg[3][k] &= (char)job_sell<T>(po, A.A);
             po.x = sel<T>(A.xw, A.xw32); po.r = rk; po.d = sel<T>(A.dinv, A.dinv32); po.o1 = xk;
             po.active = act;
             bh->amg_post[k].host.push_back(po);
@@ -1930,6 +1954,7 @@ static int build_tables(mgr_batch bh) {
         }
         // outer product w = A z_j -> V_{j+1}
         BJob o; o.n = bh->b == 1 ? n : n; o.rp = h->brp; o.ci = h->bci; o.v = h->bval;
+        if (bh->b == 1) sell_outer = job_sell<double>(o, h->Aout) && sell_outer;
         o.x = K.Z; o.sx = n; o.o1 = K.V + n; o.so1 = n; o.active = act;
         bh->outer.host.push_back(o);
         // Arnoldi: w = V_{j+1} = V + n + j n
@@ -1951,6 +1976,17 @@ static int build_tables(mgr_batch bh) {
         BJob v0; v0.n = n; v0.x = K.r; v0.o1 = K.V; v0.d = K.beta; v0.active = act;
         bh->v0scale.host.push_back(v0);
     }
+    for (int l = 0; l < L; l++) {
+        bh->mgr_restrict[l].sell_ok = sell_all[0][l];
+        bh->mgr_interp[l].sell_ok = sell_all[1][l];
+    }
+    for (int k = 0; k < bh->kmax; k++) {
+        bh->amg_resid[k].sell_ok = sell_amg[0][k];
+        bh->amg_restrict[k].sell_ok = sell_amg[1][k];
+        bh->amg_prolong[k].sell_ok = sell_amg[2][k];
+        bh->amg_post[k].sell_ok = sell_amg[3][k];
+    }
+    bh->outer.sell_ok = sell_outer;
     auto setR = [](std::vector<BTable> &v, int kind) { for (auto &t : v) t.kind = kind; };
     setR(bh->mgr_first, 1); setR(bh->mgr_scatter, 1);
     setR(bh->mgr_restrict, 0); setR(bh->mgr_interp, 0);
@@ -1995,26 +2031,36 @@ static int table_R0(mgr_batch bh, BTable &t) {
 template <class T>
 static void run_chunk(mgr_batch bh, BTable &t, int op, int js, bool top) {
     if (!t.total) return;
-    KScope ks(bh->hs[0], "batched_chunk", op, 0.0);
+    KScope ks(bh->hs[0], t.kind == 3 ? "batched_sell" : "batched_chunk", op, 0.0);
+    if (t.kind == 3) {
+        if (top) launch_bsell<T, double>(op, t.jobs, t.prefix, t.njobs, t.total, js, bh->s);
+        else launch_bsell<T, T>(op, t.jobs, t.prefix, t.njobs, t.total, js, bh->s);
+        return;
+    }
     if (top) launch_bchunk<T, double>(op, t.jobs, t.prefix, t.njobs, t.total, t.R, js, bh->s);
     else launch_bchunk<T, T>(op, t.jobs, t.prefix, t.njobs, t.total, t.R, js, bh->s);
 }
 
-// Autotuner: for every chunk table try R0/2, R0, 2 R0 (within 1..32), time
-// three launches of each (the first discarded) and keep the fastest; the
-// buffers hold no solve state yet, so the trial launches are harmless.
+// Autotuner: for every row-product table try the members' SELL copies (one
+// item per slice) and the chunk engine with R0/2, R0, 2 R0 rows per warp
+// (within 1..32); time three launches of each (the first discarded) and keep
+// the fastest.  The buffers hold no solve state yet, so the trial launches
+// are harmless.
 template <class T>
 static int autotune(mgr_batch bh, BTable &t, int op, bool top) {
     if (t.kind != 0 || t.host.empty()) return upload_table(bh, t);
     int R0 = table_R0(bh, t);
-    int cands[3] = {R0 / 2, R0, R0 * 2};
+    // candidates: (kind, R)
+    int cands[4][2] = {{3, 1}, {0, R0 / 2}, {0, R0}, {0, R0 * 2}};
     float best = 1e30f;
-    int bestR = R0;
+    int bestK = 0, bestR = R0;
     cudaEvent_t a, b;
     cudaEventCreate(&a); cudaEventCreate(&b);
-    for (int c = 0; c < 3; c++) {
-        int R = cands[c];
-        if (R < 1 || R > 32) continue;
+    for (int c = 0; c < 4; c++) {
+        const int kind = cands[c][0], R = cands[c][1];
+        if (kind == 3 && !t.sell_ok) continue;
+        if (kind == 0 && (R < 1 || R > 32)) continue;
+        t.kind = kind;
         t.R = R;
         if (upload_table(bh, t)) { cudaEventDestroy(a); cudaEventDestroy(b); return ST_NOMEM; }
         float ms = 0.f;
@@ -2027,9 +2073,10 @@ static int autotune(mgr_batch bh, BTable &t, int op, bool top) {
             cudaEventElapsedTime(&e, a, b);
             if (rep > 0) ms += e;
         }
-        if (ms < best) { best = ms; bestR = R; }
+        if (ms < best) { best = ms; bestK = kind; bestR = R; }
     }
     cudaEventDestroy(a); cudaEventDestroy(b);
+    t.kind = bestK;
     t.R = bestR;
     return upload_table(bh, t);
 }
@@ -2096,7 +2143,9 @@ static void bstep(mgr_batch bh, int j) {
     else bvcycle<double>(bh, j);
     {
         KScope ks(bh->hs[0], "batched_spmv_A", -1, 0.0);
-        if (bh->b == 1) launch_bchunk<double, double>(BOP_OUTER_CSR, bh->outer.jobs, bh->outer.prefix, bh->outer.njobs, bh->outer.total, bh->outer.R, j, s);
+        if (bh->b == 1 && bh->outer.kind == 3)
+            launch_bsell<double, double>(BOP_OUTER_CSR, bh->outer.jobs, bh->outer.prefix, bh->outer.njobs, bh->outer.total, j, s);
+        else if (bh->b == 1) launch_bchunk<double, double>(BOP_OUTER_CSR, bh->outer.jobs, bh->outer.prefix, bh->outer.njobs, bh->outer.total, bh->outer.R, j, s);
         else launch_bbsr(bh->b, bh->outer.jobs, bh->outer.prefix, bh->outer.njobs, bh->outer.total, j, s);
     }
     const int k = j + 1;
@@ -2249,7 +2298,9 @@ extern "C" mgr_status mgr_solve_batched(mgr_batch bh, const double *const *bvec,
         BJob u; u.n = h->n; u.v = h->kr.Z; u.r = h->kr.y; u.o1 = xvec[i]; u.gz = bh->kk + i;
         bh->xupd.host.push_back(u);
     }
-    bh->resid_user.R = bh->outer.R;
+    // b == 1: a CSR chunk table (rows per warp from its density when the
+    // outer product runs on SELL slices); b > 1: one item per scalar row
+    bh->resid_user.R = bh->b == 1 && bh->outer.kind == 3 ? table_R0(bh, bh->resid_user) : bh->outer.R;
     if (upload_table(bh, bh->resid_user) || upload_table(bh, bh->xupd)) return bfail(bh, MGR_ERR_NOMEM, "tables");
     std::vector<int> act(ns, 1), done(ns, 0), iters(ns, 0), kk(ns, 0);
     std::vector<double> bn(ns, 0.0), relres(ns, 0.0);

@@ -101,4 +101,4 @@ def test_batched_48_uneven_systems():
     assert all(inf["status"] == 0 and inf["rel_residual"] <= 1e-8 for inf in infos)
     for i in (0, 17, 47):
         ro = O.Oracle(systems[i]).solve(systems[i].rhs, rtol=1e-8)
-        assert abs(infos[i]["iterations"] - ro["iters"]) <= 2
+        assert abs(infos[i]["iterations"] - ro["iters"]) <= 1, (i, infos[i]["iterations"], ro["iters"])
