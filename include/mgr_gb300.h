@@ -82,14 +82,14 @@ enum { MGR_PREC_FP64 = 0, MGR_PREC_FP32 = 1 };
  * parameters below and relax_functions[l] functions of the unknown approach
  * (function of an F dof = its F index mod relax_functions[l]); the
  * interpolation uses D_FF = diag(A_FF).  A sweep computes
- * z_F += omega * B (v_F - A_FF z_F) with B the V-cycle.  Batched solves do
- * not take it (MGR_ERR_UNSUPPORTED).
+ * z_F += omega * B (v_F - A_FF z_F) with B the V-cycle.  Batched solves take
+ * it with one sweep.
  * restrict_type[l]: MGR_RESTRICT_INJECTION (R~ = [0, I], the default) or
  * MGR_RESTRICT_JACOBI (R~ = [-A_CF D^{-1}, I] of Eq. 5, the transpose of
  * P~ for symmetric A): the coarse operator becomes the triple product
  * R~ A P~ and the cycle restricts v_C - A_CF z_F + Z (v_F - A_FF z_F),
  * Z = -A_CF D^{-1}.  It needs a diagonal D (not block-Jacobi:
- * MGR_ERR_UNSUPPORTED); batched solves restrict by injection only.
+ * MGR_ERR_UNSUPPORTED); batched solves take it too.
  * spin_limit: polls before a grid-barrier wait of the fused AMG tail gives
  * up (0: the default, about half a second); a test knob that makes the wait
  * run out on purpose, so that the MGR_ERR_TIMEOUT path can be exercised
@@ -240,10 +240,14 @@ mgr_status mgr_residual_norm_noalloc(int32_t nb, int32_t b, const int32_t *row_p
  * together.  Each system keeps its own hierarchy, and every kernel class of
  * the V-cycle, the outer product and the Arnoldi reductions runs as one
  * launch over all systems (a job table of per-system operands; per-system
- * convergence flags drop finished systems).  Chunk shapes of the sparse
- * products are picked at setup by timing candidates (autotuner).  All
- * systems need the same block size, MGR level count and options, at least
- * one MGR level, and one F-relaxation sweep (MGR_ERR_UNSUPPORTED otherwise).
+ * convergence flags drop finished systems).  The sparse products run over
+ * the members' SELL-C-sigma copies or the chunk engine, whichever the
+ * autotuner timed faster at setup for that kernel class and level.  An AMG
+ * F-relaxation level (MGR_U) runs its members' F hierarchies as one
+ * level-synchronous V-cycle; the restriction of Eq. 5 adds its two products.
+ * All systems need the same block size, MGR level count and options, at
+ * least one MGR level, and one F-relaxation sweep (MGR_ERR_UNSUPPORTED
+ * otherwise).
  */
 typedef struct mgr_batch_ctx *mgr_batch;
 

@@ -83,6 +83,12 @@ template <class T, class TV> struct BOpT<T, TV, BOP_MGR_INTERP> {
         return {J.idx, (const T *)J.zF, (TV *)J.o1 + js * J.so1};
     }
 };
+template <class T, class TV> struct BOpT<T, TV, BOP_FRELAX_RESID> {  // r_F = v[fidx] - A_FF z_F
+    __device__ static XPlain<T, T> xf(const BJob &J, int) { return {(const T *)J.x}; }
+    __device__ static EGatherMinus<T, TV> epi(const BJob &J, int js) {
+        return {J.idx, (const TV *)J.r + js * J.sr, (T)-1, (T *)J.o1};
+    }
+};
 template <class T, class TV> struct BOpT<T, TV, BOP_OUTER_CSR> {
     __device__ static XPlain<double, double> xf(const BJob &J, int js) { return {(const double *)J.x + js * J.sx}; }
     __device__ static EOuter epi(const BJob &J, int js) { return {(const double *)J.r, (double *)J.o1 + js * J.so1}; }
@@ -152,6 +158,7 @@ void launch_bchunk(int op, const BJob *jobs, const long long *prefix, int njobs,
         case BOP_POST: bchunk_dispatch<T, TV, BOP_POST>(jobs, prefix, njobs, total, R, js, s); break;
         case BOP_MGR_RESTRICT: bchunk_dispatch<T, TV, BOP_MGR_RESTRICT>(jobs, prefix, njobs, total, R, js, s); break;
         case BOP_MGR_INTERP: bchunk_dispatch<T, TV, BOP_MGR_INTERP>(jobs, prefix, njobs, total, R, js, s); break;
+        case BOP_FRELAX_RESID: bchunk_dispatch<T, TV, BOP_FRELAX_RESID>(jobs, prefix, njobs, total, R, js, s); break;
         default: break;
     }
 }
@@ -166,6 +173,7 @@ void launch_bchunk<double, double>(int op, const BJob *jobs, const long long *pr
         case BOP_POST: bchunk_dispatch<double, double, BOP_POST>(jobs, prefix, njobs, total, R, js, s); break;
         case BOP_MGR_RESTRICT: bchunk_dispatch<double, double, BOP_MGR_RESTRICT>(jobs, prefix, njobs, total, R, js, s); break;
         case BOP_MGR_INTERP: bchunk_dispatch<double, double, BOP_MGR_INTERP>(jobs, prefix, njobs, total, R, js, s); break;
+        case BOP_FRELAX_RESID: bchunk_dispatch<double, double, BOP_FRELAX_RESID>(jobs, prefix, njobs, total, R, js, s); break;
         case BOP_OUTER_CSR: bchunk_dispatch<double, double, BOP_OUTER_CSR>(jobs, prefix, njobs, total, R, js, s); break;
         default: break;
     }
@@ -221,6 +229,7 @@ void launch_bsell(int op, const BJob *jobs, const long long *prefix, int njobs, 
         case BOP_POST: bsell_dispatch<T, TV, BOP_POST>(jobs, prefix, njobs, total, js, s); break;
         case BOP_MGR_RESTRICT: bsell_dispatch<T, TV, BOP_MGR_RESTRICT>(jobs, prefix, njobs, total, js, s); break;
         case BOP_MGR_INTERP: bsell_dispatch<T, TV, BOP_MGR_INTERP>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_FRELAX_RESID: bsell_dispatch<T, TV, BOP_FRELAX_RESID>(jobs, prefix, njobs, total, js, s); break;
         default: break;
     }
 }
@@ -235,6 +244,7 @@ void launch_bsell<double, double>(int op, const BJob *jobs, const long long *pre
         case BOP_POST: bsell_dispatch<double, double, BOP_POST>(jobs, prefix, njobs, total, js, s); break;
         case BOP_MGR_RESTRICT: bsell_dispatch<double, double, BOP_MGR_RESTRICT>(jobs, prefix, njobs, total, js, s); break;
         case BOP_MGR_INTERP: bsell_dispatch<double, double, BOP_MGR_INTERP>(jobs, prefix, njobs, total, js, s); break;
+        case BOP_FRELAX_RESID: bsell_dispatch<double, double, BOP_FRELAX_RESID>(jobs, prefix, njobs, total, js, s); break;
         case BOP_OUTER_CSR: bsell_dispatch<double, double, BOP_OUTER_CSR>(jobs, prefix, njobs, total, js, s); break;
         default: break;
     }
@@ -293,6 +303,57 @@ template <class T, class TV>
 void launch_bscatter(const BJob *jobs, const long long *prefix, int njobs, long long total, int js,
                      cudaStream_t s) {
     if (total > 0) launch_plain(k_bscatter<T, TV>, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs, js);
+}
+
+// gather of the F-relaxation input v_F (o1 = r[idx]) with the seed of the
+// F hierarchy's pre-smoothing (o2 = d .* v_F); idx null reads r itself, o1
+// null skips the store (the seed of the final AMG after the Z product)
+template <class T, class TV>
+__global__ void k_bgather(const BJob *jobs, const long long *prefix, int njobs, int js) {
+    pdl_wait();
+    pdl_launch_dependents();
+    const long long total = prefix[njobs];
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int j = find_job(prefix, njobs, g);
+        const BJob &J = jobs[j];
+        if (job_off(J)) continue;
+        const int i = (int)(g - prefix[j]);
+        const TV *r = (const TV *)J.r + js * J.sr;
+        const T v = (T)r[J.idx ? J.idx[i] : i];
+        if (J.o1) ((T *)J.o1)[i] = v;
+        if (J.d) ((T *)J.o2)[i] = ((const T *)J.d)[i] * v;
+    }
+}
+
+template <class T, class TV>
+void launch_bgather(const BJob *jobs, const long long *prefix, int njobs, long long total, int js,
+                    cudaStream_t s) {
+    if (total > 0) launch_plain(k_bgather<T, TV>, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs, js);
+}
+
+__device__ __forceinline__ double bmul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float bmul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+template <class T>
+__global__ void k_bomega(const BJob *jobs, const long long *prefix, int njobs, T omega) {
+    pdl_wait();
+    pdl_launch_dependents();
+    const long long total = prefix[njobs];
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int j = find_job(prefix, njobs, g);
+        const BJob &J = jobs[j];
+        if (job_off(J)) continue;
+        const int i = (int)(g - prefix[j]);
+        ((T *)J.o1)[i] = bmul_rn(omega, ((const T *)J.x)[i]);
+    }
+}
+
+template <class T>
+void launch_bomega(const BJob *jobs, const long long *prefix, int njobs, long long total, T omega,
+                   cudaStream_t s) {
+    if (total > 0) launch_plain(k_bomega<T>, dim3(elem_grid(total)), dim3(256), s, jobs, prefix, njobs, omega);
 }
 
 // coarsest dense solves: one warp per row over every system's coarsest grid
@@ -578,6 +639,11 @@ template void launch_bfrelax_first<float, float>(const BJob *, const long long *
 template void launch_bscatter<double, double>(const BJob *, const long long *, int, long long, int, cudaStream_t);
 template void launch_bscatter<float, double>(const BJob *, const long long *, int, long long, int, cudaStream_t);
 template void launch_bscatter<float, float>(const BJob *, const long long *, int, long long, int, cudaStream_t);
+template void launch_bgather<double, double>(const BJob *, const long long *, int, long long, int, cudaStream_t);
+template void launch_bgather<float, double>(const BJob *, const long long *, int, long long, int, cudaStream_t);
+template void launch_bgather<float, float>(const BJob *, const long long *, int, long long, int, cudaStream_t);
+template void launch_bomega<double>(const BJob *, const long long *, int, long long, double, cudaStream_t);
+template void launch_bomega<float>(const BJob *, const long long *, int, long long, float, cudaStream_t);
 template void launch_bdense<double>(const BJob *, const long long *, int, long long, int, cudaStream_t);
 template void launch_bdense<float>(const BJob *, const long long *, int, long long, int, cudaStream_t);
 

@@ -310,7 +310,7 @@ struct BJob {
 
 // batched table launches (T = value type, TV = top-level vector type)
 enum BOp { BOP_RESID, BOP_RESTRICT, BOP_PROLONG, BOP_POST, BOP_MGR_RESTRICT, BOP_MGR_INTERP,
-           BOP_OUTER_CSR };
+           BOP_OUTER_CSR, BOP_FRELAX_RESID };
 template <class T, class TV>
 void launch_bchunk(int op, const BJob *jobs, const long long *prefix, int njobs, long long total,
                    int R, int jsel, cudaStream_t s);
@@ -324,6 +324,15 @@ void launch_bfrelax_first(const BJob *jobs, const long long *prefix, int njobs, 
 template <class T, class TV>
 void launch_bscatter(const BJob *jobs, const long long *prefix, int njobs, long long total,
                      int jsel, cudaStream_t s);
+// element jobs of the AMG F-relaxation and the restriction of Eq. 5:
+// o1 = r[idx] (idx null: r) when o1 is set, o2 = d .* that value when d is set
+template <class T, class TV>
+void launch_bgather(const BJob *jobs, const long long *prefix, int njobs, long long total, int jsel,
+                    cudaStream_t s);
+// o1 = omega * x, rounded as one multiplication (a weighted first F sweep)
+template <class T>
+void launch_bomega(const BJob *jobs, const long long *prefix, int njobs, long long total, T omega,
+                   cudaStream_t s);
 template <class TV>
 void launch_bdense(const BJob *jobs, const long long *prefix, int njobs, long long total, int jsel,
                    cudaStream_t s);

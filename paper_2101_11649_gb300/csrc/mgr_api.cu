@@ -1811,6 +1811,18 @@ struct mgr_batch_ctx {
     // tables
     std::vector<BTable> mgr_first, mgr_restrict, mgr_interp, mgr_scatter;
     std::vector<BTable> amg_resid, amg_restrict, amg_prolong, amg_post;
+    // per MGR level: the AMG F-relaxation (gather of v_F with the seed of the
+    // F hierarchy's pre-smoothing, that hierarchy's cycle, the weight) and the
+    // restriction of Eq. 5 (r_F = v_F - A_FF z_F, v_C += Z r_F, the seed of the
+    // final AMG's pre-smoothing)
+    struct BAmg {
+        std::vector<BTable> resid, restr, prolong, post;
+        BTable coarse;
+        int kmax = 0;
+    };
+    std::vector<BAmg> famg;
+    std::vector<BTable> fgather, fomega, frres, zres;
+    BTable cprep;
     BTable coarse, outer, dots1, dots2, upd1, upd2, vnorm, rnorm, v0scale;
     BTable resid_user, xupd;
     std::vector<cudaGraphExec_t> graphs;
@@ -1877,6 +1889,65 @@ static void amg_io(mgr_handle h, int k, void **r, void **x) {
     }
 }
 
+// AMG tables of one hierarchy per member (hier(s)), level 0's input and
+// output given by io0(s) and the coarser levels' by the hierarchy's own
+// buffers: residual, restriction (with the next level's pre-smoothing seed),
+// prolongation, post-smoothing per level, and each member's coarsest solve.
+template <class T, class H, class IO>
+static void build_amg_tables(mgr_batch bh, mgr_batch_ctx::BAmg &B, H hier, IO io0) {
+    B.kmax = 0;
+    for (int s = 0; s < bh->nsys; s++) B.kmax = std::max(B.kmax, hier(s).namg - 1);
+    B.resid.assign(B.kmax, BTable()); B.restr.assign(B.kmax, BTable());
+    B.prolong.assign(B.kmax, BTable()); B.post.assign(B.kmax, BTable());
+    B.coarse = BTable();
+    std::vector<char> ok[4];
+    for (auto &v : ok) v.assign(B.kmax, 1);
+    for (int s = 0; s < bh->nsys; s++) {
+        AmgH &G = hier(s);
+        int *act = bh->active + s;
+        auto io = [&](int k, void **r, void **x) {
+            if (k == 0) { io0(s, r, x); return; }
+            *r = sel<T>(G.amg[k].r, G.amg[k].r32);
+            *x = sel<T>(G.amg[k].x, G.amg[k].x32);
+        };
+        const int cl = G.namg - 1;
+        for (int k = 0; k < cl; k++) {
+            AmgLevel &A = G.amg[k];
+            AmgLevel &C = G.amg[k + 1];
+            void *rk, *xk, *rc, *xc;
+            io(k, &rk, &xk);
+            io(k + 1, &rc, &xc);
+            BJob e; e.n = A.A.n; e.rp = A.A.rp; e.ci = A.A.ci; e.v = vals_of<T>(A.A);
+            ok[0][k] &= (char)job_sell<T>(e, A.A);
+            e.x = sel<T>(A.xw, A.xw32); e.r = rk; e.o1 = sel<T>(A.res, A.res32); e.active = act;
+            B.resid[k].host.push_back(e);
+            BJob q; q.n = A.R.n; q.rp = A.R.rp; q.ci = A.R.ci; q.v = vals_of<T>(A.R);
+            ok[1][k] &= (char)job_sell<T>(q, A.R);
+            q.x = sel<T>(A.res, A.res32); q.o1 = rc; q.active = act;
+            if (k + 1 < cl) { q.d = sel<T>(C.dinv, C.dinv32); q.o2 = sel<T>(C.xw, C.xw32); }
+            B.restr[k].host.push_back(q);
+            BJob pr; pr.n = A.P.n; pr.rp = A.P.rp; pr.ci = A.P.ci; pr.v = vals_of<T>(A.P);
+            ok[2][k] &= (char)job_sell<T>(pr, A.P);
+            pr.x = xc; pr.o1 = sel<T>(A.xw, A.xw32); pr.active = act;
+            B.prolong[k].host.push_back(pr);
+            BJob po; po.n = A.A.n; po.rp = A.A.rp; po.ci = A.A.ci; po.v = vals_of<T>(A.A);
+            ok[3][k] &= (char)job_sell<T>(po, A.A);
+            po.x = sel<T>(A.xw, A.xw32); po.r = rk; po.d = sel<T>(A.dinv, A.dinv32); po.o1 = xk;
+            po.active = act;
+            B.post[k].host.push_back(po);
+        }
+        void *rc, *xc;
+        io(cl, &rc, &xc);
+        BJob c; c.n = G.nco; c.v = G.coinv; c.r = rc; c.o1 = xc; c.active = act;
+        B.coarse.host.push_back(c);
+    }
+    for (int k = 0; k < B.kmax; k++) {
+        B.resid[k].sell_ok = ok[0][k]; B.restr[k].sell_ok = ok[1][k];
+        B.prolong[k].sell_ok = ok[2][k]; B.post[k].sell_ok = ok[3][k];
+    }
+    B.coarse.kind = 1;
+}
+
 template <class T>
 static int build_tables(mgr_batch bh) {
     const int L = bh->nlev;
@@ -1884,6 +1955,11 @@ static int build_tables(mgr_batch bh) {
     bh->mgr_interp.assign(L, BTable()); bh->mgr_scatter.assign(L, BTable());
     bh->amg_resid.assign(bh->kmax, BTable()); bh->amg_restrict.assign(bh->kmax, BTable());
     bh->amg_prolong.assign(bh->kmax, BTable()); bh->amg_post.assign(bh->kmax, BTable());
+    bh->famg.assign(L, mgr_batch_ctx::BAmg());
+    bh->fgather.assign(L, BTable()); bh->fomega.assign(L, BTable());
+    bh->frres.assign(L, BTable()); bh->zres.assign(L, BTable());
+    bh->cprep = BTable();
+    std::vector<char> sell_fr(L, 1), sell_z(L, 1);
     std::vector<char> sell_all[2] = {std::vector<char>(L, 1), std::vector<char>(L, 1)};
     std::vector<char> sell_amg[4];
     for (auto &v : sell_amg) v.assign(bh->kmax, 1);
@@ -1898,14 +1974,42 @@ static int build_tables(mgr_batch bh) {
             const void *vin = l == 0 ? (const void *)K.V : sel<T>(h->lev[l - 1].vC, h->lev[l - 1].vC32);
             void *zout = l == 0 ? (void *)K.Z : sel<T>(h->lev[l - 1].eC, h->lev[l - 1].eC32);
             long long st = l == 0 ? n : 0;
-            BJob f; f.n = M.nF; f.r = vin; f.sr = st; f.d = sel<T>(M.dinv, M.dinv32); f.gs = M.gstart;
-            f.gz = M.gsize; f.idx = M.fidx; f.o1 = sel<T>(M.zF, M.zF32); f.active = act;
-            bh->mgr_first[l].host.push_back(f);
+            if (M.famg) {
+                // v_F, and the seed D_0 v_F of the F hierarchy's pre-smoothing
+                AmgH &G = *M.famg;
+                BJob g; g.n = M.nF; g.r = vin; g.sr = st; g.idx = M.fidx; g.o1 = sel<T>(M.rF, M.rF32);
+                if (G.namg > 1) { g.d = sel<T>(G.amg[0].dinv, G.amg[0].dinv32); g.o2 = sel<T>(G.amg[0].xw, G.amg[0].xw32); }
+                g.active = act;
+                bh->fgather[l].host.push_back(g);
+                BJob w0; w0.n = M.nF; w0.x = sel<T>(M.tF, M.tF32); w0.o1 = sel<T>(M.zF, M.zF32); w0.active = act;
+                bh->fomega[l].host.push_back(w0);
+            } else {
+                BJob f; f.n = M.nF; f.r = vin; f.sr = st; f.d = sel<T>(M.dinv, M.dinv32); f.gs = M.gstart;
+                f.gz = M.gsize; f.idx = M.fidx; f.o1 = sel<T>(M.zF, M.zF32); f.active = act;
+                bh->mgr_first[l].host.push_back(f);
+            }
+            if (M.rtype == MGR_RESTRICT_JACOBI) {
+                // r_F = v_F - A_FF z_F, then v_C += Z r_F (Eq. 5)
+                BJob fr; fr.n = M.nF; fr.rp = M.AFF.rp; fr.ci = M.AFF.ci; fr.v = vals_of<T>(M.AFF);
+                sell_fr[l] &= (char)job_sell<T>(fr, M.AFF);
+                fr.x = sel<T>(M.zF, M.zF32); fr.idx = M.fidx; fr.r = vin; fr.sr = st;
+                fr.o1 = sel<T>(M.rF, M.rF32); fr.active = act;
+                bh->frres[l].host.push_back(fr);
+                BJob z; z.n = M.nC; z.rp = M.Z.rp; z.ci = M.Z.ci; z.v = vals_of<T>(M.Z);
+                sell_z[l] &= (char)job_sell<T>(z, M.Z);
+                z.x = sel<T>(M.rF, M.rF32); z.o1 = sel<T>(M.vC, M.vC32); z.active = act;
+                bh->zres[l].host.push_back(z);
+                if (l + 1 == L && h->H.namg > 1) {
+                    BJob c; c.n = M.nC; c.r = sel<T>(M.vC, M.vC32); c.d = sel<T>(h->H.amg[0].dinv, h->H.amg[0].dinv32);
+                    c.o2 = sel<T>(h->H.amg[0].xw, h->H.amg[0].xw32); c.active = act;
+                    bh->cprep.host.push_back(c);
+                }
+            }
             BJob r; r.n = M.nC; r.rp = M.ACF.rp; r.ci = M.ACF.ci; r.v = vals_of<T>(M.ACF);
             sell_all[0][l] &= (char)job_sell<T>(r, M.ACF);
             r.x = sel<T>(M.zF, M.zF32); r.idx = M.cidx; r.r = vin; r.sr = st;
             r.o1 = sel<T>(M.vC, M.vC32); r.active = act;
-            if (l + 1 == L && h->H.namg > 1) {
+            if (l + 1 == L && h->H.namg > 1 && M.rtype == MGR_RESTRICT_INJECTION) {
                 r.d = sel<T>(h->H.amg[0].dinv, h->H.amg[0].dinv32);
                 r.o2 = sel<T>(h->H.amg[0].xw, h->H.amg[0].xw32);
             }
@@ -1979,7 +2083,21 @@ static int build_tables(mgr_batch bh) {
     for (int l = 0; l < L; l++) {
         bh->mgr_restrict[l].sell_ok = sell_all[0][l];
         bh->mgr_interp[l].sell_ok = sell_all[1][l];
+        bh->frres[l].sell_ok = sell_fr[l];
+        bh->zres[l].sell_ok = sell_z[l];
+        bh->fgather[l].kind = bh->fomega[l].kind = 1;
+        bh->frres[l].kind = bh->zres[l].kind = 0;
+        if (bh->hs[0]->lev[l].famg) {
+            const bool w1 = bh->hs[0]->lev[l].omega == 1.0;
+            build_amg_tables<T>(bh, bh->famg[l], [&](int s) -> AmgH & { return *bh->hs[s]->lev[l].famg; },
+                                [&](int s, void **r, void **x) {
+                                    MgrLevel &M = bh->hs[s]->lev[l];
+                                    *r = sel<T>(M.rF, M.rF32);
+                                    *x = w1 ? sel<T>(M.zF, M.zF32) : sel<T>(M.tF, M.tF32);
+                                });
+        }
     }
+    bh->cprep.kind = 1;
     for (int k = 0; k < bh->kmax; k++) {
         bh->amg_resid[k].sell_ok = sell_amg[0][k];
         bh->amg_restrict[k].sell_ok = sell_amg[1][k];
@@ -2087,6 +2205,18 @@ static int finish_tables(mgr_batch bh) {
     for (int l = 0; l < bh->nlev && !rc; l++) {
         rc |= upload_table(bh, bh->mgr_first[l]);
         rc |= upload_table(bh, bh->mgr_scatter[l]);
+        rc |= upload_table(bh, bh->fgather[l]);
+        rc |= upload_table(bh, bh->fomega[l]);
+        if (!bh->frres[l].host.empty()) rc |= autotune<T>(bh, bh->frres[l], BOP_FRELAX_RESID, l == 0);
+        if (!bh->zres[l].host.empty()) rc |= autotune<T>(bh, bh->zres[l], BOP_PROLONG, false);
+        mgr_batch_ctx::BAmg &F = bh->famg[l];
+        for (int k = 0; k < F.kmax && !rc; k++) {
+            rc |= autotune<T>(bh, F.resid[k], BOP_RESID, false);
+            rc |= autotune<T>(bh, F.restr[k], BOP_RESTRICT, false);
+            rc |= autotune<T>(bh, F.prolong[k], BOP_PROLONG, false);
+            rc |= autotune<T>(bh, F.post[k], BOP_POST, false);
+        }
+        if (!F.coarse.host.empty()) rc |= upload_table(bh, F.coarse);
         rc |= autotune<T>(bh, bh->mgr_restrict[l], BOP_MGR_RESTRICT, l == 0);
         rc |= autotune<T>(bh, bh->mgr_interp[l], BOP_MGR_INTERP, l == 0);
     }
@@ -2097,6 +2227,7 @@ static int finish_tables(mgr_batch bh) {
         rc |= autotune<T>(bh, bh->amg_post[k], BOP_POST, false);
     }
     rc |= upload_table(bh, bh->coarse);
+    rc |= upload_table(bh, bh->cprep);
     if (bh->b == 1) rc |= autotune<double>(bh, bh->outer, BOP_OUTER_CSR, true);
     else rc |= upload_table(bh, bh->outer);
     rc |= upload_table(bh, bh->dots1); rc |= upload_table(bh, bh->dots2);
@@ -2107,16 +2238,55 @@ static int finish_tables(mgr_batch bh) {
 }
 
 // One batched MGR V-cycle on V_j -> Z_j of every active system.
+// One level-synchronous AMG V(1,1) over every member's hierarchy of a table set.
+template <class T>
+static void bamg_cycle(mgr_batch bh, mgr_batch_ctx::BAmg &B, int j) {
+    for (int k = 0; k < B.kmax; k++) {
+        run_chunk<T>(bh, B.resid[k], BOP_RESID, j, false);
+        run_chunk<T>(bh, B.restr[k], BOP_RESTRICT, j, false);
+    }
+    { KScope ks(bh->hs[0], "batched_coarsest", -1, 0.0);
+      launch_bdense<T>(B.coarse.jobs, B.coarse.prefix, B.coarse.njobs, B.coarse.total, j, bh->s); }
+    for (int k = B.kmax - 1; k >= 0; k--) {
+        run_chunk<T>(bh, B.prolong[k], BOP_PROLONG, j, false);
+        run_chunk<T>(bh, B.post[k], BOP_POST, j, false);
+    }
+}
+
 template <class T>
 static void bvcycle(mgr_batch bh, int j) {
     cudaStream_t s = bh->s;
     const int L = bh->nlev;
     for (int l = 0; l < L; l++) {
-        BTable &f = bh->mgr_first[l];
-        { KScope ks(bh->hs[0], "batched_frelax_first", l, 0.0);
-          if (l == 0) launch_bfrelax_first<T, double>(f.jobs, f.prefix, f.njobs, f.total, (T)bh->hs[0]->lev[l].omega, j, s);
-          else launch_bfrelax_first<T, T>(f.jobs, f.prefix, f.njobs, f.total, (T)bh->hs[0]->lev[l].omega, j, s); }
+        const MgrLevel &M0 = bh->hs[0]->lev[l];  // options are the same for every member
+        if (M0.famg) {
+            // AMG F-relaxation (MGR_U, Sec. 4.3): z_F = omega * B v_F
+            BTable &g = bh->fgather[l];
+            { KScope ks(bh->hs[0], "batched_frelax_gather", l, 0.0);
+              if (l == 0) launch_bgather<T, double>(g.jobs, g.prefix, g.njobs, g.total, j, s);
+              else launch_bgather<T, T>(g.jobs, g.prefix, g.njobs, g.total, j, s); }
+            bamg_cycle<T>(bh, bh->famg[l], j);
+            if (M0.omega != 1.0) {
+                BTable &w = bh->fomega[l];
+                KScope ks(bh->hs[0], "batched_frelax_scale", l, 0.0);
+                launch_bomega<T>(w.jobs, w.prefix, w.njobs, w.total, (T)M0.omega, s);
+            }
+        } else {
+            BTable &f = bh->mgr_first[l];
+            KScope ks(bh->hs[0], "batched_frelax_first", l, 0.0);
+            if (l == 0) launch_bfrelax_first<T, double>(f.jobs, f.prefix, f.njobs, f.total, (T)M0.omega, j, s);
+            else launch_bfrelax_first<T, T>(f.jobs, f.prefix, f.njobs, f.total, (T)M0.omega, j, s);
+        }
+        if (M0.rtype == MGR_RESTRICT_JACOBI) run_chunk<T>(bh, bh->frres[l], BOP_FRELAX_RESID, j, l == 0);
         run_chunk<T>(bh, bh->mgr_restrict[l], BOP_MGR_RESTRICT, j, l == 0);
+        if (M0.rtype == MGR_RESTRICT_JACOBI) {
+            run_chunk<T>(bh, bh->zres[l], BOP_PROLONG, j, false);  // v_C += Z r_F
+            if (l + 1 == L) {
+                BTable &c = bh->cprep;
+                KScope ks(bh->hs[0], "batched_amg_scale", -1, 0.0);
+                launch_bgather<T, T>(c.jobs, c.prefix, c.njobs, c.total, j, s);
+            }
+        }
     }
     for (int k = 0; k < bh->kmax; k++) {
         run_chunk<T>(bh, bh->amg_resid[k], BOP_RESID, j, false);
@@ -2217,8 +2387,7 @@ extern "C" mgr_status mgr_setup_batched(int32_t nsys, const mgr_bsr *A, const mg
     if (bh->nlev < 1) { mgr_free_batched(bh); return bfail(nullptr, MGR_ERR_UNSUPPORTED, "batched solves need at least one MGR level"); }
     for (int l = 0; l < bh->nlev; l++) {
         if (o.relax_sweeps[l] > 1) { mgr_free_batched(bh); return bfail(nullptr, MGR_ERR_UNSUPPORTED, "batched solves use one F-relaxation sweep"); }
-        if (o.relax_type[l] == MGR_RELAX_AMG) { mgr_free_batched(bh); return bfail(nullptr, MGR_ERR_UNSUPPORTED, "batched solves take diagonal or block F-relaxations"); }
-        if (o.restrict_type[l] != MGR_RESTRICT_INJECTION) { mgr_free_batched(bh); return bfail(nullptr, MGR_ERR_UNSUPPORTED, "batched solves restrict by injection"); }
+
     }
     for (int s = 0; s < nsys; s++) {
         if (A[s].b != bh->b || cf[s].num_levels != bh->nlev) {

@@ -450,6 +450,7 @@ class MGRBatch:
         self.device = torch.device(device or "cuda")
         ns = len(systems)
         s0 = systems[0]
+        kw.setdefault("relax_functions", tuple(getattr(s0, "relax_functions", ())))
         self.opts = options(relax=tuple(s0.relax), num_functions=s0.num_functions,
                             precision=precision, **kw)
         keep = []

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from paper_2101_11649_gb300.synth import make_batch
+from paper_2101_11649_gb300.synth import make_batch, make_poromech, make_two_phase
 
 pytestmark = pytest.mark.gpu
 
@@ -102,3 +102,48 @@ def test_batched_48_uneven_systems():
     for i in (0, 17, 47):
         ro = O.Oracle(systems[i]).solve(systems[i].rhs, rtol=1e-8)
         assert abs(infos[i]["iterations"] - ro["iters"]) <= 1, (i, infos[i]["iterations"], ro["iters"])
+
+
+# the paper's strategies in a batch: MGR_U (one AMG V-cycle as F-relaxation,
+# Sec. 4.3), with and without a weight, and the restriction of Eq. 5
+STRATEGIES = {
+    "mgr_u": (lambda: [make_poromech(n, f, seed=k, strategy="mgr_u")
+                       for k, (n, f) in enumerate(((6, 4), (8, 4), (10, 6)))],
+              dict(max_coarse=32)),
+    "mgr_u_weighted_eq5": (lambda: [make_poromech(n, f, seed=k, strategy="mgr_u")
+                                    for k, (n, f) in enumerate(((6, 4), (8, 6)))],
+                           dict(max_coarse=32, weights=[0.9], restrict=["jacobi"])),
+    "eq5": (lambda: [make_two_phase(*g) for g in GRIDS[:4]],
+            dict(max_coarse=32, restrict=["jacobi"])),
+}
+
+
+@pytest.mark.parametrize("name", list(STRATEGIES))
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_paper_strategies_match_single_system_path(name, precision):
+    """Each member of a batch with an AMG F-relaxation or the restriction of
+    Eq. 5 converges like its own single-system handle (iterations +-1, the
+    same true residual bound) and, in FP64, like the oracle (+-1)."""
+    make, kw = STRATEGIES[name]
+    systems = make()
+    batch = M.MGRBatch(systems, precision=precision, **kw)
+    xs, infos = batch.solve([t(s.rhs) for s in systems], rtol=1e-8, maxit=500)
+    for s, x, inf in zip(systems, xs, infos):
+        single = M.MGRSolver.from_system(s, precision=precision, **kw)
+        _, i1 = single.solve(t(s.rhs), rtol=1e-8, maxit=500)
+        assert inf["status"] == 0 and inf["rel_residual"] <= 1e-8, inf
+        assert abs(inf["iterations"] - i1["iterations"]) <= 1, (inf["iterations"], i1["iterations"])
+        if precision == "fp64":
+            okw = dict(kw)
+            ro = O.Oracle(s, O.Options(relax=list(s.relax), num_functions=s.num_functions,
+                                       relax_functions=list(s.relax_functions),
+                                       max_coarse=okw.get("max_coarse", 1024),
+                                       weights=okw.get("weights", []),
+                                       restrict=okw.get("restrict", []))).solve(s.rhs, rtol=1e-8)
+            assert abs(inf["iterations"] - ro["iters"]) <= 1, (inf["iterations"], ro["iters"])
+    # converged tightly, the batched solution is the single-system one
+    xs, _ = batch.solve([t(s.rhs) for s in systems], rtol=1e-12, maxit=1000)
+    for s, x in zip(systems, xs):
+        single = M.MGRSolver.from_system(s, precision=precision, **kw)
+        x1, _ = single.solve(t(s.rhs), rtol=1e-12, maxit=1000)
+        assert float(torch.linalg.norm(x - x1) / torch.linalg.norm(x1)) <= 1e-8

@@ -329,13 +329,6 @@ def test_mgr_u_fewer_iterations_than_mgr_p_on_gpu():
     assert its["mgr_u"] < its["mgr_p"], its
 
 
-def test_batched_rejects_amg_frelax():
-    s = SMALL["poromech_mgr_u"]()
-    with pytest.raises(M.MGRError) as e:
-        M.MGRBatch([s, s])
-    assert e.value.status == M.MGR_ERR_UNSUPPORTED
-
-
 # the restriction of Eq. 5 (R = [-A_CF D^-1, I]) on every level
 RESTRICT_CASES = ["two_phase", "mimetic", "poromech", "poromech_mgr_u", "compositional_4level"]
 
@@ -390,14 +383,13 @@ def test_jacobi_restriction_solve_parity(name):
     assert il["status"] == 0 and abs(il["iterations"] - rl["iters"]) <= 1
 
 
-def test_jacobi_restriction_rejected_with_block_jacobi_and_in_batches():
+def test_jacobi_restriction_rejected_with_block_jacobi():
     s = SMALL["compositional"]()
     with pytest.raises(M.MGRError) as e:
         solver(s, restrict=["jacobi", "injection"])
     assert e.value.status == M.MGR_ERR_UNSUPPORTED
-    s2 = SMALL["two_phase"]()
     with pytest.raises(M.MGRError) as e:
-        M.MGRBatch([s2, s2], restrict=["jacobi"])
+        M.MGRBatch([s, s], restrict=["jacobi", "injection"])
     assert e.value.status == M.MGR_ERR_UNSUPPORTED
 
 
