@@ -524,6 +524,31 @@ def run_gb300(args, world, rank, local):
                              "iterations_max": max(its), "iterations_mean": round(sum(its) / len(its), 2),
                              "all_converged": all(i["status"] == 0 for i in infos),
                              "unknowns_per_s": round(nunk / (ms / 1e3), 1)}
+            # the batched V-cycle against HBM: each member's cycle bytes (a
+            # profiled apply through its own handle) times its iterations,
+            # over the summed event time of the batched V-cycle launches of
+            # one profiled batched solve (graphs off while profiling)
+            vbytes = 0.0
+            for i, q in enumerate(systems):
+                sv = bt.system(i)
+                v = torch.randn(q.n, dtype=torch.float64, device=dev)
+                sv.profile(True)
+                sv.apply(v, torch.empty_like(v))
+                vb = sum(r["bytes_per_launch"] * r["launches"] for r in sv.profile_table())
+                sv.profile(False)
+                vbytes += vb * its[i]
+            sv0 = bt.system(0)
+            sv0.profile(True)
+            bt.solve(rhs, rtol=args.rtol)
+            tab = sv0.profile_table()
+            sv0.profile(False)
+            outside = ("batched_spmv_A", "batched_arnoldi", "batched_givens", "batched_vec_scale",
+                       "batched_residual")
+            vms = sum(r["ms"] for r in tab if not r["name"].startswith(outside))
+            if vms > 0:
+                batched[prec]["vcycle"] = {"bytes": vbytes, "ms": round(vms, 3),
+                                           "gbs": round(vbytes / (vms / 1e3) / 1e9, 1),
+                                           "frac": round(vbytes / (vms / 1e3) / 1e9 / peak_gbs, 4)}
             if prec == "fp64":
                 # the same systems one after another through their single-system handles
                 seq = 0.0

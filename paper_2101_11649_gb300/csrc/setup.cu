@@ -1473,9 +1473,213 @@ __global__ void k_gj_extract(int n, const double *M, double *inv) {
     }
 }
 
+// Blocked Gauss-Jordan (the same partial pivoting: the largest |entry| of
+// the column among the rows not yet pivots, ties to the lower row).  Panel
+// k0..k0+NB-1: one CTA, one thread per row, runs the panel's NB pivot steps
+// on the panel columns in shared memory.  Each row also carries, in
+// registers, its coefficients on the panel's pivot rows (X: a row's final
+// value is its own old row, for rows that are not pivots, plus
+// sum_i X[r][i] * old pivot row i), and the row permutation of the panel's
+// swaps is kept in shared memory.  A grid-wide launch then applies the
+// panel to the trailing columns: Q_new[r] = (r not a pivot ? Q[perm[r]] : 0)
+// + sum_i X[r][i] Q[perm[k0+i]], and writes the panel's columns as unit
+// columns.  n/NB panel launches replace n one-column launches.
+static constexpr int GJB_NB = 16;
+static constexpr int GJB_MAXN = 1024;
+
+__global__ void __launch_bounds__(GJB_MAXN) k_gjb_panel(int n, int k0, int nb, const double *__restrict__ Q,
+                                                       long long ld, double *__restrict__ X,
+                                                       int *__restrict__ perm, int *errw) {
+    extern __shared__ double gjb_sm[];
+    double *P = gjb_sm;                          // [GJB_NB][n] panel columns, column-major
+    double *xrow = P + (size_t)n * GJB_NB;       // [GJB_NB] pivot row's coefficients
+    double *xswap = xrow + GJB_NB;               // [2][GJB_NB] coefficient exchange of a swap
+    double *rv = xswap + 2 * GJB_NB;             // [32] reduction values
+    int *ri = (int *)(rv + 32);                  // [32] reduction rows
+    int *sperm = ri + 32;                        // [n] row of the panel's input at each position
+    __shared__ int piv, bad;
+    __shared__ double sdinv;
+    const int r = threadIdx.x, lane = r & 31, w = r >> 5, nw = blockDim.x >> 5;
+    double x[GJB_NB];
+#pragma unroll
+    for (int i = 0; i < GJB_NB; i++) x[i] = 0.0;
+    if (r < n) {
+        for (int i = 0; i < nb; i++) P[i * n + r] = Q[(long long)r * ld + k0 + i];
+        sperm[r] = r;
+    }
+    if (r == 0) bad = 0;
+    __syncthreads();
+    for (int jj = 0; jj < nb; jj++) {
+        const int j = k0 + jj;
+        // pivot: the largest |P[q][jj]| over q >= j, ties to the lower row
+        double best = -1.0;
+        int bi = 0x7fffffff;
+        if (r >= j && r < n) { best = fabs(P[jj * n + r]); bi = r; }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double b2 = __shfl_down_sync(0xffffffffu, best, o);
+            const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+            if (b2 > best || (b2 == best && i2 < bi)) { best = b2; bi = i2; }
+        }
+        if (lane == 0) { rv[w] = best; ri[w] = bi; }
+        __syncthreads();
+        if (r == 0) {
+            double b = rv[0];
+            int ib = ri[0];
+            for (int q = 1; q < nw; q++)
+                if (rv[q] > b || (rv[q] == b && ri[q] < ib)) { b = rv[q]; ib = ri[q]; }
+            piv = ib;
+            if (!(b > 0.0) || ib >= n) bad = 1;
+        }
+        __syncthreads();
+        if (bad) {
+            if (r == 0) atomicOr(errw, ERRW_SINGULAR);
+            return;
+        }
+        const int p = piv;
+        // swap rows j and p: panel entries, coefficients, permutation
+        if (p != j) {
+            if (r == j) {
+#pragma unroll
+                for (int i = 0; i < GJB_NB; i++) xswap[i] = x[i];
+            }
+            if (r == p) {
+#pragma unroll
+                for (int i = 0; i < GJB_NB; i++) xswap[GJB_NB + i] = x[i];
+            }
+            if (r < nb) {
+                const double t = P[r * n + j];
+                P[r * n + j] = P[r * n + p];
+                P[r * n + p] = t;
+            }
+            if (r == 0) {
+                const int t = sperm[j];
+                sperm[j] = sperm[p];
+                sperm[p] = t;
+            }
+            __syncthreads();
+            if (r == j) {
+#pragma unroll
+                for (int i = 0; i < GJB_NB; i++) x[i] = xswap[GJB_NB + i];
+            }
+            if (r == p) {
+#pragma unroll
+                for (int i = 0; i < GJB_NB; i++) x[i] = xswap[i];
+            }
+        }
+        // the pivot row: its own row is pivot jj; scale it by 1/pivot (one
+        // division per step), the panel entries by the first nb threads
+        if (r == j) sdinv = 1.0 / P[jj * n + j];
+        __syncthreads();
+        const double dinv = sdinv;
+        if (r == j) {
+#pragma unroll
+            for (int i = 0; i < GJB_NB; i++) {
+                if (i == jj) x[i] = 1.0;
+                if (i <= jj) x[i] = x[i] * dinv;
+                xrow[i] = x[i];
+            }
+        }
+        __syncthreads();
+        if (r < nb && r > jj) P[r * n + j] = P[r * n + j] * dinv;
+        __syncthreads();
+        // every other row: subtract f times the pivot row (coefficients on
+        // pivots 0..jj, panel entries right of jj)
+        if (r < n && r != j) {
+            const double f = P[jj * n + r];
+            for (int i = jj + 1; i < nb; i++) P[i * n + r] = fma(-f, P[i * n + j], P[i * n + r]);
+            P[jj * n + r] = 0.0;
+#pragma unroll
+            for (int i = 0; i < GJB_NB; i++)
+                if (i <= jj) x[i] = fma(-f, xrow[i], x[i]);
+        }
+        __syncthreads();
+        if (r == j) P[jj * n + j] = 1.0;
+    }
+    if (r < n) {
+#pragma unroll
+        for (int i = 0; i < GJB_NB; i++) X[(long long)r * GJB_NB + i] = x[i];
+        perm[r] = sperm[r];
+    }
+}
+
+// trailing columns c >= k0 (A part and identity part) of Qout from Qin;
+// a block: 8 rows x 256 columns, the pivot rows' entries of a column in
+// registers
+__global__ void __launch_bounds__(256) k_gjb_update(int n, int k0, int nb, const double *__restrict__ Qin,
+                                                   double *__restrict__ Qout, long long ld,
+                                                   const double *__restrict__ X, const int *__restrict__ perm) {
+    __shared__ double xs[8][GJB_NB];
+    const int c = k0 + blockIdx.x * 256 + threadIdx.x;
+    const int r0 = blockIdx.y * 8;
+    if (threadIdx.x < 8 * GJB_NB) {
+        const int rr = threadIdx.x / GJB_NB, i = threadIdx.x % GJB_NB;
+        xs[rr][i] = (r0 + rr < n && i < nb) ? X[(long long)(r0 + rr) * GJB_NB + i] : 0.0;
+    }
+    __syncthreads();
+    if (c >= 2 * n) return;
+    const int k1 = k0 + nb;
+    if (c < k1) {  // the panel's columns: unit columns
+        for (int rr = 0; rr < 8 && r0 + rr < n; rr++) Qout[(long long)(r0 + rr) * ld + c] = (r0 + rr == c) ? 1.0 : 0.0;
+        return;
+    }
+    double pv[GJB_NB];
+#pragma unroll
+    for (int i = 0; i < GJB_NB; i++) pv[i] = i < nb ? Qin[(long long)perm[k0 + i] * ld + c] : 0.0;
+    for (int rr = 0; rr < 8; rr++) {
+        const int r = r0 + rr;
+        if (r >= n) break;
+        double acc = (r >= k0 && r < k1) ? 0.0 : Qin[(long long)perm[r] * ld + c];
+#pragma unroll
+        for (int i = 0; i < GJB_NB; i++) acc = fma(xs[rr][i], pv[i], acc);
+        Qout[(long long)r * ld + c] = acc;
+    }
+}
+
+static int dense_inverse_blocked(int n, double *M, double *M2, double *inv, int *errw, cudaStream_t s,
+                                 Arena &ar) {
+    double *X = ar.alloc<double>((size_t)n * GJB_NB);
+    int *perm = ar.alloc<int>(n);
+    if (!X || !perm) return ST_NOMEM;
+    // a panel that meets a zero pivot stops before writing X and perm: the
+    // updates that follow must still index rows inside the matrix
+    cudaMemsetAsync(X, 0, sizeof(double) * n * GJB_NB, s);
+    cudaMemsetAsync(perm, 0, sizeof(int) * n, s);
+    const size_t sh = (size_t)n * GJB_NB * sizeof(double) + (3 * GJB_NB + 32) * sizeof(double) +
+                      (32 + (size_t)n) * sizeof(int);
+    if (cudaFuncSetAttribute(k_gjb_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh) != cudaSuccess)
+        return ST_CUDA;
+    const long long ld = 2LL * n;
+    const int threads = ((n + 31) / 32) * 32;
+    double *a = M, *b = M2;
+    for (int k0 = 0; k0 < n; k0 += GJB_NB) {
+        const int nb = n - k0 < GJB_NB ? n - k0 : GJB_NB;
+        k_gjb_panel<<<1, threads, sh, s>>>(n, k0, nb, a, ld, X, perm, errw);
+        const dim3 grid((unsigned)((2 * n - k0 + 255) / 256), (unsigned)((n + 7) / 8));
+        k_gjb_update<<<grid, 256, 0, s>>>(n, k0, nb, a, b, ld, X, perm);
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    k_gj_extract<<<GRID((long long)n * n, 256) > 8192 ? 8192 : GRID((long long)n * n, 256), 256, 0, s>>>(n, a, inv);
+    cudaStreamSynchronize(s);
+    ar.release(X);
+    ar.release(perm);
+    return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
 int dense_inverse(const DCSR &A, double *inv, int *errw, cudaStream_t s, Arena &ar) {
     const int n = A.n;
     if (n <= 0) return ST_OK;
+    if (n <= GJB_MAXN) {
+        double *M = ar.alloc<double>((size_t)n * 2 * n + 1);
+        double *M2 = ar.alloc<double>((size_t)n * 2 * n + 1);
+        if (!M || !M2) return ST_NOMEM;
+        k_dense_fill<<<n, 256, 0, s>>>(n, A.rp, A.ci, A.v, M);
+        const int rc = dense_inverse_blocked(n, M, M2, inv, errw, s, ar);
+        ar.release(M);
+        ar.release(M2);
+        return rc;
+    }
     double *M = ar.alloc<double>((size_t)n * 2 * n + 1);
     double *M2 = ar.alloc<double>((size_t)n * 2 * n + 1);
     const long long tot = 2LL * n * n;
