@@ -1459,6 +1459,18 @@ extern "C" mgr_status mgr_refresh(mgr_handle h, const double *val, int32_t on_de
         h->kr.graphs[d].clear();
     }
     h->ready = false;
+    // the slice order each product was timed into at setup: the pattern is
+    // the same, so the rebuilt copies keep it instead of being timed again
+    std::vector<int> sched_lev, sched_amg;
+    auto lev_mats = [](MgrLevel &L) {
+        return std::vector<DCSR *>{&L.AFF, &L.ACF, &L.W, &L.AFFT, &L.ACFT, &L.WT, &L.Z, &L.ZT};
+    };
+    for (int l = 0; l < h->nlev; l++)
+        for (DCSR *m : lev_mats(h->lev[l])) sched_lev.push_back(m->sched);
+    const int old_namg = h->H.namg;
+    for (int k = 0; k < old_namg; k++)
+        for (DCSR *m : {&h->H.amg[k].A, &h->H.amg[k].AT, &h->H.amg[k].P, &h->H.amg[k].R})
+            sched_amg.push_back(m->sched);
     for (int l = 0; l < MGR_MAX_LEVELS; l++) {
         AmgH *keep = h->lev[l].famg;
         h->lev[l] = MgrLevel();
@@ -1466,7 +1478,27 @@ extern "C" mgr_status mgr_refresh(mgr_handle h, const double *val, int32_t on_de
     }
     h->H = AmgH();
     h->lar.recycle();  // the new hierarchy has the old one's sizes: reuse its blocks
+    const bool no_tune = g_no_tune;
+    g_no_tune = true;
     st = build_levels(h, true);
+    g_no_tune = no_tune;
+    if (st == MGR_OK) {
+        size_t q = 0;
+        for (int l = 0; l < h->nlev; l++)
+            for (DCSR *m : lev_mats(h->lev[l])) m->sched = sched_lev[q++];
+        q = 0;
+        for (int k = 0; k < old_namg && k < h->H.namg; k++)
+            for (DCSR *m : {&h->H.amg[k].A, &h->H.amg[k].AT, &h->H.amg[k].P, &h->H.amg[k].R})
+                m->sched = sched_amg[q++];
+        // A_FF shared with a kept F hierarchy carries that hierarchy's order
+        for (int l = 0; l < h->nlev; l++) {
+            MgrLevel &L = h->lev[l];
+            if (L.fshared && L.famg && L.famg->namg > 1) {
+                L.AFF.sched = L.famg->amg[0].A.sched;
+                L.AFFT.sched = L.famg->amg[0].AT.sched;
+            }
+        }
+    }
     if (st != MGR_OK) {
         // a partly built F-relaxation hierarchy must not be kept by a later refresh
         for (int l = 0; l < MGR_MAX_LEVELS; l++) {
