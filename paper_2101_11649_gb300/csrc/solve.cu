@@ -7,6 +7,7 @@
 // order, so repeated runs give identical bits.
 #include <cuda_runtime.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include "common.cuh"
 #include "sell.cuh"
@@ -328,8 +329,26 @@ static int sell_tune_t(DCSR &M, const T *vals, cudaStream_t s, Arena &ar, const 
     return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
 }
 
+// MGR_SELL_ORDER=grid or =contig puts every SELL product of a setup into
+// that order instead of timing it (a test knob: the two orders must give the
+// same bits); anything else, or unset, times each product.
+static int forced_order() {
+    static const int f = [] {
+        const char *e = getenv("MGR_SELL_ORDER");
+        if (!e) return -1;
+        if (!strcmp(e, "grid")) return 0;
+        if (!strcmp(e, "contig")) return 1;
+        return -1;
+    }();
+    return f;
+}
+
 int sell_tune(DCSR &M, const SellTune &tn, cudaStream_t s, Arena &ar) {
     M.sched = 0;
+    if (forced_order() >= 0) {
+        if (M.sptr) M.sched = forced_order();
+        return ST_OK;
+    }
     // a product of fewer slices than one wave of warps runs the same in both orders
     if (!M.sptr || M.nsl < SELL_TUNE_MIN_SLICES || !tn.flush) return ST_OK;
     if (tn.fp32) return M.sv32 ? sell_tune_t<float>(M, M.sv32, s, ar, tn) : ST_OK;

@@ -199,6 +199,40 @@ def test_programmatic_launch_changes_no_bits(tmp_path):
         assert np.array_equal(x0.view(np.int64), x.cpu().numpy().view(np.int64)), p
 
 
+def test_slice_order_changes_no_bits(tmp_path):
+    """Setup times each SELL product in two slice orders (grid-stride and
+    contiguous per block) and keeps the faster; which warp sums a row must
+    not change a bit.  Solves in fresh processes with every product forced
+    into one order and then the other (MGR_SELL_ORDER), both precisions,
+    forward and transposed, give the same bits."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import numpy as np, torch, sys\n"
+        "from paper_2101_11649_gb300 import mgr as M\n"
+        "from paper_2101_11649_gb300.synth import make_compositional, make_mimetic\n"
+        "for name, s in (('mim', make_mimetic(24, 24, 24)), ('comp', make_compositional(32, 24, 8))):\n"
+        "    b = torch.as_tensor(s.rhs, device='cuda')\n"
+        "    for p in ('fp64', 'fp32'):\n"
+        "        g = M.MGRSolver.from_system(s, precision=p)\n"
+        "        for tr in (False, True):\n"
+        "            x, info = g.solve(b, rtol=1e-10, transpose=tr)\n"
+        "            np.save(sys.argv[1] + f'/{name}_{p}_{tr}.npy', x.cpu().numpy())\n")
+    outs = {}
+    for order in ("grid", "contig"):
+        d = tmp_path / order
+        d.mkdir()
+        env = dict(os.environ, MGR_SELL_ORDER=order)
+        subprocess.run([sys.executable, "-c", code, str(d)], env=env, check=True, cwd=root, timeout=900)
+        outs[order] = d
+    for f in sorted(os.listdir(outs["grid"])):
+        a = np.load(outs["grid"] / f)
+        b = np.load(outs["contig"] / f)
+        assert np.array_equal(a.view(np.int64), b.view(np.int64)), f
+
+
 # ------------------------------------------------------ setup, bit-exact
 def _same_csr(a, b, what):
     assert a is not None and b is not None, what
