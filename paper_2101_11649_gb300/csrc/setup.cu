@@ -1474,196 +1474,379 @@ __global__ void k_gj_extract(int n, const double *M, double *inv) {
 }
 
 // Blocked Gauss-Jordan (the same partial pivoting: the largest |entry| of
-// the column among the rows not yet pivots, ties to the lower row).  Panel
-// k0..k0+NB-1: one CTA, one thread per row, runs the panel's NB pivot steps
-// on the panel columns in shared memory.  Each row also carries, in
-// registers, its coefficients on the panel's pivot rows (X: a row's final
-// value is its own old row, for rows that are not pivots, plus
-// sum_i X[r][i] * old pivot row i), and the row permutation of the panel's
-// swaps is kept in shared memory.  A grid-wide launch then applies the
-// panel to the trailing columns: Q_new[r] = (r not a pivot ? Q[perm[r]] : 0)
-// + sum_i X[r][i] Q[perm[k0+i]], and writes the panel's columns as unit
-// columns.  n/NB panel launches replace n one-column launches.
+// the column among the rows not yet pivots, ties to the lower position), for
+// n <= GJB_MAXN.  Panel k0..k0+nb-1 (nb <= 16):
+//  * k_gjb_panel: one cluster of GJB_CL CTAs, one thread per row (CTA c owns
+//    the rows that sit at positions c*R .. c*R+R-1 when the panel starts).
+//    Each pivot step picks the pivot (each CTA reduces its rows' keys, |v|'s
+//    IEEE bits compared as integers, and sends its best row to every CTA of
+//    the cluster through distributed shared memory; one cluster barrier per
+//    step) and eliminates the panel columns of every other row (LU-style: the
+//    pivot rows of the panel are not reduced against each other here).  Out:
+//    each row's multipliers f (F), the panel's pivot block as L\U with the
+//    pivots' reciprocals (LG), the new row order (perm: position -> row of
+//    the input) and the original row index of each position (orig).
+//  * k_gjb_update: the rest of the step on the other columns.  With B the
+//    panel columns of the pivot rows (B = L U), the Gauss-Jordan result is
+//    new pivot rows = B^-1 (old pivot rows) = U^-1 W and every other row
+//    old - f W, where W = L^-1 (old pivot rows).
+// Right-half column bookkeeping: the right half of [A | I] keeps, for each
+// position s < k0, the column of the inverse that belongs to the row placed
+// at s (orig[s]); a column whose row has not been a pivot yet is still a unit
+// vector and is not stored.  So each panel updates n columns (the left
+// columns right of the panel and the right-half slots 0..k0+nb-1), not 2n-k0,
+// and the slots of the panel's own pivots start as unit vectors (o = e_i).
+// The inverse is read out at the end as inv[r][orig[s]] = Q[r][n+s].
 static constexpr int GJB_NB = 16;
 static constexpr int GJB_MAXN = 1024;
+static constexpr int GJB_CL = 8;                   // CTAs per cluster (portable size)
+static constexpr int GJB_MAXT = GJB_MAXN / GJB_CL;  // threads per CTA
+static constexpr int GJB_STRIP = 8;                // most columns per update block
+static constexpr int GJB_SMS = 152;                // update blocks (one per SM)
+void launch_iota(int *a, int n, cudaStream_t s);
 
-__global__ void __launch_bounds__(GJB_MAXN) k_gjb_panel(int n, int k0, int nb, const double *__restrict__ Q,
-                                                       long long ld, double *__restrict__ X,
-                                                       int *__restrict__ perm, int *errw) {
-    extern __shared__ double gjb_sm[];
-    double *P = gjb_sm;                          // [GJB_NB][n] panel columns, column-major
-    double *xrow = P + (size_t)n * GJB_NB;       // [GJB_NB] pivot row's coefficients
-    double *xswap = xrow + GJB_NB;               // [2][GJB_NB] coefficient exchange of a swap
-    double *rv = xswap + 2 * GJB_NB;             // [32] reduction values
-    int *ri = (int *)(rv + 32);                  // [32] reduction rows
-    int *sperm = ri + 32;                        // [n] row of the panel's input at each position
-    __shared__ int piv, bad;
-    __shared__ double sdinv;
-    const int r = threadIdx.x, lane = r & 31, w = r >> 5, nw = blockDim.x >> 5;
-    double x[GJB_NB];
+// 1/v by Newton's iteration for the reciprocal (r <- r + r (1 - m r), twice)
+// on the mantissa m in [1, 2), from a single-precision seed with about 2^-22
+// relative error, so two steps reach double precision; the exponent is put
+// back with integer arithmetic.  A pivot step waits on this chain, and FP64
+// latency is long here, so 4 dependent FMAs replace the longer division
+// sequence.  Zero, subnormal and very large |v| take the division.
+__device__ __forceinline__ double gj_recip(double v) {
+    const long long b = __double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0 || ex > 2044) return 1.0 / v;
+    const double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    const float mf = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));
+    const int fb = __float_as_int(rf);
+    double r = __longlong_as_double(((long long)(((fb >> 23) & 0xff) - 127 + 1023) << 52) |
+                                    ((long long)(fb & 0x7fffff) << 29));
+    double e = fma(-m, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-m, r, 1.0);
+    r = fma(r, e, r);
+    const long long rb = __double_as_longlong(r);
+    const long long re = ((rb >> 52) & 0x7ff) - (ex - 1023);
+    return __longlong_as_double((b & (long long)0x8000000000000000ULL) | (re << 52) | (rb & 0x000fffffffffffffLL));
+}
+
+// a CTA's candidate for one pivot step, as 64-bit words: the row's panel
+// entries (its multipliers left of the step), the key (|v|'s bits), position
+// | row << 32, the value and its reciprocal
+enum { GJW_KEY = GJB_NB, GJW_POS, GJW_V, GJW_DINV, GJW_N };
+struct GJRec {
+    unsigned long long wd[GJW_N];
+};
+
+// warp argmax of the key (hi, lo), lowest position among equal keys; every
+// lane gets the result and the winning lane's index
+__device__ __forceinline__ int gjb_warp_best(unsigned &hi, unsigned &lo, unsigned &pos) {
+    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    const unsigned mp = __reduce_min_sync(0xffffffffu, (hi == mh && lo == ml) ? pos : 0xffffffffu);
+    const unsigned bal = __ballot_sync(0xffffffffu, hi == mh && lo == ml && pos == mp);
+    hi = mh;
+    lo = ml;
+    pos = mp;
+    return __ffs(bal) - 1;
+}
+
+__device__ __forceinline__ unsigned gjb_cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// all threads of the cluster; release/acquire orders the records sent before it
+__device__ __forceinline__ void gjb_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void gjb_store_remote(const void *local, unsigned rank, unsigned long long v) {
+    const unsigned l = (unsigned)__cvta_generic_to_shared(local);
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(l), "r"(rank));
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(r), "l"(v) : "memory");
+}
+
+// P[i][tid] -= f e[i] for i = JJ+1 .. nb-1 (the pivot row's entries loaded
+// first, so the loads and FMAs pipeline); returns the new entry JJ+1
+template <int JJ>
+__device__ __forceinline__ double gjb_elim(double f, const unsigned long long *e, double *P, int T, int tid, int nb) {
+    double ev[GJB_NB], pv[GJB_NB];
 #pragma unroll
-    for (int i = 0; i < GJB_NB; i++) x[i] = 0.0;
-    if (r < n) {
-        for (int i = 0; i < nb; i++) P[i * n + r] = Q[(long long)r * ld + k0 + i];
-        sperm[r] = r;
+    for (int i = JJ + 1; i < GJB_NB; i++) {
+        ev[i] = __longlong_as_double((long long)e[i]);
+        pv[i] = P[i * T + tid];
     }
-    if (r == 0) bad = 0;
-    __syncthreads();
+    double r = 0.0;
+#pragma unroll
+    for (int i = JJ + 1; i < GJB_NB; i++)
+        if (i < nb) {
+            const double x = fma(-f, ev[i], pv[i]);
+            P[i * T + tid] = x;
+            if (i == JJ + 1) r = x;
+        }
+    return r;
+}
+
+__global__ void __launch_bounds__(GJB_MAXT) k_gjb_panel(int n, int k0, int nb, const double *__restrict__ Q,
+                                                       long long ld, double *__restrict__ F, int *__restrict__ perm,
+                                                       int *__restrict__ orig, double *__restrict__ LG, int *errw) {
+    extern __shared__ double gjb_sm[];
+    const int T = blockDim.x;
+    double *P = gjb_sm;                              // [GJB_NB][T] this CTA's rows, panel columns
+    GJRec *rec = (GJRec *)(P + (size_t)GJB_NB * T);  // [2][GJB_CL] candidates (by step parity)
+    double *LU = (double *)(rec + 2 * GJB_CL);       // [GJB_NB][GJB_NB]
+    double *dv = LU + GJB_NB * GJB_NB;               // [GJB_NB] pivot reciprocals
+    unsigned *wk = (unsigned *)(dv + GJB_NB);        // [4][32] warp keys: hi, lo, pos, thread
+    const unsigned cta = gjb_cluster_rank();
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = T >> 5;
+    const int R = (n + GJB_CL - 1) / GJB_CL;
+    const int g = (int)cta * R + tid;
+    const bool valid = tid < R && g < n;
+    int mypos = g, done = 0, og = 0;
+    double cur = 0.0;  // this row's entry in the current pivot column
+    if (valid) {
+        for (int l = 0; l < GJB_NB; l++) P[l * T + tid] = l < nb ? Q[(long long)g * ld + k0 + l] : 0.0;
+        cur = P[tid];
+        og = orig[g];
+    }
     for (int jj = 0; jj < nb; jj++) {
-        const int j = k0 + jj;
-        // pivot: the largest |P[q][jj]| over q >= j, ties to the lower row
-        double best = -1.0;
-        int bi = 0x7fffffff;
-        if (r >= j && r < n) { best = fabs(P[jj * n + r]); bi = r; }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double b2 = __shfl_down_sync(0xffffffffu, best, o);
-            const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
-            if (b2 > best || (b2 == best && i2 < bi)) { best = b2; bi = i2; }
+        const int j = k0 + jj, par = jj & 1;
+        // this CTA's best candidate (rows at positions >= j not yet pivots)
+        unsigned hi = 0u, lo = 0u, pos = 0xffffffffu;
+        if (valid && !done && mypos >= j) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(cur) & 0x7fffffffffffffffULL;
+            hi = (unsigned)(b >> 32);
+            lo = (unsigned)b;
+            pos = (unsigned)mypos;
         }
-        if (lane == 0) { rv[w] = best; ri[w] = bi; }
-        __syncthreads();
-        if (r == 0) {
-            double b = rv[0];
-            int ib = ri[0];
-            for (int q = 1; q < nw; q++)
-                if (rv[q] > b || (rv[q] == b && ri[q] < ib)) { b = rv[q]; ib = ri[q]; }
-            piv = ib;
-            if (!(b > 0.0) || ib >= n) bad = 1;
+        const int wl = gjb_warp_best(hi, lo, pos);
+        if (lane == 0) {
+            wk[w] = hi;
+            wk[32 + w] = lo;
+            wk[64 + w] = pos;
+            wk[96 + w] = (unsigned)(w * 32 + wl);
         }
         __syncthreads();
-        if (bad) {
-            if (r == 0) atomicOr(errw, ERRW_SINGULAR);
+        if (w == 0) {
+            hi = lane < nw ? wk[lane] : 0u;
+            lo = lane < nw ? wk[32 + lane] : 0u;
+            pos = lane < nw ? wk[64 + lane] : 0xffffffffu;
+            const int bl = gjb_warp_best(hi, lo, pos);
+            const int t = (int)__shfl_sync(0xffffffffu, lane < nw ? wk[96 + lane] : 0u, bl);
+            const bool have = pos != 0xffffffffu;
+            const double vv = have ? P[jj * T + t] : 0.0;
+            const double di = (have && (hi | lo)) ? gj_recip(vv) : 0.0;
+            unsigned long long word = 0ull;
+            if (lane < GJB_NB) word = (have && lane < nb) ? (unsigned long long)__double_as_longlong(P[lane * T + t]) : 0ull;
+            else if (lane == GJW_KEY) word = ((unsigned long long)hi << 32) | lo;
+            else if (lane == GJW_POS)
+                word = (unsigned long long)pos | ((unsigned long long)(unsigned)(have ? (int)cta * R + t : 0) << 32);
+            else if (lane == GJW_V) word = (unsigned long long)__double_as_longlong(vv);
+            else if (lane == GJW_DINV) word = (unsigned long long)__double_as_longlong(di);
+            // one word per lane to every CTA's slot for this CTA (records of
+            // step jj+2 reuse the slot only after the barrier of step jj+1,
+            // which every CTA reaches after reading this step's records)
+            if (lane < GJW_N) {
+                const GJRec *mine = rec + par * GJB_CL + cta;
+#pragma unroll
+                for (int c = 0; c < GJB_CL; c++) gjb_store_remote(&mine->wd[lane], (unsigned)c, word);
+            }
+        }
+        gjb_cluster_sync();
+        // the cluster's pivot: the best CTA record (each warp on its own; every
+        // thread of the cluster reaches the same decision)
+        const GJRec *rs = rec + par * GJB_CL;
+        unsigned bh = 0u, bo = 0u, bp = 0xffffffffu;
+        if (lane < GJB_CL) {
+            const unsigned long long k = rs[lane].wd[GJW_KEY];
+            bh = (unsigned)(k >> 32);
+            bo = (unsigned)k;
+            bp = (unsigned)rs[lane].wd[GJW_POS];
+        }
+        const int cb = gjb_warp_best(bh, bo, bp);
+        // a zero, infinite or NaN pivot (or no candidate row) ends the panel
+        if (bp == 0xffffffffu || (bh | bo) == 0u || bh >= 0x7ff00000u) {
+            if (cta == 0 && tid == 0) atomicOr(errw, ERRW_SINGULAR);
             return;
         }
-        const int p = piv;
-        // swap rows j and p: panel entries, coefficients, permutation
-        if (p != j) {
-            if (r == j) {
-#pragma unroll
-                for (int i = 0; i < GJB_NB; i++) xswap[i] = x[i];
-            }
-            if (r == p) {
-#pragma unroll
-                for (int i = 0; i < GJB_NB; i++) xswap[GJB_NB + i] = x[i];
-            }
-            if (r < nb) {
-                const double t = P[r * n + j];
-                P[r * n + j] = P[r * n + p];
-                P[r * n + p] = t;
-            }
-            if (r == 0) {
-                const int t = sperm[j];
-                sperm[j] = sperm[p];
-                sperm[p] = t;
-            }
-            __syncthreads();
-            if (r == j) {
-#pragma unroll
-                for (int i = 0; i < GJB_NB; i++) x[i] = xswap[GJB_NB + i];
-            }
-            if (r == p) {
-#pragma unroll
-                for (int i = 0; i < GJB_NB; i++) x[i] = xswap[i];
+        const GJRec &pr = rs[cb];
+        const int prow = (int)(pr.wd[GJW_POS] >> 32);
+        const double dinv = __longlong_as_double((long long)pr.wd[GJW_DINV]);
+        if (tid < GJB_NB) LU[jj * GJB_NB + tid] = __longlong_as_double((long long)pr.wd[tid]);
+        if (tid == GJB_NB) dv[jj] = dinv;
+        // the pivot moves to position j, the row at j to the pivot's position
+        if (mypos == j) mypos = (int)bp;
+        else if (g == prow) mypos = j;
+        if (g == prow) done = 1;
+        if (valid && !done) {
+            const double f = cur * dinv;
+            P[jj * T + tid] = f;
+            switch (jj) {
+#define GJB_E(J) \
+    case J: cur = gjb_elim<J>(f, pr.wd, P, T, tid, nb); break;
+                GJB_E(0) GJB_E(1) GJB_E(2) GJB_E(3) GJB_E(4) GJB_E(5) GJB_E(6) GJB_E(7)
+                GJB_E(8) GJB_E(9) GJB_E(10) GJB_E(11) GJB_E(12) GJB_E(13) GJB_E(14) GJB_E(15)
+#undef GJB_E
+                default: break;
             }
         }
-        // the pivot row: its own row is pivot jj; scale it by 1/pivot (one
-        // division per step), the panel entries by the first nb threads
-        if (r == j) sdinv = 1.0 / P[jj * n + j];
-        __syncthreads();
-        const double dinv = sdinv;
-        if (r == j) {
-#pragma unroll
-            for (int i = 0; i < GJB_NB; i++) {
-                if (i == jj) x[i] = 1.0;
-                if (i <= jj) x[i] = x[i] * dinv;
-                xrow[i] = x[i];
-            }
-        }
-        __syncthreads();
-        if (r < nb && r > jj) P[r * n + j] = P[r * n + j] * dinv;
-        __syncthreads();
-        // every other row: subtract f times the pivot row (coefficients on
-        // pivots 0..jj, panel entries right of jj)
-        if (r < n && r != j) {
-            const double f = P[jj * n + r];
-            for (int i = jj + 1; i < nb; i++) P[i * n + r] = fma(-f, P[i * n + j], P[i * n + r]);
-            P[jj * n + r] = 0.0;
-#pragma unroll
-            for (int i = 0; i < GJB_NB; i++)
-                if (i <= jj) x[i] = fma(-f, xrow[i], x[i]);
-        }
-        __syncthreads();
-        if (r == j) P[jj * n + j] = 1.0;
     }
-    if (r < n) {
+    __syncthreads();
+    if (valid) {
+        for (int l = 0; l < GJB_NB; l++) F[(long long)g * GJB_NB + l] = l < nb ? P[l * T + tid] : 0.0;
+        perm[mypos] = g;
+        orig[mypos] = og;  // every CTA read orig before the first barrier
+    }
+    if (cta == 0)
+        for (int e = tid; e < GJB_NB * GJB_NB + GJB_NB; e += T)
+            LG[e] = e < GJB_NB * GJB_NB ? LU[e] : dv[e - GJB_NB * GJB_NB];
+}
+
+// Block b takes a strip of NC active columns (left columns k0+nb..n-1, then
+// right-half slots 0..k0+nb-1) and every row.  Per column, one half-warp:
+// the pivot rows' old entries o (a unit vector for a slot of this panel's
+// pivots), W = L^-1 o, the new pivot rows U^-1 W.  Then each other row:
+// old - f . W, the strip's columns as independent FMA chains.
+template <int NC>
+__device__ __forceinline__ void gjb_rows(int n, int k0, int nb, int tid, const double *__restrict__ Qin,
+                                        double *__restrict__ Qout, long long ld, const double *__restrict__ F,
+                                        const int *__restrict__ perm, const int *colv, const double (*W)[GJB_NB]) {
+    for (int pos = tid; pos < n; pos += 256) {
+        if (pos >= k0 && pos < k0 + nb) continue;
+        const int src = perm[pos];
+        const double *fr = F + (long long)src * GJB_NB;
+        double acc[NC];
 #pragma unroll
-        for (int i = 0; i < GJB_NB; i++) X[(long long)r * GJB_NB + i] = x[i];
-        perm[r] = sperm[r];
+        for (int q = 0; q < NC; q++) {
+            const int col = colv[q];
+            acc[q] = (col >= n && col - n >= k0) ? 0.0 : Qin[(long long)src * ld + col];
+        }
+#pragma unroll 4
+        for (int l = 0; l < nb; l++) {
+            const double fl = fr[l];
+#pragma unroll
+            for (int q = 0; q < NC; q++) acc[q] = fma(-fl, W[q][l], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NC; q++) Qout[(long long)pos * ld + colv[q]] = acc[q];
     }
 }
 
-// trailing columns c >= k0 (A part and identity part) of Qout from Qin;
-// a block: 8 rows x 256 columns, the pivot rows' entries of a column in
-// registers
 __global__ void __launch_bounds__(256) k_gjb_update(int n, int k0, int nb, const double *__restrict__ Qin,
                                                    double *__restrict__ Qout, long long ld,
-                                                   const double *__restrict__ X, const int *__restrict__ perm) {
-    __shared__ double xs[8][GJB_NB];
-    const int c = k0 + blockIdx.x * 256 + threadIdx.x;
-    const int r0 = blockIdx.y * 8;
-    if (threadIdx.x < 8 * GJB_NB) {
-        const int rr = threadIdx.x / GJB_NB, i = threadIdx.x % GJB_NB;
-        xs[rr][i] = (r0 + rr < n && i < nb) ? X[(long long)(r0 + rr) * GJB_NB + i] : 0.0;
+                                                   const double *__restrict__ F, const int *__restrict__ perm,
+                                                   const double *__restrict__ LG) {
+    __shared__ double Ls[GJB_NB * GJB_NB + GJB_NB];
+    __shared__ double W[GJB_STRIP][GJB_NB];
+    __shared__ int pivr[GJB_NB], colv[GJB_STRIP];
+    const int c0 = (int)(((long long)blockIdx.x * n) / gridDim.x);
+    const int c1 = (int)(((long long)(blockIdx.x + 1) * n) / gridDim.x);
+    const int nc = c1 - c0;
+    const int tid = threadIdx.x, nl = n - k0 - nb;
+    for (int e = tid; e < GJB_NB * GJB_NB + GJB_NB; e += 256) Ls[e] = LG[e];
+    if (tid < GJB_NB) pivr[tid] = tid < nb ? perm[k0 + tid] : 0;
+    if (tid < GJB_STRIP) {
+        int col = 0;
+        if (tid < nc) {
+            const int cc = c0 + tid;
+            col = cc < nl ? k0 + nb + cc : n + (cc - nl);
+        }
+        colv[tid] = col;
     }
     __syncthreads();
-    if (c >= 2 * n) return;
-    const int k1 = k0 + nb;
-    if (c < k1) {  // the panel's columns: unit columns
-        for (int rr = 0; rr < 8 && r0 + rr < n; rr++) Qout[(long long)(r0 + rr) * ld + c] = (r0 + rr == c) ? 1.0 : 0.0;
-        return;
+    const double *dvs = Ls + GJB_NB * GJB_NB;
+    const int q = tid >> 4, i = tid & 15;
+    const bool act = q < nc;
+    const int col = act ? colv[q] : 0;
+    const int slot = col - n - k0;  // >= 0: a slot of this panel's pivots
+    double o = 0.0;
+    if (act && i < nb) o = (col >= n && slot >= 0) ? (i == slot ? 1.0 : 0.0) : Qin[(long long)pivr[i] * ld + col];
+    // every lane runs the same shuffles; lanes outside the strip carry zeros
+    for (int l = 0; l < nb; l++) {
+        const double wl = __shfl_sync(0xffffffffu, o, l, 16);
+        if (i > l && i < nb) o = fma(-Ls[i * GJB_NB + l], wl, o);
     }
-    double pv[GJB_NB];
-#pragma unroll
-    for (int i = 0; i < GJB_NB; i++) pv[i] = i < nb ? Qin[(long long)perm[k0 + i] * ld + c] : 0.0;
-    for (int rr = 0; rr < 8; rr++) {
-        const int r = r0 + rr;
-        if (r >= n) break;
-        double acc = (r >= k0 && r < k1) ? 0.0 : Qin[(long long)perm[r] * ld + c];
-#pragma unroll
-        for (int i = 0; i < GJB_NB; i++) acc = fma(xs[rr][i], pv[i], acc);
-        Qout[(long long)r * ld + c] = acc;
+    if (act) W[q][i] = o;
+    for (int l = nb - 1; l >= 0; l--) {
+        if (i == l) o *= dvs[l];
+        const double zl = __shfl_sync(0xffffffffu, o, l, 16);
+        if (i < l) o = fma(-Ls[i * GJB_NB + l], zl, o);
+    }
+    if (act && i < nb) Qout[(long long)(k0 + i) * ld + col] = o;
+    __syncthreads();
+    switch (nc) {
+#define GJB_R(C) \
+    case C: gjb_rows<C>(n, k0, nb, tid, Qin, Qout, ld, F, perm, colv, W); break;
+        GJB_R(1) GJB_R(2) GJB_R(3) GJB_R(4) GJB_R(5) GJB_R(6) GJB_R(7) GJB_R(8)
+#undef GJB_R
+        default: break;
+    }
+}
+
+__global__ void k_gjb_extract(int n, const double *__restrict__ Q, const int *__restrict__ orig, double *inv) {
+    const long long ld = 2LL * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), s = (int)(e % n);
+        inv[(long long)r * n + orig[s]] = Q[r * ld + n + s];
     }
 }
 
 static int dense_inverse_blocked(int n, double *M, double *M2, double *inv, int *errw, cudaStream_t s,
                                  Arena &ar) {
-    double *X = ar.alloc<double>((size_t)n * GJB_NB);
+    double *F = ar.alloc<double>((size_t)n * GJB_NB);
+    double *LG = ar.alloc<double>(GJB_NB * GJB_NB + GJB_NB);
     int *perm = ar.alloc<int>(n);
-    if (!X || !perm) return ST_NOMEM;
-    // a panel that meets a zero pivot stops before writing X and perm: the
-    // updates that follow must still index rows inside the matrix
-    cudaMemsetAsync(X, 0, sizeof(double) * n * GJB_NB, s);
-    cudaMemsetAsync(perm, 0, sizeof(int) * n, s);
-    const size_t sh = (size_t)n * GJB_NB * sizeof(double) + (3 * GJB_NB + 32) * sizeof(double) +
-                      (32 + (size_t)n) * sizeof(int);
+    int *orig = ar.alloc<int>(n);
+    if (!F || !LG || !perm || !orig) return ST_NOMEM;
+    // perm and orig always hold row indexes inside the matrix, also after a
+    // panel that meets a zero pivot and stops before writing them
+    launch_iota(perm, n, s);
+    launch_iota(orig, n, s);
+    cudaMemsetAsync(F, 0, sizeof(double) * n * GJB_NB, s);
+    cudaMemsetAsync(LG, 0, sizeof(double) * (GJB_NB * GJB_NB + GJB_NB), s);
+    const int R = (n + GJB_CL - 1) / GJB_CL;
+    const int T = ((R + 31) / 32) * 32;
+    const size_t sh = (size_t)GJB_NB * T * sizeof(double) + 2 * GJB_CL * sizeof(GJRec) +
+                      (GJB_NB * GJB_NB + GJB_NB) * sizeof(double) + 128 * sizeof(unsigned);
     if (cudaFuncSetAttribute(k_gjb_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh) != cudaSuccess)
         return ST_CUDA;
     const long long ld = 2LL * n;
-    const int threads = ((n + 31) / 32) * 32;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(GJB_CL);
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = sh;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = GJB_CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // update blocks: n columns in strips of at most GJB_STRIP (n <= 1024 over
+    // min(n, GJB_SMS) blocks gives at most 7)
+    const int ub = n < GJB_SMS ? n : GJB_SMS;
     double *a = M, *b = M2;
     for (int k0 = 0; k0 < n; k0 += GJB_NB) {
         const int nb = n - k0 < GJB_NB ? n - k0 : GJB_NB;
-        k_gjb_panel<<<1, threads, sh, s>>>(n, k0, nb, a, ld, X, perm, errw);
-        const dim3 grid((unsigned)((2 * n - k0 + 255) / 256), (unsigned)((n + 7) / 8));
-        k_gjb_update<<<grid, 256, 0, s>>>(n, k0, nb, a, b, ld, X, perm);
+        if (cudaLaunchKernelEx(&cfg, k_gjb_panel, n, k0, nb, (const double *)a, ld, F, perm, orig, LG, errw) !=
+            cudaSuccess)
+            return ST_CUDA;
+        k_gjb_update<<<ub, 256, 0, s>>>(n, k0, nb, a, b, ld, F, perm, LG);
         double *t = a;
         a = b;
         b = t;
     }
-    k_gj_extract<<<GRID((long long)n * n, 256) > 8192 ? 8192 : GRID((long long)n * n, 256), 256, 0, s>>>(n, a, inv);
+    k_gjb_extract<<<GRID((long long)n * n, 256) > 8192 ? 8192 : GRID((long long)n * n, 256), 256, 0, s>>>(n, a, orig,
+                                                                                                        inv);
     cudaStreamSynchronize(s);
-    ar.release(X);
+    ar.release(F);
+    ar.release(LG);
     ar.release(perm);
+    ar.release(orig);
     return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
 }
 
