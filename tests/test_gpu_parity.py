@@ -309,6 +309,43 @@ def test_vcycle_parity(name):
         cycle_close(s, zg, zo, 1e-11, f"trans={trans}")
 
 
+# Coarsest AMG grids that stay large under the default coarsest size (1024):
+# the GPU inverts them in panels of 16 columns (a ragged last panel for 924,
+# 969 and 759 rows; 1024 is the largest size that takes the blocked form),
+# the oracle factors them (LU, partial pivoting).
+LARGE_COARSEST = {
+    "two_phase_924": lambda: make_two_phase(12, 11, 7),
+    "mimetic_969": lambda: make_mimetic(10, 10, 10),
+    "compositional_1024": lambda: make_compositional(16, 16, 4),
+    "poromech_759": lambda: make_poromech(10, 5),
+}
+
+
+@pytest.mark.parametrize("name", list(LARGE_COARSEST))
+def test_vcycle_parity_large_coarsest_grid(name):
+    s = LARGE_COARSEST[name]()
+    g = solver(s)
+    o = oracle_of(s)
+    assert g.info()["amg_levels"] == o.amg_nlevels
+    k = o.amg_nlevels - 1
+    _same_csr(g.matrix(1, k, 0), o.amg_matrix(k, "A"), f"AMG A_{k}")
+    rp, ci, v, (nc, _) = o.amg_matrix(k)
+    assert 700 <= nc <= 1024
+    dense = np.zeros((nc, nc))
+    for i in range(nc):
+        dense[i, ci[rp[i]:rp[i + 1]]] = v[rp[i]:rp[i + 1]]
+    # an explicit inverse and an LU solve, both backward stable with partial
+    # pivoting, agree to a small multiple of eps * cond(A_c) on the coarse
+    # correction
+    tol = max(1e-11, 64 * np.finfo(np.float64).eps * np.linalg.cond(dense))
+    rng = np.random.default_rng(11)
+    for trans in (False, True):
+        v0 = rng.standard_normal(s.n)
+        zg = g.apply(t(v0), transpose=trans).cpu().numpy()
+        zo = o.apply_transpose(v0) if trans else o.apply(v0)
+        cycle_close(s, zg, zo, tol, f"trans={trans}")
+
+
 @pytest.mark.parametrize("name", ["poromech_mgr_u", "two_phase_amg_relax"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("sweeps,omega", [(2, 0.8), (3, 1.0)])
