@@ -221,14 +221,11 @@ def max_over_ranks(world, v, dev):
     return float(t.item())
 
 
-KERNEL_SOURCES = ("sell.cuh", "spmv.cuh", "reduce.cuh", "solve.cu", "krylov.cu")
-
-
-def kernel_sources_sha1():
-    """SHA-1 over the solve-phase kernel sources, in a fixed order."""
+def sources_sha1(names):
+    """SHA-1 over the named kernel sources (csrc/), in the given order."""
     import hashlib
     h = hashlib.sha1()
-    for name in KERNEL_SOURCES:
+    for name in names:
         h.update(open(os.path.join(ROOT, "paper_2101_11649_gb300", "csrc", name), "rb").read())
     return h.hexdigest()
 
@@ -236,17 +233,15 @@ def kernel_sources_sha1():
 def ncu_traffic(config, kernel_class):
     """DRAM bytes per launch of a kernel class of a configuration from the
     committed ncu capture (profiles/traffic.json), or None when there is
-    none or the kernel sources changed since."""
+    none or the sources of that kernel (its entry's "sources") changed
+    since."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
-        sha = kernel_sources_sha1()
+        k = d.get("configs", {}).get(config, {}).get(kernel_class)
+        if not k or "note" in k or k.get("sources_sha1") != sources_sha1(k["sources"]):
+            return None
     except Exception:
-        return None
-    if d.get("kernel_sources_sha1") != sha:
-        return None
-    k = d.get("configs", {}).get(config, {}).get(kernel_class)
-    if not k or "note" in k:
         return None
     return k["dram_bytes"]
 

@@ -426,10 +426,23 @@ void launch_bbsr(int b, const BJob *jobs, const long long *prefix, int njobs, lo
     }
 }
 
-// y = x / scale or x * scale, per system (scale a device scalar in J.d)
+// y = x * (1/scale) or x * scale, per system (scale a device scalar in J.d).
+// Each block forms the systems' factors once (up to BSCALE_CACHE systems):
+// an FP64 division per element would cost more FP64 issue than the pass.
+static constexpr int BSCALE_CACHE = 1024;
 __global__ void k_bscale(const BJob *jobs, const long long *prefix, int njobs, int js, int invert) {
+    __shared__ double fs[BSCALE_CACHE];
     pdl_wait();
     pdl_launch_dependents();
+    const bool cached = njobs <= BSCALE_CACHE;
+    if (cached)
+        for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+            const BJob &J = jobs[j];
+            if (job_off(J)) continue;
+            const double sc = *(const double *)J.d;
+            fs[j] = invert ? 1.0 / sc : sc;
+        }
+    __syncthreads();
     const long long total = prefix[njobs];
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
          g += (long long)gridDim.x * blockDim.x) {
@@ -437,8 +450,12 @@ __global__ void k_bscale(const BJob *jobs, const long long *prefix, int njobs, i
         const BJob &J = jobs[j];
         if (job_off(J)) continue;
         const long long e = g - prefix[j];
-        const double sc = *(const double *)J.d;
-        const double f = invert ? 1.0 / sc : sc;
+        double f;
+        if (cached) f = fs[j];
+        else {
+            const double sc = *(const double *)J.d;
+            f = invert ? 1.0 / sc : sc;
+        }
         ((double *)J.o1 + js * J.so1)[e] = ((const double *)J.x + js * J.sx)[e] * f;
     }
 }

@@ -173,11 +173,16 @@ void launch_dot(const double *x, const double *y, int n, double *partial, double
     launch_k(k_dot2, dim3(nblk), dim3(RED_THREADS), s, x, y, n, partial, out, ticket, sqrt_out);
 }
 
-// y = x * s  or  y = x / s  (s a device scalar)
+// y = x * s  or  y = x * (1/s)  (s a device scalar).  The factor is formed
+// once per block: an FP64 division in every thread costs more FP64 issue
+// than the whole pass over n.
 __global__ void k_vec_scale(const double *x, double *y, const double *sc, int invert, int n) {
+    __shared__ double fs;
     pdl_wait();
     pdl_launch_dependents();
-    const double f = invert ? 1.0 / *sc : *sc;
+    if (threadIdx.x == 0) fs = invert ? 1.0 / *sc : *sc;
+    __syncthreads();
+    const double f = fs;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x)
         y[e] = x[e] * f;
