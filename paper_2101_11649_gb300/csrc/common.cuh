@@ -35,7 +35,8 @@ struct DCSR {
     double *sv = nullptr;        // padded values (FP64)
     float *sv32 = nullptr;       // padded values (FP32)
     long long sell_stored = 0;   // stored entries including padding
-    int sched = 0;               // slice order of the product kernel: 0 grid-stride, 1 contiguous per block
+    int sched = 0;               // SELL product form: bit 0 slice order (0 grid-stride, 1 contiguous per
+                                 // block), bit 1 the pipelined FP64 chain
 };
 
 
@@ -144,17 +145,19 @@ int amg_tail_grid(void);
 
 // Slice-order tuning of a SELL product: the values' precision, a flush
 // buffer larger than L2 and an event pair (owned by the caller)
+constexpr int SELL_TUNE_ROUNDS = 8;  // timed launches per product (2 per form)
 struct SellTune {
     int fp32 = 0;
     void *flush = nullptr;
     size_t flush_bytes = 0;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t ev[2 * SELL_TUNE_ROUNDS] = {};  // a pair around each timed launch
 };
 constexpr int SELL_TUNE_MIN_SLICES = 4096;
 constexpr size_t SELL_TUNE_FLUSH_BYTES = 192u << 20;
 // SELL-C-sigma build from the CSR arrays (values of both precisions when
-// present); with tn, the product is then timed in both slice orders with the
-// values of tn's precision and the faster order kept (sell_tune)
+// present); with tn, the product is then timed in each form (both slice
+// orders; FP64 also with the pipelined chain) with the values of tn's
+// precision and the fastest kept (sell_tune)
 int build_sell(DCSR &M, cudaStream_t s, Arena &ar, const SellTune *tn = nullptr);
 int sell_tune(DCSR &M, const SellTune &tn, cudaStream_t s, Arena &ar);
 // re-copy the values of a built SELL layout after the CSR values changed

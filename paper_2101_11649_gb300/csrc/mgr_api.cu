@@ -163,10 +163,10 @@ static thread_local std::string g_last_error;
 // solve does not use SELL products; the members keep the grid-stride order).
 static thread_local bool g_no_tune = false;
 
-// Resources of the slice-order timing of SELL products (sell_tune): a flush
-// buffer larger than L2 and an event pair, held only while a setup builds its
-// SELL copies.  nullptr when tuning is off or a resource is missing (every
-// product then keeps the grid-stride order).
+// Resources of the timing of SELL product forms (sell_tune): a flush buffer
+// larger than L2 and an event pair, held only while a setup builds its SELL
+// copies.  nullptr when tuning is off or a resource is missing (every product
+// then keeps the plain grid-stride form).
 static const SellTune *tune_begin(SellTune &t) {
     if (g_no_tune) return nullptr;
     t.flush_bytes = SELL_TUNE_FLUSH_BYTES;
@@ -175,17 +175,18 @@ static const SellTune *tune_begin(SellTune &t) {
         t.flush = nullptr;
         return nullptr;
     }
-    if (cudaEventCreate(&t.e0) != cudaSuccess || cudaEventCreate(&t.e1) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
+    for (cudaEvent_t &e : t.ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
     return &t;
 }
 
 static void tune_end(SellTune &t) {
     if (t.flush) cudaFree(t.flush);
-    if (t.e0) cudaEventDestroy(t.e0);
-    if (t.e1) cudaEventDestroy(t.e1);
+    for (cudaEvent_t e : t.ev)
+        if (e) cudaEventDestroy(e);
     t = SellTune();
 }
 

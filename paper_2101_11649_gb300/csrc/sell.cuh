@@ -101,13 +101,62 @@ __device__ __forceinline__ T sell_chain(int L, long long base, const int *__rest
     return acc;
 }
 
+// The same chain with the next round's values and columns loaded before
+// this round's FMAs, so that the loads overlap the FMAs (the FMA order, and
+// so the bits, are those of sell_chain).  It holds one more round of values
+// and columns in registers (64 per thread for FP64, SELL_BLOCKS_PIPE blocks
+// per SM).  On GB300 it shortens the FP64 products of long rows, where the
+// FP64 FMAs and the loads would otherwise take turns, and lengthens those of
+// short rows (fewer resident warps, nothing to overlap): the setup times both
+// per matrix (DCSR::sched bit 1).
+constexpr int SELL_BLOCKS_PIPE = 4;
+template <class T, class XF>
+__device__ __forceinline__ T sell_chain_pipe(int L, long long base, const int *__restrict__ sci,
+                                             const T *__restrict__ sv, const XF &xf) {
+    constexpr int U = SellCfg<T>::U;
+    T acc = (T)0, vv[U];
+    int cc[U];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if (u < L) {
+            const long long o = base + (long long)u * 32;
+            vv[u] = ld_stream(sv + o);
+            cc[u] = ld_stream(sci + o);
+        }
+    for (int t = 0; t < L; t += U) {
+        T xx[U], vn[U];
+        int cn[U];
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (t + u < L) xx[u] = xf(cc[u]);
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (t + U + u < L) {
+                const long long o = base + (long long)(t + U + u) * 32;
+                vn[u] = ld_stream(sv + o);
+                cn[u] = ld_stream(sci + o);
+            }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (t + u < L) acc = fma(vv[u], xx[u], acc);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            vv[u] = vn[u];
+            cc[u] = cn[u];
+        }
+    }
+    return acc;
+}
+
 // The G partial sums of a row meet in a fixed shuffle tree (lane distances
 // G/2, G/4, .., 1); every lane of the group ends with the row's sum.  The
 // run-time-G form performs the same additions in the same order.
-template <int G, class T, class XF>
+template <int G, class T, class XF, int PIPE = 0>
 __device__ __forceinline__ T sell_rows(int L, long long base, const int *__restrict__ sci,
                                        const T *__restrict__ sv, const XF &xf) {
-    T acc = sell_chain<T>(L, base, sci, sv, xf);
+    T acc;
+    if constexpr (PIPE) acc = sell_chain_pipe<T>(L, base, sci, sv, xf);
+    else acc = sell_chain<T>(L, base, sci, sv, xf);
     if (G > 1) acc = group_sum<G, T>(acc);
     return acc;
 }

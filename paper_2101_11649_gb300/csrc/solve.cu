@@ -310,34 +310,49 @@ static int sell_tune_t(DCSR &M, const T *vals, cudaStream_t s, Arena &ar, const 
     T *y = ar.alloc<T>((size_t)(M.n > 0 ? M.n : 1));
     if (!x || !y) return ST_NOMEM;
     cudaMemsetAsync(x, 0, sizeof(T) * (M.m > 0 ? M.m : 1), s);
-    float best[2] = {1e30f, 1e30f};
-    for (int round = 0; round < 4; round++) {
-        const int mode = round & 1;
-        M.sched = mode;
+    // the forms: both slice orders; FP64 also with the pipelined chain, when
+    // a lane's chain averages two load rounds or more (with fewer there is no
+    // next round to load early)
+    const double lane_len = (double)M.sell_stored / (32.0 * M.nsl);
+    const int nform = (sizeof(T) == 8 && lane_len >= 2.0 * SellCfg<T>::U) ? 4 : 2;
+    const int nround = 2 * nform;  // <= SELL_TUNE_ROUNDS
+    for (int round = 0; round < nround; round++) {
+        M.sched = round % nform;
         cudaMemsetAsync(tn.flush, round, tn.flush_bytes, s);
-        cudaEventRecord(tn.e0, s);
+        cudaEventRecord(tn.ev[2 * round], s);
         spmv_rows<T>(M, vals, XPlain<T, T>{x}, EStore<T, T>{y}, s);
-        cudaEventRecord(tn.e1, s);
-        if (cudaEventSynchronize(tn.e1) != cudaSuccess) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, tn.e0, tn.e1);
-        if (ms < best[mode]) best[mode] = ms;
+        cudaEventRecord(tn.ev[2 * round + 1], s);
     }
+    float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+    if (cudaEventSynchronize(tn.ev[2 * nround - 1]) == cudaSuccess)
+        for (int round = 0; round < nround; round++) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, tn.ev[2 * round], tn.ev[2 * round + 1]) == cudaSuccess &&
+                ms < best[round % nform])
+                best[round % nform] = ms;
+        }
     ar.release(x);
     ar.release(y);
-    M.sched = best[1] < 0.95f * best[0] ? 1 : 0;
+    // another form only when it is at least 5% faster than the first
+    int pick = 0;
+    for (int f = 1; f < nform; f++)
+        if (best[f] < 0.95f * best[0] && best[f] < best[pick]) pick = f;
+    M.sched = pick;
     return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
 }
 
-// MGR_SELL_ORDER=grid or =contig puts every SELL product of a setup into
-// that order instead of timing it (a test knob: the two orders must give the
-// same bits); anything else, or unset, times each product.
+// MGR_SELL_ORDER=grid, contig, grid_pipe or contig_pipe puts every SELL
+// product of a setup into that form instead of timing it (a test knob: all
+// forms must give the same bits; FP32 products ignore _pipe); anything else,
+// or unset, times each product.
 static int forced_order() {
     static const int f = [] {
         const char *e = getenv("MGR_SELL_ORDER");
         if (!e) return -1;
         if (!strcmp(e, "grid")) return 0;
         if (!strcmp(e, "contig")) return 1;
+        if (!strcmp(e, "grid_pipe")) return 2;
+        if (!strcmp(e, "contig_pipe")) return 3;
         return -1;
     }();
     return f;
@@ -346,10 +361,10 @@ static int forced_order() {
 int sell_tune(DCSR &M, const SellTune &tn, cudaStream_t s, Arena &ar) {
     M.sched = 0;
     if (forced_order() >= 0) {
-        if (M.sptr) M.sched = forced_order();
+        if (M.sptr) M.sched = tn.fp32 ? (forced_order() & 1) : forced_order();
         return ST_OK;
     }
-    // a product of fewer slices than one wave of warps runs the same in both orders
+    // a product of fewer slices than one wave of warps runs the same in every form
     if (!M.sptr || M.nsl < SELL_TUNE_MIN_SLICES || !tn.flush) return ST_OK;
     if (tn.fp32) return M.sv32 ? sell_tune_t<float>(M, M.sv32, s, ar, tn) : ST_OK;
     return M.sv ? sell_tune_t<double>(M, M.sv, s, ar, tn) : ST_OK;

@@ -125,9 +125,10 @@ static void csr_chunk(int n, long long nnz, const int *rp, const int *ci, const 
 // (CONTIG = 0), or a contiguous range of slices per block whose warps
 // interleave inside it (CONTIG = 1), so that the warps of an SM gather from
 // neighbouring rows and L1 keeps the vector lines they share (a structured
-// stencil's neighbouring grid lines).  Every row's sum is the same either way.
-template <int G, class T, class XF, class EPI, int CONTIG>
-__global__ void __launch_bounds__(256, SELL_BLOCKS)
+// stencil's neighbouring grid lines).  Every row's sum is the same either way,
+// and with the pipelined chain (PIPE, FP64; sell.cuh).
+template <int G, class T, class XF, class EPI, int CONTIG, int PIPE>
+__global__ void __launch_bounds__(256, PIPE ? SELL_BLOCKS_PIPE : SELL_BLOCKS)
     k_sell(int nsl, const long long *__restrict__ sptr, const int *__restrict__ slen,
            const int *__restrict__ perm, const int *__restrict__ sci, const T *__restrict__ sv, XF xf,
            EPI epi) {
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(256, SELL_BLOCKS)
             base2 = __ldg(sptr + nx) + lane;
             row2 = __ldg(perm + (long long)nx * C + lane / G);
         }
-        const T acc = sell_rows<G, T>(L, base, sci, sv, xf);
+        const T acc = sell_rows<G, T, XF, PIPE>(L, base, sci, sv, xf);
         if (own) epi.put(row, acc, PF ? pre : epi.pre(row));
         if (nx >= nsl) break;
         sl = nx;
@@ -221,14 +222,24 @@ __global__ void __launch_bounds__(256, SELL_BLOCKS)
 // contiguous order (each block's range is its whole share)
 template <int G, class T, class XF, class EPI>
 static void sell_launch(const DCSR &M, const T *vals, XF xf, EPI epi, cudaStream_t s) {
+    const int contig = M.sched & 1;
+    const bool pipe = sizeof(T) == 8 && (M.sched & 2);
     long long blocks = ((long long)M.nsl * 32 + 255) / 256;
-    const long long cap = (long long)NUM_SMS * SELL_BLOCKS * (M.sched ? 1 : 2);
+    const long long cap = (long long)NUM_SMS * (pipe ? SELL_BLOCKS_PIPE : SELL_BLOCKS) * (contig ? 1 : 2);
     if (blocks > cap) blocks = cap;
     const dim3 grid((unsigned)(blocks < 1 ? 1 : blocks));
-    if (M.sched)
-        launch_k(k_sell<G, T, XF, EPI, 1>, grid, dim3(256), s, M.nsl, M.sptr, M.slen, M.perm, M.sci, vals, xf, epi);
-    else
-        launch_k(k_sell<G, T, XF, EPI, 0>, grid, dim3(256), s, M.nsl, M.sptr, M.slen, M.perm, M.sci, vals, xf, epi);
+#define SELL_GO(C, P) \
+    launch_k(k_sell<G, T, XF, EPI, C, P>, grid, dim3(256), s, M.nsl, M.sptr, M.slen, M.perm, M.sci, vals, xf, epi)
+    if constexpr (sizeof(T) == 8) {
+        if (pipe) {
+            if (contig) SELL_GO(1, 1);
+            else SELL_GO(0, 1);
+            return;
+        }
+    }
+    if (contig) SELL_GO(1, 0);
+    else SELL_GO(0, 0);
+#undef SELL_GO
 }
 
 // Row products over a matrix: SELL-C-sigma when built, else the chunk engine.

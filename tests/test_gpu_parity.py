@@ -201,10 +201,11 @@ def test_programmatic_launch_changes_no_bits(tmp_path):
 
 def test_slice_order_changes_no_bits(tmp_path):
     """Setup times each SELL product in two slice orders (grid-stride and
-    contiguous per block) and keeps the faster; which warp sums a row must
-    not change a bit.  Solves in fresh processes with every product forced
-    into one order and then the other (MGR_SELL_ORDER), both precisions,
-    forward and transposed, give the same bits."""
+    contiguous per block), FP64 products also with the pipelined chain, and
+    keeps the fastest form; which warp sums a row, and when its loads are
+    issued, must not change a bit.  Solves in fresh processes with every
+    product forced into each form (MGR_SELL_ORDER), both precisions, forward
+    and transposed, give the same bits."""
     import os
     import subprocess
     import sys
@@ -221,7 +222,8 @@ def test_slice_order_changes_no_bits(tmp_path):
         "            x, info = g.solve(b, rtol=1e-10, transpose=tr)\n"
         "            np.save(sys.argv[1] + f'/{name}_{p}_{tr}.npy', x.cpu().numpy())\n")
     outs = {}
-    for order in ("grid", "contig"):
+    forms = ("grid", "contig", "grid_pipe", "contig_pipe")
+    for order in forms:
         d = tmp_path / order
         d.mkdir()
         env = dict(os.environ, MGR_SELL_ORDER=order)
@@ -229,8 +231,9 @@ def test_slice_order_changes_no_bits(tmp_path):
         outs[order] = d
     for f in sorted(os.listdir(outs["grid"])):
         a = np.load(outs["grid"] / f)
-        b = np.load(outs["contig"] / f)
-        assert np.array_equal(a.view(np.int64), b.view(np.int64)), f
+        for order in forms[1:]:
+            b = np.load(outs[order] / f)
+            assert np.array_equal(a.view(np.int64), b.view(np.int64)), (f, order)
 
 
 # ------------------------------------------------------ setup, bit-exact
