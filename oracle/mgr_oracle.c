@@ -15,7 +15,9 @@
  *
  * Parity pins: see tests/test_oracle_*.py.  AMG coarsening and
  * interpolation (PMIS, extended+i) are not defined by the paper; they are
- * pinned only by structural invariants (parity partially unpinned).
+ * pinned by invariants and by the cases with a closed form (PMIS's first
+ * round from the published measure, extended+i's direct-interpolation and
+ * 1D limits), not in general (parity partially unpinned).
  */
 #include <math.h>
 #include <stdint.h>

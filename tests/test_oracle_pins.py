@@ -274,6 +274,81 @@ def test_pmis_independent_and_covering(shape):
     assert set(np.unique(cf)) <= {-1, 1}
 
 
+def _random_2d_coupling(nx, ny, seed):
+    """Symmetric 2D 5-point M-matrix with couplings U(0.05, 1): some
+    connections fall below theta * max and are weak; rows sum to U(0.05, 0.5)."""
+    rng = np.random.default_rng(seed)
+    n = nx * ny
+    idx = np.arange(n).reshape(ny, nx)
+    pairs = [(idx[:, :-1].ravel(), idx[:, 1:].ravel()), (idx[:-1, :].ravel(), idx[1:, :].ravel())]
+    a = np.concatenate([p[0] for p in pairs]); b = np.concatenate([p[1] for p in pairs])
+    w = rng.uniform(0.05, 1.0, a.size)
+    diag = np.bincount(a, w, n) + np.bincount(b, w, n) + rng.uniform(0.05, 0.5, n)
+    rows = np.concatenate([a, b, np.arange(n)]); cols = np.concatenate([b, a, np.arange(n)])
+    from paper_2101_11649_gb300.synth.bsr import assemble_bsr
+    rp, ci, v = assemble_bsr(n, 1, rows, cols, np.concatenate([-w, -w, diag]))
+    return rp, ci, v.ravel()
+
+
+@pytest.mark.parametrize("case", ["poisson2d", "random2d", "poisson3d"])
+def test_pmis_first_round_from_the_published_measure(case):
+    """PMIS (De Sterck, Yang & Heys 2006) with measure w_i = |S^T_i| + u_i,
+    u_i the published SplitMix64 draw: a point that influences nobody is F;
+    every other point whose measure beats those of all its strong neighbours
+    that influence somebody (S_i u S^T_i; ties to the larger index) is
+    selected in the first round, so it is C, and every point that strongly
+    depends on such a point is F.  Catches a measure built from |S_i|, a
+    reversed comparison, or another random stream."""
+    rp, ci, v = {"poisson2d": lambda: poisson(13, 11), "random2d": lambda: _random_2d_coupling(17, 13, 3),
+                 "poisson3d": lambda: poisson(7, 6, 5)}[case]()
+    cf, _ = O.amg_split_interp(rp, ci, v)
+    S, ST = _strength_sets(rp, ci, v)
+    n = rp.size - 1
+    w = np.array([len(ST[i]) + O.pmis_u01(i, 0) for i in range(n)])
+    first = []
+    for i in range(n):
+        if not ST[i]:
+            assert cf[i] == -1, i
+            continue
+        rivals = [j for j in (S[i] | ST[i]) if ST[j]]
+        if all(w[j] < w[i] or (w[j] == w[i] and j < i) for j in rivals):
+            first.append(i)
+    assert first
+    for i in first:
+        assert cf[i] == 1, i
+    for i in range(n):
+        if S[i] & set(first):
+            assert cf[i] == -1, i
+
+
+def test_extpi_reduces_to_direct_interpolation_without_strong_f_neighbours():
+    """Where every strong neighbour of an F point is a C point, extended+i
+    (De Sterck, Falgout, Nolting & Yang 2008) is classical direct
+    interpolation with the weak connections lumped into the diagonal:
+    w_ij = -a_ij / (a_ii + sum over weak k of a_ik), j in C_i^s."""
+    for seed in (3, 4):
+        rp, ci, v = _random_2d_coupling(19, 15, seed)
+        cf, P = O.amg_split_interp(rp, ci, v, pmax=0)
+        S, _ = _strength_sets(rp, ci, v)
+        A = np.zeros((rp.size - 1,) * 2)
+        for i in range(rp.size - 1):
+            A[i, ci[rp[i]:rp[i + 1]]] = v[rp[i]:rp[i + 1]]
+        Pd = csr_dense(P)
+        cols = np.flatnonzero(cf == 1)          # P's columns: C points in ascending order
+        checked = 0
+        for i in np.flatnonzero(cf == -1):
+            if any(cf[j] == -1 for j in S[i]) or not S[i]:
+                continue
+            weak = [k for k in np.flatnonzero(A[i]) if k != i and k not in S[i]]
+            d = A[i, i] + sum(A[i, k] for k in weak)
+            ref = np.zeros(cols.size)
+            for j in S[i]:
+                ref[np.searchsorted(cols, j)] = -A[i, j] / d
+            assert np.allclose(Pd[i], ref, rtol=1e-14, atol=0), i
+            checked += 1
+        assert checked > 20
+
+
 def test_extpi_reproduces_constants_zero_row_sum():
     """Extended+i interpolates constants exactly when rows sum to zero (De
     Sterck et al. 2008), with truncation rescaled to keep row sums."""
