@@ -14,10 +14,11 @@
  * bit.  Compile with -ffp-contract=off (no fused multiply-add).
  *
  * Parity pins: see tests/test_oracle_*.py.  AMG coarsening and
- * interpolation (PMIS, extended+i) are not defined by the paper; they are
- * pinned by invariants and by the cases with a closed form (PMIS's first
- * round from the published measure, extended+i's direct-interpolation and
- * 1D limits), not in general (parity partially unpinned).
+ * interpolation (PMIS, extended+i) are not defined by the paper.  PMIS is
+ * pinned exactly (the published measure and hash; its split equals one
+ * sequential pass in measure order); extended+i by invariants and by the
+ * cases with a closed form (direct-interpolation and 1D limits), not its
+ * general weights with strong F-F couplings (parity partially unpinned).
  */
 #include <math.h>
 #include <stdint.h>

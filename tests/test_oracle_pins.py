@@ -321,6 +321,49 @@ def test_pmis_first_round_from_the_published_measure(case):
             assert cf[i] == -1, i
 
 
+def _upwind_2d(nx, ny, seed):
+    """Nonsymmetric 2D M-matrix (diffusion plus first-order upwinding of a
+    random velocity): S and S^T differ."""
+    rng = np.random.default_rng(seed)
+    n = nx * ny
+    idx = np.arange(n).reshape(ny, nx)
+    rows, cols, vals = [], [], []
+    for a, b in ((idx[:, :-1].ravel(), idx[:, 1:].ravel()), (idx[:-1, :].ravel(), idx[1:, :].ravel())):
+        d = rng.uniform(0.2, 1.0, a.size)
+        u = rng.uniform(-3.0, 3.0, a.size)
+        rows += [a, b]; cols += [b, a]
+        vals += [-(d + np.maximum(-u, 0)), -(d + np.maximum(u, 0))]
+    rows = np.concatenate(rows); cols = np.concatenate(cols); vals = np.concatenate(vals)
+    diag = -np.bincount(rows, vals, n) + rng.uniform(0.05, 0.5, n)
+    from paper_2101_11649_gb300.synth.bsr import assemble_bsr
+    rp, ci, v = assemble_bsr(n, 1, np.concatenate([rows, np.arange(n)]),
+                             np.concatenate([cols, np.arange(n)]), np.concatenate([vals, diag]))
+    return rp, ci, v.ravel()
+
+
+@pytest.mark.parametrize("case", ["poisson2d", "random2d", "upwind2d", "poisson3d"])
+def test_pmis_equals_the_sequential_pass_in_measure_order(case):
+    """With fixed measures w_i = |S^T_i| + u_i, PMIS's parallel rounds give
+    the split of one sequential pass over the points in decreasing measure
+    (ties: larger index first): a point that influences nobody is F; any
+    other point is F when a point of its S_i already made C, else C.  (A
+    point becomes F only through a C point of its S_i that beat it, and is
+    selected only once every neighbour above it is decided.)"""
+    rp, ci, v = {"poisson2d": lambda: poisson(13, 11), "random2d": lambda: _random_2d_coupling(17, 13, 3),
+                 "upwind2d": lambda: _upwind_2d(18, 14, 5), "poisson3d": lambda: poisson(7, 6, 5)}[case]()
+    cf, _ = O.amg_split_interp(rp, ci, v)
+    S, ST = _strength_sets(rp, ci, v)
+    n = rp.size - 1
+    w = [len(ST[i]) + O.pmis_u01(i, 0) for i in range(n)]
+    status = np.zeros(n, np.int32)
+    for i in sorted(range(n), key=lambda i: (w[i], i), reverse=True):
+        if not ST[i] or any(status[j] == 1 for j in S[i]):
+            status[i] = -1
+        else:
+            status[i] = 1
+    assert np.array_equal(cf, status)
+
+
 def test_extpi_reduces_to_direct_interpolation_without_strong_f_neighbours():
     """Where every strong neighbour of an F point is a C point, extended+i
     (De Sterck, Falgout, Nolting & Yang 2008) is classical direct
