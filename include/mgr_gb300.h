@@ -35,7 +35,7 @@ typedef enum {
     MGR_ERR_SINGULAR = 4,      /* a zero pivot in D_FF, a block inverse or the coarsest solve */
     MGR_ERR_NOT_CONVERGED = 5, /* maxit reached; x holds the last iterate */
     MGR_ERR_TIMEOUT = 6,       /* a bounded device wait ran out */
-    MGR_ERR_UNSUPPORTED = 7    /* valid request outside what this build supports */
+    MGR_ERR_UNSUPPORTED = 7    /* valid request outside what the library supports */
 } mgr_status;
 
 typedef struct mgr_ctx *mgr_handle;
