@@ -392,6 +392,30 @@ def test_extpi_reduces_to_direct_interpolation_without_strong_f_neighbours():
         assert checked > 20
 
 
+def test_extpi_truncation_keeps_the_largest_and_the_row_sum():
+    """P_max truncation (BoomerAMG's rule, as the oracle states it): with the
+    split unchanged, each row of the truncated interpolation keeps the pmax
+    weights of largest magnitude of the untruncated row (ties: lower column),
+    rescaled by (sum of all weights) / (sum of kept weights)."""
+    for rp, ci, v in (_random_2d_coupling(19, 15, 7), _upwind_2d(18, 14, 9), poisson(9, 8, 6)):
+        cf0, P0 = O.amg_split_interp(rp, ci, v, pmax=0)
+        cf4, P4 = O.amg_split_interp(rp, ci, v, pmax=4)
+        assert np.array_equal(cf0, cf4)
+        D0, D4 = csr_dense(P0), csr_dense(P4)
+        wide = 0
+        for i in range(D0.shape[0]):
+            nz = np.flatnonzero(D0[i])
+            if nz.size <= 4:
+                assert np.array_equal(D0[i], D4[i]), i
+                continue
+            wide += 1
+            order = sorted(nz, key=lambda j: (-abs(D0[i, j]), j))[:4]
+            ref = np.zeros_like(D0[i])
+            ref[order] = D0[i, order] * (D0[i, nz].sum() / D0[i, order].sum())
+            assert np.allclose(D4[i], ref, rtol=1e-13, atol=0), i
+        assert wide > 0
+
+
 def test_extpi_reproduces_constants_zero_row_sum():
     """Extended+i interpolates constants exactly when rows sum to zero (De
     Sterck et al. 2008), with truncation rescaled to keep row sums."""
